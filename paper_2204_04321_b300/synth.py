@@ -1,0 +1,264 @@
+"""Seeded synthetic inputs for the first-order (Blatter-Pattyn) Stokes assembly.
+
+This module is the only code shared by the CUDA path's tests/bench and the CPU oracle.
+It holds input generation only -- meshes, geometry fields, sliding coefficients and
+velocity vectors -- and none of the method's arithmetic (no basis functions, no
+quadrature, no viscosity, no residual).  Every random number is drawn here from
+numpy's PCG64 with an explicit seed and handed to both sides as data.
+
+Geometry follows the paper's "topologically extruded" setting (Sec. 2): a 2D base
+triangulation extruded vertically by sigma layers, z = b + sigma * H, so the margins
+are vertical.  The synthetic problem (dome, bed, beta) stands in for the paper's
+Greenland / Antarctica datasets, which are not available:
+
+* base mesh: an m x m grid on [-220, 220]^2 km whose interior points are jittered by
+  up to +-0.2 h per coordinate (boundary points slide along their edge), every quad
+  split along the diagonal chosen by the in-circle predicate, i.e. the Delaunay
+  triangulation of the jittered points; triangles counter-clockwise;
+* thickness: the radially symmetric dome H(r) = H0 (1 - (r/R)^(4/3))^(3/7), R = 200 km,
+  floored at H_min = 10 m so the whole square carries ice;
+* bed: flat, or b = A_b sin(2 pi x / lam) sin(2 pi y / lam) with A_b = 500 m, lam = 20 km;
+* beta: lognormal with mean 1e3 Pa yr / m and log-sd 0.5, either iid per vertex or a
+  Gaussian field with 10 km correlation length built from 512 random Fourier features;
+* velocities: iid uniform in [-100, 100] m/yr per node and component.
+
+Degrees of freedom are numbered column-major and interleaved:
+dof(a, l, c) = 2 * (a * (L + 1) + l) + c for base vertex a, node level l, component c
+(c = 0 for u, 1 for v).
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+RHO_ICE = 910.0       # kg m^-3
+GRAVITY = 9.81        # m s^-2
+GLEN_N = 3.0
+RATE_FACTOR = 1e-16   # Pa^-3 yr^-1
+DELTA = 1e-10         # yr^-2, regularises the effective strain rate at U = 0
+HALF_WIDTH = 220e3    # m
+DOME_RADIUS = 200e3   # m
+H_MIN = 10.0          # m
+BED_AMPLITUDE = 500.0  # m
+BED_WAVELENGTH = 20e3  # m
+BETA_MEAN = 1e3       # Pa yr m^-1
+BETA_LOG_SD = 0.5
+BETA_CORR_LEN = 10e3  # m
+N_FOURIER = 512
+
+
+@dataclasses.dataclass
+class Params:
+    """Physical constants (units m, yr, Pa)."""
+
+    n: float = GLEN_N
+    A: float = RATE_FACTOR
+    rho: float = RHO_ICE
+    g: float = GRAVITY
+    delta: float = DELTA
+
+    def as_array(self) -> np.ndarray:
+        return np.array([self.n, self.A, self.rho, self.g, self.delta], dtype=np.float64)
+
+
+@dataclasses.dataclass
+class Mesh:
+    """An extruded wedge mesh: base triangulation + per-vertex fields + sigma levels."""
+
+    xy: np.ndarray      # [nv, 2] float64
+    tri: np.ndarray     # [ntri, 3] int32, counter-clockwise
+    bed: np.ndarray     # [nv] float64
+    thick: np.ndarray   # [nv] float64
+    beta: np.ndarray    # [nv] float64
+    sigma: np.ndarray   # [nlayers + 1] float64, 0 = bed ... 1 = surface
+    params: Params = dataclasses.field(default_factory=Params)
+    name: str = ""
+
+    @property
+    def nv(self) -> int:
+        return int(self.xy.shape[0])
+
+    @property
+    def ntri(self) -> int:
+        return int(self.tri.shape[0])
+
+    @property
+    def nlayers(self) -> int:
+        return int(self.sigma.shape[0] - 1)
+
+    @property
+    def nwedges(self) -> int:
+        return self.ntri * self.nlayers
+
+    @property
+    def ndof(self) -> int:
+        return 2 * self.nv * (self.nlayers + 1)
+
+    def dof(self, a, l, c):
+        return 2 * (np.asarray(a) * (self.nlayers + 1) + np.asarray(l)) + np.asarray(c)
+
+    def edges(self) -> np.ndarray:
+        """Unique undirected base edges [E, 2] (sorted pairs)."""
+        t = self.tri.astype(np.int64)
+        e = np.concatenate([t[:, [0, 1]], t[:, [1, 2]], t[:, [2, 0]]])
+        e.sort(axis=1)
+        return np.unique(e, axis=0)
+
+    def expected_nnz(self) -> int:
+        """Size of the extruded pattern: 4 (V + 2E)(3L + 1).
+
+        Each base vertex pair (a, b) with a == b or a ~ b couples node levels |l - l'| <= 1,
+        i.e. (L + 1) + 2L = 3L + 1 level pairs, times 4 component pairs.
+        """
+        return 4 * (self.nv + 2 * len(self.edges())) * (3 * self.nlayers + 1)
+
+
+def _incircle(ax, ay, bx, by, cx, cy, dx, dy):
+    """Sign of the in-circle determinant: > 0 when d lies inside the circle abc (abc CCW)."""
+    adx, ady = ax - dx, ay - dy
+    bdx, bdy = bx - dx, by - dy
+    cdx, cdy = cx - dx, cy - dy
+    return ((adx * adx + ady * ady) * (bdx * cdy - cdx * bdy)
+            - (bdx * bdx + bdy * bdy) * (adx * cdy - cdx * ady)
+            + (cdx * cdx + cdy * cdy) * (adx * bdy - bdx * ady))
+
+
+def jittered_grid(m: int, seed: int, half_width: float = HALF_WIDTH, jitter: float = 0.2):
+    """Jittered m x m grid triangulated by the Delaunay (in-circle) diagonal choice.
+
+    Returns (xy [nv,2], tri [2 m^2, 3] int32 CCW).  Vertex (i, j) has index j * (m+1) + i.
+    """
+    rng = np.random.default_rng(seed)
+    n1 = m + 1
+    h = 2.0 * half_width / m
+    gx, gy = np.meshgrid(np.arange(n1), np.arange(n1), indexing="xy")  # gx varies along axis 1
+    x = -half_width + gx * h
+    y = -half_width + gy * h
+    jx = rng.uniform(-jitter * h, jitter * h, size=x.shape)
+    jy = rng.uniform(-jitter * h, jitter * h, size=y.shape)
+    # boundary points slide only along their edge; corners stay fixed
+    on_x_edge = (gx == 0) | (gx == m)
+    on_y_edge = (gy == 0) | (gy == m)
+    jx = np.where(on_x_edge, 0.0, jx)
+    jy = np.where(on_y_edge, 0.0, jy)
+    xy = np.stack([(x + jx).ravel(), (y + jy).ravel()], axis=1)
+
+    i, j = np.meshgrid(np.arange(m), np.arange(m), indexing="xy")
+    i = i.ravel()
+    j = j.ravel()
+    v00 = j * n1 + i
+    v10 = v00 + 1
+    v01 = v00 + n1
+    v11 = v01 + 1
+    # quad v00 v10 v11 v01 (CCW).  Diagonal v00-v11 unless v01 lies inside circle(v00, v10, v11).
+    P = xy
+    inside = _incircle(P[v00, 0], P[v00, 1], P[v10, 0], P[v10, 1], P[v11, 0], P[v11, 1],
+                       P[v01, 0], P[v01, 1]) > 0
+    t_a = np.where(inside[:, None], np.stack([v00, v10, v01], 1), np.stack([v00, v10, v11], 1))
+    t_b = np.where(inside[:, None], np.stack([v10, v11, v01], 1), np.stack([v00, v11, v01], 1))
+    tri = np.empty((2 * m * m, 3), dtype=np.int32)
+    tri[0::2] = t_a
+    tri[1::2] = t_b
+    return xy, tri
+
+
+def dome_thickness(xy: np.ndarray, H0: float = 2000.0, R: float = DOME_RADIUS,
+                   h_min: float = H_MIN) -> np.ndarray:
+    r = np.hypot(xy[:, 0], xy[:, 1])
+    core = np.clip(1.0 - (r / R) ** (4.0 / 3.0), 0.0, None)
+    return np.maximum(H0 * core ** (3.0 / 7.0), h_min)
+
+
+def sinusoidal_bed(xy: np.ndarray, amplitude: float = BED_AMPLITUDE,
+                   wavelength: float = BED_WAVELENGTH) -> np.ndarray:
+    k = 2.0 * math.pi / wavelength
+    return amplitude * np.sin(k * xy[:, 0]) * np.sin(k * xy[:, 1])
+
+
+def lognormal_beta_iid(nv: int, seed: int, mean: float = BETA_MEAN, log_sd: float = BETA_LOG_SD):
+    rng = np.random.default_rng(seed)
+    mu = math.log(mean) - 0.5 * log_sd ** 2
+    return np.exp(rng.normal(mu, log_sd, size=nv))
+
+
+def lognormal_beta_field(xy: np.ndarray, seed: int, mean: float = BETA_MEAN,
+                         log_sd: float = BETA_LOG_SD, corr_len: float = BETA_CORR_LEN,
+                         nfeat: int = N_FOURIER) -> np.ndarray:
+    """Correlated lognormal field from random Fourier features (Gaussian covariance)."""
+    rng = np.random.default_rng(seed)
+    kvec = rng.normal(0.0, 1.0 / corr_len, size=(nfeat, 2))
+    phase = rng.uniform(0.0, 2.0 * math.pi, size=nfeat)
+    field = np.zeros(xy.shape[0])
+    chunk = 65536
+    for s in range(0, xy.shape[0], chunk):
+        arg = xy[s:s + chunk] @ kvec.T + phase[None, :]
+        field[s:s + chunk] = np.cos(arg).sum(axis=1)
+    field = (field - field.mean()) / field.std()
+    mu = math.log(mean) - 0.5 * log_sd ** 2
+    return np.exp(mu + log_sd * field)
+
+
+def uniform_sigma(nlayers: int) -> np.ndarray:
+    return np.linspace(0.0, 1.0, nlayers + 1)
+
+
+def random_velocity(mesh: Mesh, seed: int, amplitude: float = 100.0) -> np.ndarray:
+    rng = np.random.default_rng(seed)
+    return rng.uniform(-amplitude, amplitude, size=mesh.ndof)
+
+
+def dome_mesh(m: int, nlayers: int, mesh_seed: int, beta_seed: int, H0: float = 2000.0,
+              bed: str = "flat", beta: str = "iid", name: str = "") -> Mesh:
+    xy, tri = jittered_grid(m, mesh_seed)
+    thick = dome_thickness(xy, H0=H0)
+    b = np.zeros(xy.shape[0]) if bed == "flat" else sinusoidal_bed(xy)
+    be = (lognormal_beta_iid(xy.shape[0], beta_seed) if beta == "iid"
+          else lognormal_beta_field(xy, beta_seed))
+    return Mesh(xy=xy, tri=tri, bed=b, thick=thick, beta=be, sigma=uniform_sigma(nlayers),
+                name=name)
+
+
+# ---------------------------------------------------------------- named workloads
+
+def config_small() -> Mesh:
+    """Dome on a 32 x 32 jittered grid (2,048 triangles) x 5 layers = 10,240 wedges, flat bed."""
+    return dome_mesh(32, 5, 101, 102, bed="flat", beta="iid", name="dome-2k-tri-x5")
+
+
+def config_medium() -> Mesh:
+    """224 x 224 grid (100,352 triangles) x 10 layers = 1,003,520 wedges, sinusoidal bed."""
+    return dome_mesh(224, 10, 201, 202, bed="sinusoidal", beta="field", name="dome-100k-tri-x10")
+
+
+def config_large() -> Mesh:
+    """447 x 447 grid (399,618 triangles) x 10 layers = 3,996,180 wedges, sinusoidal bed."""
+    return dome_mesh(447, 10, 301, 302, bed="sinusoidal", beta="field", name="dome-400k-tri-x10")
+
+
+def ensemble_members(count: int = 64, seed0: int = 4000, scale: float = 1.0):
+    """Uneven ensemble: member i has T in [5k, 50k] triangles, L in [5, 20], H0 in [1, 3] km.
+
+    `scale` shrinks the triangle counts (for small tests); the draw per member is seeded
+    by seed0 + i so any subset of members is reproducible on its own.
+    """
+    members = []
+    for i in range(count):
+        rng = np.random.default_rng(seed0 + i)
+        T = rng.uniform(5e3, 50e3) * scale
+        L = int(rng.integers(5, 21))
+        H0 = float(rng.uniform(1000.0, 3000.0))
+        m = max(2, int(round(math.sqrt(T / 2.0))))
+        members.append(dome_mesh(m, L, seed0 + i, seed0 + 1000 + i, H0=H0, bed="sinusoidal",
+                                 beta="field", name=f"member{i}"))
+    return members
+
+
+def slab_mesh(m: int, nlayers: int, slope: float, thickness: float, beta: float,
+              half_width: float = 20e3, seed: int = 7, jitter: float = 0.0) -> Mesh:
+    """Inclined slab: constant H, surface and bed both of slope `slope` in x."""
+    xy, tri = jittered_grid(m, seed, half_width=half_width, jitter=jitter)
+    b = slope * xy[:, 0]
+    return Mesh(xy=xy, tri=tri, bed=b, thick=np.full(xy.shape[0], thickness),
+                beta=np.full(xy.shape[0], beta), sigma=uniform_sigma(nlayers), name="slab")
