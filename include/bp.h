@@ -1,0 +1,146 @@
+/*
+ * bp.h -- C ABI of libbp: first-order (Blatter-Pattyn) Stokes velocity assembly and Newton
+ * solve on extruded wedge meshes, for NVIDIA B300 (sm_103a).
+ *
+ * The operations follow arXiv 2204.04321 ("Performance portable ice-sheet modeling with
+ * MALI"):
+ *   - Sec. 2, Eq. FOStokes / effvisc / effeps: the momentum equations
+ *       -div(2 mu eps_1) + rho g ds/dx = 0,  -div(2 mu eps_2) + rho g ds/dy = 0,
+ *     Glen viscosity mu = 1/2 A^(-1/n) (eps_e^2 + delta)^((1-n)/(2n)) (delta regularises U = 0),
+ *     a stress-free surface, the linear sliding (Robin) law 2 mu eps . n + beta u = 0 at the bed
+ *     and stress-free vertical margins;
+ *   - Sec. 3.1, Eq. residual: low-order nodal prismatic (6-node wedge) finite elements on the
+ *     3D mesh extruded from a base triangulation give the residual F(U; {phi_i}, {grad phi_i}, H, beta);
+ *   - Sec. 3.1, Eq. linearsystem: damped Newton J delta = -F, U <- U + alpha delta;
+ *   - Sec. 3.2: the Jacobian is the exact derivative of the residual (forward-mode automatic
+ *     differentiation in the paper), scattered into a sparse matrix.
+ *
+ * Fixed discretisation (part of the ABI): reference wedge lambda = (1 - xi - eta, xi, eta),
+ * N = lambda_a (1 -/+ zeta)/2, 3-point triangle rule x 2-point Gauss in zeta (6 points),
+ * basal face with the same triangle rule over the true (3D) face area.
+ *
+ * Degrees of freedom are column-major and interleaved: for base vertex a, node level
+ * l = 0..L (0 = bed) and component c (0 = u, 1 = v): dof = 2 * (a * (L + 1) + l) + c.
+ * The Jacobian is stored in CSR over all structurally coupled pairs (base vertices equal or
+ * sharing a triangle, |l - l'| <= 1, all four component pairs), columns sorted, explicit zeros
+ * kept.  Row pointers are int64, column indices int32.
+ *
+ * Conventions for every call:
+ *   - the return value is a bp_status (0 = success);
+ *   - device buffers U, R, J are owned by the caller; the mesh object owns the mesh arrays,
+ *     the sparsity pattern and all scratch it needs, all on the device current at upload;
+ *   - calls that take a stream are asynchronous on that stream (a cudaStream_t passed as
+ *     void*, NULL = legacy default stream) unless documented as synchronising;
+ *   - residual / Jacobian outputs are overwritten, never accumulated;
+ *   - units are m, yr, Pa; no rescaling happens inside the library;
+ *   - there is no CPU fallback: every computation runs in the library's CUDA kernels.
+ */
+#ifndef BP_H
+#define BP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  BP_OK = 0,
+  BP_EINVAL = 1,    /* a NULL pointer, a size out of range or an unknown option */
+  BP_EMESH = 2,     /* invalid mesh: bad index, non-positive area or thickness, sigma not increasing */
+  BP_ENOMEM = 3,    /* device allocation failed */
+  BP_ECUDA = 4,     /* a CUDA runtime call failed */
+  BP_ENAN = 5,      /* a non-finite value was met */
+  BP_ENOCONV = 6,   /* an iteration limit was reached before the tolerance */
+  BP_EUNSUP = 7     /* a parameter combination the kernels do not implement (e.g. n != 3) */
+} bp_status;
+
+/* Glen exponent n (must be 3: the kernels use rcbrt), rate factor A [Pa^-n yr^-1],
+ * ice density rho [kg m^-3], gravity g [m s^-2], regularisation delta [yr^-2]. */
+typedef struct {
+  double n, A, rho, g, delta;
+} bp_params;
+
+/* Host description of an extruded mesh; all arrays are read during bp_mesh_upload only. */
+typedef struct {
+  int32_t nv;           /* base vertices */
+  int32_t ntri;         /* base triangles */
+  int32_t nlayers;      /* L >= 1 element layers, L + 1 node levels */
+  int32_t reserved;
+  const double* xy;     /* [nv][2] horizontal coordinates (m) */
+  const int32_t* tri;   /* [ntri][3] vertex indices, counter-clockwise */
+  const double* bed;    /* [nv] bed elevation b (m) */
+  const double* thick;  /* [nv] ice thickness H > 0 (m); node z = b + sigma_l H, surface s = b + H */
+  const double* beta;   /* [nv] sliding coefficient >= 0 (Pa yr m^-1) */
+  const double* sigma;  /* [nlayers + 1] 0 = sigma_0 < ... < sigma_L = 1 */
+  bp_params params;
+} bp_mesh_desc;
+
+typedef struct bp_mesh bp_mesh; /* opaque, library-owned */
+
+typedef struct {
+  int64_t ndof;        /* 2 nv (L + 1) */
+  int64_t nnz;         /* 4 (nv + 2 E)(3 L + 1), E = base edges */
+  int64_t nwedges;     /* ntri * L */
+  int32_t nv, ntri, nlayers, ncolors; /* ncolors: triangle colours of the coloured scatter */
+  int64_t device_bytes; /* device memory held by the mesh object */
+} bp_mesh_info_t;
+
+/* Jacobian precision of the derivative lanes (the residual is always FP64). */
+enum { BP_F64 = 0, BP_F32 = 1 };
+/* Scatter of element contributions: atomics, or colour by colour with plain read-modify-write. */
+enum { BP_SCATTER_AUTO = 0, BP_SCATTER_ATOMIC = 1, BP_SCATTER_COLOR = 2 };
+/* How the element Jacobian is formed: forward-mode dual numbers with 12 lanes (one per
+ * element dof), or the same tangent sum-factorised over the extruded quadrature. */
+enum { BP_JAC_AUTO = 0, BP_JAC_DUAL = 1, BP_JAC_FACTORED = 2 };
+
+/* Library version string (static storage). */
+const char* bp_version(void);
+/* Human-readable text of a status code (static storage). */
+const char* bp_strerror(int status);
+
+/*
+ * Validate the mesh, build the extruded CSR pattern, the per-triangle scatter slots, the
+ * triangle colouring and the solution-independent data (driving-stress load vector,
+ * basal friction matrices), and copy everything to the current device.  Mirrors the paper's
+ * memoisation (Sec. 4.1): data that do not change between Newton iterations are formed once.
+ * Synchronises `stream` before returning.  On error *out is NULL and nothing is leaked.
+ * Errors: BP_EINVAL (NULL pointers, nv/ntri/nlayers < 1), BP_EMESH (index out of range,
+ * clockwise or degenerate triangle, H <= 0, beta < 0, sigma not strictly increasing from 0 to 1),
+ * BP_EUNSUP (n != 3), BP_ENOMEM, BP_ECUDA.
+ */
+int bp_mesh_upload(const bp_mesh_desc* desc, void* stream, bp_mesh** out);
+
+/* Free a mesh (NULL is a no-op).  Synchronises the device. */
+void bp_mesh_free(bp_mesh* mesh);
+
+/* Sizes of an uploaded mesh. */
+int bp_mesh_info(const bp_mesh* mesh, bp_mesh_info_t* info);
+
+/* Borrowed device pointers to the CSR pattern (valid until bp_mesh_free):
+ * rowptr [ndof + 1] int64, colidx [nnz] int32. */
+int bp_csr_pattern(const bp_mesh* mesh, const int64_t** rowptr_dev, const int32_t** colidx_dev);
+
+/*
+ * Residual R(U) (Eq. residual), FP64.  U_dev, R_dev: device arrays of ndof doubles in the
+ * dof order above; R is overwritten.  Asynchronous on `stream`.
+ * Errors: BP_EINVAL (NULL arguments), BP_ECUDA (launch failure).
+ */
+int bp_assemble_residual(bp_mesh* mesh, const double* U_dev, double* R_dev, void* stream);
+
+/*
+ * Jacobian dR/dU at U (Sec. 3.2) into J_vals_dev ([nnz] values on the bp_csr_pattern
+ * pattern: double for BP_F64, float for BP_F32) and, if R_dev != NULL, the FP64 residual.
+ * Both outputs are overwritten (zeroing is part of the call).  `scatter` is a BP_SCATTER_*,
+ * `method` a BP_JAC_*.  Asynchronous on `stream`.
+ * Errors: BP_EINVAL (NULL U/J, unknown precision/scatter/method), BP_ENOMEM (first call with
+ * R_dev == NULL allocates a residual scratch in the mesh object), BP_ECUDA.
+ */
+int bp_assemble_jacobian(bp_mesh* mesh, const double* U_dev, double* R_dev, void* J_vals_dev,
+                         int precision, int scatter, int method, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BP_H */

@@ -1,0 +1,216 @@
+"""Thin ctypes binding of libbp (include/bp.h): the same entry points, argument marshalling only.
+
+Device buffers are torch CUDA tensors (PyTorch supplies device memory and streams); every
+computation runs in libbp's kernels.  There is no CPU fallback: if libbp.so is missing or
+cannot be loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libbp.so")
+
+BP_OK, BP_EINVAL, BP_EMESH, BP_ENOMEM, BP_ECUDA, BP_ENAN, BP_ENOCONV, BP_EUNSUP = range(8)
+BP_F64, BP_F32 = 0, 1
+BP_SCATTER_AUTO, BP_SCATTER_ATOMIC, BP_SCATTER_COLOR = 0, 1, 2
+BP_JAC_AUTO, BP_JAC_DUAL, BP_JAC_FACTORED = 0, 1, 2
+
+
+class BPError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__(f"{what}: {bp_strerror(status)} (status {status})")
+        self.status = status
+
+
+class bp_params(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_double), ("A", ctypes.c_double), ("rho", ctypes.c_double),
+                ("g", ctypes.c_double), ("delta", ctypes.c_double)]
+
+
+class bp_mesh_desc(ctypes.Structure):
+    _fields_ = [("nv", ctypes.c_int32), ("ntri", ctypes.c_int32), ("nlayers", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("xy", ctypes.c_void_p), ("tri", ctypes.c_void_p),
+                ("bed", ctypes.c_void_p), ("thick", ctypes.c_void_p), ("beta", ctypes.c_void_p),
+                ("sigma", ctypes.c_void_p), ("params", bp_params)]
+
+
+class bp_mesh_info_t(ctypes.Structure):
+    _fields_ = [("ndof", ctypes.c_int64), ("nnz", ctypes.c_int64), ("nwedges", ctypes.c_int64),
+                ("nv", ctypes.c_int32), ("ntri", ctypes.c_int32), ("nlayers", ctypes.c_int32),
+                ("ncolors", ctypes.c_int32), ("device_bytes", ctypes.c_int64)]
+
+
+# (name, restype, argtypes) of every exported entry point
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+SIGNATURES = {
+    "bp_version": (ctypes.c_char_p, []),
+    "bp_strerror": (ctypes.c_char_p, [_I]),
+    "bp_mesh_upload": (_I, [_P, _P, _P]),
+    "bp_mesh_free": (None, [_P]),
+    "bp_mesh_info": (_I, [_P, _P]),
+    "bp_csr_pattern": (_I, [_P, _P, _P]),
+    "bp_assemble_residual": (_I, [_P, _P, _P, _P]),
+    "bp_assemble_jacobian": (_I, [_P, _P, _P, _P, _I, _I, _I, _P]),
+}
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib():
+    """Load libbp.so (raises if it is missing: there is no fallback path)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"libbp.so not built ({LIB_PATH}); run paper_2204_04321_b300/build.py")
+            L = ctypes.CDLL(LIB_PATH)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _check(status: int, what: str):
+    if status != BP_OK:
+        raise BPError(status, what)
+
+
+def _stream_ptr(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def bp_version() -> str:
+    return lib().bp_version().decode()
+
+
+def bp_strerror(status: int) -> str:
+    return lib().bp_strerror(status).decode()
+
+
+def make_desc(mesh):
+    """bp_mesh_desc for a `synth.Mesh`; returns (desc, keepalive arrays)."""
+    keep = [np.ascontiguousarray(mesh.xy, dtype=np.float64),
+            np.ascontiguousarray(mesh.tri, dtype=np.int32),
+            np.ascontiguousarray(mesh.bed, dtype=np.float64),
+            np.ascontiguousarray(mesh.thick, dtype=np.float64),
+            np.ascontiguousarray(mesh.beta, dtype=np.float64),
+            np.ascontiguousarray(mesh.sigma, dtype=np.float64)]
+    p = mesh.params
+    desc = bp_mesh_desc(mesh.nv, mesh.ntri, mesh.nlayers, 0,
+                        *[a.ctypes.data for a in keep],
+                        bp_params(p.n, p.A, p.rho, p.g, p.delta))
+    return desc, keep
+
+
+def bp_mesh_upload(mesh, stream=None) -> ctypes.c_void_p:
+    desc, keep = make_desc(mesh)
+    out = ctypes.c_void_p()
+    _check(lib().bp_mesh_upload(ctypes.byref(desc), _stream_ptr(stream), ctypes.byref(out)),
+           "bp_mesh_upload")
+    del keep
+    return out
+
+
+def bp_mesh_free(handle) -> None:
+    lib().bp_mesh_free(handle)
+
+
+def bp_mesh_info(handle) -> dict:
+    info = bp_mesh_info_t()
+    _check(lib().bp_mesh_info(handle, ctypes.byref(info)), "bp_mesh_info")
+    return {f: getattr(info, f) for f, _ in bp_mesh_info_t._fields_}
+
+
+def bp_csr_pattern(handle):
+    """(rowptr_dev, colidx_dev) raw device pointers (borrowed)."""
+    rp, ci = ctypes.c_void_p(), ctypes.c_void_p()
+    _check(lib().bp_csr_pattern(handle, ctypes.byref(rp), ctypes.byref(ci)), "bp_csr_pattern")
+    return rp.value, ci.value
+
+
+def bp_assemble_residual(handle, U, R, stream=None) -> None:
+    _check(lib().bp_assemble_residual(handle, _dptr(U), _dptr(R), _stream_ptr(stream)),
+           "bp_assemble_residual")
+
+
+def bp_assemble_jacobian(handle, U, R, J, precision=BP_F64, scatter=BP_SCATTER_AUTO,
+                         method=BP_JAC_AUTO, stream=None) -> None:
+    _check(lib().bp_assemble_jacobian(handle, _dptr(U), None if R is None else _dptr(R), _dptr(J),
+                                      precision, scatter, method, _stream_ptr(stream)),
+           "bp_assemble_jacobian")
+
+
+class DeviceMesh:
+    """Convenience owner of an uploaded mesh (frees it on close / garbage collection)."""
+
+    def __init__(self, mesh, stream=None):
+        import torch
+        self.mesh = mesh
+        self.handle = bp_mesh_upload(mesh, stream)
+        self.info = bp_mesh_info(self.handle)
+        self.ndof = self.info["ndof"]
+        self.nnz = self.info["nnz"]
+        self.device = torch.device("cuda", torch.cuda.current_device())
+
+    def pattern(self):
+        """rowptr, colidx as torch tensors (copies of the library-owned arrays)."""
+        rp, ci = bp_csr_pattern(self.handle)
+        return (_borrow(rp, self.ndof + 1, "<i8").clone(), _borrow(ci, self.nnz, "<i4").clone())
+
+    def residual(self, U, R=None, stream=None):
+        import torch
+        if R is None:
+            R = torch.empty(self.ndof, dtype=torch.float64, device=self.device)
+        bp_assemble_residual(self.handle, U, R, stream)
+        return R
+
+    def jacobian(self, U, precision=BP_F64, scatter=BP_SCATTER_AUTO, method=BP_JAC_AUTO,
+                 R=None, J=None, want_residual=True, stream=None):
+        import torch
+        if J is None:
+            J = torch.empty(self.nnz, dtype=torch.float64 if precision == BP_F64 else torch.float32,
+                            device=self.device)
+        if R is None and want_residual:
+            R = torch.empty(self.ndof, dtype=torch.float64, device=self.device)
+        bp_assemble_jacobian(self.handle, U, R, J, precision, scatter, method, stream)
+        return J, R
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            bp_mesh_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class _DevArray:
+    """Minimal __cuda_array_interface__ wrapper of a borrowed device pointer."""
+
+    def __init__(self, ptr: int, n: int, typestr: str):
+        self.__cuda_array_interface__ = {"shape": (n,), "typestr": typestr, "data": (ptr, False),
+                                         "version": 3, "strides": None}
+
+
+def _borrow(ptr: int, n: int, typestr: str):
+    import torch
+    return torch.as_tensor(_DevArray(ptr, n, typestr), device="cuda")

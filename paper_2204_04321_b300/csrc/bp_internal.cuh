@@ -1,0 +1,98 @@
+// Internal declarations of libbp (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <vector>
+
+#include "bp.h"
+
+#define BP_CUDA_TRY(expr)                                   \
+  do {                                                      \
+    cudaError_t bp_err_ = (expr);                           \
+    if (bp_err_ != cudaSuccess) {                           \
+      bp_set_last_cuda_error(bp_err_, #expr, __LINE__);     \
+      return BP_ECUDA;                                      \
+    }                                                       \
+  } while (0)
+
+void bp_set_last_cuda_error(cudaError_t err, const char* what, int line);
+
+// Quadrature constants of the fixed wedge rule (see bp.h).
+// zeta = -+1/sqrt(3): psi_0 = (1 - zeta)/2, psi_1 = (1 + zeta)/2 take the values P and Q.
+#define BP_QP_P 0.78867513459481288225457439025098  // (1 + 1/sqrt(3)) / 2
+#define BP_QP_Q 0.21132486540518711774542560974902  // (1 - 1/sqrt(3)) / 2
+
+struct bp_mesh {
+  int device = 0;
+  int32_t nv = 0, ntri = 0, nl = 0;
+  int64_t ndof = 0, nnz = 0;
+  bp_params p{};
+  double cA = 0.0;  // A^(-1/3): 2 mu = cA (eps_e^2 + delta)^(-1/3) for n = 3
+
+  // per vertex
+  double2* xy = nullptr;
+  double* bed = nullptr;
+  double* thick = nullptr;
+  double* beta = nullptr;
+  int64_t* vstart = nullptr;  // first CSR entry of the vertex's row block
+  int32_t* vdeg = nullptr;    // |{a} U neighbours(a)|
+  int32_t* nbr_ptr = nullptr; // [nv + 1] sorted closed neighbourhoods
+  int32_t* nbr_idx = nullptr;
+  // per level
+  double* sigma = nullptr;
+  // per triangle
+  int32_t* tri = nullptr;     // [ntri][3]
+  int32_t* slots = nullptr;   // [ntri][9]: slot[a][b] = rank of tri[b] in the closed neighbourhood of tri[a]
+  double* basal = nullptr;    // [ntri][6]: basal friction matrix entries 00 01 02 11 12 22
+  int32_t* color_tris = nullptr;  // [ntri] triangles grouped by colour
+  std::vector<int32_t> color_off; // host copy: [ncolors + 1]
+  int32_t ncolors = 0;
+  // per dof / per entry
+  int64_t* rowptr = nullptr;
+  int32_t* colidx = nullptr;
+  double* load = nullptr;     // [ndof] driving-stress load rho g grad s . int N_i (solution independent)
+  double* rscratch = nullptr; // [ndof] residual scratch for Jacobian calls with R = NULL
+
+  int64_t device_bytes = 0;
+  std::vector<void*> allocations;
+};
+
+// Allocation helper that records the pointer in the mesh (freed by bp_mesh_free).
+template <class T>
+int bp_alloc(bp_mesh* m, T** ptr, size_t count) {
+  *ptr = nullptr;
+  if (count == 0) count = 1;
+  void* p = nullptr;
+  if (cudaMalloc(&p, count * sizeof(T)) != cudaSuccess) {
+    cudaGetLastError();
+    return BP_ENOMEM;
+  }
+  m->allocations.push_back(p);
+  m->device_bytes += (int64_t)(count * sizeof(T));
+  *ptr = static_cast<T*>(p);
+  return BP_OK;
+}
+
+// Makes the mesh's device current for the scope of a call and restores the caller's device.
+struct bp_device_guard {
+  int prev = -1;
+  explicit bp_device_guard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~bp_device_guard() {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+// Node level helpers of the extruded CSR pattern.
+__host__ __device__ inline int bp_nlev(int level, int L) { return (level == 0 || level == L) ? 2 : 3; }
+__host__ __device__ inline int bp_levels_before(int level) { return level == 0 ? 0 : 3 * level - 1; }
+__host__ __device__ inline int64_t bp_dof(int64_t a, int l, int c, int L) {
+  return 2 * (a * (L + 1) + l) + c;
+}

@@ -1,0 +1,77 @@
+"""C ABI checks that need no GPU: the library loads, exports every declared entry point,
+and rejects invalid meshes on the host before touching the device."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2204_04321_b300 import capi, synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_entry_points():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names.update(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(bp_\w+)\s*\(", src, flags=re.M))
+    return names
+
+
+def test_library_exports_every_declared_symbol():
+    L = capi.lib()
+    names = declared_entry_points()
+    assert "bp_assemble_jacobian" in names and len(names) >= 8
+    for n in sorted(names):
+        assert hasattr(L, n), n
+    assert set(capi.SIGNATURES) == names
+
+
+def test_version_and_strerror():
+    assert "sm_103a" in capi.bp_version()
+    assert capi.bp_strerror(capi.BP_EMESH) == "invalid mesh"
+    assert capi.bp_strerror(12345) == "unknown status"
+
+
+def _upload_status(mesh):
+    import ctypes
+    desc, keep = capi.make_desc(mesh)
+    out = ctypes.c_void_p(1)
+    rc = capi.lib().bp_mesh_upload(ctypes.byref(desc), None, ctypes.byref(out))
+    return rc, out.value
+
+
+def tiny():
+    return synth.dome_mesh(3, 2, 1, 2)
+
+
+@pytest.mark.parametrize("corrupt,status", [
+    (lambda m: m.tri.__setitem__((0, 1), m.nv + 5), capi.BP_EMESH),          # index out of range
+    (lambda m: m.tri.__setitem__((0, slice(None)), m.tri[0, ::-1].copy()), capi.BP_EMESH),  # clockwise
+    (lambda m: m.thick.__setitem__(3, 0.0), capi.BP_EMESH),                  # zero thickness
+    (lambda m: m.beta.__setitem__(2, -1.0), capi.BP_EMESH),                  # negative beta
+    (lambda m: m.sigma.__setitem__(1, m.sigma[2]), capi.BP_EMESH),           # sigma not increasing
+    (lambda m: setattr(m.params, "n", 4.0), capi.BP_EUNSUP),                 # only n = 3
+    (lambda m: m.xy.__setitem__((4, 0), np.nan), capi.BP_EMESH),             # non-finite coordinate
+])
+def test_invalid_mesh_rejected_on_host(corrupt, status):
+    m = tiny()
+    corrupt(m)
+    rc, out = _upload_status(m)
+    assert rc == status
+    assert out is None
+
+
+def test_null_arguments_rejected():
+    import ctypes
+    L = capi.lib()
+    assert L.bp_mesh_upload(None, None, None) == capi.BP_EINVAL
+    out = ctypes.c_void_p()
+    assert L.bp_mesh_upload(None, None, ctypes.byref(out)) == capi.BP_EINVAL
+    assert L.bp_mesh_info(None, None) == capi.BP_EINVAL
+    assert L.bp_assemble_residual(None, None, None, None) == capi.BP_EINVAL
+    assert L.bp_assemble_jacobian(None, None, None, None, 0, 0, 0, None) == capi.BP_EINVAL
+    L.bp_mesh_free(None)  # no-op
