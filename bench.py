@@ -1,0 +1,353 @@
+"""Benchmark: FP64 residual + Jacobian assembly of the first-order Stokes system (wedge cells/s).
+
+One step = one bp_assemble_jacobian call (FP64 lanes, residual requested, zero-initialisation
+included) on the 1,003,520-wedge dome (100,352 base triangles x 10 layers), i.e. every row of
+the assembly path: gather, basis, interpolation, viscosity, residual, Jacobian, scatter.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+`--impl reference` times the CPU oracle (single-threaded FP64 C++) on a bounded sample of the
+same workload.  Under torchrun (N > 1) every rank assembles its own replica of the workload
+(no collective on the data path: weak scaling); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "residual+Jacobian wedge cells/s"
+UNIT = "wedges/s"
+FP64_PEAK_TFLOPS = 1.25     # nominal B300 FP64 (no tensor-core FP64 path is used)
+FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12   # 148 SMs x 128 FP32 lanes x FMA x max clock
+# FP64 flops per wedge of the residual + Jacobian assembly (factored formulation), counted with
+# ncu on 450,000 wedges: (2 x DFMA + DADD + DMUL) / wedges.  Fixed as the algorithm's work figure.
+FLOPS_PER_WEDGE_JAC64 = 3211  # ncu: (2 DFMA + DADD + DMUL) per wedge of the factored kernel
+L2_FLUSH_BYTES = 512 << 20
+
+
+def read_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.idx = device_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in getattr(self, "lines", []):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for name, val in zip(names, f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_oracle_sample(seconds_budget: float = 20.0):
+    """Time the CPU oracle (residual + dual-number Jacobian, single thread) on a sample mesh of the
+    workload's generator: a 100 x 100 grid (20,000 triangles) x 10 layers = 200,000 wedges."""
+    import oracle
+    from paper_2204_04321_b300 import synth
+    mesh = synth.dome_mesh(100, 10, 201, 202, bed="sinusoidal", beta="field", name="dome-20k-tri-x10")
+    om = oracle.OracleMesh(mesh)
+    U = synth.random_velocity(mesh, 5, 50.0)
+    om.pattern()
+    runs = []
+    t_end = time.perf_counter() + seconds_budget
+    while True:
+        t0 = time.perf_counter()
+        om.jacobian(U)
+        runs.append(time.perf_counter() - t0)
+        if time.perf_counter() > t_end or len(runs) >= 5:
+            break
+    t = statistics.median(runs)
+    return {"value": mesh.nwedges / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{mesh.name}: {mesh.nwedges} wedges, residual + 12-lane dual Jacobian into CSR, "
+                      f"median of {len(runs)} runs, g++ -O2, 1 thread"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    from paper_2204_04321_b300 import synth
+    import oracle
+    mesh = synth.dome_mesh(100, 10, 201, 202, bed="sinusoidal", beta="field", name="dome-20k-tri-x10")
+    om = oracle.OracleMesh(mesh)
+    U = synth.random_velocity(mesh, 5, 50.0)
+    om.pattern()
+    for _ in range(args.warmup):
+        om.jacobian(U)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        om.jacobian(U)
+    dt = time.perf_counter() - t0
+    value = mesh.nwedges * args.steps / dt
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "dome-100k-tri-x10 (each step a bounded sample: dome-20k-tri-x10, "
+                                   "200,000 wedges, same generators)", "oracle": "CPU FP64, 1 thread"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "dome-20k-tri-x10, 200,000 wedges per step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    from paper_2204_04321_b300 import capi, synth
+
+    ws, rank, local = dist_env()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device")
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    if (args.mesh_m, args.layers) == (224, 10):
+        mesh = synth.config_medium()
+    else:  # smaller case of the same generators (profiling captures)
+        mesh = synth.dome_mesh(args.mesh_m, args.layers, 201, 202, bed="sinusoidal", beta="field",
+                               name=f"dome-{2 * args.mesh_m ** 2 // 1000}k-tri-x{args.layers}")
+    W = mesh.nwedges
+    dm = capi.DeviceMesh(mesh)
+    U_host = torch.from_numpy(synth.random_velocity(mesh, 5, 50.0) + 0.0).pin_memory()
+    U = U_host.to(dev)
+    R = torch.empty(dm.ndof, dtype=torch.float64, device=dev)
+    J = torch.empty(dm.nnz, dtype=torch.float64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        capi.bp_assemble_jacobian(dm.handle, U, R, J, capi.BP_F64, capi.BP_SCATTER_ATOMIC,
+                                  capi.BP_JAC_FACTORED, stream)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        t_wall0 = time.perf_counter()
+        for e0, e1 in ev:
+            flush.fill_(1)              # L2 flush outside the timed events
+            e0.record(stream)
+            step()
+            e1.record(stream)
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter() - t_wall0
+    barrier()
+    step_ms = [e0.elapsed_time(e1) for e0, e1 in ev]
+    total_ms = sum(step_ms)
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = ws * W * args.steps / (total_ms * 1e-3)
+
+    # zero-initialisation share of a step (memset of J + copy of the memoised load into R), timed alone
+    z0, z1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    zs = []
+    for _ in range(5):
+        flush.fill_(1)
+        z0.record(stream)
+        J.zero_()
+        R.zero_()
+        z1.record(stream)
+        torch.cuda.synchronize()
+        zs.append(z0.elapsed_time(z1))
+    zero_ms = statistics.median(zs)
+    kernel_ms = max(ms_per_step - zero_ms, 1e-6)
+
+    # secondary: residual only, FP32-lane Jacobian (same workload)
+    def timed(fn, reps=10):
+        for _ in range(3):
+            fn()
+        ts = []
+        for _ in range(reps):
+            flush.fill_(1)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        return statistics.median(ts)
+
+    res_ms = timed(lambda: capi.bp_assemble_residual(dm.handle, U, R, stream))
+    J32 = torch.empty(dm.nnz, dtype=torch.float32, device=dev)
+    jac32_ms = timed(lambda: capi.bp_assemble_jacobian(dm.handle, U, R, J32, capi.BP_F32,
+                                                       capi.BP_SCATTER_ATOMIC, capi.BP_JAC_FACTORED, stream))
+    dual_ms = timed(lambda: capi.bp_assemble_jacobian(dm.handle, U, R, J, capi.BP_F64,
+                                                      capi.BP_SCATTER_ATOMIC, capi.BP_JAC_DUAL, stream), reps=5)
+    del J32
+
+    # end to end through the C ABI with host buffers: U from pinned host memory, R and J back to host
+    R_host = torch.empty(dm.ndof, dtype=torch.float64).pin_memory()
+    J_host = torch.empty(dm.nnz, dtype=torch.float64).pin_memory()
+
+    def e2e_step():
+        U.copy_(U_host, non_blocking=True)
+        step()
+        R_host.copy_(R, non_blocking=True)
+        J_host.copy_(J, non_blocking=True)
+
+    for _ in range(2):
+        e2e_step()
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = ws * W * args.steps / e2e_s
+
+    flops = FLOPS_PER_WEDGE_JAC64 * W
+    achieved = flops / (kernel_ms * 1e-3) / 1e12
+    peaks = read_peaks()
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "assemble_jacobian_f64_traffic.json")
+    if os.path.exists(prof):
+        with open(prof) as f:
+            pj = json.load(f)
+        if pj.get("kernel_source_hash") == kernel_hash():
+            traffic = pj["bytes_per_wedge"] * W
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{mesh.name}: dome on a {args.mesh_m}x{args.mesh_m} jittered Delaunay grid, "
+                                   f"{mesh.ntri} triangles x {mesh.nlayers} layers = {W} wedges, "
+                                   "sinusoidal bed, correlated lognormal beta",
+                       "ndof": dm.ndof, "nnz": dm.nnz, "lanes": "f64, sum-factorised",
+                       "scatter": "atomic", "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU",
+                       "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MB write outside the timed events)"},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
+                         "kernel": "k_assemble<factored, double, atomic>",
+                         "kernel_ms": kernel_ms, "flops_per_wedge": FLOPS_PER_WEDGE_JAC64,
+                         "peak_note": "FP64 nominal 1.25 TFLOP/s (no FP64 entry in MEASURED_PEAKS.json); "
+                                      "HBM measured " + str(peaks.get("hbm_gbs")) + " GB/s"},
+            "secondary": {
+                "residual_only": {"value": W / (res_ms * 1e-3), "unit": UNIT, "ms": res_ms},
+                "jacobian_f32_lanes": {"value": W / (jac32_ms * 1e-3), "unit": UNIT, "ms": jac32_ms},
+                "jacobian_f64_dual12": {"value": W / (dual_ms * 1e-3), "unit": UNIT, "ms": dual_ms},
+                "zero_init_ms": zero_ms, "wall_s_timed_region": t_wall},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * dm.ndof,
+                    "d2h_bytes_per_step": 8 * dm.ndof + 8 * dm.nnz},
+            "gpu_launches": args.steps,
+            "clocks": clk.summary(),
+        }
+        if not args.no_cpu_baseline and ws == 1:
+            line["cpu_baseline"] = cpu_oracle_sample()
+        print(json.dumps(line), flush=True)
+    dm.close()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def kernel_hash():
+    import hashlib
+    with open(os.path.join(ROOT, "paper_2204_04321_b300", "csrc", "bp_assemble.cu"), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mesh-m", type=int, default=224, help="base grid size (224: the 1M-wedge workload)")
+    ap.add_argument("--layers", type=int, default=10)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())
