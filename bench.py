@@ -329,9 +329,13 @@ def run_ours(args):
 
 
 def kernel_hash():
+    """Hash of the assembly kernel's source text (the k_assemble template and its helpers)."""
     import hashlib
-    with open(os.path.join(ROOT, "paper_2204_04321_b300", "csrc", "bp_assemble.cu"), "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+    with open(os.path.join(ROOT, "paper_2204_04321_b300", "csrc", "bp_assemble.cu")) as f:
+        src = f.read()
+    a = src.index("constexpr int MODE_RES")
+    b = src.index("AsmArgs make_args")
+    return hashlib.sha256(src[a:b].encode()).hexdigest()[:16]
 
 
 def main():
