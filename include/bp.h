@@ -52,7 +52,8 @@ typedef enum {
   BP_ECUDA = 4,     /* a CUDA runtime call failed */
   BP_ENAN = 5,      /* a non-finite value was met */
   BP_ENOCONV = 6,   /* an iteration limit was reached before the tolerance */
-  BP_EUNSUP = 7     /* a parameter combination the kernels do not implement (e.g. n != 3) */
+  BP_EUNSUP = 7,    /* a parameter combination the kernels do not implement (e.g. n != 3) */
+  BP_ESIZE = 8      /* the problem exceeds a fixed capacity of the call (see BP_NOALLOC_MAX_NDOF) */
 } bp_status;
 
 /* Glen exponent n (must be 3: the kernels use rcbrt), rate factor A [Pa^-n yr^-1],
@@ -138,6 +139,27 @@ int bp_assemble_residual(bp_mesh* mesh, const double* U_dev, double* R_dev, void
  */
 int bp_assemble_jacobian(bp_mesh* mesh, const double* U_dev, double* R_dev, void* J_vals_dev,
                          int precision, int scatter, int method, void* stream);
+
+/*
+ * Allocation-free variant of bp_assemble_jacobian (R not returned).  The paper has no
+ * counterpart: this entry point exists for callers that must not allocate device memory once
+ * running (a fixed device-memory budget, or a host framework whose allocator owns all device
+ * memory), for whom the residual scratch that bp_assemble_jacobian allocates on its first call
+ * with R_dev == NULL is not acceptable.  Its residual scratch is a fixed array inside the
+ * library of BP_NOALLOC_MAX_NDOF doubles (8 MiB), which every GPU that loads the library holds
+ * until the process exits; the call itself performs no allocation.
+ *   - J_vals_dev, precision, scatter, method: as for bp_assemble_jacobian; J is overwritten.
+ *   - The first call on each device looks up the array's device address (cudaGetSymbolAddress)
+ *     with that device current; make that first call before any stream capture.
+ *   - All calls share the one array and leave their residual in it; each call starts it afresh.
+ *     Calls whose executions overlap on the GPU (different streams, or different meshes on the
+ *     same device at the same time) race on the array: serialise them.
+ * Errors: BP_ESIZE if the mesh has more than BP_NOALLOC_MAX_NDOF degrees of freedom,
+ * BP_EINVAL (NULL U/J, unknown precision/scatter/method), BP_ECUDA.
+ */
+#define BP_NOALLOC_MAX_NDOF 1048576
+int bp_assemble_jacobian_noalloc(bp_mesh* mesh, const double* U_dev, void* J_vals_dev, int precision,
+                                 int scatter, int method, void* stream);
 
 #ifdef __cplusplus
 }

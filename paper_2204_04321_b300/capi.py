@@ -15,7 +15,8 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libbp.so")
 
-BP_OK, BP_EINVAL, BP_EMESH, BP_ENOMEM, BP_ECUDA, BP_ENAN, BP_ENOCONV, BP_EUNSUP = range(8)
+BP_OK, BP_EINVAL, BP_EMESH, BP_ENOMEM, BP_ECUDA, BP_ENAN, BP_ENOCONV, BP_EUNSUP, BP_ESIZE = range(9)
+BP_NOALLOC_MAX_NDOF = 1048576
 BP_F64, BP_F32 = 0, 1
 BP_SCATTER_AUTO, BP_SCATTER_ATOMIC, BP_SCATTER_COLOR = 0, 1, 2
 BP_JAC_AUTO, BP_JAC_DUAL, BP_JAC_FACTORED = 0, 1, 2
@@ -57,6 +58,7 @@ SIGNATURES = {
     "bp_csr_pattern": (_I, [_P, _P, _P]),
     "bp_assemble_residual": (_I, [_P, _P, _P, _P]),
     "bp_assemble_jacobian": (_I, [_P, _P, _P, _P, _I, _I, _I, _P]),
+    "bp_assemble_jacobian_noalloc": (_I, [_P, _P, _P, _I, _I, _I, _P]),
 }
 
 _lock = threading.Lock()
@@ -154,6 +156,13 @@ def bp_assemble_jacobian(handle, U, R, J, precision=BP_F64, scatter=BP_SCATTER_A
     _check(lib().bp_assemble_jacobian(handle, _dptr(U), None if R is None else _dptr(R), _dptr(J),
                                       precision, scatter, method, _stream_ptr(stream)),
            "bp_assemble_jacobian")
+
+
+def bp_assemble_jacobian_noalloc(handle, U, J, precision=BP_F64, scatter=BP_SCATTER_AUTO,
+                                 method=BP_JAC_AUTO, stream=None) -> None:
+    _check(lib().bp_assemble_jacobian_noalloc(handle, _dptr(U), _dptr(J), precision, scatter, method,
+                                              _stream_ptr(stream)),
+           "bp_assemble_jacobian_noalloc")
 
 
 class DeviceMesh:

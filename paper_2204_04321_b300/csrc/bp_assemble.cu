@@ -22,6 +22,7 @@
 // sum-factorised over the wedge's quadrature structure (BP_JAC_FACTORED).  The lane type TL is
 // double (BP_F64) or float (BP_F32); the residual stays FP64 either way.
 #include <cmath>
+#include <mutex>
 
 #include "bp_internal.cuh"
 
@@ -616,6 +617,66 @@ extern "C" int bp_assemble_jacobian(bp_mesh* m, const double* U, double* R, void
     }
     Rw = m->rscratch;
   }
+  BP_CUDA_TRY(cudaMemcpyAsync(Rw, m->load, m->ndof * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  BP_CUDA_TRY(cudaMemsetAsync(J, 0, m->nnz * (precision == BP_F64 ? sizeof(double) : sizeof(float)), s));
+  const AsmArgs a = make_args(m, U, Rw, J);
+  if (precision == BP_F64)
+    return method == BP_JAC_DUAL ? launch<MODE_DUAL, double>(m, a, scatter, s)
+                                 : launch<MODE_FACT, double>(m, a, scatter, s);
+  return method == BP_JAC_DUAL ? launch<MODE_DUAL, float>(m, a, scatter, s)
+                               : launch<MODE_FACT, float>(m, a, scatter, s);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Allocation-free Jacobian assembly.
+//
+// bp_assemble_jacobian with R == NULL allocates a residual scratch (ndof doubles) in the mesh
+// object on its first call.  Callers that may not allocate device memory once they are running
+// -- code under a fixed device-memory budget, or inside a framework whose allocator owns all
+// device memory and forbids direct cudaMalloc -- use bp_assemble_jacobian_noalloc instead: its
+// residual scratch is this file-scope device array, so the call itself never allocates.
+//
+// The array is part of the library's module image: every GPU on which the library's module is
+// loaded holds BP_NOALLOC_MAX_NDOF doubles (8 MiB) of it until the process exits.  In host code
+// the name g_noalloc_residual is only a host-side stand-in; the device address is looked up with
+// cudaGetSymbolAddress once per device, with that device current, on the entry point's first
+// call there.
+static __device__ __align__(256) double g_noalloc_residual[BP_NOALLOC_MAX_NDOF];
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+double* g_noalloc_ptr[kMaxDevices] = {};
+
+// Device address of g_noalloc_residual on `device` (current); looked up once per device.
+int noalloc_scratch(int device, double** out) {
+  if (device < 0 || device >= kMaxDevices) return BP_EUNSUP;
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_ptr[device]) {
+    void* p = nullptr;
+    BP_CUDA_TRY(cudaGetSymbolAddress(&p, g_noalloc_residual));
+    g_noalloc_ptr[device] = static_cast<double*>(p);
+  }
+  *out = g_noalloc_ptr[device];
+  return BP_OK;
+}
+}  // namespace
+
+extern "C" int bp_assemble_jacobian_noalloc(bp_mesh* m, const double* U, void* J, int precision,
+                                            int scatter, int method, void* stream) {
+  if (!m || !U || !J) return BP_EINVAL;
+  if (precision != BP_F64 && precision != BP_F32) return BP_EINVAL;
+  if (scatter < BP_SCATTER_AUTO || scatter > BP_SCATTER_COLOR) return BP_EINVAL;
+  if (method < BP_JAC_AUTO || method > BP_JAC_FACTORED) return BP_EINVAL;
+  if (m->ndof > BP_NOALLOC_MAX_NDOF) return BP_ESIZE;
+  bp_device_guard g(m->device);
+  double* Rw = nullptr;
+  int rc = noalloc_scratch(m->device, &Rw);
+  if (rc) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (scatter == BP_SCATTER_AUTO) scatter = BP_SCATTER_ATOMIC;
+  if (method == BP_JAC_AUTO) method = BP_JAC_FACTORED;
+  // the scratch keeps the previous call's residual: start it again from the memoised load
   BP_CUDA_TRY(cudaMemcpyAsync(Rw, m->load, m->ndof * sizeof(double), cudaMemcpyDeviceToDevice, s));
   BP_CUDA_TRY(cudaMemsetAsync(J, 0, m->nnz * (precision == BP_F64 ? sizeof(double) : sizeof(float)), s));
   const AsmArgs a = make_args(m, U, Rw, J);

@@ -28,6 +28,7 @@ extern "C" const char* bp_strerror(int status) {
     case BP_ENAN: return "non-finite value";
     case BP_ENOCONV: return "iteration limit reached before the tolerance";
     case BP_EUNSUP: return "unsupported parameters (the kernels implement Glen exponent n = 3)";
+    case BP_ESIZE: return "problem exceeds the fixed capacity of this call (BP_NOALLOC_MAX_NDOF dofs)";
     default: return "unknown status";
   }
 }
