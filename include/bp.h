@@ -140,6 +140,99 @@ int bp_assemble_residual(bp_mesh* mesh, const double* U_dev, double* R_dev, void
 int bp_assemble_jacobian(bp_mesh* mesh, const double* U_dev, double* R_dev, void* J_vals_dev,
                          int precision, int scatter, int method, void* stream);
 
+/* ------------------------------------------------------------------------------------------
+ * Solver (Sec. 3.1 Eq. linearsystem, Sec. 3.3 / 4.4).  All vectors are device arrays of ndof
+ * doubles in the dof order above.
+ * ------------------------------------------------------------------------------------------ */
+
+/*
+ * y = J x for a Jacobian on the bp_csr_pattern pattern (J_vals_dev: double for BP_F64, float for
+ * BP_F32; products and sums in FP64).  The operator application "Op*x" of the linear solve.
+ * Asynchronous.  Errors: BP_EINVAL, BP_ENOMEM (first call allocates solver workspace), BP_ECUDA.
+ */
+int bp_spmv(bp_mesh* mesh, const void* J_vals_dev, int precision, const double* x_dev, double* y_dev,
+            void* stream);
+
+/*
+ * Vertical-line preconditioner: for every base vertex, the block-tridiagonal part of J that
+ * couples the (L + 1) levels of its column (2 x 2 blocks) is factorised by block Thomas elimination
+ * without pivoting (J is symmetric positive definite), one thread per column -- the per-vertical-line
+ * batched LU of the paper's semicoarsening prolongation (Sec. 4.4).  bp_colprec_setup factorises
+ * (in FP64) and keeps the factors in the mesh; bp_colprec_apply computes z = P^-1 r.  Asynchronous.
+ * Errors: BP_EINVAL, BP_ENOMEM (workspace), BP_ECUDA.
+ */
+int bp_colprec_setup(bp_mesh* mesh, const void* J_vals_dev, int precision, void* stream);
+int bp_colprec_apply(bp_mesh* mesh, const double* r_dev, double* z_dev, void* stream);
+
+/*
+ * Discrete energy Pi_h(U) = sum_q w det J A^(-1/n) 2n/(n+1) (eps_e^2 + delta)^((n+1)/(2n))
+ * + sum_i load_i U_i + 1/2 sum_bed U_b^T M_beta U_b, whose gradient is the residual (same
+ * quadrature).  Not written in the paper: it follows from Eq. effvisc / effeps and is the merit
+ * function of the damped Newton line search.  Writes the value to *out_host; synchronises `stream`.
+ */
+int bp_energy(bp_mesh* mesh, const double* U_dev, double* out_host, void* stream);
+
+/*
+ * Energy change Pi_h(U + alpha D) - Pi_h(U), formed term by term as differences (the stress term
+ * through the exact expansion of eps_e^2 in alpha and a^2 - b^2 = (a - b)(a + b) on cube roots),
+ * so it stays accurate when it is far below the rounding level of Pi_h itself -- the quantity the
+ * Newton line search compares.  Writes *out_host; synchronises `stream`.
+ */
+int bp_energy_change(bp_mesh* mesh, const double* U_dev, const double* D_dev, double alpha, double* out_host,
+                     void* stream);
+
+/* Initial guesses of the Newton solve (not in the paper). */
+enum { BP_GUESS_ZERO = 0, BP_GUESS_SIA = 1 };
+/*
+ * U = 0, or the shallow-ice + linear-sliding profile
+ *   u(z) = -(2A/(n+1)) (rho g)^n |grad s|^(n-1) grad s (H^(n+1) - (s - z)^(n+1)) - rho g H grad s / beta
+ * with the nodal grad s = area-weighted mean of the P1 gradients of the adjacent triangles
+ * (beta = 0 at a vertex gives the non-sliding profile).  Asynchronous.
+ */
+int bp_initial_guess(bp_mesh* mesh, int kind, double* U_dev, void* stream);
+
+enum { BP_KRYLOV_CG = 0 };
+typedef struct {
+  double rtol;        /* stop when ||F(U)||_2 <= rtol ||F(0)||_2 (F(0) is the driving-stress load) */
+  int max_newton;     /* Newton iteration limit (<= 64) */
+  int max_krylov;     /* Krylov iterations per Newton step */
+  double eta_max;     /* Eisenstat-Walker forcing term cap (choice 2, gamma = 0.9) */
+  int precision;      /* BP_F64: FP64 Jacobian and Krylov; BP_F32: FP32 Jacobian lanes and Krylov
+                         (inexact Newton); the residual, viscosity, norms and update stay FP64 */
+  int krylov;         /* BP_KRYLOV_CG (the Jacobian is SPD) */
+  int line_search;    /* 1: Armijo backtracking on the energy, alpha = 1, 1/2, ..., 2^-10 */
+  int check_every;    /* Krylov convergence is read back every check_every iterations */
+} bp_solve_opts;
+
+typedef struct {
+  int newton_iters;          /* Newton steps taken */
+  int krylov_iters;          /* total Krylov iterations */
+  int converged;             /* 1 if ||F|| <= rtol ||F(0)|| */
+  int pad;
+  double fnorm_ref;          /* ||F(0)||_2 */
+  double fnorm_initial;      /* ||F(U_0)||_2 */
+  double fnorm_final;        /* ||F(U)||_2 at return */
+  double history[65];        /* ||F(U_k)|| / ||F(0)|| for k = 0..newton_iters */
+  int krylov_per_newton[64];
+  double alpha[64];          /* accepted damping factors */
+  double t_total, t_assemble, t_precond, t_krylov, t_linesearch; /* seconds (CUDA events) */
+} bp_solve_report;
+
+/* Defaults: rtol 1e-8, 50 Newton, 1000 Krylov, eta_max 0.1, BP_F64, CG, line search on, check 8. */
+void bp_solve_opts_default(bp_solve_opts* opts);
+
+/*
+ * Damped Newton (Eq. linearsystem) from the guess in U_dev to ||F|| <= rtol ||F(0)||: per step
+ * the Jacobian and residual are assembled (bp_assemble_jacobian), the column preconditioner is
+ * factorised, J delta = -F is solved by preconditioned CG to the Eisenstat-Walker tolerance, and
+ * alpha is the first of 1, 1/2, ..., 2^-10 with bp_energy_change(U, delta, alpha) <= 1e-4 alpha F . delta
+ * (Armijo on the energy).  U_dev holds the last iterate on return.
+ * Synchronises `stream`.  Errors: BP_EINVAL, BP_ENOMEM, BP_ECUDA, BP_ENAN (non-finite residual),
+ * BP_ENOCONV (max_newton reached; the report is filled either way).
+ */
+int bp_newton_solve(bp_mesh* mesh, double* U_dev, const bp_solve_opts* opts, bp_solve_report* report,
+                    void* stream);
+
 /*
  * Allocation-free variant of bp_assemble_jacobian (R not returned).  The paper has no
  * counterpart: this entry point exists for callers that must not allocate device memory once

@@ -20,6 +20,8 @@ BP_NOALLOC_MAX_NDOF = 1048576
 BP_F64, BP_F32 = 0, 1
 BP_SCATTER_AUTO, BP_SCATTER_ATOMIC, BP_SCATTER_COLOR = 0, 1, 2
 BP_JAC_AUTO, BP_JAC_DUAL, BP_JAC_FACTORED = 0, 1, 2
+BP_GUESS_ZERO, BP_GUESS_SIA = 0, 1
+BP_KRYLOV_CG = 0
 
 
 class BPError(RuntimeError):
@@ -46,6 +48,29 @@ class bp_mesh_info_t(ctypes.Structure):
                 ("ncolors", ctypes.c_int32), ("device_bytes", ctypes.c_int64)]
 
 
+class bp_solve_opts(ctypes.Structure):
+    _fields_ = [("rtol", ctypes.c_double), ("max_newton", ctypes.c_int), ("max_krylov", ctypes.c_int),
+                ("eta_max", ctypes.c_double), ("precision", ctypes.c_int), ("krylov", ctypes.c_int),
+                ("line_search", ctypes.c_int), ("check_every", ctypes.c_int)]
+
+
+class bp_solve_report(ctypes.Structure):
+    _fields_ = [("newton_iters", ctypes.c_int), ("krylov_iters", ctypes.c_int), ("converged", ctypes.c_int),
+                ("pad", ctypes.c_int), ("fnorm_ref", ctypes.c_double), ("fnorm_initial", ctypes.c_double),
+                ("fnorm_final", ctypes.c_double), ("history", ctypes.c_double * 65),
+                ("krylov_per_newton", ctypes.c_int * 64), ("alpha", ctypes.c_double * 64),
+                ("t_total", ctypes.c_double), ("t_assemble", ctypes.c_double), ("t_precond", ctypes.c_double),
+                ("t_krylov", ctypes.c_double), ("t_linesearch", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        k = self.newton_iters
+        return {"newton_iters": k, "krylov_iters": self.krylov_iters, "converged": bool(self.converged),
+                "fnorm_ref": self.fnorm_ref, "fnorm_initial": self.fnorm_initial, "fnorm_final": self.fnorm_final,
+                "history": list(self.history[:k + 1]), "krylov_per_newton": list(self.krylov_per_newton[:k]),
+                "alpha": list(self.alpha[:k]), "t_total": self.t_total, "t_assemble": self.t_assemble,
+                "t_precond": self.t_precond, "t_krylov": self.t_krylov, "t_linesearch": self.t_linesearch}
+
+
 # (name, restype, argtypes) of every exported entry point
 _P = ctypes.c_void_p
 _I = ctypes.c_int
@@ -59,6 +84,14 @@ SIGNATURES = {
     "bp_assemble_residual": (_I, [_P, _P, _P, _P]),
     "bp_assemble_jacobian": (_I, [_P, _P, _P, _P, _I, _I, _I, _P]),
     "bp_assemble_jacobian_noalloc": (_I, [_P, _P, _P, _I, _I, _I, _P]),
+    "bp_spmv": (_I, [_P, _P, _I, _P, _P, _P]),
+    "bp_colprec_setup": (_I, [_P, _P, _I, _P]),
+    "bp_colprec_apply": (_I, [_P, _P, _P, _P]),
+    "bp_energy": (_I, [_P, _P, _P, _P]),
+    "bp_energy_change": (_I, [_P, _P, _P, ctypes.c_double, _P, _P]),
+    "bp_initial_guess": (_I, [_P, _I, _P, _P]),
+    "bp_solve_opts_default": (None, [_P]),
+    "bp_newton_solve": (_I, [_P, _P, _P, _P, _P]),
 }
 
 _lock = threading.Lock()
@@ -163,6 +196,54 @@ def bp_assemble_jacobian_noalloc(handle, U, J, precision=BP_F64, scatter=BP_SCAT
     _check(lib().bp_assemble_jacobian_noalloc(handle, _dptr(U), _dptr(J), precision, scatter, method,
                                               _stream_ptr(stream)),
            "bp_assemble_jacobian_noalloc")
+
+
+def bp_spmv(handle, J, x, y, precision=BP_F64, stream=None) -> None:
+    _check(lib().bp_spmv(handle, _dptr(J), precision, _dptr(x), _dptr(y), _stream_ptr(stream)), "bp_spmv")
+
+
+def bp_colprec_setup(handle, J, precision=BP_F64, stream=None) -> None:
+    _check(lib().bp_colprec_setup(handle, _dptr(J), precision, _stream_ptr(stream)), "bp_colprec_setup")
+
+
+def bp_colprec_apply(handle, r, z, stream=None) -> None:
+    _check(lib().bp_colprec_apply(handle, _dptr(r), _dptr(z), _stream_ptr(stream)), "bp_colprec_apply")
+
+
+def bp_energy(handle, U, stream=None) -> float:
+    out = ctypes.c_double()
+    _check(lib().bp_energy(handle, _dptr(U), ctypes.byref(out), _stream_ptr(stream)), "bp_energy")
+    return out.value
+
+
+def bp_energy_change(handle, U, D, alpha, stream=None) -> float:
+    out = ctypes.c_double()
+    _check(lib().bp_energy_change(handle, _dptr(U), _dptr(D), alpha, ctypes.byref(out), _stream_ptr(stream)),
+           "bp_energy_change")
+    return out.value
+
+
+def bp_initial_guess(handle, kind, U, stream=None) -> None:
+    _check(lib().bp_initial_guess(handle, kind, _dptr(U), _stream_ptr(stream)), "bp_initial_guess")
+
+
+def bp_solve_opts_default() -> bp_solve_opts:
+    o = bp_solve_opts()
+    lib().bp_solve_opts_default(ctypes.byref(o))
+    return o
+
+
+def bp_newton_solve(handle, U, opts=None, stream=None, **kw):
+    """Runs the Newton solve in place on U; returns (status, report dict).  BP_ENOCONV is returned,
+    not raised, so the caller can read the report."""
+    o = opts if opts is not None else bp_solve_opts_default()
+    for k, v in kw.items():
+        setattr(o, k, v)
+    rep = bp_solve_report()
+    rc = lib().bp_newton_solve(handle, _dptr(U), ctypes.byref(o), ctypes.byref(rep), _stream_ptr(stream))
+    if rc not in (BP_OK, BP_ENOCONV):
+        raise BPError(rc, "bp_newton_solve")
+    return rc, rep.as_dict()
 
 
 class DeviceMesh:

@@ -25,6 +25,26 @@ void bp_set_last_cuda_error(cudaError_t err, const char* what, int line);
 #define BP_QP_P 0.78867513459481288225457439025098  // (1 + 1/sqrt(3)) / 2
 #define BP_QP_Q 0.21132486540518711774542560974902  // (1 - 1/sqrt(3)) / 2
 
+// Newton-Krylov workspace, allocated on the first solver call and owned by the mesh.
+struct bp_solver_ws {
+  int32_t* dslot = nullptr;   // [nv] rank of the vertex in its own closed neighbourhood
+  double* Lm = nullptr;       // [L][4][nv]   E_l G_{l-1}^-1 (block Thomas multipliers), l = 1..L
+  double* Ginv = nullptr;     // [L+1][4][nv] inverses of the eliminated diagonal blocks
+  double* Fu = nullptr;       // [L][4][nv]   super-diagonal blocks J(l, l+1)
+  double *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr;  // Krylov vectors
+  double* J = nullptr;        // [nnz] Jacobian values (double, or float in the first half)
+  double* R = nullptr;        // [ndof] residual
+  double* Ut = nullptr;       // [ndof] trial iterate of the line search
+  double* scal = nullptr;     // [3 (cap + 2)] per Krylov iteration: p.q, r.z, r.r
+  int scal_cap = 0;
+  int* stop = nullptr;        // Krylov stop flag (1 converged, 2 breakdown)
+  double* red = nullptr;      // [8] reduction scalars
+  double* sia = nullptr;      // [3 nv] shallow-ice scratch
+  double* host = nullptr;     // pinned host mirror of scal / red
+  int host_cap = 0;
+  bool has_prec = false;
+};
+
 struct bp_mesh {
   int device = 0;
   int32_t nv = 0, ntri = 0, nl = 0;
@@ -58,7 +78,10 @@ struct bp_mesh {
 
   int64_t device_bytes = 0;
   std::vector<void*> allocations;
+  bp_solver_ws* ws = nullptr;
 };
+
+void bp_solver_ws_free(bp_mesh* m);
 
 // Allocation helper that records the pointer in the mesh (freed by bp_mesh_free).
 template <class T>

@@ -176,6 +176,7 @@ extern "C" void bp_mesh_free(bp_mesh* m) {
   if (!m) return;
   bp_device_guard g(m->device);
   cudaDeviceSynchronize();
+  bp_solver_ws_free(m);
   for (void* p : m->allocations) cudaFree(p);
   delete m;
 }

@@ -1,0 +1,917 @@
+// Newton-Krylov solve of the discrete first-order Stokes system (paper Sec. 3.1, Eq. linearsystem):
+// CSR SpMV ("Op*x"), a vertical-line block-tridiagonal preconditioner (the per-line batched LU of
+// Sec. 4.4, here used directly as the preconditioner), preconditioned CG with device-resident
+// scalars (the Jacobian is symmetric positive definite: it is the Hessian of a convex energy),
+// the discrete energy for the damped-Newton line search, and a shallow-ice initial guess.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "bp_internal.cuh"
+
+namespace {
+
+constexpr int MAXL = 64;       // largest layer count the column kernels handle
+constexpr int TPR = 8;         // SpMV threads per row (rows hold 2 nlev deg ~ 40 entries)
+constexpr int NT = 256;        // threads per block of the vector kernels
+constexpr int SCAL_CAP = 8192; // Krylov iterations per linear solve (scalar history capacity)
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-wide sum of v, atomically added to *out.  Every thread of the block must call it.
+__device__ __forceinline__ void block_add(double v, double* out) {
+  __shared__ double sh[NT / 32];
+  v = warp_sum(v);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double w = threadIdx.x < (blockDim.x >> 5) ? sh[threadIdx.x] : 0.0;
+    w = warp_sum(w);
+    if (threadIdx.x == 0) atomicAdd(out, w);
+  }
+  __syncthreads();
+}
+
+// ------------------------------------------------------------------ vectors
+template <class A, class B>
+__global__ void __launch_bounds__(NT) k_dot(const A* __restrict__ a, const B* __restrict__ b, int64_t n,
+                                            double* out) {
+  double s = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    s += (double)a[i] * (double)b[i];
+  block_add(s, out);
+}
+
+template <class V>
+__global__ void __launch_bounds__(NT) k_axpy_to(const double* __restrict__ U, const V* __restrict__ d, double alpha,
+                                                int64_t n, double* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = U[i] + alpha * (double)d[i];
+}
+
+__global__ void k_find_dslot(const int32_t* __restrict__ nbr_ptr, const int32_t* __restrict__ nbr_idx, int nv,
+                             int32_t* __restrict__ dslot) {
+  const int a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= nv) return;
+  int s = 0;
+  for (int k = nbr_ptr[a]; k < nbr_ptr[a + 1]; ++k)
+    if (nbr_idx[k] == a) s = k - nbr_ptr[a];
+  dslot[a] = s;
+}
+
+// ------------------------------------------------------------------ SpMV
+// y = A x (row-parallel CSR, TPR threads per row); optionally adds x . y to *dot.
+template <class M, class V, bool DOT>
+__global__ void __launch_bounds__(NT) k_spmv(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
+                                             const M* __restrict__ vals, int64_t n, const V* __restrict__ x,
+                                             V* __restrict__ y, double* dot, const int* stop) {
+  if (stop && *stop) return;
+  const int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / TPR;
+  const int lane = threadIdx.x % TPR;
+  V sum = V(0);
+  if (row < n) {
+    const int64_t e1 = rowptr[row + 1];
+    for (int64_t e = rowptr[row] + lane; e < e1; e += TPR) sum += (V)vals[e] * x[colidx[e]];
+  }
+#pragma unroll
+  for (int o = TPR / 2; o; o >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, o, TPR);
+  double d = 0.0;
+  if (row < n && lane == 0) {
+    y[row] = sum;
+    if (DOT) d = (double)x[row] * (double)sum;
+  }
+  if (DOT) block_add(d, dot);
+}
+
+// ------------------------------------------------------------------ column preconditioner
+__device__ __forceinline__ int64_t col_entry(int64_t vs, int dg, int ds, int l, int c, int lp, int cp, int L) {
+  const int nl = bp_nlev(l, L);
+  const int lmin = l > 0 ? l - 1 : 0;
+  return vs + (int64_t)dg * (4 * bp_levels_before(l) + 2 * c * nl) + 2 * (ds * nl + lp - lmin) + cp;
+}
+
+// Block Thomas elimination of the column's block-tridiagonal part of J (2 x 2 blocks, FP64):
+//   G_0 = D_0,  Lm_l = E_l G_{l-1}^-1,  G_l = D_l - Lm_l F_{l-1},  store Lm_l, G_l^-1, F_l.
+template <class M>
+__global__ void __launch_bounds__(128) k_colprec_setup(const M* __restrict__ J, const int64_t* __restrict__ vstart,
+                                                       const int32_t* __restrict__ vdeg,
+                                                       const int32_t* __restrict__ dslot, int nv, int L,
+                                                       double* __restrict__ Lm, double* __restrict__ Ginv,
+                                                       double* __restrict__ Fu) {
+  const int a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= nv) return;
+  const int64_t vs = vstart[a];
+  const int dg = vdeg[a], ds = dslot[a];
+  auto at = [&](int l, int c, int lp, int cp) -> double {
+    return (double)J[col_entry(vs, dg, ds, l, c, lp, cp, L)];
+  };
+  double Gp[4] = {0, 0, 0, 0}, Fp[4] = {0, 0, 0, 0};
+  for (int l = 0; l <= L; ++l) {
+    double G[4] = {at(l, 0, l, 0), at(l, 0, l, 1), at(l, 1, l, 0), at(l, 1, l, 1)};
+    if (l > 0) {
+      const double E[4] = {at(l, 0, l - 1, 0), at(l, 0, l - 1, 1), at(l, 1, l - 1, 0), at(l, 1, l - 1, 1)};
+      const double Lmat[4] = {E[0] * Gp[0] + E[1] * Gp[2], E[0] * Gp[1] + E[1] * Gp[3],
+                              E[2] * Gp[0] + E[3] * Gp[2], E[2] * Gp[1] + E[3] * Gp[3]};
+      G[0] -= Lmat[0] * Fp[0] + Lmat[1] * Fp[2];
+      G[1] -= Lmat[0] * Fp[1] + Lmat[1] * Fp[3];
+      G[2] -= Lmat[2] * Fp[0] + Lmat[3] * Fp[2];
+      G[3] -= Lmat[2] * Fp[1] + Lmat[3] * Fp[3];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) Lm[((int64_t)(l - 1) * 4 + e) * nv + a] = Lmat[e];
+    }
+    const double idet = 1.0 / (G[0] * G[3] - G[1] * G[2]);
+    Gp[0] = G[3] * idet;
+    Gp[1] = -G[1] * idet;
+    Gp[2] = -G[2] * idet;
+    Gp[3] = G[0] * idet;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) Ginv[((int64_t)l * 4 + e) * nv + a] = Gp[e];
+    if (l < L) {
+      Fp[0] = at(l, 0, l + 1, 0);
+      Fp[1] = at(l, 0, l + 1, 1);
+      Fp[2] = at(l, 1, l + 1, 0);
+      Fp[3] = at(l, 1, l + 1, 1);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) Fu[((int64_t)l * 4 + e) * nv + a] = Fp[e];
+    }
+  }
+}
+
+struct Prec {
+  const double* Lm;
+  const double* Ginv;
+  const double* Fu;
+  int nv, L;
+};
+
+// z = P^-1 r on column a (forward and backward block substitution); returns (r.z, r.r) of the column.
+template <class V>
+__device__ __forceinline__ void colprec_apply(const Prec& P, int a, const V* __restrict__ r, V* __restrict__ z,
+                                              double* rz, double* rr) {
+  const int L = P.L;
+  const int64_t base = 2LL * a * (L + 1);
+  double y[2 * (MAXL + 1)];
+  double srr = 0.0;
+  for (int l = 0; l <= L; ++l) {
+    double r0 = (double)r[base + 2 * l], r1 = (double)r[base + 2 * l + 1];
+    srr += r0 * r0 + r1 * r1;
+    if (l > 0) {
+      const double* Lp = P.Lm + (int64_t)(l - 1) * 4 * P.nv + a;
+      r0 -= Lp[0] * y[2 * l - 2] + Lp[P.nv] * y[2 * l - 1];
+      r1 -= Lp[2 * (int64_t)P.nv] * y[2 * l - 2] + Lp[3 * (int64_t)P.nv] * y[2 * l - 1];
+    }
+    y[2 * l] = r0;
+    y[2 * l + 1] = r1;
+  }
+  double srz = 0.0;
+  for (int l = L; l >= 0; --l) {
+    double t0 = y[2 * l], t1 = y[2 * l + 1];
+    if (l < L) {
+      const double* Fp = P.Fu + (int64_t)l * 4 * P.nv + a;
+      t0 -= Fp[0] * y[2 * l + 2] + Fp[P.nv] * y[2 * l + 3];
+      t1 -= Fp[2 * (int64_t)P.nv] * y[2 * l + 2] + Fp[3 * (int64_t)P.nv] * y[2 * l + 3];
+    }
+    const double* Gp = P.Ginv + (int64_t)l * 4 * P.nv + a;
+    const double z0 = Gp[0] * t0 + Gp[P.nv] * t1;
+    const double z1 = Gp[2 * (int64_t)P.nv] * t0 + Gp[3 * (int64_t)P.nv] * t1;
+    y[2 * l] = z0;
+    y[2 * l + 1] = z1;
+    z[base + 2 * l] = (V)z0;
+    z[base + 2 * l + 1] = (V)z1;
+    srz += (double)r[base + 2 * l] * z0 + (double)r[base + 2 * l + 1] * z1;
+  }
+  *rz = srz;
+  *rr = srr;
+}
+
+template <class V>
+__global__ void __launch_bounds__(128) k_colprec_apply(const Prec P, const V* __restrict__ r, V* __restrict__ z) {
+  const int a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= P.nv) return;
+  double rz, rr;
+  colprec_apply(P, a, r, z, &rz, &rr);
+}
+
+// ------------------------------------------------------------------ preconditioned CG (device scalars)
+// scal[3k] = p_k . A p_k, scal[3k+1] = r_k . z_k, scal[3k+2] = r_k . r_k.
+template <class V>
+__global__ void __launch_bounds__(NT) k_cg_init(const Prec P, const double* __restrict__ R, V* __restrict__ x,
+                                                V* __restrict__ r, V* __restrict__ z, V* __restrict__ p,
+                                                double* scal) {
+  const int a = blockIdx.x * blockDim.x + threadIdx.x;
+  double rz = 0.0, rr = 0.0;
+  if (a < P.nv) {
+    const int64_t base = 2LL * a * (P.L + 1);
+    for (int i = 0; i < 2 * (P.L + 1); ++i) {
+      r[base + i] = (V)(-R[base + i]);
+      x[base + i] = V(0);
+    }
+    colprec_apply(P, a, r, z, &rz, &rr);
+    for (int i = 0; i < 2 * (P.L + 1); ++i) p[base + i] = z[base + i];
+  }
+  block_add(rz, scal + 1);
+  block_add(rr, scal + 2);
+}
+
+// alpha = r.z / p.Ap;  x += alpha p;  r -= alpha q;  z = P^-1 r;  accumulate r.z, r.r of step k+1
+template <class V>
+__global__ void __launch_bounds__(NT) k_cg_update(const Prec P, int k, V* __restrict__ x, V* __restrict__ r,
+                                                  V* __restrict__ z, const V* __restrict__ p,
+                                                  const V* __restrict__ q, double* scal, int* stop) {
+  if (*stop) return;
+  const double pq = scal[3 * k], rzk = scal[3 * k + 1];
+  if (!(pq > 0.0) || !isfinite(rzk)) {  // not positive definite in this direction: stop (breakdown)
+    if (blockIdx.x == 0 && threadIdx.x == 0) *stop = 2;
+    return;
+  }
+  const V alpha = (V)(rzk / pq);
+  const int a = blockIdx.x * blockDim.x + threadIdx.x;
+  double rz = 0.0, rr = 0.0;
+  if (a < P.nv) {
+    const int64_t base = 2LL * a * (P.L + 1);
+    for (int i = 0; i < 2 * (P.L + 1); ++i) {
+      x[base + i] += alpha * p[base + i];
+      r[base + i] -= alpha * q[base + i];
+    }
+    colprec_apply(P, a, r, z, &rz, &rr);
+  }
+  block_add(rz, scal + 3 * (k + 1) + 1);
+  block_add(rr, scal + 3 * (k + 1) + 2);
+}
+
+// beta = r_{k+1}.z_{k+1} / r_k.z_k;  p = z + beta p;  stop once r.r <= tol2 r_0.r_0
+template <class V>
+__global__ void __launch_bounds__(NT) k_cg_direction(int k, double tol2, int64_t n, const V* __restrict__ z,
+                                                     V* __restrict__ p, const double* scal, int* stop) {
+  if (*stop) return;
+  const double rr = scal[3 * (k + 1) + 2];
+  if (rr <= tol2 * scal[2] || !isfinite(rr)) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) *stop = 1;
+    return;
+  }
+  const V beta = (V)(scal[3 * (k + 1) + 1] / scal[3 * k + 1]);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = z[i] + beta * p[i];
+}
+
+// ------------------------------------------------------------------ energy
+// Pi_h = sum_q c_q (3/2) A^(-1/3) (eps_e^2 + delta)^(2/3) + load . U + 1/2 sum_bed U_b^T M U_b   (n = 3)
+__global__ void __launch_bounds__(128) k_energy(const double2* __restrict__ xy, const double* __restrict__ bed,
+                                                const double* __restrict__ thick, const double* __restrict__ sigma,
+                                                const int32_t* __restrict__ tri, const double* __restrict__ basal,
+                                                const double* __restrict__ load, int ntri, int L, int64_t ndof,
+                                                double cA, double delta, const double* __restrict__ U,
+                                                double* out) {
+  double acc = 0.0;
+  // driving-stress part: load . U
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < ndof; i += (int64_t)gridDim.x * blockDim.x)
+    acc += load[i] * U[i];
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < ntri) {
+    int v[3];
+    double x[3], y[3], H[3], bb[3];
+    for (int a = 0; a < 3; ++a) {
+      v[a] = tri[3 * t + a];
+      const double2 p = xy[v[a]];
+      x[a] = p.x;
+      y[a] = p.y;
+      H[a] = thick[v[a]];
+      bb[a] = bed[v[a]];
+    }
+    const double d = (x[1] - x[0]) * (y[2] - y[0]) - (x[2] - x[0]) * (y[1] - y[0]);
+    const double inv_d = 1.0 / d;
+    double lx[3], ly[3];
+    for (int a = 0; a < 3; ++a) {
+      lx[a] = (y[(a + 1) % 3] - y[(a + 2) % 3]) * inv_d;
+      ly[a] = (x[(a + 2) % 3] - x[(a + 1) % 3]) * inv_d;
+    }
+    const double gbx = bb[0] * lx[0] + bb[1] * lx[1] + bb[2] * lx[2];
+    const double gby = bb[0] * ly[0] + bb[1] * ly[1] + bb[2] * ly[2];
+    const double gHx = H[0] * lx[0] + H[1] * lx[1] + H[2] * lx[2];
+    const double gHy = H[0] * ly[0] + H[1] * ly[1] + H[2] * ly[2];
+    const double Hs6 = (H[0] + H[1] + H[2]) * (1.0 / 6.0);
+    double Hq[3];
+    for (int tp = 0; tp < 3; ++tp) Hq[tp] = Hs6 + 0.5 * H[tp];
+    int64_t ub[3];
+    for (int a = 0; a < 3; ++a) ub[a] = 2LL * v[a] * (L + 1);
+    // basal friction energy
+    {
+      const double* Mb = basal + 6 * (int64_t)t;
+      const double M[3][3] = {{Mb[0], Mb[1], Mb[2]}, {Mb[1], Mb[3], Mb[4]}, {Mb[2], Mb[4], Mb[5]}};
+      double uu[3], vv[3];
+      for (int a = 0; a < 3; ++a) {
+        uu[a] = U[ub[a]];
+        vv[a] = U[ub[a] + 1];
+      }
+      for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) acc += 0.5 * M[a][b] * (uu[a] * uu[b] + vv[a] * vv[b]);
+    }
+    for (int l = 0; l < L; ++l) {
+      double u0[3], v0[3], u1[3], v1[3];
+      for (int a = 0; a < 3; ++a) {
+        u0[a] = U[ub[a] + 2 * l];
+        v0[a] = U[ub[a] + 2 * l + 1];
+        u1[a] = U[ub[a] + 2 * l + 2];
+        v1[a] = U[ub[a] + 2 * l + 3];
+      }
+      const double s_l = sigma[l], ds = sigma[l + 1] - sigma[l];
+      for (int z = 0; z < 2; ++z) {
+        const double p0 = z == 0 ? BP_QP_P : BP_QP_Q, p1 = z == 0 ? BP_QP_Q : BP_QP_P;
+        const double sz = s_l + p1 * ds;
+        const double Gzx = gbx + sz * gHx, Gzy = gby + sz * gHy;
+        double GUx = 0, GUy = 0, GVx = 0, GVy = 0;
+        for (int a = 0; a < 3; ++a) {
+          const double ua = p0 * u0[a] + p1 * u1[a], va = p0 * v0[a] + p1 * v1[a];
+          GUx += ua * lx[a];
+          GUy += ua * ly[a];
+          GVx += va * lx[a];
+          GVy += va * ly[a];
+        }
+        for (int tp = 0; tp < 3; ++tp) {
+          const double h = ds * Hq[tp];
+          double du = 0, dv = 0;
+          for (int a = 0; a < 3; ++a) {
+            const double la = (a == tp) ? 2.0 / 3.0 : 1.0 / 6.0;
+            du += la * (u1[a] - u0[a]);
+            dv += la * (v1[a] - v0[a]);
+          }
+          const double uz = du / h, vz = dv / h;
+          const double ux = GUx - uz * Gzx, uy = GUy - uz * Gzy, vx = GVx - vz * Gzx, vy = GVy - vz * Gzy;
+          const double exy = 0.5 * (uy + vx);
+          const double e2 = ux * ux + vy * vy + ux * vy + exy * exy + 0.25 * (uz * uz + vz * vz);
+          const double xx = e2 + delta;
+          acc += (d * h / 12.0) * 1.5 * cA * xx * rcbrt(xx);
+        }
+      }
+    }
+  }
+  block_add(acc, out);
+}
+
+// Energy change Pi_h(U + alpha d) - Pi_h(U), formed term by term as differences so that it keeps
+// its relative accuracy when it is many orders smaller than Pi_h itself (near convergence):
+//   driving:  alpha load . d;   basal: alpha d^T M u + alpha^2/2 d^T M d;
+//   stress:   x = eps_e^2 + delta is quadratic in the velocity gradient G, so
+//             x1 - x0 = alpha (2 B(G0, Gd)) + alpha^2 Q(Gd) exactly, and
+//             x1^(2/3) - x0^(2/3) = (a - b)(a + b), a - b = (x1 - x0) / (a^2 + a b + b^2), a, b = cube roots.
+__device__ __forceinline__ void qp_gradient(const double* u0, const double* v0, const double* u1, const double* v1,
+                                            const double* lx, const double* ly, double p0, double p1, int tp,
+                                            double h, double Gzx, double Gzy, double G[6]) {
+  double GUx = 0, GUy = 0, GVx = 0, GVy = 0, du = 0, dv = 0;
+  for (int a = 0; a < 3; ++a) {
+    const double ua = p0 * u0[a] + p1 * u1[a], va = p0 * v0[a] + p1 * v1[a];
+    GUx += ua * lx[a];
+    GUy += ua * ly[a];
+    GVx += va * lx[a];
+    GVy += va * ly[a];
+    const double la = (a == tp) ? 2.0 / 3.0 : 1.0 / 6.0;
+    du += la * (u1[a] - u0[a]);
+    dv += la * (v1[a] - v0[a]);
+  }
+  const double uz = du / h, vz = dv / h;
+  G[0] = GUx - uz * Gzx;  // u_x
+  G[1] = GUy - uz * Gzy;  // u_y
+  G[2] = uz;
+  G[3] = GVx - vz * Gzx;  // v_x
+  G[4] = GVy - vz * Gzy;  // v_y
+  G[5] = vz;
+}
+
+// symmetric bilinear form of eps_e^2: Q(G) = B(G, G)
+__device__ __forceinline__ double eps_bilinear(const double* A, const double* B) {
+  const double exyA = 0.5 * (A[1] + A[3]), exyB = 0.5 * (B[1] + B[3]);
+  return A[0] * B[0] + A[4] * B[4] + 0.5 * (A[0] * B[4] + B[0] * A[4]) + exyA * exyB +
+         0.25 * (A[2] * B[2] + A[5] * B[5]);
+}
+
+__global__ void __launch_bounds__(128) k_energy_change(const double2* __restrict__ xy, const double* __restrict__ bed,
+                                                       const double* __restrict__ thick,
+                                                       const double* __restrict__ sigma,
+                                                       const int32_t* __restrict__ tri,
+                                                       const double* __restrict__ basal,
+                                                       const double* __restrict__ load, int ntri, int L,
+                                                       int64_t ndof, double cA, double delta, double alpha,
+                                                       const double* __restrict__ U, const double* __restrict__ D,
+                                                       double* out) {
+  double acc = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < ndof; i += (int64_t)gridDim.x * blockDim.x)
+    acc += alpha * load[i] * D[i];
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < ntri) {
+    int v[3];
+    double x[3], y[3], H[3], bb[3];
+    for (int a = 0; a < 3; ++a) {
+      v[a] = tri[3 * t + a];
+      const double2 p = xy[v[a]];
+      x[a] = p.x;
+      y[a] = p.y;
+      H[a] = thick[v[a]];
+      bb[a] = bed[v[a]];
+    }
+    const double d = (x[1] - x[0]) * (y[2] - y[0]) - (x[2] - x[0]) * (y[1] - y[0]);
+    const double inv_d = 1.0 / d;
+    double lx[3], ly[3];
+    for (int a = 0; a < 3; ++a) {
+      lx[a] = (y[(a + 1) % 3] - y[(a + 2) % 3]) * inv_d;
+      ly[a] = (x[(a + 2) % 3] - x[(a + 1) % 3]) * inv_d;
+    }
+    const double gbx = bb[0] * lx[0] + bb[1] * lx[1] + bb[2] * lx[2];
+    const double gby = bb[0] * ly[0] + bb[1] * ly[1] + bb[2] * ly[2];
+    const double gHx = H[0] * lx[0] + H[1] * lx[1] + H[2] * lx[2];
+    const double gHy = H[0] * ly[0] + H[1] * ly[1] + H[2] * ly[2];
+    const double Hs6 = (H[0] + H[1] + H[2]) * (1.0 / 6.0);
+    int64_t ub[3];
+    for (int a = 0; a < 3; ++a) ub[a] = 2LL * v[a] * (L + 1);
+    {
+      const double* Mb = basal + 6 * (int64_t)t;
+      const double M[3][3] = {{Mb[0], Mb[1], Mb[2]}, {Mb[1], Mb[3], Mb[4]}, {Mb[2], Mb[4], Mb[5]}};
+      for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+          const double du = D[ub[a]], dv = D[ub[a] + 1];
+          acc += M[a][b] * (alpha * (du * U[ub[b]] + dv * U[ub[b] + 1]) +
+                            0.5 * alpha * alpha * (du * D[ub[b]] + dv * D[ub[b] + 1]));
+        }
+    }
+    for (int l = 0; l < L; ++l) {
+      double u0[3], v0[3], u1[3], v1[3], a0[3], b0[3], a1[3], b1[3];
+      for (int a = 0; a < 3; ++a) {
+        u0[a] = U[ub[a] + 2 * l];
+        v0[a] = U[ub[a] + 2 * l + 1];
+        u1[a] = U[ub[a] + 2 * l + 2];
+        v1[a] = U[ub[a] + 2 * l + 3];
+        a0[a] = D[ub[a] + 2 * l];
+        b0[a] = D[ub[a] + 2 * l + 1];
+        a1[a] = D[ub[a] + 2 * l + 2];
+        b1[a] = D[ub[a] + 2 * l + 3];
+      }
+      const double s_l = sigma[l], ds = sigma[l + 1] - sigma[l];
+      for (int z = 0; z < 2; ++z) {
+        const double p0 = z == 0 ? BP_QP_P : BP_QP_Q, p1 = z == 0 ? BP_QP_Q : BP_QP_P;
+        const double sz = s_l + p1 * ds;
+        const double Gzx = gbx + sz * gHx, Gzy = gby + sz * gHy;
+        for (int tp = 0; tp < 3; ++tp) {
+          const double h = ds * (Hs6 + 0.5 * H[tp]);
+          double G0[6], Gd[6];
+          qp_gradient(u0, v0, u1, v1, lx, ly, p0, p1, tp, h, Gzx, Gzy, G0);
+          qp_gradient(a0, b0, a1, b1, lx, ly, p0, p1, tp, h, Gzx, Gzy, Gd);
+          const double x0 = eps_bilinear(G0, G0) + delta;
+          const double dx = alpha * (2.0 * eps_bilinear(G0, Gd) + alpha * eps_bilinear(Gd, Gd));
+          const double x1 = x0 + dx;
+          const double ca = cbrt(x1), cb = cbrt(x0);
+          const double diff23 = dx / (ca * ca + ca * cb + cb * cb) * (ca + cb);
+          acc += (d * h / 12.0) * 1.5 * cA * diff23;
+        }
+      }
+    }
+  }
+  block_add(acc, out);
+}
+
+// ------------------------------------------------------------------ shallow-ice guess
+__global__ void k_sia_accum(const double2* __restrict__ xy, const double* __restrict__ bed,
+                            const double* __restrict__ thick, const int32_t* __restrict__ tri, int ntri,
+                            double* __restrict__ acc /* [3][nv] */, int nv) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= ntri) return;
+  int v[3];
+  double x[3], y[3], s[3];
+  for (int a = 0; a < 3; ++a) {
+    v[a] = tri[3 * t + a];
+    x[a] = xy[v[a]].x;
+    y[a] = xy[v[a]].y;
+    s[a] = bed[v[a]] + thick[v[a]];
+  }
+  const double d = (x[1] - x[0]) * (y[2] - y[0]) - (x[2] - x[0]) * (y[1] - y[0]);
+  double sx = 0, sy = 0;
+  for (int a = 0; a < 3; ++a) {
+    sx += s[a] * (y[(a + 1) % 3] - y[(a + 2) % 3]) / d;
+    sy += s[a] * (x[(a + 2) % 3] - x[(a + 1) % 3]) / d;
+  }
+  const double area = 0.5 * d;
+  for (int a = 0; a < 3; ++a) {
+    atomicAdd(acc + v[a], area * sx);
+    atomicAdd(acc + nv + v[a], area * sy);
+    atomicAdd(acc + 2 * nv + v[a], area);
+  }
+}
+
+__global__ void k_sia_fill(const double* __restrict__ acc, const double* __restrict__ bed,
+                           const double* __restrict__ thick, const double* __restrict__ beta,
+                           const double* __restrict__ sigma, int nv, int L, double A, double rho_g,
+                           double* __restrict__ U) {
+  const int a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= nv) return;
+  const double w = acc[2 * nv + a];
+  const double sx = acc[a] / w, sy = acc[nv + a] / w;
+  const double g2 = sx * sx + sy * sy;
+  const double H = thick[a];
+  const double H4 = (H * H) * (H * H);
+  const double slide = beta[a] > 0.0 ? rho_g * H / beta[a] : 0.0;
+  const double c = 0.5 * A * rho_g * rho_g * rho_g * g2;  // 2A/(n+1) (rho g)^n |grad s|^(n-1), n = 3
+  for (int l = 0; l <= L; ++l) {
+    const double dep = (1.0 - sigma[l]) * H;
+    const double d4 = (dep * dep) * (dep * dep);
+    const double f = c * (H4 - d4) + slide;
+    U[2 * ((int64_t)a * (L + 1) + l)] = -f * sx;
+    U[2 * ((int64_t)a * (L + 1) + l) + 1] = -f * sy;
+  }
+}
+
+// ------------------------------------------------------------------ host helpers
+int grid_for(int64_t n, int threads) {
+  int64_t g = (n + threads - 1) / threads;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(g, 148LL * 32));
+}
+
+int ensure_ws(bp_mesh* m, cudaStream_t s) {
+  if (m->ws) return BP_OK;
+  if (m->nl > MAXL) return BP_EUNSUP;
+  bp_solver_ws tmp;
+  bp_solver_ws* w = &tmp;
+  int rc;
+  const int64_t n = m->ndof, nv = m->nv, L = m->nl;
+  // on failure the arrays already allocated stay recorded in the mesh and are freed with it
+#define WS_ALLOC(ptr, cnt) \
+  if ((rc = bp_alloc(m, &(ptr), (cnt))) != BP_OK) return rc
+  WS_ALLOC(w->dslot, nv);
+  WS_ALLOC(w->Lm, 4 * L * nv);
+  WS_ALLOC(w->Ginv, 4 * (L + 1) * nv);
+  WS_ALLOC(w->Fu, 4 * L * nv);
+  WS_ALLOC(w->x, n);
+  WS_ALLOC(w->r, n);
+  WS_ALLOC(w->z, n);
+  WS_ALLOC(w->p, n);
+  WS_ALLOC(w->q, n);
+  WS_ALLOC(w->R, n);
+  WS_ALLOC(w->Ut, n);
+  WS_ALLOC(w->scal, 3 * (SCAL_CAP + 2));
+  WS_ALLOC(w->stop, 1);
+  WS_ALLOC(w->red, 8);
+  WS_ALLOC(w->sia, 3 * nv);
+#undef WS_ALLOC
+  w->scal_cap = SCAL_CAP;
+  w->host_cap = 3 * (SCAL_CAP + 2) + 8;
+  if (cudaMallocHost(&w->host, w->host_cap * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    return BP_ENOMEM;
+  }
+  k_find_dslot<<<(m->nv + 127) / 128, 128, 0, s>>>(m->nbr_ptr, m->nbr_idx, m->nv, w->dslot);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    cudaFreeHost(w->host);
+    bp_set_last_cuda_error(e, "k_find_dslot", __LINE__);
+    return BP_ECUDA;
+  }
+  m->ws = new bp_solver_ws(tmp);
+  return BP_OK;
+}
+
+int ensure_jac(bp_mesh* m) {
+  if (m->ws->J) return BP_OK;
+  return bp_alloc(m, &m->ws->J, m->nnz);
+}
+
+Prec prec_of(const bp_mesh* m) { return Prec{m->ws->Lm, m->ws->Ginv, m->ws->Fu, m->nv, m->nl}; }
+
+// synchronous dot product a . b (FP64 result on the host)
+template <class A, class B>
+int dot_host(bp_mesh* m, const A* a, const B* b, int64_t n, cudaStream_t s, double* out) {
+  bp_solver_ws* w = m->ws;
+  BP_CUDA_TRY(cudaMemsetAsync(w->red, 0, sizeof(double), s));
+  k_dot<<<grid_for(n, NT), NT, 0, s>>>(a, b, n, w->red);
+  BP_CUDA_TRY(cudaGetLastError());
+  BP_CUDA_TRY(cudaMemcpyAsync(w->host, w->red, sizeof(double), cudaMemcpyDeviceToHost, s));
+  BP_CUDA_TRY(cudaStreamSynchronize(s));
+  *out = w->host[0];
+  return BP_OK;
+}
+
+int energy_host(bp_mesh* m, const double* U, cudaStream_t s, double* out) {
+  bp_solver_ws* w = m->ws;
+  BP_CUDA_TRY(cudaMemsetAsync(w->red + 1, 0, sizeof(double), s));
+  const int grid = (int)std::max<int64_t>((m->ntri + 127) / 128, std::min<int64_t>((m->ndof + 127) / 128, 148 * 16));
+  k_energy<<<grid, 128, 0, s>>>(m->xy, m->bed, m->thick, m->sigma, m->tri, m->basal, m->load, m->ntri, m->nl,
+                                m->ndof, m->cA, m->p.delta, U, w->red + 1);
+  BP_CUDA_TRY(cudaGetLastError());
+  BP_CUDA_TRY(cudaMemcpyAsync(w->host, w->red + 1, sizeof(double), cudaMemcpyDeviceToHost, s));
+  BP_CUDA_TRY(cudaStreamSynchronize(s));
+  *out = w->host[0];
+  return BP_OK;
+}
+
+// synchronous energy change Pi(U + alpha D) - Pi(U)
+int energy_change_host(bp_mesh* m, const double* U, const double* D, double alpha, cudaStream_t s, double* out) {
+  bp_solver_ws* w = m->ws;
+  BP_CUDA_TRY(cudaMemsetAsync(w->red + 2, 0, sizeof(double), s));
+  const int grid = (int)std::max<int64_t>((m->ntri + 127) / 128, std::min<int64_t>((m->ndof + 127) / 128, 148 * 16));
+  k_energy_change<<<grid, 128, 0, s>>>(m->xy, m->bed, m->thick, m->sigma, m->tri, m->basal, m->load, m->ntri, m->nl,
+                                       m->ndof, m->cA, m->p.delta, alpha, U, D, w->red + 2);
+  BP_CUDA_TRY(cudaGetLastError());
+  BP_CUDA_TRY(cudaMemcpyAsync(w->host, w->red + 2, sizeof(double), cudaMemcpyDeviceToHost, s));
+  BP_CUDA_TRY(cudaStreamSynchronize(s));
+  *out = w->host[0];
+  return BP_OK;
+}
+
+template <class M>
+int colprec_setup_t(bp_mesh* m, const M* J, cudaStream_t s) {
+  bp_solver_ws* w = m->ws;
+  k_colprec_setup<M><<<(m->nv + 127) / 128, 128, 0, s>>>(J, m->vstart, m->vdeg, w->dslot, m->nv, m->nl, w->Lm,
+                                                         w->Ginv, w->Fu);
+  BP_CUDA_TRY(cudaGetLastError());
+  w->has_prec = true;
+  return BP_OK;
+}
+
+// Preconditioned CG on J delta = -R to ||r|| <= eta ||R||.  delta is left in ws->x (type V).
+template <class M, class V>
+int cg_solve(bp_mesh* m, const M* J, double eta, int maxit, int check_every, cudaStream_t s, int* iters,
+             int* status) {
+  bp_solver_ws* w = m->ws;
+  const Prec P = prec_of(m);
+  const int64_t n = m->ndof;
+  maxit = std::min(maxit, w->scal_cap);
+  V* x = reinterpret_cast<V*>(w->x);
+  V* r = reinterpret_cast<V*>(w->r);
+  V* z = reinterpret_cast<V*>(w->z);
+  V* p = reinterpret_cast<V*>(w->p);
+  V* q = reinterpret_cast<V*>(w->q);
+  BP_CUDA_TRY(cudaMemsetAsync(w->scal, 0, 3 * (size_t)(maxit + 2) * sizeof(double), s));
+  BP_CUDA_TRY(cudaMemsetAsync(w->stop, 0, sizeof(int), s));
+  const int gcol = (m->nv + NT - 1) / NT;
+  k_cg_init<V><<<gcol, NT, 0, s>>>(P, w->R, x, r, z, p, w->scal);
+  const double tol2 = eta * eta;
+  const int gspmv = (int)((n * TPR + NT - 1) / NT);
+  int k = 0, done = 0;
+  *status = 0;
+  while (!done) {
+    const int kend = std::min(maxit, k + check_every);
+    for (; k < kend; ++k) {
+      k_spmv<M, V, true><<<gspmv, NT, 0, s>>>(m->rowptr, m->colidx, J, n, p, q, w->scal + 3 * k, w->stop);
+      k_cg_update<V><<<gcol, NT, 0, s>>>(P, k, x, r, z, p, q, w->scal, w->stop);
+      k_cg_direction<V><<<grid_for(n, NT), NT, 0, s>>>(k, tol2, n, z, p, w->scal, w->stop);
+    }
+    BP_CUDA_TRY(cudaGetLastError());
+    BP_CUDA_TRY(cudaMemcpyAsync(w->host, w->scal, 3 * (size_t)(k + 1) * sizeof(double), cudaMemcpyDeviceToHost, s));
+    BP_CUDA_TRY(cudaMemcpyAsync(w->host + w->host_cap - 1, w->stop, sizeof(int), cudaMemcpyDeviceToHost, s));
+    BP_CUDA_TRY(cudaStreamSynchronize(s));
+    int stopflag;
+    std::memcpy(&stopflag, w->host + w->host_cap - 1, sizeof(int));
+    if (stopflag || k >= maxit) done = 1;
+    if (stopflag == 2) *status = 2;
+  }
+  // iterations actually taken: first j with r_j.r_j <= tol2 r_0.r_0
+  const double rr0 = w->host[2];
+  int taken = k;
+  for (int j = 1; j <= k; ++j) {
+    const double rr = w->host[3 * j + 2];
+    if (rr <= tol2 * rr0 || !std::isfinite(rr)) {
+      taken = j;
+      break;
+    }
+    if (w->host[3 * j + 2] == 0.0 && w->host[3 * j + 1] == 0.0) {  // never reached (breakdown stop)
+      taken = j - 1;
+      break;
+    }
+  }
+  *iters = taken;
+  if (!std::isfinite(rr0)) *status = 3;
+  return BP_OK;
+}
+
+double elapsed(cudaEvent_t a, cudaEvent_t b) {
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, a, b);
+  return 1e-3 * ms;
+}
+
+}  // namespace
+
+void bp_solver_ws_free(bp_mesh* m) {
+  if (!m->ws) return;
+  if (m->ws->host) cudaFreeHost(m->ws->host);
+  delete m->ws;  // device arrays are in m->allocations
+  m->ws = nullptr;
+}
+
+extern "C" int bp_spmv(bp_mesh* m, const void* J, int precision, const double* x, double* y, void* stream) {
+  if (!m || !J || !x || !y) return BP_EINVAL;
+  if (precision != BP_F64 && precision != BP_F32) return BP_EINVAL;
+  bp_device_guard g(m->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  const int grid = (int)((m->ndof * TPR + NT - 1) / NT);
+  if (precision == BP_F64)
+    k_spmv<double, double, false><<<grid, NT, 0, s>>>(m->rowptr, m->colidx, (const double*)J, m->ndof, x, y,
+                                                      nullptr, nullptr);
+  else
+    k_spmv<float, double, false><<<grid, NT, 0, s>>>(m->rowptr, m->colidx, (const float*)J, m->ndof, x, y,
+                                                     nullptr, nullptr);
+  BP_CUDA_TRY(cudaGetLastError());
+  return BP_OK;
+}
+
+extern "C" int bp_colprec_setup(bp_mesh* m, const void* J, int precision, void* stream) {
+  if (!m || !J) return BP_EINVAL;
+  if (precision != BP_F64 && precision != BP_F32) return BP_EINVAL;
+  bp_device_guard g(m->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc = ensure_ws(m, s);
+  if (rc) return rc;
+  return precision == BP_F64 ? colprec_setup_t(m, (const double*)J, s) : colprec_setup_t(m, (const float*)J, s);
+}
+
+extern "C" int bp_colprec_apply(bp_mesh* m, const double* r, double* z, void* stream) {
+  if (!m || !r || !z) return BP_EINVAL;
+  if (!m->ws || !m->ws->has_prec) return BP_EINVAL;
+  bp_device_guard g(m->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  k_colprec_apply<double><<<(m->nv + 127) / 128, 128, 0, s>>>(prec_of(m), r, z);
+  BP_CUDA_TRY(cudaGetLastError());
+  return BP_OK;
+}
+
+extern "C" int bp_energy(bp_mesh* m, const double* U, double* out, void* stream) {
+  if (!m || !U || !out) return BP_EINVAL;
+  bp_device_guard g(m->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc = ensure_ws(m, s);
+  if (rc) return rc;
+  return energy_host(m, U, s, out);
+}
+
+extern "C" int bp_energy_change(bp_mesh* m, const double* U, const double* D, double alpha, double* out,
+                                void* stream) {
+  if (!m || !U || !D || !out) return BP_EINVAL;
+  bp_device_guard g(m->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc = ensure_ws(m, s);
+  if (rc) return rc;
+  return energy_change_host(m, U, D, alpha, s, out);
+}
+
+extern "C" int bp_initial_guess(bp_mesh* m, int kind, double* U, void* stream) {
+  if (!m || !U) return BP_EINVAL;
+  if (kind != BP_GUESS_ZERO && kind != BP_GUESS_SIA) return BP_EINVAL;
+  bp_device_guard g(m->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (kind == BP_GUESS_ZERO) {
+    BP_CUDA_TRY(cudaMemsetAsync(U, 0, m->ndof * sizeof(double), s));
+    return BP_OK;
+  }
+  int rc = ensure_ws(m, s);
+  if (rc) return rc;
+  bp_solver_ws* w = m->ws;
+  BP_CUDA_TRY(cudaMemsetAsync(w->sia, 0, 3 * (size_t)m->nv * sizeof(double), s));
+  k_sia_accum<<<(m->ntri + 127) / 128, 128, 0, s>>>(m->xy, m->bed, m->thick, m->tri, m->ntri, w->sia, m->nv);
+  k_sia_fill<<<(m->nv + 127) / 128, 128, 0, s>>>(w->sia, m->bed, m->thick, m->beta, m->sigma, m->nv, m->nl, m->p.A,
+                                                 m->p.rho * m->p.g, U);
+  BP_CUDA_TRY(cudaGetLastError());
+  return BP_OK;
+}
+
+extern "C" void bp_solve_opts_default(bp_solve_opts* o) {
+  if (!o) return;
+  o->rtol = 1e-8;
+  o->max_newton = 50;
+  o->max_krylov = 1000;
+  o->eta_max = 0.1;
+  o->precision = BP_F64;
+  o->krylov = BP_KRYLOV_CG;
+  o->line_search = 1;
+  o->check_every = 8;
+}
+
+extern "C" int bp_newton_solve(bp_mesh* m, double* U, const bp_solve_opts* opts, bp_solve_report* rep,
+                               void* stream) {
+  if (!m || !U || !opts || !rep) return BP_EINVAL;
+  const bp_solve_opts o = *opts;
+  if (!(o.rtol > 0) || o.max_newton < 0 || o.max_newton > 64 || o.max_krylov < 1 || o.check_every < 1 ||
+      (o.precision != BP_F64 && o.precision != BP_F32) || o.krylov != BP_KRYLOV_CG || !(o.eta_max > 0))
+    return BP_EINVAL;
+  bp_device_guard g(m->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc = ensure_ws(m, s);
+  if (rc) return rc;
+  if ((rc = ensure_jac(m))) return rc;
+  bp_solver_ws* w = m->ws;
+  std::memset(rep, 0, sizeof(*rep));
+  cudaEvent_t ev[10];
+  for (auto& e : ev) BP_CUDA_TRY(cudaEventCreate(&e));
+  struct EvFree {
+    cudaEvent_t* e;
+    ~EvFree() {
+      for (int i = 0; i < 10; ++i) cudaEventDestroy(e[i]);
+    }
+  } evfree{ev};
+  BP_CUDA_TRY(cudaEventRecord(ev[0], s));
+  double fref;
+  if ((rc = dot_host(m, m->load, m->load, m->ndof, s, &fref))) return rc;
+  fref = std::sqrt(fref);  // ||F(0)||: at U = 0 the residual is the driving-stress load
+  rep->fnorm_ref = fref;
+  const bool f32 = o.precision == BP_F32;
+  const double eta_floor = f32 ? 1e-5 : 1e-10;
+  double eta = o.eta_max, fprev = 0.0;
+  int status = BP_ENOCONV;
+  for (int k = 0;; ++k) {
+    // assemble J and F at U
+    BP_CUDA_TRY(cudaEventRecord(ev[1], s));
+    if ((rc = bp_assemble_jacobian(m, U, w->R, w->J, o.precision, BP_SCATTER_ATOMIC, BP_JAC_FACTORED, s)))
+      return rc;
+    BP_CUDA_TRY(cudaEventRecord(ev[2], s));
+    double fn;
+    if ((rc = dot_host(m, w->R, w->R, m->ndof, s, &fn))) return rc;
+    fn = std::sqrt(fn);
+    rep->t_assemble += elapsed(ev[1], ev[2]);
+    if (!std::isfinite(fn)) {
+      status = BP_ENAN;
+      break;
+    }
+    if (k == 0) rep->fnorm_initial = fn;
+    rep->history[k] = fn / fref;
+    rep->fnorm_final = fn;
+    rep->newton_iters = k;
+    if (fn <= o.rtol * fref) {
+      status = BP_OK;
+      rep->converged = 1;
+      break;
+    }
+    if (k >= o.max_newton) break;
+    // forcing term (Eisenstat-Walker choice 2), not below what the final tolerance needs
+    if (k > 0) {
+      double e = 0.9 * (fn / fprev) * (fn / fprev);
+      const double safe = 0.9 * eta * eta;
+      if (safe > 0.1) e = std::max(e, safe);
+      eta = std::min(e, o.eta_max);
+    }
+    eta = std::max(eta, 0.5 * o.rtol * fref / fn);
+    eta = std::max(eta, eta_floor);
+    fprev = fn;
+    // preconditioner + Krylov
+    BP_CUDA_TRY(cudaEventRecord(ev[3], s));
+    if ((rc = f32 ? colprec_setup_t(m, reinterpret_cast<const float*>(w->J), s) : colprec_setup_t(m, w->J, s)))
+      return rc;
+    BP_CUDA_TRY(cudaEventRecord(ev[4], s));
+    int its = 0, kst = 0;
+    if (f32)
+      rc = cg_solve<float, float>(m, reinterpret_cast<const float*>(w->J), eta, o.max_krylov, o.check_every, s,
+                                  &its, &kst);
+    else
+      rc = cg_solve<double, double>(m, w->J, eta, o.max_krylov, o.check_every, s, &its, &kst);
+    if (rc) return rc;
+    BP_CUDA_TRY(cudaEventRecord(ev[5], s));
+    BP_CUDA_TRY(cudaEventSynchronize(ev[5]));
+    rep->t_precond += elapsed(ev[3], ev[4]);
+    rep->t_krylov += elapsed(ev[4], ev[5]);
+    rep->krylov_per_newton[k] = its;
+    rep->krylov_iters += its;
+    if (kst == 3) {
+      status = BP_ENAN;
+      break;
+    }
+    // line search on the energy
+    BP_CUDA_TRY(cudaEventRecord(ev[6], s));
+    double slope;
+    if (f32)
+      rc = dot_host(m, w->R, reinterpret_cast<const float*>(w->x), m->ndof, s, &slope);
+    else
+      rc = dot_host(m, w->R, w->x, m->ndof, s, &slope);
+    if (rc) return rc;
+    double alpha = 1.0;
+    if (o.line_search && slope < 0.0) {
+      // Armijo on the energy: Pi(U + alpha delta) - Pi(U) <= c alpha F . delta, alpha = 1, 1/2, ..., 2^-10.
+      // The step is handed to the energy-change kernel in FP64.
+      const double* D = w->x;
+      if (f32) {  // widen the FP32 step into the FP64 trial buffer: Ut = 0 + 1 * delta
+        BP_CUDA_TRY(cudaMemsetAsync(w->Ut, 0, m->ndof * sizeof(double), s));
+        k_axpy_to<float><<<grid_for(m->ndof, NT), NT, 0, s>>>(w->Ut, reinterpret_cast<const float*>(w->x), 1.0,
+                                                             m->ndof, w->Ut);
+        D = w->Ut;
+      }
+      const double c = 1e-4;
+      for (int h = 0; h <= 10; ++h) {
+        double dE;
+        if ((rc = energy_change_host(m, U, D, alpha, s, &dE))) return rc;
+        if (dE <= c * alpha * slope || h == 10) break;
+        alpha *= 0.5;
+      }
+    }
+    if (f32)
+      k_axpy_to<float><<<grid_for(m->ndof, NT), NT, 0, s>>>(U, reinterpret_cast<const float*>(w->x), alpha, m->ndof,
+                                                           U);
+    else
+      k_axpy_to<double><<<grid_for(m->ndof, NT), NT, 0, s>>>(U, w->x, alpha, m->ndof, U);
+    BP_CUDA_TRY(cudaGetLastError());
+    BP_CUDA_TRY(cudaEventRecord(ev[7], s));
+    BP_CUDA_TRY(cudaEventSynchronize(ev[7]));
+    rep->t_linesearch += elapsed(ev[6], ev[7]);
+    rep->alpha[k] = alpha;
+  }
+  BP_CUDA_TRY(cudaEventRecord(ev[8], s));
+  BP_CUDA_TRY(cudaEventSynchronize(ev[8]));
+  rep->t_total = elapsed(ev[0], ev[8]);
+  return status;
+}

@@ -1,0 +1,180 @@
+"""Parity of the solver kernels (through the C ABI) with plain CPU statements of the same steps.
+
+SpMV against scipy's CSR product; the column preconditioner against dense solves of each
+column's block-tridiagonal matrix; energy and the shallow-ice guess against the oracle; the
+Newton solution against the oracle's Newton solution (the discrete problem has a unique
+minimiser) and, at full size, the final residual recomputed by the oracle.
+"""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import oracle
+from oracle.newton import newton as oracle_newton
+from paper_2204_04321_b300 import synth
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _need_cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+
+
+def capi():
+    from paper_2204_04321_b300 import capi as c
+    return c
+
+
+def dev(x):
+    return torch.as_tensor(np.ascontiguousarray(x), device="cuda")
+
+
+def rel_inf(a, b):
+    return float(np.abs(a - b).max() / np.abs(b).max())
+
+
+def _host_csr(dm, J):
+    rp, ci = dm.pattern()
+    return sp.csr_matrix((J.cpu().numpy().astype(np.float64), ci.cpu().numpy(), rp.cpu().numpy()),
+                         shape=(dm.ndof, dm.ndof))
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_spmv_matches_scipy(precision):
+    c = capi()
+    mesh = synth.dome_mesh(23, 4, 31, 32, bed="sinusoidal")
+    dm = c.DeviceMesh(mesh)
+    U = dev(synth.random_velocity(mesh, 3))
+    J, _ = dm.jacobian(U, precision=precision)
+    x = np.random.default_rng(1).normal(size=dm.ndof)
+    y = torch.empty(dm.ndof, dtype=torch.float64, device="cuda")
+    c.bp_spmv(dm.handle, J, dev(x), y, precision=precision)
+    A = _host_csr(dm, J)
+    assert rel_inf(y.cpu().numpy(), A @ x) <= 1e-13
+
+
+def _column_blocks(A, mesh, a):
+    L = mesh.nlayers
+    idx = np.array([mesh.dof(a, l, c) for l in range(L + 1) for c in (0, 1)])
+    B = A[idx][:, idx].toarray()
+    # keep only the block-tridiagonal part (levels |l - l'| <= 1 is all there is within a column)
+    return idx, B
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_column_preconditioner_is_exact_block_tridiagonal_solve(precision):
+    c = capi()
+    mesh = synth.dome_mesh(12, 6, 51, 52, bed="sinusoidal")
+    dm = c.DeviceMesh(mesh)
+    U = dev(synth.random_velocity(mesh, 4))
+    J, _ = dm.jacobian(U, precision=precision)
+    c.bp_colprec_setup(dm.handle, J, precision=precision)
+    r = np.random.default_rng(2).normal(size=dm.ndof)
+    z = torch.empty(dm.ndof, dtype=torch.float64, device="cuda")
+    c.bp_colprec_apply(dm.handle, dev(r), z)
+    z = z.cpu().numpy()
+    A = _host_csr(dm, J)
+    for a in range(0, mesh.nv, 7):
+        idx, B = _column_blocks(A, mesh, a)
+        zc = np.linalg.solve(B, r[idx])
+        assert rel_inf(z[idx], zc) <= 1e-11
+
+
+@pytest.mark.parametrize("kind", ["random", "sia"])
+def test_energy_matches_oracle(kind):
+    c = capi()
+    mesh = synth.dome_mesh(20, 5, 61, 62, bed="sinusoidal", beta="field")
+    om = oracle.OracleMesh(mesh)
+    U = synth.random_velocity(mesh, 5) if kind == "random" else om.sia()
+    dm = c.DeviceMesh(mesh)
+    E = c.bp_energy(dm.handle, dev(U))
+    assert E == pytest.approx(om.energy(U), rel=1e-12)
+
+
+@pytest.mark.parametrize("alpha", [1.0, 1e-3])
+def test_energy_change_matches_oracle_difference(alpha):
+    """Against the oracle's energy difference at steps large enough for that difference to be accurate;
+    at a tiny step the GPU's change must agree with the first-order prediction alpha R . D."""
+    c = capi()
+    mesh = synth.dome_mesh(20, 5, 61, 62, bed="sinusoidal", beta="field")
+    om = oracle.OracleMesh(mesh)
+    U = om.sia()
+    D = synth.random_velocity(mesh, 8, amplitude=30.0)
+    dm = c.DeviceMesh(mesh)
+    dE = c.bp_energy_change(dm.handle, dev(U), dev(D), alpha)
+    E0 = om.energy(U)
+    ref = om.energy(U + alpha * D) - E0
+    assert abs(dE - ref) <= 1e-9 * abs(ref) + 1e-13 * abs(E0)  # the oracle difference carries E0's rounding
+    # derivative at alpha = 0 equals R . D: Richardson-extrapolate dE(a)/a (error O(a) -> O(a^2)); a must
+    # be far below the step at which the strain of a D crosses the regularisation scale sqrt(delta)
+    a = 1e-9
+    d1 = c.bp_energy_change(dm.handle, dev(U), dev(D), a) / a
+    d2 = c.bp_energy_change(dm.handle, dev(U), dev(D), 2 * a) / (2 * a)
+    slope = float(om.residual(U) @ D)
+    assert 2 * d1 - d2 == pytest.approx(slope, rel=1e-5)
+
+
+def test_shallow_ice_guess_matches_oracle():
+    c = capi()
+    mesh = synth.config_small()
+    om = oracle.OracleMesh(mesh)
+    dm = c.DeviceMesh(mesh)
+    U = torch.empty(dm.ndof, dtype=torch.float64, device="cuda")
+    c.bp_initial_guess(dm.handle, c.BP_GUESS_SIA, U)
+    assert rel_inf(U.cpu().numpy(), om.sia()) <= 1e-12
+    c.bp_initial_guess(dm.handle, c.BP_GUESS_ZERO, U)
+    assert float(U.abs().max()) == 0.0
+
+
+def test_newton_matches_oracle_newton_on_tiny_mesh():
+    c = capi()
+    mesh = synth.dome_mesh(4, 3, 71, 72, bed="sinusoidal", beta="iid")
+    om = oracle.OracleMesh(mesh)
+    Uo, info = oracle_newton(om, np.zeros(mesh.ndof), rtol=1e-10)
+    assert info["converged"]
+    dm = c.DeviceMesh(mesh)
+    U = torch.zeros(dm.ndof, dtype=torch.float64, device="cuda")
+    rc, rep = c.bp_newton_solve(dm.handle, U, rtol=1e-10, max_krylov=4000)
+    assert rc == c.BP_OK and rep["converged"], rep
+    assert rel_inf(U.cpu().numpy(), Uo) <= 1e-7
+    # the GPU's final residual, recomputed by the oracle
+    assert np.linalg.norm(om.residual(U.cpu().numpy())) <= 1.5e-10 * np.linalg.norm(om.residual(0 * Uo))
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_newton_small_dome_converges_from_zero_and_sia_to_same_solution(precision):
+    c = capi()
+    mesh = synth.config_small()
+    om = oracle.OracleMesh(mesh)
+    dm = c.DeviceMesh(mesh)
+    sols = []
+    for guess in (c.BP_GUESS_ZERO, c.BP_GUESS_SIA):
+        U = torch.empty(dm.ndof, dtype=torch.float64, device="cuda")
+        c.bp_initial_guess(dm.handle, guess, U)
+        rc, rep = c.bp_newton_solve(dm.handle, U, precision=precision)
+        assert rc == c.BP_OK, rep
+        assert rep["history"][-1] <= 1e-8
+        Uh = U.cpu().numpy()
+        fo = np.linalg.norm(om.residual(Uh)) / np.linalg.norm(om.residual(np.zeros_like(Uh)))
+        assert fo <= 1.1e-8
+        sols.append(Uh)
+    assert rel_inf(sols[0], sols[1]) <= 1e-6
+
+
+@pytest.mark.slow
+def test_newton_full_size_dome_reaches_1e8_checked_by_oracle():
+    c = capi()
+    mesh = synth.config_medium()
+    dm = c.DeviceMesh(mesh)
+    U = torch.empty(dm.ndof, dtype=torch.float64, device="cuda")
+    c.bp_initial_guess(dm.handle, c.BP_GUESS_SIA, U)
+    rc, rep = c.bp_newton_solve(dm.handle, U, max_krylov=4000)
+    assert rc == c.BP_OK, rep
+    om = oracle.OracleMesh(mesh)
+    Uh = U.cpu().numpy()
+    f = np.linalg.norm(om.residual(Uh)) / np.linalg.norm(om.residual(np.zeros_like(Uh)))
+    assert f <= 1.1e-8, f
