@@ -280,6 +280,7 @@ def run_ours(args):
         e2e_s = float(t.item())
     e2e_value = ws * W * args.steps / e2e_s
 
+    newton = newton_section(capi, synth, dm, mesh, dev, skip_large=args.no_large) if not args.no_newton else None
     flops = FLOPS_PER_WEDGE_JAC64 * W
     achieved = flops / (kernel_ms * 1e-3) / 1e12
     peaks = read_peaks()
@@ -315,6 +316,7 @@ def run_ours(args):
                 "zero_init_ms": zero_ms, "wall_s_timed_region": t_wall},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * dm.ndof,
                     "d2h_bytes_per_step": 8 * dm.ndof + 8 * dm.nnz},
+            "newton": newton,
             "gpu_launches": args.steps,
             "clocks": clk.summary(),
         }
@@ -326,6 +328,45 @@ def run_ours(args):
         import torch.distributed as dist
         dist.destroy_process_group()
     return 0
+
+
+def newton_section(capi, synth, dm, mesh, dev, skip_large=False):
+    """Time to ||F(U)|| <= 1e-8 ||F(0)|| from the shallow-ice guess: plain FP64 path and the
+    mixed-precision path (FP32 Jacobian lanes and Krylov, FP64 residual/viscosity/update)."""
+    import torch
+
+    def solve(dmx, prec, reps=3):
+        times, rep, U = [], None, None
+        for _ in range(reps):
+            U = torch.empty(dmx.ndof, dtype=torch.float64, device=dev)
+            capi.bp_initial_guess(dmx.handle, capi.BP_GUESS_SIA, U)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            rc, rep = capi.bp_newton_solve(dmx.handle, U, precision=prec, max_krylov=4000)
+            torch.cuda.synchronize()
+            times.append(time.perf_counter() - t0)
+            if rc != capi.BP_OK:
+                break
+        return {"s": statistics.median(times), "converged": rep["converged"], "newton_iters": rep["newton_iters"],
+                "krylov_iters": rep["krylov_iters"], "final_rel_residual": rep["history"][-1],
+                "t_assemble": rep["t_assemble"], "t_precond": rep["t_precond"], "t_krylov": rep["t_krylov"],
+                "t_linesearch": rep["t_linesearch"]}, U
+
+    out = {"metric": "time to 1e-8 rel. FP64 residual Newton solve", "unit": "s", "start": "shallow-ice guess"}
+    f64, U64 = solve(dm, capi.BP_F64)
+    f32, U32 = solve(dm, capi.BP_F32)
+    out[mesh.name] = {"f64": f64, "mixed_f32": f32, "speedup_mixed": f64["s"] / f32["s"],
+                      "mixed_vs_f64_solution_rel_inf": float((U32 - U64).abs().max() / U64.abs().max())}
+    if not skip_large:
+        big = synth.config_large()
+        dmb = capi.DeviceMesh(big)
+        b64, V64 = solve(dmb, capi.BP_F64, reps=1)
+        b32, V32 = solve(dmb, capi.BP_F32, reps=1)
+        out[big.name] = {"wedges": big.nwedges, "f64": b64, "mixed_f32": b32, "speedup_mixed": b64["s"] / b32["s"],
+                         "mixed_vs_f64_solution_rel_inf": float((V32 - V64).abs().max() / V64.abs().max())}
+        del V64, V32
+        dmb.close()
+    return out
 
 
 def kernel_hash():
@@ -345,6 +386,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-newton", action="store_true", help="skip the Newton-solve measurements")
+    ap.add_argument("--no-large", action="store_true", help="skip the 4M-wedge mixed-precision solve")
     ap.add_argument("--mesh-m", type=int, default=224, help="base grid size (224: the 1M-wedge workload)")
     ap.add_argument("--layers", type=int, default=10)
     args = ap.parse_args()
