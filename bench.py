@@ -370,13 +370,12 @@ def newton_section(capi, synth, dm, mesh, dev, skip_large=False):
 
 
 def kernel_hash():
-    """Hash of the assembly kernel's source text (the k_assemble template and its helpers)."""
+    """Hash of the assembly kernel's source text (the per-column body and its helpers)."""
     import hashlib
-    with open(os.path.join(ROOT, "paper_2204_04321_b300", "csrc", "bp_assemble.cu")) as f:
+    with open(os.path.join(ROOT, "paper_2204_04321_b300", "csrc", "bp_column.cuh")) as f:
         src = f.read()
     a = src.index("constexpr int MODE_RES")
-    b = src.index("AsmArgs make_args")
-    return hashlib.sha256(src[a:b].encode()).hexdigest()[:16]
+    return hashlib.sha256(src[a:].encode()).hexdigest()[:16]
 
 
 def main():

@@ -1,554 +1,16 @@
-// Fused finite-element assembly of the first-order Stokes residual and Jacobian
-// (paper Sec. 3.2: Gather -> Interpolate -> Evaluate -> Scatter, here one kernel).
-//
-// One thread walks one column of wedges (a base triangle times all layers) from the bed up.
-// The value path is FP64 and uses the extruded structure of the wedge: x, y do not depend
-// on zeta, so for N_{a,k} = lambda_a(xi, eta) psi_k(zeta)
-//     grad N_{a,k} = psi_k Lambda_a + lambda_a psi_k' Z,   Z = grad zeta = (2/h)(-grad z|zeta, 1),
-// with Lambda_a the constant 2D gradient of the barycentric coordinate, h the local layer
-// thickness and grad z|zeta the (constant) slope of the zeta-level surface.  The velocity
-// gradient at a quadrature point is then
-//     u_z = sum_a lambda_a (u_top - u_bot)_a / h,   u_xy = grad_2D u(zeta) - u_z grad z|zeta.
-// Sums over the 6 quadrature points are factored into sums over the 2 zeta levels and the 3
-// triangle points.  Values shared by consecutive wedges of a column (the level velocities
-// and their 2D gradients, the top-face residual) are carried in registers.
-//
-// Jacobian (Sec. 3.2; the paper differentiates with forward-mode dual numbers, SFad):
-//   K_ij = sum_q c_q [eta B^{c_i c_j}(grad N_i, grad N_j) + eta' p_i p_j],
-//   eta = 2 mu, eta' = d eta / d eps_e^2, p_i = eps_{c_i} . grad N_i = d eps_e^2 / dU_i,
-//   B^{uu}(X, Y) = 2 X_x Y_x + X_y Y_y / 2 + X_z Y_z / 2,  B^{uv} = X_x Y_y + X_y Y_x / 2,
-//   B^{vu} = X_x Y_y / 2 + X_y Y_x,  B^{vv} = X_x Y_x / 2 + 2 X_y Y_y + X_z Y_z / 2,
-// formed either with literal 12-lane dual numbers (BP_JAC_DUAL, one lane per element dof) or
-// sum-factorised over the wedge's quadrature structure (BP_JAC_FACTORED).  The lane type TL is
-// double (BP_F64) or float (BP_F32); the residual stays FP64 either way.
+// Entry points of the fused residual / Jacobian assembly (the kernel body is in bp_column.cuh).
 #include <cmath>
 #include <mutex>
 
-#include "bp_internal.cuh"
+#include "bp_column.cuh"
 
 namespace {
 
-constexpr int MODE_RES = 0;
-constexpr int MODE_DUAL = 1;
-constexpr int MODE_FACT = 2;
-
-struct AsmArgs {
-  const double2* xy;
-  const double* bed;
-  const double* thick;
-  const double* sigma;
-  const int32_t* tri;
-  const int32_t* slots;
-  const double* basal;
-  const int64_t* vstart;
-  const int32_t* vdeg;
-  const int32_t* tri_list;  // nullable: the triangles of one colour
-  int32_t count;            // columns handled by this launch
-  int32_t L;
-  double cA, delta;
-  const double* U;
-  double* R;
-  void* J;
-};
-
-__device__ __forceinline__ constexpr double psi(int k, int z) {  // psi_k at zeta level z
-  return (k == z) ? BP_QP_P : BP_QP_Q;
-}
-__device__ __forceinline__ constexpr double dpsi(int k) { return k == 0 ? -0.5 : 0.5; }
-__device__ __forceinline__ constexpr double lam(int a, int tp) {  // lambda_a at triangle point tp
-  return (a == tp) ? 2.0 / 3.0 : 1.0 / 6.0;
-}
-__device__ __forceinline__ constexpr int uidx(int i, int j) {  // upper-triangle index, i <= j < 12
-  return i * 12 - (i * (i - 1)) / 2 + (j - i);
-}
-
-template <bool ATOMIC, class T>
-__device__ __forceinline__ void scatter_add(T* p, T v) {
-  if constexpr (ATOMIC) {
-    atomicAdd(p, v);
-  } else {
-    *p += v;
-  }
-}
-
-// ------------------------------------------------------------------ dual numbers
-// Forward-mode dual number with an FP64 value and NL derivative lanes of type TL.
-template <class TL, int NL>
-struct Dual {
-  double v;
-  TL d[NL];
-};
-template <class TL, int NL>
-__device__ __forceinline__ Dual<TL, NL> operator+(const Dual<TL, NL>& a, const Dual<TL, NL>& b) {
-  Dual<TL, NL> r;
-  r.v = a.v + b.v;
-#pragma unroll
-  for (int k = 0; k < NL; ++k) r.d[k] = a.d[k] + b.d[k];
-  return r;
-}
-template <class TL, int NL>
-__device__ __forceinline__ Dual<TL, NL> operator*(const Dual<TL, NL>& a, const Dual<TL, NL>& b) {
-  Dual<TL, NL> r;
-  r.v = a.v * b.v;
-  const TL av = (TL)a.v, bv = (TL)b.v;
-#pragma unroll
-  for (int k = 0; k < NL; ++k) r.d[k] = a.d[k] * bv + av * b.d[k];
-  return r;
-}
-template <class TL, int NL>
-__device__ __forceinline__ Dual<TL, NL> operator*(double s, const Dual<TL, NL>& a) {
-  Dual<TL, NL> r;
-  r.v = s * a.v;
-  const TL ts = (TL)s;
-#pragma unroll
-  for (int k = 0; k < NL; ++k) r.d[k] = ts * a.d[k];
-  return r;
-}
-
-// ------------------------------------------------------------------ the column kernel
 template <int MODE, class TL, bool ATOMIC>
 __global__ void __launch_bounds__(128) k_assemble(const AsmArgs A) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= A.count) return;
-  const int t = A.tri_list ? A.tri_list[idx] : idx;
-  const int L = A.L;
-
-  // ---- column geometry (per base triangle)
-  int v[3];
-  double x[3], y[3], H[3], bb[3];
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    v[a] = A.tri[3 * t + a];
-    const double2 p = A.xy[v[a]];
-    x[a] = p.x;
-    y[a] = p.y;
-    H[a] = A.thick[v[a]];
-    bb[a] = A.bed[v[a]];
-  }
-  const double d = (x[1] - x[0]) * (y[2] - y[0]) - (x[2] - x[0]) * (y[1] - y[0]);  // 2 * area
-  const double inv_d = 1.0 / d;
-  double lx[3], ly[3];  // grad lambda_a
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    lx[a] = (y[(a + 1) % 3] - y[(a + 2) % 3]) * inv_d;
-    ly[a] = (x[(a + 2) % 3] - x[(a + 1) % 3]) * inv_d;
-  }
-  const double gbx = bb[0] * lx[0] + bb[1] * lx[1] + bb[2] * lx[2];
-  const double gby = bb[0] * ly[0] + bb[1] * ly[1] + bb[2] * ly[2];
-  const double gHx = H[0] * lx[0] + H[1] * lx[1] + H[2] * lx[2];
-  const double gHy = H[0] * ly[0] + H[1] * ly[1] + H[2] * ly[2];
-  const double Hs6 = (H[0] + H[1] + H[2]) * (1.0 / 6.0);
-  double Hq[3], invHq[3];
-#pragma unroll
-  for (int tp = 0; tp < 3; ++tp) {
-    Hq[tp] = Hs6 + 0.5 * H[tp];
-    invHq[tp] = 1.0 / Hq[tp];
-  }
-  const double d12 = d * (1.0 / 12.0);
-  const double d6 = d * (1.0 / 6.0);
-
-  int64_t ubase[3];
-#pragma unroll
-  for (int a = 0; a < 3; ++a) ubase[a] = 2LL * v[a] * (L + 1);
-
-  int64_t vs[3];
-  int dg[3], sl[9];
-  if constexpr (MODE != MODE_RES) {
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      vs[a] = A.vstart[v[a]];
-      dg[a] = A.vdeg[v[a]];
-    }
-#pragma unroll
-    for (int k = 0; k < 9; ++k) sl[k] = A.slots[9 * t + k];
-  }
-
-  // ---- bottom level
-  double ub[3], vb[3];
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    const double2 w = *reinterpret_cast<const double2*>(A.U + ubase[a]);
-    ub[a] = w.x;
-    vb[a] = w.y;
-  }
-  double gubx = ub[0] * lx[0] + ub[1] * lx[1] + ub[2] * lx[2];
-  double guby = ub[0] * ly[0] + ub[1] * ly[1] + ub[2] * ly[2];
-  double gvbx = vb[0] * lx[0] + vb[1] * lx[1] + vb[2] * lx[2];
-  double gvby = vb[0] * ly[0] + vb[1] * ly[1] + vb[2] * ly[2];
-  double carry[3][2] = {{0, 0}, {0, 0}, {0, 0}};  // residual of the current bottom level from the wedge below
-
-  for (int l = 0; l < L; ++l) {
-    double ut[3], vt[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      const double2 w = *reinterpret_cast<const double2*>(A.U + ubase[a] + 2 * (l + 1));
-      ut[a] = w.x;
-      vt[a] = w.y;
-    }
-    const double gutx = ut[0] * lx[0] + ut[1] * lx[1] + ut[2] * lx[2];
-    const double guty = ut[0] * ly[0] + ut[1] * ly[1] + ut[2] * ly[2];
-    const double gvtx = vt[0] * lx[0] + vt[1] * lx[1] + vt[2] * lx[2];
-    const double gvty = vt[0] * ly[0] + vt[1] * ly[1] + vt[2] * ly[2];
-    const double s_l = A.sigma[l];
-    const double ds = A.sigma[l + 1] - s_l;
-    const double invds = 1.0 / ds;
-
-    // per zeta level: slope of the level surface and the 2D velocity gradients
-    double Gzx[2], Gzy[2], GUx[2], GUy[2], GVx[2], GVy[2];
-#pragma unroll
-    for (int z = 0; z < 2; ++z) {
-      const double sz = s_l + psi(1, z) * ds;
-      Gzx[z] = gbx + sz * gHx;
-      Gzy[z] = gby + sz * gHy;
-      GUx[z] = psi(0, z) * gubx + psi(1, z) * gutx;
-      GUy[z] = psi(0, z) * guby + psi(1, z) * guty;
-      GVx[z] = psi(0, z) * gvbx + psi(1, z) * gvtx;
-      GVy[z] = psi(0, z) * gvby + psi(1, z) * gvty;
-    }
-    // per triangle point: vertical shear, weights
-    const double dus6 = (ut[0] - ub[0] + ut[1] - ub[1] + ut[2] - ub[2]) * (1.0 / 6.0);
-    const double dvs6 = (vt[0] - vb[0] + vt[1] - vb[1] + vt[2] - vb[2]) * (1.0 / 6.0);
-    double uz[3], vz[3], cq[3], ez[3], invh[3];
-#pragma unroll
-    for (int tp = 0; tp < 3; ++tp) {
-      invh[tp] = invds * invHq[tp];
-      uz[tp] = (dus6 + 0.5 * (ut[tp] - ub[tp])) * invh[tp];
-      vz[tp] = (dvs6 + 0.5 * (vt[tp] - vb[tp])) * invh[tp];
-      ez[tp] = 0.25 * (uz[tp] * uz[tp] + vz[tp] * vz[tp]);
-      cq[tp] = d12 * ds * Hq[tp];
-    }
-
-    double Rl[2][3][2];  // [k][a][c] residual of this wedge
-    TL K[78];            // upper triangle of the element matrix
-    TL eta_q[2][3];      // 2 mu at the quadrature points (factored Jacobian)
-    if constexpr (MODE != MODE_RES) {
-#pragma unroll
-      for (int k = 0; k < 78; ++k) K[k] = TL(0);
-    }
-
-    if constexpr (MODE == MODE_DUAL) {
-      // ---- literal forward mode: 12 lanes, lane j = d / dU_j (j = 2 * (3k + a) + c)
-#pragma unroll
-      for (int k = 0; k < 2; ++k)
-#pragma unroll
-        for (int a = 0; a < 3; ++a) Rl[k][a][0] = Rl[k][a][1] = 0.0;
-#pragma unroll
-      for (int z = 0; z < 2; ++z) {
-#pragma unroll
-        for (int tp = 0; tp < 3; ++tp) {
-          const double Zx = -2.0 * invh[tp] * Gzx[z], Zy = -2.0 * invh[tp] * Gzy[z], Zz = 2.0 * invh[tp];
-          double gNd[6][3];  // physical basis gradients, node n = 3k + a (value path, FP64)
-          TL gN[6][3];       // the same in lane precision
-#pragma unroll
-          for (int k = 0; k < 2; ++k)
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-              const double c = lam(a, tp) * dpsi(k);
-              gNd[3 * k + a][0] = psi(k, z) * lx[a] + c * Zx;
-              gNd[3 * k + a][1] = psi(k, z) * ly[a] + c * Zy;
-              gNd[3 * k + a][2] = c * Zz;
-#pragma unroll
-              for (int r = 0; r < 3; ++r) gN[3 * k + a][r] = (TL)gNd[3 * k + a][r];
-            }
-          Dual<TL, 12> ux, uy, uzd, vx, vy, vzd;
-          ux.v = GUx[z] - uz[tp] * Gzx[z];
-          uy.v = GUy[z] - uz[tp] * Gzy[z];
-          vx.v = GVx[z] - vz[tp] * Gzx[z];
-          vy.v = GVy[z] - vz[tp] * Gzy[z];
-          uzd.v = uz[tp];
-          vzd.v = vz[tp];
-#pragma unroll
-          for (int n = 0; n < 6; ++n) {  // seed: d(grad u)/dU_(n,u) = grad N_n, d(grad v)/dU_(n,v) = grad N_n
-            ux.d[2 * n] = gN[n][0];
-            ux.d[2 * n + 1] = TL(0);
-            uy.d[2 * n] = gN[n][1];
-            uy.d[2 * n + 1] = TL(0);
-            uzd.d[2 * n] = gN[n][2];
-            uzd.d[2 * n + 1] = TL(0);
-            vx.d[2 * n] = TL(0);
-            vx.d[2 * n + 1] = gN[n][0];
-            vy.d[2 * n] = TL(0);
-            vy.d[2 * n + 1] = gN[n][1];
-            vzd.d[2 * n] = TL(0);
-            vzd.d[2 * n + 1] = gN[n][2];
-          }
-          const Dual<TL, 12> exy = 0.5 * (uy + vx);
-          const Dual<TL, 12> exz = 0.5 * uzd;
-          const Dual<TL, 12> eyz = 0.5 * vzd;
-          const Dual<TL, 12> e2 = ux * ux + vy * (vy + ux) + exy * exy + exz * exz + eyz * eyz;
-          const double xx = e2.v + A.delta;
-          const double r = rcbrt(xx);
-          Dual<TL, 12> eta;  // eta = cA (e2 + delta)^(-1/3), d eta / d e2 = -eta / (3 (e2 + delta))
-          eta.v = A.cA * r;
-          const TL detad = (TL)(-(1.0 / 3.0) * eta.v * (r * r * r));
-#pragma unroll
-          for (int j = 0; j < 12; ++j) eta.d[j] = detad * e2.d[j];
-          const Dual<TL, 12> g1x = 2.0 * ux + vy, g2y = ux + 2.0 * vy;
-          const double c = cq[tp];
-#pragma unroll
-          for (int n = 0; n < 6; ++n) {
-#pragma unroll
-            for (int comp = 0; comp < 2; ++comp) {
-              const int i = 2 * n + comp;
-              const Dual<TL, 12>& ga = comp == 0 ? g1x : exy;
-              const Dual<TL, 12>& gb = comp == 0 ? exy : g2y;
-              const Dual<TL, 12>& gc = comp == 0 ? exz : eyz;
-              Dual<TL, 12> pi;  // p_i = g_c . grad N_n
-              pi.v = ga.v * gNd[n][0] + gb.v * gNd[n][1] + gc.v * gNd[n][2];
-#pragma unroll
-              for (int j = 0; j < 12; ++j) pi.d[j] = ga.d[j] * gN[n][0] + gb.d[j] * gN[n][1] + gc.d[j] * gN[n][2];
-              const Dual<TL, 12> ri = eta * pi;
-              Rl[n / 3][n % 3][comp] += c * ri.v;
-#pragma unroll
-              for (int j = i; j < 12; ++j) K[uidx(i, j)] += (TL)c * ri.d[j];
-            }
-          }
-        }
-      }
-    } else {
-      // ---- structured value path (+ sum-factorised Jacobian lanes)
-      double P1x[2] = {0, 0}, P1y[2] = {0, 0}, P2x[2] = {0, 0}, P2y[2] = {0, 0};
-      double TW1[3] = {0, 0, 0}, TW2[3] = {0, 0, 0};
-#pragma unroll
-      for (int z = 0; z < 2; ++z) {
-#pragma unroll
-        for (int tp = 0; tp < 3; ++tp) {
-          const double ux = GUx[z] - uz[tp] * Gzx[z];
-          const double uy = GUy[z] - uz[tp] * Gzy[z];
-          const double vx = GVx[z] - vz[tp] * Gzx[z];
-          const double vy = GVy[z] - vz[tp] * Gzy[z];
-          const double exy = 0.5 * (uy + vx);
-          const double e2 = fma(ux, ux, fma(vy, vy + ux, fma(exy, exy, ez[tp])));
-          const double xx = e2 + A.delta;
-          const double r = rcbrt(xx);
-          const double eta = A.cA * r;
-          const double W = cq[tp] * eta;
-          const double g1x = 2.0 * ux + vy, g2y = ux + 2.0 * vy;
-          P1x[z] = fma(W, g1x, P1x[z]);
-          P1y[z] = fma(W, exy, P1y[z]);
-          P2x[z] = fma(W, exy, P2x[z]);
-          P2y[z] = fma(W, g2y, P2y[z]);
-          const double t1 = 0.5 * uz[tp] - g1x * Gzx[z] - exy * Gzy[z];
-          const double t2 = 0.5 * vz[tp] - exy * Gzx[z] - g2y * Gzy[z];
-          const double W6 = d6 * eta;
-          TW1[tp] = fma(W6, t1, TW1[tp]);
-          TW2[tp] = fma(W6, t2, TW2[tp]);
-          if constexpr (MODE == MODE_FACT) {
-            eta_q[z][tp] = (TL)eta;
-            // rank-one part eta' p_i p_j with p_{(a,k),c} = psi_k g_c,xy . Lambda_a + lambda_a psi_k' g_c . Z
-            const TL Wp = (TL)(-(1.0 / 3.0) * W * (r * r * r));
-            const TL tau1 = (TL)(2.0 * invh[tp] * t1), tau2 = (TL)(2.0 * invh[tp] * t2);
-            const TL fg1x = (TL)g1x, fexy = (TL)exy, fg2y = (TL)g2y;
-            TL p[12];
-#pragma unroll
-            for (int k = 0; k < 2; ++k)
-#pragma unroll
-              for (int a = 0; a < 3; ++a) {
-                const TL al1 = fg1x * (TL)lx[a] + fexy * (TL)ly[a];
-                const TL al2 = fexy * (TL)lx[a] + fg2y * (TL)ly[a];
-                const TL ps = (TL)psi(k, z), lp = (TL)(lam(a, tp) * dpsi(k));
-                p[2 * (3 * k + a)] = ps * al1 + lp * tau1;
-                p[2 * (3 * k + a) + 1] = ps * al2 + lp * tau2;
-              }
-#pragma unroll
-            for (int i = 0; i < 12; ++i) {
-              const TL pw = Wp * p[i];
-#pragma unroll
-              for (int j = i; j < 12; ++j) K[uidx(i, j)] += pw * p[j];
-            }
-          }
-        }
-      }
-      // residual: R_{a,k,c} = Lambda_a . sum_z psi_k(z) P_c(z) + psi_k' sum_tp lambda_a(tp) TW_c(tp)
-      const double T1s = (TW1[0] + TW1[1] + TW1[2]) * (1.0 / 6.0);
-      const double T2s = (TW2[0] + TW2[1] + TW2[2]) * (1.0 / 6.0);
-#pragma unroll
-      for (int k = 0; k < 2; ++k) {
-        const double A1x = psi(k, 0) * P1x[0] + psi(k, 1) * P1x[1];
-        const double A1y = psi(k, 0) * P1y[0] + psi(k, 1) * P1y[1];
-        const double A2x = psi(k, 0) * P2x[0] + psi(k, 1) * P2x[1];
-        const double A2y = psi(k, 0) * P2y[0] + psi(k, 1) * P2y[1];
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-          Rl[k][a][0] = lx[a] * A1x + ly[a] * A1y + dpsi(k) * (T1s + 0.5 * TW1[a]);
-          Rl[k][a][1] = lx[a] * A2x + ly[a] * A2y + dpsi(k) * (T2s + 0.5 * TW2[a]);
-        }
-      }
-      if constexpr (MODE == MODE_FACT) {
-        // eta B(grad N_i, grad N_j) summed over the quadrature, B bilinear:
-        //  (I)   Q_km B(Lambda_a, Lambda_b),          Q_km = sum_q W psi_k psi_m
-        //  (II)  psi_m' B(Lambda_a, V^k_b),           V^k_b = sum_q W psi_k lambda_b Z_xy
-        //  (III) psi_k' B(V^m_a, Lambda_b)
-        //  (IV)  psi_k' psi_m' Y_ab,                  Y_ab = sum_q W lambda_a lambda_b B(Z, Z)
-        TL Qs[2], E[2][3], F[2][6];
-#pragma unroll
-        for (int z = 0; z < 2; ++z) {
-          Qs[z] = TL(0);
-#pragma unroll
-          for (int tp = 0; tp < 3; ++tp) Qs[z] += (TL)cq[tp] * eta_q[z][tp];
-          const TL es = (eta_q[z][0] + eta_q[z][1] + eta_q[z][2]) * TL(1.0 / 6.0);
-          TL ei[3];
-#pragma unroll
-          for (int tp = 0; tp < 3; ++tp) {
-            E[z][tp] = es + TL(0.5) * eta_q[z][tp];
-            ei[tp] = eta_q[z][tp] * (TL)invh[tp];
-          }
-          // F_ab = sum_tp lambda_a lambda_b eta / h, pairs 00 01 02 11 12 22
-          int pr = 0;
-#pragma unroll
-          for (int a = 0; a < 3; ++a)
-#pragma unroll
-            for (int b = a; b < 3; ++b) {
-              TL f = TL(0);
-#pragma unroll
-              for (int tp = 0; tp < 3; ++tp) f += (TL)(lam(a, tp) * lam(b, tp)) * ei[tp];
-              F[z][pr++] = f;
-            }
-        }
-        TL Q[2][2];
-        Q[0][0] = (TL)(BP_QP_P * BP_QP_P) * Qs[0] + (TL)(BP_QP_Q * BP_QP_Q) * Qs[1];
-        Q[1][1] = (TL)(BP_QP_Q * BP_QP_Q) * Qs[0] + (TL)(BP_QP_P * BP_QP_P) * Qs[1];
-        Q[0][1] = Q[1][0] = (TL)(BP_QP_P * BP_QP_Q) * (Qs[0] + Qs[1]);
-        // V^k_b scaled by 1/2 (the magnitude of psi'): V = -(d/12) sum_z psi_k E_b Gz
-        TL Vx[2][3], Vy[2][3];
-#pragma unroll
-        for (int k = 0; k < 2; ++k)
-#pragma unroll
-          for (int b = 0; b < 3; ++b) {
-            const TL w0 = (TL)psi(k, 0) * E[0][b], w1 = (TL)psi(k, 1) * E[1][b];
-            Vx[k][b] = (TL)(-d * (1.0 / 12.0)) * (w0 * (TL)Gzx[0] + w1 * (TL)Gzx[1]);
-            Vy[k][b] = (TL)(-d * (1.0 / 12.0)) * (w0 * (TL)Gzy[0] + w1 * (TL)Gzy[1]);
-          }
-        // Y scaled by 1/4 (|psi_k' psi_m'|): (d/12) sum_z F_ab(z) B_zz(z)
-        TL Yuu[6], Yvv[6], Yuv[6];
-        {
-          TL Buu[2], Bvv[2], Buv[2];
-#pragma unroll
-          for (int z = 0; z < 2; ++z) {
-            const TL gx = (TL)Gzx[z], gy = (TL)Gzy[z];
-            Buu[z] = TL(2) * gx * gx + TL(0.5) * gy * gy + TL(0.5);
-            Bvv[z] = TL(0.5) * gx * gx + TL(2) * gy * gy + TL(0.5);
-            Buv[z] = TL(1.5) * gx * gy;
-          }
-          const TL s = (TL)(d * (1.0 / 12.0));
-#pragma unroll
-          for (int pr = 0; pr < 6; ++pr) {
-            Yuu[pr] = s * (F[0][pr] * Buu[0] + F[1][pr] * Buu[1]);
-            Yvv[pr] = s * (F[0][pr] * Bvv[0] + F[1][pr] * Bvv[1]);
-            Yuv[pr] = s * (F[0][pr] * Buv[0] + F[1][pr] * Buv[1]);
-          }
-        }
-        TL flx[3], fly[3];
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-          flx[a] = (TL)lx[a];
-          fly[a] = (TL)ly[a];
-        }
-#pragma unroll
-        for (int i = 0; i < 12; ++i) {
-          const int ni = i >> 1, ci = i & 1, ki = ni / 3, ai = ni % 3;
-#pragma unroll
-          for (int j = i; j < 12; ++j) {
-            const int nj = j >> 1, cj = j & 1, kj = nj / 3, bj = nj % 3;
-            const TL ax = flx[ai], ay = fly[ai], bx = flx[bj], by = fly[bj];
-            // B^{c_i c_j}(X, Y) for the in-plane pieces (Lambda has no z component)
-            auto Bxy = [&](TL Xx, TL Xy, TL Yx, TL Yy) -> TL {
-              if (ci == 0 && cj == 0) return TL(2) * Xx * Yx + TL(0.5) * Xy * Yy;
-              if (ci == 0 && cj == 1) return Xx * Yy + TL(0.5) * Xy * Yx;
-              if (ci == 1 && cj == 0) return TL(0.5) * Xx * Yy + Xy * Yx;
-              return TL(0.5) * Xx * Yx + TL(2) * Xy * Yy;
-            };
-            TL val = Q[ki][kj] * Bxy(ax, ay, bx, by);
-            const TL sm = (kj == 0) ? TL(-1) : TL(1);  // sign of psi_m'
-            const TL sk = (ki == 0) ? TL(-1) : TL(1);  // sign of psi_k'
-            val += sm * Bxy(ax, ay, Vx[ki][bj], Vy[ki][bj]);
-            val += sk * Bxy(Vx[kj][ai], Vy[kj][ai], bx, by);
-            const int lo = ai < bj ? ai : bj, hi = ai < bj ? bj : ai;
-            const int pr = lo * 3 - (lo * (lo - 1)) / 2 + (hi - lo);
-            const TL y = (ci == 0 && cj == 0) ? Yuu[pr] : ((ci == 1 && cj == 1) ? Yvv[pr] : Yuv[pr]);
-            val += sk * sm * y;
-            K[uidx(i, j)] += val;
-          }
-        }
-      }
-    }
-
-    // ---- basal friction (bottom face of the first layer), memoised 3x3 matrix per triangle
-    if (l == 0) {
-      const double* Mb = A.basal + 6 * (int64_t)t;
-      const double M[3][3] = {{Mb[0], Mb[1], Mb[2]}, {Mb[1], Mb[3], Mb[4]}, {Mb[2], Mb[4], Mb[5]}};
-#pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        Rl[0][a][0] += M[a][0] * ub[0] + M[a][1] * ub[1] + M[a][2] * ub[2];
-        Rl[0][a][1] += M[a][0] * vb[0] + M[a][1] * vb[1] + M[a][2] * vb[2];
-      }
-      if constexpr (MODE != MODE_RES) {
-#pragma unroll
-        for (int a = 0; a < 3; ++a)
-#pragma unroll
-          for (int b = a; b < 3; ++b)
-#pragma unroll
-            for (int c = 0; c < 2; ++c) K[uidx(2 * a + c, 2 * b + c)] += (TL)M[a][b];
-      }
-    }
-
-    // ---- scatter: residual of the bottom level is complete now; the top level is carried
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      scatter_add<ATOMIC>(A.R + ubase[a] + 2 * l, Rl[0][a][0] + carry[a][0]);
-      scatter_add<ATOMIC>(A.R + ubase[a] + 2 * l + 1, Rl[0][a][1] + carry[a][1]);
-      carry[a][0] = Rl[1][a][0];
-      carry[a][1] = Rl[1][a][1];
-    }
-    if constexpr (MODE != MODE_RES) {
-      TL* J = static_cast<TL*>(A.J);
-      int64_t rowbase[6], rowhalf[6];
-      int nlev[2], off[2][2];
-#pragma unroll
-      for (int k = 0; k < 2; ++k) {
-        nlev[k] = bp_nlev(l + k, L);
-        const int lmin = (l + k) > 0 ? (l + k - 1) : 0;
-#pragma unroll
-        for (int m = 0; m < 2; ++m) off[k][m] = l + m - lmin;
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-          rowbase[3 * k + a] = vs[a] + (int64_t)dg[a] * 4 * bp_levels_before(l + k);
-          rowhalf[3 * k + a] = 2LL * nlev[k] * dg[a];
-        }
-      }
-#pragma unroll
-      for (int i = 0; i < 12; ++i) {
-        const int ni = i >> 1, ci = i & 1, ki = ni / 3, ai = ni % 3;
-#pragma unroll
-        for (int j = i; j < 12; ++j) {
-          const int nj = j >> 1, cj = j & 1, kj = nj / 3, bj = nj % 3;
-          const TL val = K[uidx(i, j)];
-          const int64_t pij = rowbase[ni] + ci * rowhalf[ni] + 2 * (sl[3 * ai + bj] * nlev[ki] + off[ki][kj]) + cj;
-          scatter_add<ATOMIC>(J + pij, val);
-          if (i != j) {
-            const int64_t pji = rowbase[nj] + cj * rowhalf[nj] + 2 * (sl[3 * bj + ai] * nlev[kj] + off[kj][ki]) + ci;
-            scatter_add<ATOMIC>(J + pji, val);
-          }
-        }
-      }
-    }
-
-    // ---- shift the top level down
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      ub[a] = ut[a];
-      vb[a] = vt[a];
-    }
-    gubx = gutx;
-    guby = guty;
-    gvbx = gvtx;
-    gvby = gvty;
-  }
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    scatter_add<ATOMIC>(A.R + ubase[a] + 2 * L, carry[a][0]);
-    scatter_add<ATOMIC>(A.R + ubase[a] + 2 * L + 1, carry[a][1]);
-  }
+  assemble_column<MODE, TL, ATOMIC>(A, A.tri_list ? A.tri_list[idx] : idx);
 }
 
 AsmArgs make_args(const bp_mesh* m, const double* U, double* R, void* J) {
