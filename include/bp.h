@@ -29,6 +29,7 @@
  *   - the return value is a bp_status (0 = success);
  *   - device buffers U, R, J are owned by the caller; the mesh object owns the mesh arrays,
  *     the sparsity pattern and all scratch it needs, all on the device current at upload;
+ *   - velocity arrays U_dev must be 16-byte aligned (the kernels load (u, v) pairs together);
  *   - calls that take a stream are asynchronous on that stream (a cudaStream_t passed as
  *     void*, NULL = legacy default stream) unless documented as synchronising;
  *   - residual / Jacobian outputs are overwritten, never accumulated;
@@ -232,6 +233,45 @@ void bp_solve_opts_default(bp_solve_opts* opts);
  */
 int bp_newton_solve(bp_mesh* mesh, double* U_dev, const bp_solve_opts* opts, bp_solve_report* report,
                     void* stream);
+
+/* ------------------------------------------------------------------------------------------
+ * Ensemble assembly: many uneven meshes in one persistent launch.
+ * ------------------------------------------------------------------------------------------ */
+typedef struct bp_ensemble bp_ensemble; /* opaque */
+
+/*
+ * Bind `count` uploaded meshes (all on the current device) to their caller-owned buffers:
+ * U_dev[i] (input, ndof_i doubles), R_dev[i] (output residual, ndof_i doubles) and J_dev[i]
+ * (output Jacobian values, nnz_i of `precision`); pointer arrays are host arrays, read here only.
+ * The Jacobian uses the sum-factorised lanes.  Members are not copied: they must outlive the
+ * ensemble.  Errors: BP_EINVAL (NULL, count < 1, meshes on another device), BP_ENOMEM, BP_ECUDA.
+ */
+int bp_ensemble_create(bp_mesh* const* members, int count, const double* const* U_dev, double* const* R_dev,
+                       void* const* J_dev, int precision, void* stream, bp_ensemble** out);
+
+/*
+ * Autotuner: times every candidate -- columns per thread block in {32, 64, 128, 256} times scatter
+ * mode {atomic: one persistent launch over a (member, tile) queue; coloured: one persistent launch
+ * per colour over all members' tiles of that colour} -- as the median of `reps` runs, keeps the
+ * fastest and captures the whole assembly (zero-initialisation + launches) in a CUDA graph.
+ * times_ms[8] (nullable) receives the medians in the order cpb-major, atomic then coloured;
+ * chosen[2] (nullable) receives (columns per block, scatter).  Synchronises `stream`.
+ */
+int bp_ensemble_tune(bp_ensemble* ens, int reps, void* stream, double* times_ms, int* chosen);
+
+/* Use the given candidate (cpb in {32, 64, 128, 256}, scatter BP_SCATTER_ATOMIC or
+ * BP_SCATTER_COLOR) instead of tuning: captures its graph.  Synchronises `stream`. */
+int bp_ensemble_select(bp_ensemble* ens, int cpb, int scatter, void* stream);
+
+/*
+ * Assemble the residuals and Jacobians of all members (overwriting them): replays the tuned graph,
+ * or launches the default candidate (128 columns per block, atomic) if bp_ensemble_tune has not
+ * run.  Asynchronous on `stream`.
+ */
+int bp_ensemble_assemble(bp_ensemble* ens, void* stream);
+
+/* Free the ensemble (not its members).  Synchronises the device. */
+void bp_ensemble_free(bp_ensemble* ens);
 
 /*
  * Allocation-free variant of bp_assemble_jacobian (R not returned).  The paper has no

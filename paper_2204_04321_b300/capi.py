@@ -92,6 +92,11 @@ SIGNATURES = {
     "bp_initial_guess": (_I, [_P, _I, _P, _P]),
     "bp_solve_opts_default": (None, [_P]),
     "bp_newton_solve": (_I, [_P, _P, _P, _P, _P]),
+    "bp_ensemble_create": (_I, [_P, _I, _P, _P, _P, _I, _P, _P]),
+    "bp_ensemble_tune": (_I, [_P, _I, _P, _P, _P]),
+    "bp_ensemble_select": (_I, [_P, _I, _I, _P]),
+    "bp_ensemble_assemble": (_I, [_P, _P]),
+    "bp_ensemble_free": (None, [_P]),
 }
 
 _lock = threading.Lock()
@@ -244,6 +249,52 @@ def bp_newton_solve(handle, U, opts=None, stream=None, **kw):
     if rc not in (BP_OK, BP_ENOCONV):
         raise BPError(rc, "bp_newton_solve")
     return rc, rep.as_dict()
+
+
+class Ensemble:
+    """Many uploaded meshes with their buffers, assembled together (bp_ensemble_*)."""
+
+    CANDIDATES = [(cpb, sc) for cpb in (32, 64, 128, 256) for sc in (BP_SCATTER_ATOMIC, BP_SCATTER_COLOR)]
+
+    def __init__(self, meshes, U_list, precision=BP_F64, stream=None):
+        import torch
+        self.dms = [m if isinstance(m, DeviceMesh) else DeviceMesh(m) for m in meshes]
+        self.U = [u.contiguous() for u in U_list]
+        self.R = [torch.empty(d.ndof, dtype=torch.float64, device=d.device) for d in self.dms]
+        jt = torch.float64 if precision == BP_F64 else torch.float32
+        self.J = [torch.empty(d.nnz, dtype=jt, device=d.device) for d in self.dms]
+        n = len(self.dms)
+        arr = lambda xs: (ctypes.c_void_p * n)(*[ctypes.c_void_p(x) for x in xs])
+        out = ctypes.c_void_p()
+        _check(lib().bp_ensemble_create(arr([d.handle.value for d in self.dms]), n,
+                                        arr([u.data_ptr() for u in self.U]), arr([r.data_ptr() for r in self.R]),
+                                        arr([j.data_ptr() for j in self.J]), precision, _stream_ptr(stream),
+                                        ctypes.byref(out)), "bp_ensemble_create")
+        self.handle = out
+
+    def tune(self, reps=3, stream=None):
+        times = (ctypes.c_double * 8)()
+        chosen = (ctypes.c_int * 2)()
+        _check(lib().bp_ensemble_tune(self.handle, reps, _stream_ptr(stream), times, chosen), "bp_ensemble_tune")
+        return {f"cpb{c}-{'color' if sc == BP_SCATTER_COLOR else 'atomic'}": times[i]
+                for i, (c, sc) in enumerate(self.CANDIDATES)}, (chosen[0], chosen[1])
+
+    def select(self, cpb, scatter, stream=None):
+        _check(lib().bp_ensemble_select(self.handle, cpb, scatter, _stream_ptr(stream)), "bp_ensemble_select")
+
+    def assemble(self, stream=None):
+        _check(lib().bp_ensemble_assemble(self.handle, _stream_ptr(stream)), "bp_ensemble_assemble")
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            lib().bp_ensemble_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class DeviceMesh:

@@ -54,7 +54,7 @@ int launch(const bp_mesh* m, AsmArgs a, int scatter, cudaStream_t s) {
 }  // namespace
 
 extern "C" int bp_assemble_residual(bp_mesh* m, const double* U, double* R, void* stream) {
-  if (!m || !U || !R) return BP_EINVAL;
+  if (!m || !U || !R || !bp_aligned16(U)) return BP_EINVAL;
   bp_device_guard g(m->device);
   cudaStream_t s = (cudaStream_t)stream;
   BP_CUDA_TRY(cudaMemcpyAsync(R, m->load, m->ndof * sizeof(double), cudaMemcpyDeviceToDevice, s));
@@ -63,7 +63,7 @@ extern "C" int bp_assemble_residual(bp_mesh* m, const double* U, double* R, void
 
 extern "C" int bp_assemble_jacobian(bp_mesh* m, const double* U, double* R, void* J, int precision,
                                     int scatter, int method, void* stream) {
-  if (!m || !U || !J) return BP_EINVAL;
+  if (!m || !U || !J || !bp_aligned16(U)) return BP_EINVAL;
   if (precision != BP_F64 && precision != BP_F32) return BP_EINVAL;
   if (scatter < BP_SCATTER_AUTO || scatter > BP_SCATTER_COLOR) return BP_EINVAL;
   if (method < BP_JAC_AUTO || method > BP_JAC_FACTORED) return BP_EINVAL;
@@ -126,7 +126,7 @@ int noalloc_scratch(int device, double** out) {
 
 extern "C" int bp_assemble_jacobian_noalloc(bp_mesh* m, const double* U, void* J, int precision,
                                             int scatter, int method, void* stream) {
-  if (!m || !U || !J) return BP_EINVAL;
+  if (!m || !U || !J || !bp_aligned16(U)) return BP_EINVAL;
   if (precision != BP_F64 && precision != BP_F32) return BP_EINVAL;
   if (scatter < BP_SCATTER_AUTO || scatter > BP_SCATTER_COLOR) return BP_EINVAL;
   if (method < BP_JAC_AUTO || method > BP_JAC_FACTORED) return BP_EINVAL;

@@ -787,7 +787,7 @@ extern "C" void bp_solve_opts_default(bp_solve_opts* o) {
 
 extern "C" int bp_newton_solve(bp_mesh* m, double* U, const bp_solve_opts* opts, bp_solve_report* rep,
                                void* stream) {
-  if (!m || !U || !opts || !rep) return BP_EINVAL;
+  if (!m || !U || !opts || !rep || !bp_aligned16(U)) return BP_EINVAL;
   const bp_solve_opts o = *opts;
   if (!(o.rtol > 0) || o.max_newton < 0 || o.max_newton > 64 || o.max_krylov < 1 || o.check_every < 1 ||
       (o.precision != BP_F64 && o.precision != BP_F32) || o.krylov != BP_KRYLOV_CG || !(o.eta_max > 0))
