@@ -330,6 +330,28 @@ def run_ours(args):
     return 0
 
 
+def learned_start(capi, dm, dev):
+    """Mixed-precision solve from the committed learned warm start (residual-judged fallback)."""
+    import torch
+    from paper_2204_04321_b300 import learned
+    if not os.path.exists(learned.DEFAULT_WEIGHTS):
+        return None
+    net = capi.Mlp()
+    net.load(learned.DEFAULT_WEIGHTS)
+    times, rep, used = [], None, None
+    for _ in range(3):
+        U = torch.empty(dm.ndof, dtype=torch.float64, device=dev)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        used = capi.bp_initial_guess_learned(dm.handle, net, U)
+        rc, rep = capi.bp_newton_solve(dm.handle, U, precision=capi.BP_F32, max_krylov=4000)
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t0)
+    net.close()
+    return {"s": statistics.median(times), "newton_iters": rep["newton_iters"], "converged": rep["converged"],
+            "network_guess_kept": used, "initial_rel_residual": rep["history"][0]}
+
+
 def newton_section(capi, synth, dm, mesh, dev, skip_large=False):
     """Time to ||F(U)|| <= 1e-8 ||F(0)|| from the shallow-ice guess: plain FP64 path and the
     mixed-precision path (FP32 Jacobian lanes and Krylov, FP64 residual/viscosity/update)."""
@@ -357,6 +379,7 @@ def newton_section(capi, synth, dm, mesh, dev, skip_large=False):
     f32, U32 = solve(dm, capi.BP_F32)
     out[mesh.name] = {"f64": f64, "mixed_f32": f32, "speedup_mixed": f64["s"] / f32["s"],
                       "mixed_vs_f64_solution_rel_inf": float((U32 - U64).abs().max() / U64.abs().max())}
+    out[mesh.name]["learned_start_mixed"] = learned_start(capi, dm, dev)
     if not skip_large:
         big = synth.config_large()
         dmb = capi.DeviceMesh(big)

@@ -273,6 +273,60 @@ int bp_ensemble_assemble(bp_ensemble* ens, void* stream);
 /* Free the ensemble (not its members).  Synchronises the device. */
 void bp_ensemble_free(bp_ensemble* ens);
 
+/* ------------------------------------------------------------------------------------------
+ * Learned warm start (not in the paper): a per-column MLP 16 -> 128 -> 128 -> 128 -> 32 (ReLU)
+ * mapping column features to the 2 (L + 1) = 22 level velocities of a 10-layer column.
+ * BF16 operands, FP32 accumulation, on the 5th-generation tensor cores (tcgen05, TMEM).
+ * ------------------------------------------------------------------------------------------ */
+#define BP_MLP_IN 16
+#define BP_MLP_HIDDEN 128
+#define BP_MLP_OUT 32
+#define BP_MLP_OUT_USED 22   /* (u, v) at 11 node levels */
+#define BP_MLP_LEVELS 11
+typedef struct bp_mlp bp_mlp; /* opaque */
+
+/* Number of FP32 parameters: [W1 (128x16), b1, W2 (128x128), b2, W3 (128x128), b3, W4 (32x128), b4],
+ * weights row-major (out x in). */
+int64_t bp_mlp_param_count(void);
+/* New network on the current device, He-uniform weights from a counter-based generator
+ * (SplitMix64 of seed and parameter index), zero biases, fresh Adam state. */
+int bp_mlp_create(uint64_t seed, bp_mlp** out);
+void bp_mlp_free(bp_mlp* mlp);
+/* Copy the FP32 master parameters to / from host memory (n = bp_mlp_param_count()); setting resets
+ * Adam.  Synchronise `stream`. */
+int bp_mlp_get_params(const bp_mlp* mlp, float* host, int64_t n, void* stream);
+int bp_mlp_set_params(bp_mlp* mlp, const float* host, int64_t n, void* stream);
+/* Y[n][32] = MLP(X[n][16]); X is BF16 (raw uint16 bits), Y FP32.  Asynchronous. */
+int bp_mlp_forward(bp_mlp* mlp, const uint16_t* X_dev, int64_t n, float* Y_dev, void* stream);
+/* Loss (1/n) sum_rows sum_{j < 22} (Y - T)^2 and its gradient (FP32, parameter layout above,
+ * overwritten in grad_dev) for X[n][16] (BF16), T[n][32] (FP32).  *loss_host (nullable) receives
+ * the loss and makes the call synchronous.  Errors: BP_EINVAL, BP_ENOMEM, BP_ECUDA. */
+int bp_mlp_gradient(bp_mlp* mlp, const uint16_t* X_dev, const float* T_dev, int64_t n, float* grad_dev,
+                    double* loss_host, void* stream);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) with the gradient of the batch; asynchronous. */
+int bp_mlp_train_step(bp_mlp* mlp, const uint16_t* X_dev, const float* T_dev, int64_t n, float lr,
+                      void* stream);
+/* Column features X[nv][16] (BF16) of an uploaded 10-layer mesh, built from the quantities
+ * q = (ln(H / 1000 m), asinh(1000 s_x) / 4, asinh(1000 s_y) / 4, ln(beta / 1000)) with the nodal
+ * grad s (area-weighted as for the shallow-ice guess): [0..7] hi/lo BF16 splits of the local q
+ * (about 16 significant bits), [8..11] q averaged over closed neighbourhoods in 8 sweeps (~5 km),
+ * [12..14] ln beta, s_x, s_y terms after 40 sweeps (~15 km), [15] sigma_1 (the layering).
+ * Errors: BP_EUNSUP if the mesh does not have 10 layers. */
+int bp_mlp_features(bp_mesh* mesh, uint16_t* X_dev, void* stream);
+/* Replace beta on an uploaded mesh (host array [nv]) and rebuild the basal friction matrices. */
+int bp_mesh_set_beta(bp_mesh* mesh, const double* beta_host, void* stream);
+/*
+ * Learned initial guess: per column and component c the network scales the sliding part
+ * b_c = u_sia,c(bed) and the deformation part d_c = u_sia,c - b_c of the shallow-ice profile,
+ * u_c = (1 + y_2c) b_c + (1 + y_2c+1) d_c, which keeps the vertical profile consistent (vertical
+ * shear dominates the stress on thin layers) and reduces to the shallow-ice guess where the network
+ * has learned nothing; written in the dof order.  Falls back to the
+ * shallow-ice guess when that has the smaller FP64 residual norm (the residual judges the
+ * prediction); *used (nullable) receives 1 if the network's prediction was kept, 0 otherwise.
+ * Synchronises `stream`.
+ */
+int bp_initial_guess_learned(bp_mesh* mesh, bp_mlp* mlp, double* U_dev, int* used, void* stream);
+
 /*
  * Allocation-free variant of bp_assemble_jacobian (R not returned).  The paper has no
  * counterpart: this entry point exists for callers that must not allocate device memory once

@@ -97,6 +97,17 @@ SIGNATURES = {
     "bp_ensemble_select": (_I, [_P, _I, _I, _P]),
     "bp_ensemble_assemble": (_I, [_P, _P]),
     "bp_ensemble_free": (None, [_P]),
+    "bp_mlp_param_count": (ctypes.c_int64, []),
+    "bp_mlp_create": (_I, [ctypes.c_uint64, _P]),
+    "bp_mlp_free": (None, [_P]),
+    "bp_mlp_get_params": (_I, [_P, _P, ctypes.c_int64, _P]),
+    "bp_mlp_set_params": (_I, [_P, _P, ctypes.c_int64, _P]),
+    "bp_mlp_forward": (_I, [_P, _P, ctypes.c_int64, _P, _P]),
+    "bp_mlp_gradient": (_I, [_P, _P, _P, ctypes.c_int64, _P, _P, _P]),
+    "bp_mlp_train_step": (_I, [_P, _P, _P, ctypes.c_int64, ctypes.c_float, _P]),
+    "bp_mlp_features": (_I, [_P, _P, _P]),
+    "bp_mesh_set_beta": (_I, [_P, _P, _P]),
+    "bp_initial_guess_learned": (_I, [_P, _P, _P, _P, _P]),
 }
 
 _lock = threading.Lock()
@@ -295,6 +306,81 @@ class Ensemble:
             self.close()
         except Exception:
             pass
+
+
+class Mlp:
+    """Per-column warm-start MLP (bp_mlp_*); X is a torch.bfloat16 [n, 16] CUDA tensor."""
+
+    def __init__(self, seed=0):
+        out = ctypes.c_void_p()
+        _check(lib().bp_mlp_create(ctypes.c_uint64(seed), ctypes.byref(out)), "bp_mlp_create")
+        self.handle = out
+        self.nparam = lib().bp_mlp_param_count()
+
+    def get_params(self):
+        p = np.empty(self.nparam, dtype=np.float32)
+        _check(lib().bp_mlp_get_params(self.handle, p.ctypes.data_as(ctypes.c_void_p), self.nparam, None),
+               "bp_mlp_get_params")
+        return p
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        _check(lib().bp_mlp_set_params(self.handle, p.ctypes.data_as(ctypes.c_void_p), self.nparam, None),
+               "bp_mlp_set_params")
+
+    def forward(self, X, Y=None, stream=None):
+        import torch
+        if Y is None:
+            Y = torch.empty(X.shape[0], 32, dtype=torch.float32, device=X.device)
+        _check(lib().bp_mlp_forward(self.handle, _dptr(X), X.shape[0], _dptr(Y), _stream_ptr(stream)),
+               "bp_mlp_forward")
+        return Y
+
+    def gradient(self, X, T, stream=None):
+        import torch
+        g = torch.empty(self.nparam, dtype=torch.float32, device=X.device)
+        loss = ctypes.c_double()
+        _check(lib().bp_mlp_gradient(self.handle, _dptr(X), _dptr(T), X.shape[0], _dptr(g), ctypes.byref(loss),
+                                     _stream_ptr(stream)), "bp_mlp_gradient")
+        return loss.value, g
+
+    def train_step(self, X, T, lr, stream=None):
+        _check(lib().bp_mlp_train_step(self.handle, _dptr(X), _dptr(T), X.shape[0], ctypes.c_float(lr),
+                                       _stream_ptr(stream)), "bp_mlp_train_step")
+
+    def save(self, path):
+        np.save(path, self.get_params())
+
+    def load(self, path):
+        self.set_params(np.load(path))
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            lib().bp_mlp_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def bp_mlp_features(handle, X, stream=None) -> None:
+    _check(lib().bp_mlp_features(handle, _dptr(X), _stream_ptr(stream)), "bp_mlp_features")
+
+
+def bp_mesh_set_beta(handle, beta, stream=None) -> None:
+    b = np.ascontiguousarray(beta, dtype=np.float64)
+    _check(lib().bp_mesh_set_beta(handle, b.ctypes.data_as(ctypes.c_void_p), _stream_ptr(stream)),
+           "bp_mesh_set_beta")
+
+
+def bp_initial_guess_learned(handle, mlp, U, stream=None) -> bool:
+    used = ctypes.c_int()
+    _check(lib().bp_initial_guess_learned(handle, mlp.handle, _dptr(U), ctypes.byref(used), _stream_ptr(stream)),
+           "bp_initial_guess_learned")
+    return bool(used.value)
 
 
 class DeviceMesh:

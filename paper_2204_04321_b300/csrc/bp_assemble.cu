@@ -1,4 +1,5 @@
 // Entry points of the fused residual / Jacobian assembly (the kernel body is in bp_column.cuh).
+#include <algorithm>
 #include <cmath>
 #include <mutex>
 

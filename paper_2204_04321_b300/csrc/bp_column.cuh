@@ -339,17 +339,19 @@ __device__ __forceinline__ void assemble_column(const AsmArgs& A, const int t) {
             const TL Wp = (TL)(-(1.0 / 3.0) * W * (r * r * r));
             const TL tau1 = (TL)(2.0 * invh[tp] * t1), tau2 = (TL)(2.0 * invh[tp] * t2);
             const TL fg1x = (TL)g1x, fexy = (TL)exy, fg2y = (TL)g2y;
+            // p_{(a,k),c} = psi_k alpha_{a,c} -/+ t_{a,c},  alpha = g_c,xy . Lambda_a,  t = lambda_a tau_c / 2
             TL p[12];
 #pragma unroll
-            for (int k = 0; k < 2; ++k)
-#pragma unroll
-              for (int a = 0; a < 3; ++a) {
-                const TL al1 = fg1x * (TL)lx[a] + fexy * (TL)ly[a];
-                const TL al2 = fexy * (TL)lx[a] + fg2y * (TL)ly[a];
-                const TL ps = (TL)psi(k, z), lp = (TL)(lam(a, tp) * dpsi(k));
-                p[2 * (3 * k + a)] = ps * al1 + lp * tau1;
-                p[2 * (3 * k + a) + 1] = ps * al2 + lp * tau2;
-              }
+            for (int a = 0; a < 3; ++a) {
+              const TL al1 = fg1x * (TL)lx[a] + fexy * (TL)ly[a];
+              const TL al2 = fexy * (TL)lx[a] + fg2y * (TL)ly[a];
+              const TL h = (TL)(0.5 * lam(a, tp));
+              const TL t1a = h * tau1, t2a = h * tau2;
+              p[2 * a] = (TL)psi(0, z) * al1 - t1a;
+              p[2 * a + 1] = (TL)psi(0, z) * al2 - t2a;
+              p[2 * (3 + a)] = (TL)psi(1, z) * al1 + t1a;
+              p[2 * (3 + a) + 1] = (TL)psi(1, z) * al2 + t2a;
+            }
 #pragma unroll
             for (int i = 0; i < 12; ++i) {
               const TL pw = Wp * p[i];
@@ -444,30 +446,46 @@ __device__ __forceinline__ void assemble_column(const AsmArgs& A, const int t) {
           flx[a] = (TL)lx[a];
           fly[a] = (TL)ly[a];
         }
+        // BV[a][k][b] = B(Lambda_a, V^k_b) for the four component pairs (uu, uv, vu, vv)
+        TL BV[3][2][3][4];
 #pragma unroll
-        for (int i = 0; i < 12; ++i) {
-          const int ni = i >> 1, ci = i & 1, ki = ni / 3, ai = ni % 3;
+        for (int a = 0; a < 3; ++a)
 #pragma unroll
-          for (int j = i; j < 12; ++j) {
-            const int nj = j >> 1, cj = j & 1, kj = nj / 3, bj = nj % 3;
-            const TL ax = flx[ai], ay = fly[ai], bx = flx[bj], by = fly[bj];
-            // B^{c_i c_j}(X, Y) for the in-plane pieces (Lambda has no z component)
-            auto Bxy = [&](TL Xx, TL Xy, TL Yx, TL Yy) -> TL {
-              if (ci == 0 && cj == 0) return TL(2) * Xx * Yx + TL(0.5) * Xy * Yy;
-              if (ci == 0 && cj == 1) return Xx * Yy + TL(0.5) * Xy * Yx;
-              if (ci == 1 && cj == 0) return TL(0.5) * Xx * Yy + Xy * Yx;
-              return TL(0.5) * Xx * Yx + TL(2) * Xy * Yy;
-            };
-            TL val = Q[ki][kj] * Bxy(ax, ay, bx, by);
-            const TL sm = (kj == 0) ? TL(-1) : TL(1);  // sign of psi_m'
-            const TL sk = (ki == 0) ? TL(-1) : TL(1);  // sign of psi_k'
-            val += sm * Bxy(ax, ay, Vx[ki][bj], Vy[ki][bj]);
-            val += sk * Bxy(Vx[kj][ai], Vy[kj][ai], bx, by);
+          for (int k = 0; k < 2; ++k)
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+              const TL xx = flx[a] * Vx[k][b], yy = fly[a] * Vy[k][b];
+              const TL xy = flx[a] * Vy[k][b], yx = fly[a] * Vx[k][b];
+              BV[a][k][b][0] = TL(2) * xx + TL(0.5) * yy;
+              BV[a][k][b][1] = xy + TL(0.5) * yx;
+              BV[a][k][b][2] = TL(0.5) * xy + yx;
+              BV[a][k][b][3] = TL(0.5) * xx + TL(2) * yy;
+            }
+        // per node pair (n1 = (a,k) <= n2 = (b,m)): the in-plane B(Lambda_a, Lambda_b) once, then
+        // K += Q_km BL + s_m BV[a][k][b] + s_k BV[b][m][a]^T + s_k s_m Y_ab   (s = sign of psi')
+#pragma unroll
+        for (int n1 = 0; n1 < 6; ++n1) {
+#pragma unroll
+          for (int n2 = n1; n2 < 6; ++n2) {
+            const int ki = n1 / 3, ai = n1 % 3, kj = n2 / 3, bj = n2 % 3;
+            const TL xx = flx[ai] * flx[bj], yy = fly[ai] * fly[bj];
+            const TL xy = flx[ai] * fly[bj], yx = fly[ai] * flx[bj];
+            const TL BL[4] = {TL(2) * xx + TL(0.5) * yy, xy + TL(0.5) * yx, TL(0.5) * xy + yx,
+                              TL(0.5) * xx + TL(2) * yy};
             const int lo = ai < bj ? ai : bj, hi = ai < bj ? bj : ai;
             const int pr = lo * 3 - (lo * (lo - 1)) / 2 + (hi - lo);
-            const TL y = (ci == 0 && cj == 0) ? Yuu[pr] : ((ci == 1 && cj == 1) ? Yvv[pr] : Yuv[pr]);
-            val += sk * sm * y;
-            K[uidx(i, j)] += val;
+            const TL Yc[4] = {Yuu[pr], Yuv[pr], Yuv[pr], Yvv[pr]};
+            const TL q = Q[ki][kj];
+            const TL sm = (kj == 0) ? TL(-1) : TL(1), sk = (ki == 0) ? TL(-1) : TL(1);
+#pragma unroll
+            for (int ci = 0; ci < 2; ++ci)
+#pragma unroll
+              for (int cj = 0; cj < 2; ++cj) {
+                const int i = 2 * n1 + ci, j = 2 * n2 + cj;
+                if (i > j) continue;
+                const int cd = 2 * ci + cj, dc = 2 * cj + ci;
+                K[uidx(i, j)] += q * BL[cd] + (sm * BV[ai][ki][bj][cd] + (sk * BV[bj][kj][ai][dc] + sk * sm * Yc[cd]));
+              }
           }
         }
       }

@@ -75,6 +75,9 @@ struct bp_mesh {
   int32_t* colidx = nullptr;
   double* load = nullptr;     // [ndof] driving-stress load rho g grad s . int N_i (solution independent)
   double* rscratch = nullptr; // [ndof] residual scratch for Jacobian calls with R = NULL
+  uint16_t* mlp_X = nullptr;  // [nv][16] BF16 features of the learned guess
+  float* mlp_Y = nullptr;     // [nv][32] network outputs
+  double* mlp_q = nullptr;    // [16][nv] feature quantities (local, ~5 km, ~15 km, scratch)
 
   int64_t device_bytes = 0;
   std::vector<void*> allocations;
@@ -82,6 +85,12 @@ struct bp_mesh {
 };
 
 void bp_solver_ws_free(bp_mesh* m);
+// nodal area-weighted surface gradient accumulators [3][nv] (sum area * grad s, sum area), in mesh scratch
+int bp_nodal_surface_gradient(bp_mesh* m, double** acc, cudaStream_t s);
+// ||v||_2 of an ndof vector (synchronous)
+int bp_norm2_host(bp_mesh* m, const double* v, cudaStream_t s, double* out);
+// scratch of the learned guess: features, outputs, a shallow-ice guess, a residual
+int bp_learned_scratch(bp_mesh* m, uint16_t** X, float** Y, double** Usia, double** R, double** red);
 
 // Allocation helper that records the pointer in the mesh (freed by bp_mesh_free).
 template <class T>

@@ -80,7 +80,7 @@ __global__ void k_colidx(const int64_t* __restrict__ rowptr, const int32_t* __re
 __global__ void k_memo(const double2* __restrict__ xy, const double* __restrict__ bed,
                        const double* __restrict__ thick, const double* __restrict__ beta,
                        const double* __restrict__ sigma, const int32_t* __restrict__ tri, int ntri, int L,
-                       double rho_g, double* __restrict__ load, double* __restrict__ basal) {
+                       double rho_g, double* __restrict__ load, double* __restrict__ basal, int do_load) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= ntri) return;
   int v[3];
@@ -105,7 +105,7 @@ __global__ void k_memo(const double2* __restrict__ xy, const double* __restrict_
     sy += s[a] * (x[a2] - x[a1]) * inv_d;
   }
   const double area = 0.5 * d;
-  for (int l = 0; l < L; ++l) {
+  for (int l = 0; do_load && l < L; ++l) {
     const double ds = sigma[l + 1] - sigma[l];
     const double hsum = ds * (H[0] + H[1] + H[2]);
     for (int a = 0; a < 3; ++a) {
@@ -312,7 +312,7 @@ extern "C" int bp_mesh_upload(const bp_mesh_desc* d, void* stream_, bp_mesh** ou
   k_rowptr<<<grid_rows, threads, 0, stream>>>(m->vstart, m->vdeg, nv, L, nnz, m->rowptr);
   k_colidx<<<grid_rows, threads, 0, stream>>>(m->rowptr, m->nbr_ptr, m->nbr_idx, nv, L, m->colidx);
   k_memo<<<(ntri + 127) / 128, 128, 0, stream>>>(m->xy, m->bed, m->thick, m->beta, m->sigma, m->tri, ntri, L,
-                                                 d->params.rho * d->params.g, m->load, m->basal);
+                                                 d->params.rho * d->params.g, m->load, m->basal, 1);
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
   if (e != cudaSuccess) {
@@ -340,5 +340,19 @@ extern "C" int bp_csr_pattern(const bp_mesh* m, const int64_t** rowptr, const in
   if (!m || !rowptr || !colidx) return BP_EINVAL;
   *rowptr = m->rowptr;
   *colidx = m->colidx;
+  return BP_OK;
+}
+
+extern "C" int bp_mesh_set_beta(bp_mesh* m, const double* beta, void* stream) {
+  if (!m || !beta) return BP_EINVAL;
+  for (int a = 0; a < m->nv; ++a)
+    if (!(beta[a] >= 0) || !std::isfinite(beta[a])) return BP_EMESH;
+  bp_device_guard g(m->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  BP_CUDA_TRY(cudaMemcpyAsync(m->beta, beta, m->nv * sizeof(double), cudaMemcpyHostToDevice, s));
+  k_memo<<<(m->ntri + 127) / 128, 128, 0, s>>>(m->xy, m->bed, m->thick, m->beta, m->sigma, m->tri, m->ntri, m->nl,
+                                               m->p.rho * m->p.g, m->load, m->basal, 0);
+  BP_CUDA_TRY(cudaGetLastError());
+  BP_CUDA_TRY(cudaStreamSynchronize(s));
   return BP_OK;
 }

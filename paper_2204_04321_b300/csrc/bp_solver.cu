@@ -698,6 +698,41 @@ void bp_solver_ws_free(bp_mesh* m) {
   m->ws = nullptr;
 }
 
+int bp_nodal_surface_gradient(bp_mesh* m, double** acc, cudaStream_t s) {
+  int rc = ensure_ws(m, s);
+  if (rc) return rc;
+  bp_solver_ws* w = m->ws;
+  BP_CUDA_TRY(cudaMemsetAsync(w->sia, 0, 3 * (size_t)m->nv * sizeof(double), s));
+  k_sia_accum<<<(m->ntri + 127) / 128, 128, 0, s>>>(m->xy, m->bed, m->thick, m->tri, m->ntri, w->sia, m->nv);
+  BP_CUDA_TRY(cudaGetLastError());
+  *acc = w->sia;
+  return BP_OK;
+}
+
+int bp_norm2_host(bp_mesh* m, const double* v, cudaStream_t s, double* out) {
+  int rc = ensure_ws(m, s);
+  if (rc) return rc;
+  double d;
+  if ((rc = dot_host(m, v, v, m->ndof, s, &d))) return rc;
+  *out = std::sqrt(d);
+  return BP_OK;
+}
+
+int bp_learned_scratch(bp_mesh* m, uint16_t** X, float** Y, double** Usia, double** R, double** red) {
+  int rc = ensure_ws(m, nullptr);
+  if (rc) return rc;
+  if (!m->mlp_X) {
+    if ((rc = bp_alloc(m, &m->mlp_X, 16 * (size_t)m->nv))) return rc;
+    if ((rc = bp_alloc(m, &m->mlp_Y, 32 * (size_t)m->nv))) return rc;
+  }
+  *X = m->mlp_X;
+  *Y = m->mlp_Y;
+  *Usia = m->ws->Ut;
+  *R = m->ws->R;
+  *red = m->ws->red;
+  return BP_OK;
+}
+
 extern "C" int bp_spmv(bp_mesh* m, const void* J, int precision, const double* x, double* y, void* stream) {
   if (!m || !J || !x || !y) return BP_EINVAL;
   if (precision != BP_F64 && precision != BP_F32) return BP_EINVAL;

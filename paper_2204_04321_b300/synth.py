@@ -15,9 +15,10 @@ Greenland / Antarctica datasets, which are not available:
   up to +-0.2 h per coordinate (boundary points slide along their edge), every quad
   split along the diagonal chosen by the in-circle predicate, i.e. the Delaunay
   triangulation of the jittered points; triangles counter-clockwise;
-* thickness: the radially symmetric dome H(r) = H0 (1 - (r/R)^(4/3))^(3/7), R = 200 km,
+* surface: the radially symmetric dome s(r) = H0 (1 - (r/R)^(4/3))^(3/7), R = 200 km,
   floored at H_min = 10 m so the whole square carries ice;
-* bed: flat, or b = A_b sin(2 pi x / lam) sin(2 pi y / lam) with A_b = 500 m, lam = 20 km;
+* bed: flat (H = s), or b = A_b sin(2 pi x / lam) sin(2 pi y / lam) with A_b = 500 m, lam = 20 km
+  beneath the same surface (H = max(s - b, H_min));
 * beta: lognormal with mean 1e3 Pa yr / m and log-sd 0.5, either iid per vertex or a
   Gaussian field with 10 km correlation length built from 512 random Fourier features;
 * velocities: iid uniform in [-100, 100] m/yr per node and component.
@@ -200,6 +201,23 @@ def lognormal_beta_field(xy: np.ndarray, seed: int, mean: float = BETA_MEAN,
     return np.exp(mu + log_sd * field)
 
 
+def lognormal_beta_field_torch(xy: np.ndarray, seed: int, device, mean: float = BETA_MEAN,
+                               log_sd: float = BETA_LOG_SD, corr_len: float = BETA_CORR_LEN,
+                               nfeat: int = N_FOURIER):
+    """The same field as `lognormal_beta_field` (same seeded draws, same formula), evaluated in FP64
+    with torch on `device` -- for generating many fields quickly.  Returns a numpy array."""
+    import torch
+    rng = np.random.default_rng(seed)
+    kvec = rng.normal(0.0, 1.0 / corr_len, size=(nfeat, 2))
+    phase = rng.uniform(0.0, 2.0 * math.pi, size=nfeat)
+    P = torch.as_tensor(xy, dtype=torch.float64, device=device)
+    arg = P @ torch.as_tensor(kvec.T, device=device) + torch.as_tensor(phase, device=device)[None, :]
+    field = torch.cos(arg).sum(dim=1)
+    field = (field - field.mean()) / field.std(correction=0)
+    mu = math.log(mean) - 0.5 * log_sd ** 2
+    return torch.exp(mu + log_sd * field).cpu().numpy()
+
+
 def uniform_sigma(nlayers: int) -> np.ndarray:
     return np.linspace(0.0, 1.0, nlayers + 1)
 
@@ -211,9 +229,17 @@ def random_velocity(mesh: Mesh, seed: int, amplitude: float = 100.0) -> np.ndarr
 
 def dome_mesh(m: int, nlayers: int, mesh_seed: int, beta_seed: int, H0: float = 2000.0,
               bed: str = "flat", beta: str = "iid", name: str = "") -> Mesh:
+    """Dome ice sheet on a jittered grid.  With the sinusoidal bed the ice surface keeps the dome
+    shape s(r) and the bed undulates beneath it (H = max(s - b, H_min)), as in bumpy-bed benchmark
+    set-ups; lifting the whole dome onto the bumps would give 15 % surface slopes."""
     xy, tri = jittered_grid(m, mesh_seed)
-    thick = dome_thickness(xy, H0=H0)
-    b = np.zeros(xy.shape[0]) if bed == "flat" else sinusoidal_bed(xy)
+    surface = dome_thickness(xy, H0=H0)
+    if bed == "flat":
+        b = np.zeros(xy.shape[0])
+        thick = surface
+    else:
+        b = sinusoidal_bed(xy)
+        thick = np.maximum(surface - b, H_MIN)
     be = (lognormal_beta_iid(xy.shape[0], beta_seed) if beta == "iid"
           else lognormal_beta_field(xy, beta_seed))
     return Mesh(xy=xy, tri=tri, bed=b, thick=thick, beta=be, sigma=uniform_sigma(nlayers),

@@ -198,3 +198,4 @@ def test_status_codes_from_device_side_calls():
     with pytest.raises(c.BPError) as e:
         c.bp_assemble_jacobian(dm.handle, U, None, J, method=9)
     assert e.value.status == c.BP_EINVAL
+

@@ -1,0 +1,191 @@
+"""Tensor-core MLP kernels (through the C ABI) against the CPU oracle of the same network.
+
+The oracle rounds exactly the tensor-core operands to BF16 and accumulates in FP64, so the two
+differ by FP32 accumulation order -- plus the rare BF16 rounding of an intermediate that falls
+on the other side of a rounding boundary in FP32 than in FP64, which moves one activation by one
+BF16 step (2^-8) and the rows downstream of it.  Hence outputs are compared row by row (almost
+all rows to 1e-5, the rest within 5e-3) and gradients (sums over rows) normwise to 3e-3 -- far
+below what a wrong transpose, layout or mask would give (order 1)."""
+import os
+
+import numpy as np
+import pytest
+
+from oracle import mlp as omlp
+from paper_2204_04321_b300 import synth
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _need_cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+
+
+def capi():
+    from paper_2204_04321_b300 import capi as c
+    return c
+
+
+def rel(a, b):
+    return float(np.abs(a - b).max() / np.abs(b).max())
+
+
+def assert_rows_match(Y, Yo, tight=1e-5, loose=5e-3, max_frac=0.02):
+    """Nearly every row agrees to accumulation order; the few rows hit by a BF16 rounding flip of an
+    intermediate stay within a couple of BF16 steps.  A wrong layout or mask breaks every row."""
+    err = np.abs(Y - Yo).max(axis=1) / np.abs(Yo).max()
+    frac = float(np.mean(err > tight))
+    assert frac <= max_frac and err.max() <= loose, (frac, float(err.max()), float(np.median(err)))
+
+
+def batch(n, seed):
+    rng = np.random.default_rng(seed)
+    X = rng.normal(size=(n, 16))
+    X[:, 15] = 0.0
+    Xb = torch.as_tensor(X, dtype=torch.float32).to(torch.bfloat16).cuda()
+    T = torch.as_tensor(rng.normal(size=(n, 32)), dtype=torch.float32).cuda()
+    return Xb, Xb.float().double().cpu().numpy(), T
+
+
+@pytest.mark.parametrize("n", [128, 1000, 5000])
+def test_forward_matches_oracle(n):
+    net = capi().Mlp(seed=3)
+    Xb, X, _ = batch(n, n)
+    Y = net.forward(Xb).double().cpu().numpy()
+    Yo, _ = omlp.forward(net.get_params().astype(np.float64), X, bf16=True)
+    assert_rows_match(Y, Yo)
+
+
+@pytest.mark.parametrize("n", [256, 1000])
+def test_gradient_matches_oracle(n):
+    net = capi().Mlp(seed=4)
+    Xb, X, T = batch(n, 10 + n)
+    loss, g = net.gradient(Xb, T)
+    lo, go = omlp.loss_and_gradient(net.get_params().astype(np.float64), X, T.double().cpu().numpy(), bf16=True)
+    assert loss == pytest.approx(lo, rel=1e-5)
+    g = g.double().cpu().numpy()
+    # per parameter block (the bias and weight gradients differ in scale)
+    off = 0
+    for name, shp in omlp.SHAPES:
+        k = int(np.prod(shp))
+        assert rel(g[off:off + k], go[off:off + k]) <= 3e-3, name
+        off += k
+
+
+def test_adam_first_step_and_training_reduces_loss():
+    net = capi().Mlp(seed=5)
+    Xb, X, T = batch(2048, 77)
+    p0 = net.get_params().astype(np.float64)
+    _, g = net.gradient(Xb, T)
+    g = g.double().cpu().numpy()
+    lr = 1e-3
+    net.train_step(Xb, T, lr)
+    dp = net.get_params().astype(np.float64) - p0
+    big = np.abs(g) > 1e-2 * np.abs(g).max()
+    # first Adam step: m_hat = g, v_hat = g^2  =>  delta = -lr g / (|g| + eps)
+    np.testing.assert_allclose(dp[big], -lr * np.sign(g[big]), rtol=0, atol=1e-6)
+    l0 = net.gradient(Xb, T)[0]
+    for _ in range(300):
+        net.train_step(Xb, T, 2e-3)
+    assert net.gradient(Xb, T)[0] < 0.5 * l0
+
+
+def test_params_roundtrip_and_set_resets():
+    net = capi().Mlp(seed=6)
+    p = net.get_params()
+    q = np.random.default_rng(0).normal(size=p.shape).astype(np.float32)
+    net.set_params(q)
+    assert np.array_equal(net.get_params(), q)
+    Xb, X, _ = batch(300, 1)
+    Yo, _ = omlp.forward(q.astype(np.float64), X, bf16=True)
+    assert_rows_match(net.forward(Xb).double().cpu().numpy(), Yo)
+
+
+def feature_quantities(mesh):
+    """numpy statement of the feature pipeline: q (local), q after 8 and 40 neighbourhood sweeps."""
+    xy, tri = mesh.xy, mesh.tri
+    s = mesh.bed + mesh.thick
+    p = xy[tri]
+    ax, ay = p[:, 1, 0] - p[:, 0, 0], p[:, 1, 1] - p[:, 0, 1]
+    bx, by = p[:, 2, 0] - p[:, 0, 0], p[:, 2, 1] - p[:, 0, 1]
+    det = ax * by - ay * bx
+    d1, d2 = s[tri[:, 1]] - s[tri[:, 0]], s[tri[:, 2]] - s[tri[:, 0]]
+    sx, sy = (d1 * by - d2 * ay) / det, (ax * d2 - bx * d1) / det
+    area = 0.5 * det
+    acc = np.zeros((3, mesh.nv))
+    for a in range(3):
+        np.add.at(acc[0], tri[:, a], area * sx)
+        np.add.at(acc[1], tri[:, a], area * sy)
+        np.add.at(acc[2], tri[:, a], area)
+    q = np.stack([np.log(mesh.thick / 1000), 0.25 * np.arcsinh(1000 * acc[0] / acc[2]),
+                  0.25 * np.arcsinh(1000 * acc[1] / acc[2]), np.log(mesh.beta / 1000)])
+    nbr = [set() for _ in range(mesh.nv)]
+    for t in tri:
+        for a in t:
+            nbr[a].update(int(x) for x in t)
+    nbr = [np.array(sorted(n)) for n in nbr]
+    def sweep(v):
+        return np.stack([[v[k][n].mean() for n in nbr] for k in range(4)])
+    cur = q
+    for it in range(40):
+        cur = sweep(cur)
+        if it == 7:
+            q8 = cur
+    return q, q8, cur
+
+
+def test_features_match_numpy():
+    c = capi()
+    mesh = synth.dome_mesh(30, 10, 201, 202, bed="sinusoidal", beta="field")
+    dm = c.DeviceMesh(mesh)
+    X = torch.empty(mesh.nv, 16, dtype=torch.bfloat16, device="cuda")
+    c.bp_mlp_features(dm.handle, X)
+    got = X.double().cpu().numpy()
+    q, q8, q40 = feature_quantities(mesh)
+    for k in range(4):  # hi + lo reproduce the FP32 value of q to ~2^-16
+        rec = got[:, 2 * k] + got[:, 2 * k + 1]
+        assert np.abs(rec - q[k]).max() <= 2e-5 * max(1.0, np.abs(q[k]).max()), k
+    want = np.stack([q8[0], q8[1], q8[2], q8[3], q40[3], q40[1], q40[2]], 1)
+    assert np.abs(got[:, 8:15] - omlp.bf16_round(want)).max() <= 8e-3 * np.abs(want).max()
+    assert np.all(got[:, 15] == omlp.bf16_round(mesh.sigma[1]))
+    bad = synth.dome_mesh(6, 5, 1, 2)
+    dmb = c.DeviceMesh(bad)
+    with pytest.raises(c.BPError) as e:
+        c.bp_mlp_features(dmb.handle, X)
+    assert e.value.status == c.BP_EUNSUP
+
+
+def test_set_beta_matches_fresh_upload():
+    c = capi()
+    mesh = synth.dome_mesh(12, 10, 201, 202, bed="sinusoidal", beta="field")
+    dm = c.DeviceMesh(mesh)
+    beta2 = synth.lognormal_beta_field(mesh.xy, 999)
+    c.bp_mesh_set_beta(dm.handle, beta2)
+    mesh2 = synth.dome_mesh(12, 10, 201, 202, bed="sinusoidal", beta="field")
+    mesh2.beta = beta2
+    dm2 = c.DeviceMesh(mesh2)
+    U = torch.as_tensor(synth.random_velocity(mesh, 3), device="cuda")
+    J1, R1 = dm.jacobian(U, scatter=c.BP_SCATTER_COLOR)
+    J2, R2 = dm2.jacobian(U, scatter=c.BP_SCATTER_COLOR)
+    assert torch.equal(J1, J2)  # the coloured scatter is deterministic
+    # R starts from the driving-stress load, summed with atomics at upload: equal up to summation order
+    assert float((R1 - R2).abs().max() / R2.abs().max()) <= 1e-14
+    bt = synth.lognormal_beta_field_torch(mesh.xy, 999, "cuda")
+    assert np.abs(bt - beta2).max() <= 1e-12 * beta2.max()
+
+
+def test_learned_guess_falls_back_to_shallow_ice_for_untrained_network():
+    c = capi()
+    mesh = synth.dome_mesh(40, 10, 201, 202, bed="sinusoidal", beta="field")
+    dm = c.DeviceMesh(mesh)
+    net = c.Mlp(seed=11)
+    U = torch.empty(dm.ndof, dtype=torch.float64, device="cuda")
+    used = c.bp_initial_guess_learned(dm.handle, net, U)
+    S = torch.empty_like(U)
+    c.bp_initial_guess(dm.handle, c.BP_GUESS_SIA, S)
+    assert not used  # the untrained network's residual is larger: the shallow-ice guess is returned
+    assert float((U - S).abs().max() / S.abs().max()) <= 1e-13  # (its nodal gradient is summed with atomics)
