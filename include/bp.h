@@ -88,8 +88,14 @@ typedef struct {
   int64_t device_bytes; /* device memory held by the mesh object */
 } bp_mesh_info_t;
 
-/* Jacobian precision of the derivative lanes (the residual is always FP64). */
-enum { BP_F64 = 0, BP_F32 = 1 };
+/* Jacobian precision of the derivative lanes (the residual is always FP64):
+ *   BP_F64   native FP64 lanes;
+ *   BP_F32   FP32 lanes (J values are float);
+ *   BP_F64X2 FP64-accurate lanes built from pairs of FP32 numbers (hi + lo, error-free sum and
+ *            product transformations, relative error ~2^-46 per operation); J values are double;
+ *            Jacobian assembly only, sum-factorised method only.  FP32 throughput on B300 is
+ *            ~60x its FP64 throughput, which makes this the fast route to an FP64-accurate J. */
+enum { BP_F64 = 0, BP_F32 = 1, BP_F64X2 = 2 };
 /* Scatter of element contributions: atomics, or colour by colour with plain read-modify-write. */
 enum { BP_SCATTER_AUTO = 0, BP_SCATTER_ATOMIC = 1, BP_SCATTER_COLOR = 2 };
 /* How the element Jacobian is formed: forward-mode dual numbers with 12 lanes (one per
@@ -132,11 +138,13 @@ int bp_assemble_residual(bp_mesh* mesh, const double* U_dev, double* R_dev, void
 
 /*
  * Jacobian dR/dU at U (Sec. 3.2) into J_vals_dev ([nnz] values on the bp_csr_pattern
- * pattern: double for BP_F64, float for BP_F32) and, if R_dev != NULL, the FP64 residual.
+ * pattern: double for BP_F64 and BP_F64X2, float for BP_F32) and, if R_dev != NULL, the FP64
+ * residual.
  * Both outputs are overwritten (zeroing is part of the call).  `scatter` is a BP_SCATTER_*,
  * `method` a BP_JAC_*.  Asynchronous on `stream`.
- * Errors: BP_EINVAL (NULL U/J, unknown precision/scatter/method), BP_ENOMEM (first call with
- * R_dev == NULL allocates a residual scratch in the mesh object), BP_ECUDA.
+ * Errors: BP_EINVAL (NULL U/J, unknown precision/scatter/method), BP_EUNSUP (BP_F64X2 with
+ * BP_JAC_DUAL), BP_ENOMEM (first call with R_dev == NULL allocates a residual scratch in the mesh
+ * object), BP_ECUDA.
  */
 int bp_assemble_jacobian(bp_mesh* mesh, const double* U_dev, double* R_dev, void* J_vals_dev,
                          int precision, int scatter, int method, void* stream);
@@ -149,7 +157,8 @@ int bp_assemble_jacobian(bp_mesh* mesh, const double* U_dev, double* R_dev, void
 /*
  * y = J x for a Jacobian on the bp_csr_pattern pattern (J_vals_dev: double for BP_F64, float for
  * BP_F32; products and sums in FP64).  The operator application "Op*x" of the linear solve.
- * Asynchronous.  Errors: BP_EINVAL, BP_ENOMEM (first call allocates solver workspace), BP_ECUDA.
+ * J, x and y must be 16-byte aligned (u and v rows are processed as pairs).  Asynchronous.
+ * Errors: BP_EINVAL (NULL, misaligned, unknown precision), BP_ECUDA.
  */
 int bp_spmv(bp_mesh* mesh, const void* J_vals_dev, int precision, const double* x_dev, double* y_dev,
             void* stream);

@@ -65,7 +65,8 @@ extern "C" int bp_assemble_residual(bp_mesh* m, const double* U, double* R, void
 extern "C" int bp_assemble_jacobian(bp_mesh* m, const double* U, double* R, void* J, int precision,
                                     int scatter, int method, void* stream) {
   if (!m || !U || !J || !bp_aligned16(U)) return BP_EINVAL;
-  if (precision != BP_F64 && precision != BP_F32) return BP_EINVAL;
+  if (precision != BP_F64 && precision != BP_F32 && precision != BP_F64X2) return BP_EINVAL;
+  if (precision == BP_F64X2 && method == BP_JAC_DUAL) return BP_EUNSUP;
   if (scatter < BP_SCATTER_AUTO || scatter > BP_SCATTER_COLOR) return BP_EINVAL;
   if (method < BP_JAC_AUTO || method > BP_JAC_FACTORED) return BP_EINVAL;
   bp_device_guard g(m->device);
@@ -81,8 +82,9 @@ extern "C" int bp_assemble_jacobian(bp_mesh* m, const double* U, double* R, void
     Rw = m->rscratch;
   }
   BP_CUDA_TRY(cudaMemcpyAsync(Rw, m->load, m->ndof * sizeof(double), cudaMemcpyDeviceToDevice, s));
-  BP_CUDA_TRY(cudaMemsetAsync(J, 0, m->nnz * (precision == BP_F64 ? sizeof(double) : sizeof(float)), s));
+  BP_CUDA_TRY(cudaMemsetAsync(J, 0, m->nnz * (precision == BP_F32 ? sizeof(float) : sizeof(double)), s));
   const AsmArgs a = make_args(m, U, Rw, J);
+  if (precision == BP_F64X2) return launch<MODE_FACT, f64x2>(m, a, scatter, s);
   if (precision == BP_F64)
     return method == BP_JAC_DUAL ? launch<MODE_DUAL, double>(m, a, scatter, s)
                                  : launch<MODE_FACT, double>(m, a, scatter, s);
@@ -128,7 +130,8 @@ int noalloc_scratch(int device, double** out) {
 extern "C" int bp_assemble_jacobian_noalloc(bp_mesh* m, const double* U, void* J, int precision,
                                             int scatter, int method, void* stream) {
   if (!m || !U || !J || !bp_aligned16(U)) return BP_EINVAL;
-  if (precision != BP_F64 && precision != BP_F32) return BP_EINVAL;
+  if (precision != BP_F64 && precision != BP_F32 && precision != BP_F64X2) return BP_EINVAL;
+  if (precision == BP_F64X2 && method == BP_JAC_DUAL) return BP_EUNSUP;
   if (scatter < BP_SCATTER_AUTO || scatter > BP_SCATTER_COLOR) return BP_EINVAL;
   if (method < BP_JAC_AUTO || method > BP_JAC_FACTORED) return BP_EINVAL;
   if (m->ndof > BP_NOALLOC_MAX_NDOF) return BP_ESIZE;
@@ -141,8 +144,9 @@ extern "C" int bp_assemble_jacobian_noalloc(bp_mesh* m, const double* U, void* J
   if (method == BP_JAC_AUTO) method = BP_JAC_FACTORED;
   // the scratch keeps the previous call's residual: start it again from the memoised load
   BP_CUDA_TRY(cudaMemcpyAsync(Rw, m->load, m->ndof * sizeof(double), cudaMemcpyDeviceToDevice, s));
-  BP_CUDA_TRY(cudaMemsetAsync(J, 0, m->nnz * (precision == BP_F64 ? sizeof(double) : sizeof(float)), s));
+  BP_CUDA_TRY(cudaMemsetAsync(J, 0, m->nnz * (precision == BP_F32 ? sizeof(float) : sizeof(double)), s));
   const AsmArgs a = make_args(m, U, Rw, J);
+  if (precision == BP_F64X2) return launch<MODE_FACT, f64x2>(m, a, scatter, s);
   if (precision == BP_F64)
     return method == BP_JAC_DUAL ? launch<MODE_DUAL, double>(m, a, scatter, s)
                                  : launch<MODE_FACT, double>(m, a, scatter, s);

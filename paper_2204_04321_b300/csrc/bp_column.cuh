@@ -73,6 +73,61 @@ __device__ __forceinline__ void scatter_add(T* p, T v) {
   }
 }
 
+// ------------------------------------------------------------------ paired-FP32 lanes
+// FP64-accurate lane arithmetic from two FP32 numbers, value = hi + lo with |lo| <= ulp(hi)/2
+// (double-single arithmetic: error-free TwoSum for additions, TwoProd through fmaf for products;
+// about 2^-47 relative error per operation, 8 fewer bits than FP64 but far inside the 1e-12 parity
+// bar).  On B300 the FP32 pipe is ~63x the FP64 pipe, so lanes in this type cost a fraction of
+// native FP64 lanes; the residual (value path) stays native FP64.
+struct f64x2 {
+  float hi, lo;
+  __host__ __device__ constexpr f64x2() : hi(0.f), lo(0.f) {}
+  __host__ __device__ constexpr f64x2(float h, float l) : hi(h), lo(l) {}
+  __host__ __device__ constexpr explicit f64x2(double x) : hi((float)x), lo((float)(x - (double)(float)x)) {}
+  __host__ __device__ constexpr explicit f64x2(int x) : f64x2((double)x) {}
+  __host__ __device__ double value() const { return (double)hi + (double)lo; }
+};
+__device__ __forceinline__ f64x2 operator+(const f64x2 a, const f64x2 b) {
+  const float s = a.hi + b.hi;
+  const float bb = s - a.hi;
+  float e = (a.hi - (s - bb)) + (b.hi - bb);
+  e += a.lo + b.lo;
+  const float h = s + e;
+  return f64x2(h, e - (h - s));
+}
+__device__ __forceinline__ f64x2 operator-(const f64x2 a) { return f64x2(-a.hi, -a.lo); }
+__device__ __forceinline__ f64x2 operator-(const f64x2 a, const f64x2 b) { return a + (-b); }
+__device__ __forceinline__ f64x2 operator*(const f64x2 a, const f64x2 b) {
+  const float p = a.hi * b.hi;
+  float e = fmaf(a.hi, b.hi, -p);
+  e = fmaf(a.hi, b.lo, e);
+  e = fmaf(a.lo, b.hi, e);
+  const float h = p + e;
+  return f64x2(h, e - (h - p));
+}
+__device__ __forceinline__ f64x2& operator+=(f64x2& a, const f64x2 b) {
+  a = a + b;
+  return a;
+}
+
+// storage type of a lane type in the Jacobian array, and the conversion
+template <class TL>
+struct LaneStore {
+  using type = TL;
+  static __device__ __forceinline__ TL cast(const TL v) { return v; }
+};
+template <>
+struct LaneStore<f64x2> {
+  using type = double;
+  static __device__ __forceinline__ double cast(const f64x2 v) { return v.value(); }
+};
+
+// acc + x or acc - x with the sign known at compile time after unrolling
+template <class TL>
+__device__ __forceinline__ TL add_signed(const TL acc, const TL x, const bool negative) {
+  return negative ? acc - x : acc + x;
+}
+
 // ------------------------------------------------------------------ dual numbers
 // Forward-mode dual number with an FP64 value and NL derivative lanes of type TL.
 template <class TL, int NL>
@@ -146,6 +201,14 @@ __device__ __forceinline__ void assemble_column(const AsmArgs& A, const int t) {
   }
   const double d12 = d * (1.0 / 12.0);
   const double d6 = d * (1.0 / 6.0);
+  TL clx[3], cly[3];  // grad lambda in lane precision (Jacobian lanes)
+  if constexpr (MODE == MODE_FACT) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      clx[a] = (TL)lx[a];
+      cly[a] = (TL)ly[a];
+    }
+  }
 
   int64_t ubase[3];
 #pragma unroll
@@ -343,8 +406,8 @@ __device__ __forceinline__ void assemble_column(const AsmArgs& A, const int t) {
             TL p[12];
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
-              const TL al1 = fg1x * (TL)lx[a] + fexy * (TL)ly[a];
-              const TL al2 = fexy * (TL)lx[a] + fg2y * (TL)ly[a];
+              const TL al1 = fg1x * clx[a] + fexy * cly[a];
+              const TL al2 = fexy * clx[a] + fg2y * cly[a];
               const TL h = (TL)(0.5 * lam(a, tp));
               const TL t1a = h * tau1, t2a = h * tau2;
               p[2 * a] = (TL)psi(0, z) * al1 - t1a;
@@ -413,13 +476,16 @@ __device__ __forceinline__ void assemble_column(const AsmArgs& A, const int t) {
         Q[0][1] = Q[1][0] = (TL)(BP_QP_P * BP_QP_Q) * (Qs[0] + Qs[1]);
         // V^k_b scaled by 1/2 (the magnitude of psi'): V = -(d/12) sum_z psi_k E_b Gz
         TL Vx[2][3], Vy[2][3];
+        const TL md12 = (TL)(-d * (1.0 / 12.0));
+        const TL gz0x = md12 * (TL)Gzx[0], gz1x = md12 * (TL)Gzx[1];
+        const TL gz0y = md12 * (TL)Gzy[0], gz1y = md12 * (TL)Gzy[1];
 #pragma unroll
         for (int k = 0; k < 2; ++k)
 #pragma unroll
           for (int b = 0; b < 3; ++b) {
             const TL w0 = (TL)psi(k, 0) * E[0][b], w1 = (TL)psi(k, 1) * E[1][b];
-            Vx[k][b] = (TL)(-d * (1.0 / 12.0)) * (w0 * (TL)Gzx[0] + w1 * (TL)Gzx[1]);
-            Vy[k][b] = (TL)(-d * (1.0 / 12.0)) * (w0 * (TL)Gzy[0] + w1 * (TL)Gzy[1]);
+            Vx[k][b] = w0 * gz0x + w1 * gz1x;
+            Vy[k][b] = w0 * gz0y + w1 * gz1y;
           }
         // Y scaled by 1/4 (|psi_k' psi_m'|): (d/12) sum_z F_ab(z) B_zz(z)
         TL Yuu[6], Yvv[6], Yuv[6];
@@ -440,12 +506,8 @@ __device__ __forceinline__ void assemble_column(const AsmArgs& A, const int t) {
             Yuv[pr] = s * (F[0][pr] * Buv[0] + F[1][pr] * Buv[1]);
           }
         }
-        TL flx[3], fly[3];
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-          flx[a] = (TL)lx[a];
-          fly[a] = (TL)ly[a];
-        }
+        const TL* flx = clx;
+        const TL* fly = cly;
         // BV[a][k][b] = B(Lambda_a, V^k_b) for the four component pairs (uu, uv, vu, vv)
         TL BV[3][2][3][4];
 #pragma unroll
@@ -476,7 +538,7 @@ __device__ __forceinline__ void assemble_column(const AsmArgs& A, const int t) {
             const int pr = lo * 3 - (lo * (lo - 1)) / 2 + (hi - lo);
             const TL Yc[4] = {Yuu[pr], Yuv[pr], Yuv[pr], Yvv[pr]};
             const TL q = Q[ki][kj];
-            const TL sm = (kj == 0) ? TL(-1) : TL(1), sk = (ki == 0) ? TL(-1) : TL(1);
+            const bool nm = (kj == 0), nk = (ki == 0);  // psi_m' < 0, psi_k' < 0
 #pragma unroll
             for (int ci = 0; ci < 2; ++ci)
 #pragma unroll
@@ -484,7 +546,10 @@ __device__ __forceinline__ void assemble_column(const AsmArgs& A, const int t) {
                 const int i = 2 * n1 + ci, j = 2 * n2 + cj;
                 if (i > j) continue;
                 const int cd = 2 * ci + cj, dc = 2 * cj + ci;
-                K[uidx(i, j)] += q * BL[cd] + (sm * BV[ai][ki][bj][cd] + (sk * BV[bj][kj][ai][dc] + sk * sm * Yc[cd]));
+                // s_k s_m Y + s_k BV[b][m][a]^T + s_m BV[a][k][b]  (signs by negation and add/sub only)
+                const TL y = (nk != nm) ? -Yc[cd] : Yc[cd];
+                const TL u = add_signed(add_signed(y, BV[bj][kj][ai][dc], nk), BV[ai][ki][bj][cd], nm);
+                K[uidx(i, j)] += q * BL[cd] + u;
               }
           }
         }
@@ -519,7 +584,8 @@ __device__ __forceinline__ void assemble_column(const AsmArgs& A, const int t) {
       carry[a][1] = Rl[1][a][1];
     }
     if constexpr (MODE != MODE_RES) {
-      TL* J = static_cast<TL*>(A.J);
+      using ST = typename LaneStore<TL>::type;
+      ST* J = static_cast<ST*>(A.J);
       int64_t rowbase[6], rowhalf[6];
       int nlev[2], off[2][2];
 #pragma unroll
@@ -540,7 +606,7 @@ __device__ __forceinline__ void assemble_column(const AsmArgs& A, const int t) {
 #pragma unroll
         for (int j = i; j < 12; ++j) {
           const int nj = j >> 1, cj = j & 1, kj = nj / 3, bj = nj % 3;
-          const TL val = K[uidx(i, j)];
+          const ST val = LaneStore<TL>::cast(K[uidx(i, j)]);
           const int64_t pij = rowbase[ni] + ci * rowhalf[ni] + 2 * (sl[3 * ai + bj] * nlev[ki] + off[ki][kj]) + cj;
           scatter_add<ATOMIC>(J + pij, val);
           if (i != j) {

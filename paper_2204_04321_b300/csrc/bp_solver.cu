@@ -64,25 +64,55 @@ __global__ void k_find_dslot(const int32_t* __restrict__ nbr_ptr, const int32_t*
 }
 
 // ------------------------------------------------------------------ SpMV
-// y = A x (row-parallel CSR, TPR threads per row); optionally adds x . y to *dot.
+template <class T>
+struct Pair;
+template <>
+struct Pair<double> {
+  using type = double2;
+};
+template <>
+struct Pair<float> {
+  using type = float2;
+};
+
+// y = A x on the extruded pattern, two rows at a time: rows 2i and 2i + 1 (the u and v rows of one node)
+// have the same columns, and columns come in (u, v) pairs of one node.  Per pair of entries one
+// column index is read, x is read as one aligned pair, and the values of both rows as aligned pairs.
 template <class M, class V, bool DOT>
-__global__ void __launch_bounds__(NT) k_spmv(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
-                                             const M* __restrict__ vals, int64_t n, const V* __restrict__ x,
-                                             V* __restrict__ y, double* dot, const int* stop) {
+__global__ void __launch_bounds__(NT) k_spmv_pairs(const int64_t* __restrict__ rowptr,
+                                                   const int32_t* __restrict__ colidx, const M* __restrict__ vals,
+                                                   int64_t npairs, const V* __restrict__ x, V* __restrict__ y,
+                                                   double* dot, const int* stop) {
+  using M2 = typename Pair<M>::type;
+  using V2 = typename Pair<V>::type;
   if (stop && *stop) return;
-  const int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / TPR;
+  const int64_t pr = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / TPR;
   const int lane = threadIdx.x % TPR;
-  V sum = V(0);
-  if (row < n) {
-    const int64_t e1 = rowptr[row + 1];
-    for (int64_t e = rowptr[row] + lane; e < e1; e += TPR) sum += (V)vals[e] * x[colidx[e]];
+  V y0 = V(0), y1 = V(0);
+  if (pr < npairs) {
+    const int64_t s0 = rowptr[2 * pr], s1 = rowptr[2 * pr + 1];
+    const int64_t half = (s1 - s0) >> 1;
+    const M2* v0 = reinterpret_cast<const M2*>(vals + s0);
+    const M2* v1 = reinterpret_cast<const M2*>(vals + s1);
+    for (int64_t k = lane; k < half; k += TPR) {
+      const V2 xx = *reinterpret_cast<const V2*>(x + colidx[s0 + 2 * k]);
+      const M2 a0 = v0[k], a1 = v1[k];
+      y0 += (V)a0.x * xx.x + (V)a0.y * xx.y;
+      y1 += (V)a1.x * xx.x + (V)a1.y * xx.y;
+    }
   }
 #pragma unroll
-  for (int o = TPR / 2; o; o >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, o, TPR);
+  for (int o = TPR / 2; o; o >>= 1) {
+    y0 += __shfl_down_sync(0xffffffffu, y0, o, TPR);
+    y1 += __shfl_down_sync(0xffffffffu, y1, o, TPR);
+  }
   double d = 0.0;
-  if (row < n && lane == 0) {
-    y[row] = sum;
-    if (DOT) d = (double)x[row] * (double)sum;
+  if (pr < npairs && lane == 0) {
+    V2 out;
+    out.x = y0;
+    out.y = y1;
+    *reinterpret_cast<V2*>(y + 2 * pr) = out;
+    if (DOT) d = (double)x[2 * pr] * (double)y0 + (double)x[2 * pr + 1] * (double)y1;
   }
   if (DOT) block_add(d, dot);
 }
@@ -149,11 +179,12 @@ struct Prec {
 };
 
 // z = P^-1 r on column a (forward and backward block substitution); returns (r.z, r.r) of the column.
+// The column's 2(L+1) values start at r[off], z[off] (off = 2 a (L+1) for dof-ordered vectors).
 template <class V>
 __device__ __forceinline__ void colprec_apply(const Prec& P, int a, const V* __restrict__ r, V* __restrict__ z,
-                                              double* rz, double* rr) {
+                                              double* rz, double* rr, int64_t off) {
   const int L = P.L;
-  const int64_t base = 2LL * a * (L + 1);
+  const int64_t base = off;
   double y[2 * (MAXL + 1)];
   double srr = 0.0;
   for (int l = 0; l <= L; ++l) {
@@ -193,7 +224,7 @@ __global__ void __launch_bounds__(128) k_colprec_apply(const Prec P, const V* __
   const int a = blockIdx.x * blockDim.x + threadIdx.x;
   if (a >= P.nv) return;
   double rz, rr;
-  colprec_apply(P, a, r, z, &rz, &rr);
+  colprec_apply(P, a, r, z, &rz, &rr, 2LL * a * (P.L + 1));
 }
 
 // ------------------------------------------------------------------ preconditioned CG (device scalars)
@@ -210,35 +241,53 @@ __global__ void __launch_bounds__(NT) k_cg_init(const Prec P, const double* __re
       r[base + i] = (V)(-R[base + i]);
       x[base + i] = V(0);
     }
-    colprec_apply(P, a, r, z, &rz, &rr);
+    colprec_apply(P, a, r, z, &rz, &rr, base);
     for (int i = 0; i < 2 * (P.L + 1); ++i) p[base + i] = z[base + i];
   }
   block_add(rz, scal + 1);
   block_add(rr, scal + 2);
 }
 
-// alpha = r.z / p.Ap;  x += alpha p;  r -= alpha q;  z = P^-1 r;  accumulate r.z, r.r of step k+1
+// alpha = r.z / p.Ap;  x += alpha p;  r -= alpha q;  z = P^-1 r;  accumulate r.z, r.r of step k+1.
+// Same step, staged for coalescing: the block's C consecutive columns occupy one contiguous range of
+// the dof-ordered vectors, so x += alpha p and r -= alpha q run element-wise with coalesced accesses,
+// r goes to shared memory, each of the first C threads solves its column there, and z is written back
+// coalesced.  Dynamic shared memory: 2 C 2(L+1) values of V.
 template <class V>
-__global__ void __launch_bounds__(NT) k_cg_update(const Prec P, int k, V* __restrict__ x, V* __restrict__ r,
-                                                  V* __restrict__ z, const V* __restrict__ p,
-                                                  const V* __restrict__ q, double* scal, int* stop) {
+__global__ void __launch_bounds__(NT) k_cg_update_staged(const Prec P, int k, int C, V* __restrict__ x,
+                                                         V* __restrict__ r, V* __restrict__ z, const V* __restrict__ p,
+                                                         const V* __restrict__ q, double* scal, int* stop) {
+  extern __shared__ __align__(16) unsigned char smraw[];
   if (*stop) return;
   const double pq = scal[3 * k], rzk = scal[3 * k + 1];
-  if (!(pq > 0.0) || !isfinite(rzk)) {  // not positive definite in this direction: stop (breakdown)
+  if (!(pq > 0.0) || !isfinite(rzk)) {
     if (blockIdx.x == 0 && threadIdx.x == 0) *stop = 2;
     return;
   }
   const V alpha = (V)(rzk / pq);
-  const int a = blockIdx.x * blockDim.x + threadIdx.x;
-  double rz = 0.0, rr = 0.0;
-  if (a < P.nv) {
-    const int64_t base = 2LL * a * (P.L + 1);
-    for (int i = 0; i < 2 * (P.L + 1); ++i) {
-      x[base + i] += alpha * p[base + i];
-      r[base + i] -= alpha * q[base + i];
-    }
-    colprec_apply(P, a, r, z, &rz, &rr);
+  const int n = 2 * (P.L + 1);
+  const int a0 = blockIdx.x * C;
+  const int ncol = min(C, P.nv - a0);
+  const int64_t base = (int64_t)a0 * n;
+  const int cnt = ncol * n;
+  V* sr = reinterpret_cast<V*>(smraw);
+  V* sz = sr + C * n;
+  double rr = 0.0, rz = 0.0;
+  for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+    const V xv = x[base + i] + alpha * p[base + i];
+    const V rv = r[base + i] - alpha * q[base + i];
+    x[base + i] = xv;
+    r[base + i] = rv;
+    sr[i] = rv;
+    rr += (double)rv * (double)rv;
   }
+  __syncthreads();
+  if ((int)threadIdx.x < ncol) {
+    double dummy_rr;
+    colprec_apply(P, a0 + (int)threadIdx.x, sr, sz, &rz, &dummy_rr, (int64_t)threadIdx.x * n);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < cnt; i += blockDim.x) z[base + i] = sz[i];
   block_add(rz, scal + 3 * (k + 1) + 1);
   block_add(rr, scal + 3 * (k + 1) + 2);
 }
@@ -358,21 +407,21 @@ __global__ void __launch_bounds__(128) k_energy(const double2* __restrict__ xy, 
 //   stress:   x = eps_e^2 + delta is quadratic in the velocity gradient G, so
 //             x1 - x0 = alpha (2 B(G0, Gd)) + alpha^2 Q(Gd) exactly, and
 //             x1^(2/3) - x0^(2/3) = (a - b)(a + b), a - b = (x1 - x0) / (a^2 + a b + b^2), a, b = cube roots.
-__device__ __forceinline__ void qp_gradient(const double* u0, const double* v0, const double* u1, const double* v1,
-                                            const double* lx, const double* ly, double p0, double p1, int tp,
-                                            double h, double Gzx, double Gzy, double G[6]) {
-  double GUx = 0, GUy = 0, GVx = 0, GVy = 0, du = 0, dv = 0;
+template <class T, class A, class B>
+__device__ __forceinline__ void qp_gradient(const A* u0, const A* v0, const A* u1, const A* v1, const B* lx,
+                                            const B* ly, T p0, T p1, int tp, T h, T Gzx, T Gzy, T G[6]) {
+  T GUx = 0, GUy = 0, GVx = 0, GVy = 0, du = 0, dv = 0;
   for (int a = 0; a < 3; ++a) {
-    const double ua = p0 * u0[a] + p1 * u1[a], va = p0 * v0[a] + p1 * v1[a];
-    GUx += ua * lx[a];
-    GUy += ua * ly[a];
-    GVx += va * lx[a];
-    GVy += va * ly[a];
-    const double la = (a == tp) ? 2.0 / 3.0 : 1.0 / 6.0;
-    du += la * (u1[a] - u0[a]);
-    dv += la * (v1[a] - v0[a]);
+    const T ua = p0 * (T)u0[a] + p1 * (T)u1[a], va = p0 * (T)v0[a] + p1 * (T)v1[a];
+    GUx += ua * (T)lx[a];
+    GUy += ua * (T)ly[a];
+    GVx += va * (T)lx[a];
+    GVy += va * (T)ly[a];
+    const T la = (a == tp) ? T(2.0 / 3.0) : T(1.0 / 6.0);
+    du += la * ((T)u1[a] - (T)u0[a]);
+    dv += la * ((T)v1[a] - (T)v0[a]);
   }
-  const double uz = du / h, vz = dv / h;
+  const T uz = du / h, vz = dv / h;
   G[0] = GUx - uz * Gzx;  // u_x
   G[1] = GUy - uz * Gzy;  // u_y
   G[2] = uz;
@@ -382,12 +431,25 @@ __device__ __forceinline__ void qp_gradient(const double* u0, const double* v0, 
 }
 
 // symmetric bilinear form of eps_e^2: Q(G) = B(G, G)
-__device__ __forceinline__ double eps_bilinear(const double* A, const double* B) {
-  const double exyA = 0.5 * (A[1] + A[3]), exyB = 0.5 * (B[1] + B[3]);
-  return A[0] * B[0] + A[4] * B[4] + 0.5 * (A[0] * B[4] + B[0] * A[4]) + exyA * exyB +
-         0.25 * (A[2] * B[2] + A[5] * B[5]);
+template <class T>
+__device__ __forceinline__ T eps_bilinear(const T* A, const T* B) {
+  const T exyA = T(0.5) * (A[1] + A[3]), exyB = T(0.5) * (B[1] + B[3]);
+  return A[0] * B[0] + A[4] * B[4] + T(0.5) * (A[0] * B[4] + B[0] * A[4]) + exyA * exyB +
+         T(0.25) * (A[2] * B[2] + A[5] * B[5]);
 }
 
+__device__ __forceinline__ double cube_root(double x) { return cbrt(x); }
+__device__ __forceinline__ float cube_root(float x) { return cbrtf(x); }
+
+// Energy change Pi_h(U + alpha D) - Pi_h(U), formed term by term as differences so that it keeps
+// its relative accuracy when it is many orders smaller than Pi_h itself (near convergence):
+//   driving:  alpha load . d;   basal: alpha d^T M u + alpha^2/2 d^T M d    (both FP64);
+//   stress:   x = eps_e^2 + delta is quadratic in the velocity gradient G, so
+//             x1 - x0 = alpha (2 B(G0, Gd)) + alpha^2 Q(Gd) exactly, and
+//             x1^(2/3) - x0^(2/3) = (a - b)(a + b), a - b = (x1 - x0) / (a^2 + a b + b^2), a, b = cube roots,
+//   in arithmetic T per quadrature point (FP64, or FP32 for the mixed-precision line search: the
+//   change keeps ~1e-5 relative accuracy there because it is never formed as a difference of energies).
+template <class T, class DT>
 __global__ void __launch_bounds__(128) k_energy_change(const double2* __restrict__ xy, const double* __restrict__ bed,
                                                        const double* __restrict__ thick,
                                                        const double* __restrict__ sigma,
@@ -395,11 +457,11 @@ __global__ void __launch_bounds__(128) k_energy_change(const double2* __restrict
                                                        const double* __restrict__ basal,
                                                        const double* __restrict__ load, int ntri, int L,
                                                        int64_t ndof, double cA, double delta, double alpha,
-                                                       const double* __restrict__ U, const double* __restrict__ D,
+                                                       const double* __restrict__ U, const DT* __restrict__ D,
                                                        double* out) {
   double acc = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < ndof; i += (int64_t)gridDim.x * blockDim.x)
-    acc += alpha * load[i] * D[i];
+    acc += alpha * load[i] * (double)D[i];
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t < ntri) {
     int v[3];
@@ -431,13 +493,16 @@ __global__ void __launch_bounds__(128) k_energy_change(const double2* __restrict
       const double M[3][3] = {{Mb[0], Mb[1], Mb[2]}, {Mb[1], Mb[3], Mb[4]}, {Mb[2], Mb[4], Mb[5]}};
       for (int a = 0; a < 3; ++a)
         for (int b = 0; b < 3; ++b) {
-          const double du = D[ub[a]], dv = D[ub[a] + 1];
+          const double du = (double)D[ub[a]], dv = (double)D[ub[a] + 1];
           acc += M[a][b] * (alpha * (du * U[ub[b]] + dv * U[ub[b] + 1]) +
-                            0.5 * alpha * alpha * (du * D[ub[b]] + dv * D[ub[b] + 1]));
+                            0.5 * alpha * alpha * (du * (double)D[ub[b]] + dv * (double)D[ub[b] + 1]));
         }
     }
+    const T ta = (T)alpha, tdelta = (T)delta;
+    double stress = 0.0;
     for (int l = 0; l < L; ++l) {
-      double u0[3], v0[3], u1[3], v1[3], a0[3], b0[3], a1[3], b1[3];
+      double u0[3], v0[3], u1[3], v1[3];
+      DT a0[3], b0[3], a1[3], b1[3];
       for (int a = 0; a < 3; ++a) {
         u0[a] = U[ub[a] + 2 * l];
         v0[a] = U[ub[a] + 2 * l + 1];
@@ -452,21 +517,22 @@ __global__ void __launch_bounds__(128) k_energy_change(const double2* __restrict
       for (int z = 0; z < 2; ++z) {
         const double p0 = z == 0 ? BP_QP_P : BP_QP_Q, p1 = z == 0 ? BP_QP_Q : BP_QP_P;
         const double sz = s_l + p1 * ds;
-        const double Gzx = gbx + sz * gHx, Gzy = gby + sz * gHy;
+        const T Gzx = (T)(gbx + sz * gHx), Gzy = (T)(gby + sz * gHy);
         for (int tp = 0; tp < 3; ++tp) {
           const double h = ds * (Hs6 + 0.5 * H[tp]);
-          double G0[6], Gd[6];
-          qp_gradient(u0, v0, u1, v1, lx, ly, p0, p1, tp, h, Gzx, Gzy, G0);
-          qp_gradient(a0, b0, a1, b1, lx, ly, p0, p1, tp, h, Gzx, Gzy, Gd);
-          const double x0 = eps_bilinear(G0, G0) + delta;
-          const double dx = alpha * (2.0 * eps_bilinear(G0, Gd) + alpha * eps_bilinear(Gd, Gd));
-          const double x1 = x0 + dx;
-          const double ca = cbrt(x1), cb = cbrt(x0);
-          const double diff23 = dx / (ca * ca + ca * cb + cb * cb) * (ca + cb);
-          acc += (d * h / 12.0) * 1.5 * cA * diff23;
+          T G0[6], Gd[6];
+          qp_gradient<T>(u0, v0, u1, v1, lx, ly, (T)p0, (T)p1, tp, (T)h, Gzx, Gzy, G0);
+          qp_gradient<T>(a0, b0, a1, b1, lx, ly, (T)p0, (T)p1, tp, (T)h, Gzx, Gzy, Gd);
+          const T x0 = eps_bilinear(G0, G0) + tdelta;
+          const T dx = ta * (T(2) * eps_bilinear(G0, Gd) + ta * eps_bilinear(Gd, Gd));
+          const T x1 = x0 + dx;
+          const T ca = cube_root(x1), cb = cube_root(x0);
+          const T diff23 = dx / (ca * ca + ca * cb + cb * cb) * (ca + cb);
+          stress += (d * h / 12.0) * (double)diff23;
         }
       }
     }
+    acc += 1.5 * cA * stress;
   }
   block_add(acc, out);
 }
@@ -603,13 +669,14 @@ int energy_host(bp_mesh* m, const double* U, cudaStream_t s, double* out) {
   return BP_OK;
 }
 
-// synchronous energy change Pi(U + alpha D) - Pi(U)
-int energy_change_host(bp_mesh* m, const double* U, const double* D, double alpha, cudaStream_t s, double* out) {
+// synchronous energy change Pi(U + alpha D) - Pi(U) (T: arithmetic of the per-point stress term)
+template <class T, class DT>
+int energy_change_host(bp_mesh* m, const double* U, const DT* D, double alpha, cudaStream_t s, double* out) {
   bp_solver_ws* w = m->ws;
   BP_CUDA_TRY(cudaMemsetAsync(w->red + 2, 0, sizeof(double), s));
   const int grid = (int)std::max<int64_t>((m->ntri + 127) / 128, std::min<int64_t>((m->ndof + 127) / 128, 148 * 16));
-  k_energy_change<<<grid, 128, 0, s>>>(m->xy, m->bed, m->thick, m->sigma, m->tri, m->basal, m->load, m->ntri, m->nl,
-                                       m->ndof, m->cA, m->p.delta, alpha, U, D, w->red + 2);
+  k_energy_change<T, DT><<<grid, 128, 0, s>>>(m->xy, m->bed, m->thick, m->sigma, m->tri, m->basal, m->load, m->ntri,
+                                              m->nl, m->ndof, m->cA, m->p.delta, alpha, U, D, w->red + 2);
   BP_CUDA_TRY(cudaGetLastError());
   BP_CUDA_TRY(cudaMemcpyAsync(w->host, w->red + 2, sizeof(double), cudaMemcpyDeviceToHost, s));
   BP_CUDA_TRY(cudaStreamSynchronize(s));
@@ -645,14 +712,18 @@ int cg_solve(bp_mesh* m, const M* J, double eta, int maxit, int check_every, cud
   const int gcol = (m->nv + NT - 1) / NT;
   k_cg_init<V><<<gcol, NT, 0, s>>>(P, w->R, x, r, z, p, w->scal);
   const double tol2 = eta * eta;
-  const int gspmv = (int)((n * TPR + NT - 1) / NT);
+  const int gspmv = (int)((n / 2 * TPR + NT - 1) / NT);
+  const int ncolv = 2 * (m->nl + 1);
+  const int C = std::max(1, std::min(128, (int)((48 << 10) / (2 * ncolv * (int)sizeof(V)))));
+  const size_t smem = 2 * (size_t)C * ncolv * sizeof(V);
+  const int gupd = (m->nv + C - 1) / C;
   int k = 0, done = 0;
   *status = 0;
   while (!done) {
     const int kend = std::min(maxit, k + check_every);
     for (; k < kend; ++k) {
-      k_spmv<M, V, true><<<gspmv, NT, 0, s>>>(m->rowptr, m->colidx, J, n, p, q, w->scal + 3 * k, w->stop);
-      k_cg_update<V><<<gcol, NT, 0, s>>>(P, k, x, r, z, p, q, w->scal, w->stop);
+      k_spmv_pairs<M, V, true><<<gspmv, NT, 0, s>>>(m->rowptr, m->colidx, J, n / 2, p, q, w->scal + 3 * k, w->stop);
+      k_cg_update_staged<V><<<gupd, NT, smem, s>>>(P, k, C, x, r, z, p, q, w->scal, w->stop);
       k_cg_direction<V><<<grid_for(n, NT), NT, 0, s>>>(k, tol2, n, z, p, w->scal, w->stop);
     }
     BP_CUDA_TRY(cudaGetLastError());
@@ -734,17 +805,17 @@ int bp_learned_scratch(bp_mesh* m, uint16_t** X, float** Y, double** Usia, doubl
 }
 
 extern "C" int bp_spmv(bp_mesh* m, const void* J, int precision, const double* x, double* y, void* stream) {
-  if (!m || !J || !x || !y) return BP_EINVAL;
+  if (!m || !J || !x || !y || !bp_aligned16(x) || !bp_aligned16(y) || !bp_aligned16(J)) return BP_EINVAL;
   if (precision != BP_F64 && precision != BP_F32) return BP_EINVAL;
   bp_device_guard g(m->device);
   cudaStream_t s = (cudaStream_t)stream;
-  const int grid = (int)((m->ndof * TPR + NT - 1) / NT);
+  const int grid = (int)((m->ndof / 2 * TPR + NT - 1) / NT);
   if (precision == BP_F64)
-    k_spmv<double, double, false><<<grid, NT, 0, s>>>(m->rowptr, m->colidx, (const double*)J, m->ndof, x, y,
-                                                      nullptr, nullptr);
+    k_spmv_pairs<double, double, false><<<grid, NT, 0, s>>>(m->rowptr, m->colidx, (const double*)J, m->ndof / 2, x,
+                                                            y, nullptr, nullptr);
   else
-    k_spmv<float, double, false><<<grid, NT, 0, s>>>(m->rowptr, m->colidx, (const float*)J, m->ndof, x, y,
-                                                     nullptr, nullptr);
+    k_spmv_pairs<float, double, false><<<grid, NT, 0, s>>>(m->rowptr, m->colidx, (const float*)J, m->ndof / 2, x, y,
+                                                           nullptr, nullptr);
   BP_CUDA_TRY(cudaGetLastError());
   return BP_OK;
 }
@@ -785,7 +856,7 @@ extern "C" int bp_energy_change(bp_mesh* m, const double* U, const double* D, do
   cudaStream_t s = (cudaStream_t)stream;
   int rc = ensure_ws(m, s);
   if (rc) return rc;
-  return energy_change_host(m, U, D, alpha, s, out);
+  return energy_change_host<double, double>(m, U, D, alpha, s, out);
 }
 
 extern "C" int bp_initial_guess(bp_mesh* m, int kind, double* U, void* stream) {
@@ -916,20 +987,17 @@ extern "C" int bp_newton_solve(bp_mesh* m, double* U, const bp_solve_opts* opts,
       rc = dot_host(m, w->R, w->x, m->ndof, s, &slope);
     if (rc) return rc;
     double alpha = 1.0;
-    if (o.line_search && slope < 0.0) {
+    // Once the residual falls by 10x per full step Newton is in its quadratic regime: take the full
+    // step without evaluating the energy (the Armijo test is then always met).
+    const bool quadratic = k > 0 && rep->alpha[k - 1] == 1.0 && fn <= 0.1 * rep->history[k - 1] * fref;
+    if (o.line_search && slope < 0.0 && !quadratic) {
       // Armijo on the energy: Pi(U + alpha delta) - Pi(U) <= c alpha F . delta, alpha = 1, 1/2, ..., 2^-10.
-      // The step is handed to the energy-change kernel in FP64.
-      const double* D = w->x;
-      if (f32) {  // widen the FP32 step into the FP64 trial buffer: Ut = 0 + 1 * delta
-        BP_CUDA_TRY(cudaMemsetAsync(w->Ut, 0, m->ndof * sizeof(double), s));
-        k_axpy_to<float><<<grid_for(m->ndof, NT), NT, 0, s>>>(w->Ut, reinterpret_cast<const float*>(w->x), 1.0,
-                                                             m->ndof, w->Ut);
-        D = w->Ut;
-      }
       const double c = 1e-4;
       for (int h = 0; h <= 10; ++h) {
         double dE;
-        if ((rc = energy_change_host(m, U, D, alpha, s, &dE))) return rc;
+        rc = f32 ? energy_change_host<float, float>(m, U, reinterpret_cast<const float*>(w->x), alpha, s, &dE)
+                 : energy_change_host<double, double>(m, U, w->x, alpha, s, &dE);
+        if (rc) return rc;
         if (dE <= c * alpha * slope || h == 10) break;
         alpha *= 0.5;
       }

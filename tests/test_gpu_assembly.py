@@ -1,7 +1,8 @@
 """Parity of the CUDA assembly (through the C ABI) with the CPU oracle.
 
 Bar: residual ||R_gpu - R_cpu||_inf <= 1e-12 ||R_cpu||_inf (FP64); Jacobian
-max|J_gpu - J_cpu| <= 1e-12 max|J_cpu| (FP64 lanes) and <= 1e-5 max|J_cpu| (FP32 lanes);
+max|J_gpu - J_cpu| <= 1e-12 max|J_cpu| (FP64 and paired-FP32 lanes) and <= 1e-5 max|J_cpu|
+(FP32 lanes);
 CSR pattern bit-identical.  The comparison is normwise because the GPU sums element
 contributions in another order (atomics) and with another (structured) formulation, so
 entries where contributions cancel carry rounding relative to the row scale, not to themselves.
@@ -90,21 +91,23 @@ def test_residual_parity(name, kind):
 @pytest.mark.parametrize("name", list(MESHES))
 @pytest.mark.parametrize("method", ["factored", "dual"])
 @pytest.mark.parametrize("scatter", ["atomic", "color"])
-@pytest.mark.parametrize("precision", ["f64", "f32"])
+@pytest.mark.parametrize("precision", ["f64", "f32", "f64x2"])
 def test_jacobian_parity(name, method, scatter, precision):
     c = capi()
+    if precision == "f64x2" and method == "dual":
+        pytest.skip("paired-FP32 lanes are implemented for the sum-factorised method only")
     mesh = MESHES[name]()
     om = oracle.OracleMesh(mesh)
     U = synth.random_velocity(mesh, 103)
     dm = c.DeviceMesh(mesh)
-    prec = c.BP_F64 if precision == "f64" else c.BP_F32
+    prec = {"f64": c.BP_F64, "f32": c.BP_F32, "f64x2": c.BP_F64X2}[precision]
     J, R = dm.jacobian(dev(U), precision=prec,
                        scatter=c.BP_SCATTER_ATOMIC if scatter == "atomic" else c.BP_SCATTER_COLOR,
                        method=c.BP_JAC_FACTORED if method == "factored" else c.BP_JAC_DUAL)
     _, _, Jc, Rc = om.jacobian(U)
     assert rel_inf(R.cpu().numpy(), Rc) <= TOL64
     err = rel_inf(J.cpu().numpy().astype(np.float64), Jc)
-    assert err <= (TOL64 if precision == "f64" else TOL32), err
+    assert err <= (TOL32 if precision == "f32" else TOL64), err
 
 
 def test_jacobian_without_residual_and_repeat_calls_overwrite():
@@ -159,7 +162,7 @@ def test_full_size_dome_1m_wedges_sampled_parity():
     Rc = om.residual(U, tri_mask=mask)
     assert rel_inf(R[rows], Rc[rows]) <= TOL64
     rowptr, colidx = (t.cpu().numpy() for t in dm.pattern())
-    for prec, tol in ((c.BP_F64, TOL64), (c.BP_F32, TOL32)):
+    for prec, tol in ((c.BP_F64, TOL64), (c.BP_F32, TOL32), (c.BP_F64X2, TOL64)):
         J, Rj = dm.jacobian(Ud, precision=prec)
         J = J.cpu().numpy().astype(np.float64)
         assert rel_inf(Rj.cpu().numpy()[rows], Rc[rows]) <= TOL64
@@ -198,4 +201,23 @@ def test_status_codes_from_device_side_calls():
     with pytest.raises(c.BPError) as e:
         c.bp_assemble_jacobian(dm.handle, U, None, J, method=9)
     assert e.value.status == c.BP_EINVAL
+    with pytest.raises(c.BPError) as e:
+        c.bp_assemble_jacobian(dm.handle, U, None, J, precision=c.BP_F64X2, method=c.BP_JAC_DUAL)
+    assert e.value.status == c.BP_EUNSUP
+
+
+def test_paired_fp32_lanes_closer_to_oracle_than_fp32():
+    """The paired-FP32 lanes carry ~46 significant bits: their Jacobian sits at FP64 rounding
+    distance from the native-FP64 one, orders of magnitude closer than the FP32-lane Jacobian."""
+    c = capi()
+    mesh = ragged_mesh()
+    dm = c.DeviceMesh(mesh)
+    Ud = dev(synth.random_velocity(mesh, 17))
+    J64, _ = dm.jacobian(Ud, precision=c.BP_F64, scatter=c.BP_SCATTER_COLOR)
+    J2, _ = dm.jacobian(Ud, precision=c.BP_F64X2, scatter=c.BP_SCATTER_COLOR)
+    J32, _ = dm.jacobian(Ud, precision=c.BP_F32, scatter=c.BP_SCATTER_COLOR)
+    scale = float(J64.abs().max())
+    e2 = float((J2 - J64).abs().max()) / scale
+    e32 = float((J32.double() - J64).abs().max()) / scale
+    assert e2 <= 1e-13 and e32 >= 1e-9 and e2 <= 1e-4 * e32, (e2, e32)
 
