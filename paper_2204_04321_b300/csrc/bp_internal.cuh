@@ -31,6 +31,7 @@ struct bp_solver_ws {
   double* Lm = nullptr;       // [L][4][nv]   E_l G_{l-1}^-1 (block Thomas multipliers), l = 1..L
   double* Ginv = nullptr;     // [L+1][4][nv] inverses of the eliminated diagonal blocks
   double* Fu = nullptr;       // [L][4][nv]   super-diagonal blocks J(l, l+1)
+                              // (double, or float in the first half of each array: prec_f32)
   double *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr;  // Krylov vectors
   double* J = nullptr;        // [nnz] Jacobian values (double, or float in the first half)
   double* R = nullptr;        // [ndof] residual
@@ -43,6 +44,7 @@ struct bp_solver_ws {
   double* host = nullptr;     // pinned host mirror of scal / red
   int host_cap = 0;
   bool has_prec = false;
+  bool prec_f32 = false;      // factors stored as float (set up from an FP32 Jacobian)
 };
 
 struct bp_mesh {

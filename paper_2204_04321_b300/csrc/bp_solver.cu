@@ -12,21 +12,28 @@
 namespace {
 
 constexpr int MAXL = 64;       // largest layer count the column kernels handle
-constexpr int TPR = 8;         // SpMV threads per row (rows hold 2 nlev deg ~ 40 entries)
+constexpr int TPR = 4;         // SpMV threads per row pair (a pair holds 2 x 2 nlev deg ~ 80 entries)
 constexpr int NT = 256;        // threads per block of the vector kernels
 constexpr int SCAL_CAP = 8192; // Krylov iterations per linear solve (scalar history capacity)
+constexpr int GRID_CAP = 148 * 8;  // grid-stride kernels: 8 blocks of NT per SM
+constexpr int UPD_NT = 128;        // threads of the staged CG update (one warp solves the block's columns)
 
-__device__ __forceinline__ double warp_sum(double v) {
+// B300 issues FP64 at ~1/64 of the FP32 rate, so the vector kernels keep per-element reductions in
+// the vector type V and spend FP64 operations only on per-warp / per-block partial sums.
+template <class T>
+__device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll
   for (int o = 16; o; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
   return v;
 }
 
-// Block-wide sum of v, atomically added to *out.  Every thread of the block must call it.
-__device__ __forceinline__ void block_add(double v, double* out) {
+// Block-wide sum of v (summed in T within each warp, in FP64 across warps), atomically added to
+// *out.  Every thread of the block must call it.
+template <class T>
+__device__ __forceinline__ void block_add(T v, double* out) {
   __shared__ double sh[NT / 32];
   v = warp_sum(v);
-  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = (double)v;
   __syncthreads();
   if (threadIdx.x < 32) {
     double w = threadIdx.x < (blockDim.x >> 5) ? sh[threadIdx.x] : 0.0;
@@ -75,46 +82,78 @@ struct Pair<float> {
   using type = float2;
 };
 
-// y = A x on the extruded pattern, two rows at a time: rows 2i and 2i + 1 (the u and v rows of one node)
-// have the same columns, and columns come in (u, v) pairs of one node.  Per pair of entries one
-// column index is read, x is read as one aligned pair, and the values of both rows as aligned pairs.
+// y = A x on the extruded pattern, one row pair per group of TPR threads.  Rows 2i and 2i + 1 (the u
+// and v rows of node i = (a, l)) are adjacent in the CSR arrays and have the same columns: for each b
+// of the sorted closed neighbourhood of vertex a, levels lmin .. lmin + nlev - 1, components u, v.
+// Column indices are therefore rebuilt from the neighbour list instead of read from colidx (which
+// halves the bytes of an FP32 SpMV), x is read as aligned (u, v) pairs and the values of both rows as
+// aligned pairs.  The two row sums are folded with one add per lane per step (after the first step
+// the lower half of the group carries row 2i, the upper half row 2i + 1).  With DOT, x . y is added
+// to *dot (summed in V per thread, in FP64 across threads, one atomic per block).  Grid-stride over
+// row pairs.
 template <class M, class V, bool DOT>
 __global__ void __launch_bounds__(NT) k_spmv_pairs(const int64_t* __restrict__ rowptr,
-                                                   const int32_t* __restrict__ colidx, const M* __restrict__ vals,
-                                                   int64_t npairs, const V* __restrict__ x, V* __restrict__ y,
-                                                   double* dot, const int* stop) {
+                                                   const int32_t* __restrict__ nbr_ptr,
+                                                   const int32_t* __restrict__ nbr_idx, int L,
+                                                   const M* __restrict__ vals, int npairs, const V* __restrict__ x,
+                                                   V* __restrict__ y, double* dot, const int* stop) {
   using M2 = typename Pair<M>::type;
   using V2 = typename Pair<V>::type;
   if (stop && *stop) return;
-  const int64_t pr = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / TPR;
   const int lane = threadIdx.x % TPR;
-  V y0 = V(0), y1 = V(0);
-  if (pr < npairs) {
-    const int64_t s0 = rowptr[2 * pr], s1 = rowptr[2 * pr + 1];
-    const int64_t half = (s1 - s0) >> 1;
-    const M2* v0 = reinterpret_cast<const M2*>(vals + s0);
-    const M2* v1 = reinterpret_cast<const M2*>(vals + s1);
-    for (int64_t k = lane; k < half; k += TPR) {
-      const V2 xx = *reinterpret_cast<const V2*>(x + colidx[s0 + 2 * k]);
-      const M2 a0 = v0[k], a1 = v1[k];
-      y0 += (V)a0.x * xx.x + (V)a0.y * xx.y;
-      y1 += (V)a1.x * xx.x + (V)a1.y * xx.y;
+  const bool upper = lane >= TPR / 2;
+  V d = V(0);  // this thread's part of x . y (in V; FP64 only across threads)
+  // warp-uniform loop bound: the shuffles below need all 32 lanes of the warp
+  const int stride = gridDim.x * (NT / TPR);
+  for (int base = blockIdx.x * (NT / TPR) + (threadIdx.x / 32) * (32 / TPR); base < npairs; base += stride) {
+    const int pr = base + (threadIdx.x % 32) / TPR;
+    V y0 = V(0), y1 = V(0);
+    if (pr < npairs) {
+      const int a = pr / (L + 1);
+      const int l = pr - a * (L + 1);
+      const int nlev = bp_nlev(l, L);
+      const int lmin = l > 0 ? l - 1 : 0;
+      const int64_t s0 = rowptr[2 * (int64_t)pr];
+      const int half = (int)((rowptr[2 * (int64_t)pr + 1] - s0) >> 1);  // column pairs per row = deg nlev
+      const int32_t* nb = nbr_idx + nbr_ptr[a];
+      const M2* v0 = reinterpret_cast<const M2*>(vals + s0);
+      const M2* v1 = v0 + half;
+      int sl = lane / nlev;  // k = sl nlev + dl
+      int dl = lane - sl * nlev;
+      for (int k = lane; k < half; k += TPR) {
+        const int b = __ldg(nb + sl);
+        const V2 xx = *reinterpret_cast<const V2*>(x + 2 * ((int64_t)b * (L + 1) + lmin + dl));
+        const M2 a0 = v0[k], a1 = v1[k];
+        y0 += (V)a0.x * xx.x + (V)a0.y * xx.y;
+        y1 += (V)a1.x * xx.x + (V)a1.y * xx.y;
+        dl += TPR;
+        while (dl >= nlev) {
+          dl -= nlev;
+          ++sl;
+        }
+      }
+    }
+    V keep = upper ? y1 : y0;
+    keep += __shfl_xor_sync(0xffffffffu, upper ? y0 : y1, TPR / 2, TPR);
+#pragma unroll
+    for (int o = TPR / 4; o; o >>= 1) keep += __shfl_xor_sync(0xffffffffu, keep, o, TPR);
+    if (pr < npairs && (lane == 0 || lane == TPR / 2)) {
+      const int64_t row = 2 * (int64_t)pr + (upper ? 1 : 0);
+      y[row] = keep;
+      if (DOT) d += x[row] * keep;
     }
   }
-#pragma unroll
-  for (int o = TPR / 2; o; o >>= 1) {
-    y0 += __shfl_down_sync(0xffffffffu, y0, o, TPR);
-    y1 += __shfl_down_sync(0xffffffffu, y1, o, TPR);
+  if (DOT) {  // only lanes 0 and TPR / 2 of each group hold a partial: one warp adds them
+    __shared__ double sd[2 * NT / TPR];
+    if (lane == 0 || lane == TPR / 2) sd[2 * (threadIdx.x / TPR) + (upper ? 1 : 0)] = (double)d;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      double w = 0.0;
+      for (int i = threadIdx.x; i < 2 * NT / TPR; i += 32) w += sd[i];
+      w = warp_sum(w);
+      if (threadIdx.x == 0) atomicAdd(dot, w);
+    }
   }
-  double d = 0.0;
-  if (pr < npairs && lane == 0) {
-    V2 out;
-    out.x = y0;
-    out.y = y1;
-    *reinterpret_cast<V2*>(y + 2 * pr) = out;
-    if (DOT) d = (double)x[2 * pr] * (double)y0 + (double)x[2 * pr + 1] * (double)y1;
-  }
-  if (DOT) block_add(d, dot);
 }
 
 // ------------------------------------------------------------------ column preconditioner
@@ -124,14 +163,15 @@ __device__ __forceinline__ int64_t col_entry(int64_t vs, int dg, int ds, int l, 
   return vs + (int64_t)dg * (4 * bp_levels_before(l) + 2 * c * nl) + 2 * (ds * nl + lp - lmin) + cp;
 }
 
-// Block Thomas elimination of the column's block-tridiagonal part of J (2 x 2 blocks, FP64):
+// Block Thomas elimination of the column's block-tridiagonal part of J (2 x 2 blocks, FP64 arithmetic,
+// factors stored as F):
 //   G_0 = D_0,  Lm_l = E_l G_{l-1}^-1,  G_l = D_l - Lm_l F_{l-1},  store Lm_l, G_l^-1, F_l.
-template <class M>
+template <class M, class F>
 __global__ void __launch_bounds__(128) k_colprec_setup(const M* __restrict__ J, const int64_t* __restrict__ vstart,
                                                        const int32_t* __restrict__ vdeg,
                                                        const int32_t* __restrict__ dslot, int nv, int L,
-                                                       double* __restrict__ Lm, double* __restrict__ Ginv,
-                                                       double* __restrict__ Fu) {
+                                                       F* __restrict__ Lm, F* __restrict__ Ginv,
+                                                       F* __restrict__ Fu) {
   const int a = blockIdx.x * blockDim.x + threadIdx.x;
   if (a >= nv) return;
   const int64_t vs = vstart[a];
@@ -151,7 +191,7 @@ __global__ void __launch_bounds__(128) k_colprec_setup(const M* __restrict__ J, 
       G[2] -= Lmat[2] * Fp[0] + Lmat[3] * Fp[2];
       G[3] -= Lmat[2] * Fp[1] + Lmat[3] * Fp[3];
 #pragma unroll
-      for (int e = 0; e < 4; ++e) Lm[((int64_t)(l - 1) * 4 + e) * nv + a] = Lmat[e];
+      for (int e = 0; e < 4; ++e) Lm[((int64_t)(l - 1) * 4 + e) * nv + a] = (F)Lmat[e];
     }
     const double idet = 1.0 / (G[0] * G[3] - G[1] * G[2]);
     Gp[0] = G[3] * idet;
@@ -159,68 +199,74 @@ __global__ void __launch_bounds__(128) k_colprec_setup(const M* __restrict__ J, 
     Gp[2] = -G[2] * idet;
     Gp[3] = G[0] * idet;
 #pragma unroll
-    for (int e = 0; e < 4; ++e) Ginv[((int64_t)l * 4 + e) * nv + a] = Gp[e];
+    for (int e = 0; e < 4; ++e) Ginv[((int64_t)l * 4 + e) * nv + a] = (F)Gp[e];
     if (l < L) {
       Fp[0] = at(l, 0, l + 1, 0);
       Fp[1] = at(l, 0, l + 1, 1);
       Fp[2] = at(l, 1, l + 1, 0);
       Fp[3] = at(l, 1, l + 1, 1);
 #pragma unroll
-      for (int e = 0; e < 4; ++e) Fu[((int64_t)l * 4 + e) * nv + a] = Fp[e];
+      for (int e = 0; e < 4; ++e) Fu[((int64_t)l * 4 + e) * nv + a] = (F)Fp[e];
     }
   }
 }
 
+template <class F>
 struct Prec {
-  const double* Lm;
-  const double* Ginv;
-  const double* Fu;
+  const F* Lm;
+  const F* Ginv;
+  const F* Fu;
   int nv, L;
 };
 
-// z = P^-1 r on column a (forward and backward block substitution); returns (r.z, r.r) of the column.
-// The column's 2(L+1) values start at r[off], z[off] (off = 2 a (L+1) for dof-ordered vectors).
-template <class V>
-__device__ __forceinline__ void colprec_apply(const Prec& P, int a, const V* __restrict__ r, V* __restrict__ z,
+// z = P^-1 r on column a (forward and backward block substitution, arithmetic in F); returns (r.z, r.r)
+// of the column.  The column's 2(L+1) values start at r[off], z[off] (off = 2 a (L+1) for dof-ordered
+// vectors).  The forward sweep's intermediate y is kept in z itself (V is at least as wide as F).
+template <class V, class F>
+__device__ __forceinline__ void colprec_apply(const Prec<F>& P, int a, const V* __restrict__ r, V* __restrict__ z,
                                               double* rz, double* rr, int64_t off) {
   const int L = P.L;
   const int64_t base = off;
-  double y[2 * (MAXL + 1)];
-  double srr = 0.0;
+  const int64_t nv = P.nv;
+  F srr = F(0), p0 = F(0), p1 = F(0);
+#pragma unroll 4
   for (int l = 0; l <= L; ++l) {
-    double r0 = (double)r[base + 2 * l], r1 = (double)r[base + 2 * l + 1];
+    F r0 = (F)r[base + 2 * l], r1 = (F)r[base + 2 * l + 1];
     srr += r0 * r0 + r1 * r1;
     if (l > 0) {
-      const double* Lp = P.Lm + (int64_t)(l - 1) * 4 * P.nv + a;
-      r0 -= Lp[0] * y[2 * l - 2] + Lp[P.nv] * y[2 * l - 1];
-      r1 -= Lp[2 * (int64_t)P.nv] * y[2 * l - 2] + Lp[3 * (int64_t)P.nv] * y[2 * l - 1];
+      const F* Lp = P.Lm + (int64_t)(l - 1) * 4 * nv + a;
+      r0 -= Lp[0] * p0 + Lp[nv] * p1;
+      r1 -= Lp[2 * nv] * p0 + Lp[3 * nv] * p1;
     }
-    y[2 * l] = r0;
-    y[2 * l + 1] = r1;
+    z[base + 2 * l] = (V)r0;
+    z[base + 2 * l + 1] = (V)r1;
+    p0 = r0;
+    p1 = r1;
   }
-  double srz = 0.0;
+  F srz = F(0);
+#pragma unroll 4
   for (int l = L; l >= 0; --l) {
-    double t0 = y[2 * l], t1 = y[2 * l + 1];
+    F t0 = (F)z[base + 2 * l], t1 = (F)z[base + 2 * l + 1];
     if (l < L) {
-      const double* Fp = P.Fu + (int64_t)l * 4 * P.nv + a;
-      t0 -= Fp[0] * y[2 * l + 2] + Fp[P.nv] * y[2 * l + 3];
-      t1 -= Fp[2 * (int64_t)P.nv] * y[2 * l + 2] + Fp[3 * (int64_t)P.nv] * y[2 * l + 3];
+      const F* Fp = P.Fu + (int64_t)l * 4 * nv + a;
+      t0 -= Fp[0] * p0 + Fp[nv] * p1;
+      t1 -= Fp[2 * nv] * p0 + Fp[3 * nv] * p1;
     }
-    const double* Gp = P.Ginv + (int64_t)l * 4 * P.nv + a;
-    const double z0 = Gp[0] * t0 + Gp[P.nv] * t1;
-    const double z1 = Gp[2 * (int64_t)P.nv] * t0 + Gp[3 * (int64_t)P.nv] * t1;
-    y[2 * l] = z0;
-    y[2 * l + 1] = z1;
+    const F* Gp = P.Ginv + (int64_t)l * 4 * nv + a;
+    const F z0 = Gp[0] * t0 + Gp[nv] * t1;
+    const F z1 = Gp[2 * nv] * t0 + Gp[3 * nv] * t1;
     z[base + 2 * l] = (V)z0;
     z[base + 2 * l + 1] = (V)z1;
-    srz += (double)r[base + 2 * l] * z0 + (double)r[base + 2 * l + 1] * z1;
+    p0 = z0;
+    p1 = z1;
+    srz += (F)r[base + 2 * l] * z0 + (F)r[base + 2 * l + 1] * z1;
   }
-  *rz = srz;
-  *rr = srr;
+  *rz = (double)srz;
+  *rr = (double)srr;
 }
 
-template <class V>
-__global__ void __launch_bounds__(128) k_colprec_apply(const Prec P, const V* __restrict__ r, V* __restrict__ z) {
+template <class V, class F>
+__global__ void __launch_bounds__(128) k_colprec_apply(const Prec<F> P, const V* __restrict__ r, V* __restrict__ z) {
   const int a = blockIdx.x * blockDim.x + threadIdx.x;
   if (a >= P.nv) return;
   double rz, rr;
@@ -229,8 +275,8 @@ __global__ void __launch_bounds__(128) k_colprec_apply(const Prec P, const V* __
 
 // ------------------------------------------------------------------ preconditioned CG (device scalars)
 // scal[3k] = p_k . A p_k, scal[3k+1] = r_k . z_k, scal[3k+2] = r_k . r_k.
-template <class V>
-__global__ void __launch_bounds__(NT) k_cg_init(const Prec P, const double* __restrict__ R, V* __restrict__ x,
+template <class V, class F>
+__global__ void __launch_bounds__(NT) k_cg_init(const Prec<F> P, const double* __restrict__ R, V* __restrict__ x,
                                                 V* __restrict__ r, V* __restrict__ z, V* __restrict__ p,
                                                 double* scal) {
   const int a = blockIdx.x * blockDim.x + threadIdx.x;
@@ -252,19 +298,24 @@ __global__ void __launch_bounds__(NT) k_cg_init(const Prec P, const double* __re
 // Same step, staged for coalescing: the block's C consecutive columns occupy one contiguous range of
 // the dof-ordered vectors, so x += alpha p and r -= alpha q run element-wise with coalesced accesses,
 // r goes to shared memory, each of the first C threads solves its column there, and z is written back
-// coalesced.  Dynamic shared memory: 2 C 2(L+1) values of V.
-template <class V>
-__global__ void __launch_bounds__(NT) k_cg_update_staged(const Prec P, int k, int C, V* __restrict__ x,
+// coalesced.  alpha is formed once per block.  Dynamic shared memory: 2 C 2(L+1) values of V.
+template <class V, class F>
+__global__ void __launch_bounds__(UPD_NT) k_cg_update_staged(const Prec<F> P, int k, int C, V* __restrict__ x,
                                                          V* __restrict__ r, V* __restrict__ z, const V* __restrict__ p,
                                                          const V* __restrict__ q, double* scal, int* stop) {
   extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ V s_alpha;
+  __shared__ int s_bad;
   if (*stop) return;
-  const double pq = scal[3 * k], rzk = scal[3 * k + 1];
-  if (!(pq > 0.0) || !isfinite(rzk)) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) *stop = 2;
-    return;
+  if (threadIdx.x == 0) {
+    const double pq = scal[3 * k], rzk = scal[3 * k + 1];
+    s_bad = !(pq > 0.0) || !isfinite(rzk);
+    s_alpha = s_bad ? V(0) : (V)(rzk / pq);
+    if (s_bad && blockIdx.x == 0) *stop = 2;
   }
-  const V alpha = (V)(rzk / pq);
+  __syncthreads();
+  if (s_bad) return;
+  const V alpha = s_alpha;
   const int n = 2 * (P.L + 1);
   const int a0 = blockIdx.x * C;
   const int ncol = min(C, P.nv - a0);
@@ -272,14 +323,15 @@ __global__ void __launch_bounds__(NT) k_cg_update_staged(const Prec P, int k, in
   const int cnt = ncol * n;
   V* sr = reinterpret_cast<V*>(smraw);
   V* sz = sr + C * n;
-  double rr = 0.0, rz = 0.0;
+  V rr = V(0);
+  double rz = 0.0;
   for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
     const V xv = x[base + i] + alpha * p[base + i];
     const V rv = r[base + i] - alpha * q[base + i];
     x[base + i] = xv;
     r[base + i] = rv;
     sr[i] = rv;
-    rr += (double)rv * (double)rv;
+    rr += rv * rv;
   }
   __syncthreads();
   if ((int)threadIdx.x < ncol) {
@@ -292,19 +344,33 @@ __global__ void __launch_bounds__(NT) k_cg_update_staged(const Prec P, int k, in
   block_add(rr, scal + 3 * (k + 1) + 2);
 }
 
-// beta = r_{k+1}.z_{k+1} / r_k.z_k;  p = z + beta p;  stop once r.r <= tol2 r_0.r_0
+// beta = r_{k+1}.z_{k+1} / r_k.z_k;  p = z + beta p;  stop once r.r <= tol2 r_0.r_0.  The scalars are
+// formed once per block; the update runs on (u, v) pairs.
 template <class V>
-__global__ void __launch_bounds__(NT) k_cg_direction(int k, double tol2, int64_t n, const V* __restrict__ z,
+__global__ void __launch_bounds__(NT) k_cg_direction(int k, double tol2, int64_t npairs, const V* __restrict__ z,
                                                      V* __restrict__ p, const double* scal, int* stop) {
+  using V2 = typename Pair<V>::type;
+  __shared__ V s_beta;
+  __shared__ int s_done;
   if (*stop) return;
-  const double rr = scal[3 * (k + 1) + 2];
-  if (rr <= tol2 * scal[2] || !isfinite(rr)) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) *stop = 1;
-    return;
+  if (threadIdx.x == 0) {
+    const double rr = scal[3 * (k + 1) + 2];
+    s_done = rr <= tol2 * scal[2] || !isfinite(rr);
+    s_beta = (V)(scal[3 * (k + 1) + 1] / scal[3 * k + 1]);
+    if (s_done && blockIdx.x == 0) *stop = 1;
   }
-  const V beta = (V)(scal[3 * (k + 1) + 1] / scal[3 * k + 1]);
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    p[i] = z[i] + beta * p[i];
+  __syncthreads();
+  if (s_done) return;
+  const V beta = s_beta;
+  const V2* z2 = reinterpret_cast<const V2*>(z);
+  V2* p2 = reinterpret_cast<V2*>(p);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < npairs; i += (int64_t)gridDim.x * blockDim.x) {
+    const V2 zz = z2[i];
+    V2 pp = p2[i];
+    pp.x = zz.x + beta * pp.x;
+    pp.y = zz.y + beta * pp.y;
+    p2[i] = pp;
+  }
 }
 
 // ------------------------------------------------------------------ energy
@@ -590,7 +656,7 @@ __global__ void k_sia_fill(const double* __restrict__ acc, const double* __restr
 // ------------------------------------------------------------------ host helpers
 int grid_for(int64_t n, int threads) {
   int64_t g = (n + threads - 1) / threads;
-  return (int)std::max<int64_t>(1, std::min<int64_t>(g, 148LL * 32));
+  return (int)std::max<int64_t>(1, std::min<int64_t>(g, GRID_CAP));
 }
 
 int ensure_ws(bp_mesh* m, cudaStream_t s) {
@@ -641,7 +707,13 @@ int ensure_jac(bp_mesh* m) {
   return bp_alloc(m, &m->ws->J, m->nnz);
 }
 
-Prec prec_of(const bp_mesh* m) { return Prec{m->ws->Lm, m->ws->Ginv, m->ws->Fu, m->nv, m->nl}; }
+// The factor arrays are allocated as double; FP32 factors (set up from an FP32 Jacobian) use the
+// first half of each.
+template <class F>
+Prec<F> prec_of(const bp_mesh* m) {
+  return Prec<F>{reinterpret_cast<const F*>(m->ws->Lm), reinterpret_cast<const F*>(m->ws->Ginv),
+                 reinterpret_cast<const F*>(m->ws->Fu), m->nv, m->nl};
+}
 
 // synchronous dot product a . b (FP64 result on the host)
 template <class A, class B>
@@ -684,13 +756,17 @@ int energy_change_host(bp_mesh* m, const double* U, const DT* D, double alpha, c
   return BP_OK;
 }
 
+// FP64 Jacobian: FP64 factors; FP32 Jacobian (mixed-precision path): FP32 factors, applied in FP32.
 template <class M>
 int colprec_setup_t(bp_mesh* m, const M* J, cudaStream_t s) {
   bp_solver_ws* w = m->ws;
-  k_colprec_setup<M><<<(m->nv + 127) / 128, 128, 0, s>>>(J, m->vstart, m->vdeg, w->dslot, m->nv, m->nl, w->Lm,
-                                                         w->Ginv, w->Fu);
+  using F = M;
+  k_colprec_setup<M, F><<<(m->nv + 127) / 128, 128, 0, s>>>(J, m->vstart, m->vdeg, w->dslot, m->nv, m->nl,
+                                                            reinterpret_cast<F*>(w->Lm), reinterpret_cast<F*>(w->Ginv),
+                                                            reinterpret_cast<F*>(w->Fu));
   BP_CUDA_TRY(cudaGetLastError());
   w->has_prec = true;
+  w->prec_f32 = sizeof(F) == sizeof(float);
   return BP_OK;
 }
 
@@ -699,7 +775,7 @@ template <class M, class V>
 int cg_solve(bp_mesh* m, const M* J, double eta, int maxit, int check_every, cudaStream_t s, int* iters,
              int* status) {
   bp_solver_ws* w = m->ws;
-  const Prec P = prec_of(m);
+  const Prec<V> P = prec_of<V>(m);  // factors set up from the same-precision Jacobian
   const int64_t n = m->ndof;
   maxit = std::min(maxit, w->scal_cap);
   V* x = reinterpret_cast<V*>(w->x);
@@ -710,11 +786,11 @@ int cg_solve(bp_mesh* m, const M* J, double eta, int maxit, int check_every, cud
   BP_CUDA_TRY(cudaMemsetAsync(w->scal, 0, 3 * (size_t)(maxit + 2) * sizeof(double), s));
   BP_CUDA_TRY(cudaMemsetAsync(w->stop, 0, sizeof(int), s));
   const int gcol = (m->nv + NT - 1) / NT;
-  k_cg_init<V><<<gcol, NT, 0, s>>>(P, w->R, x, r, z, p, w->scal);
+  k_cg_init<V, V><<<gcol, NT, 0, s>>>(P, w->R, x, r, z, p, w->scal);
   const double tol2 = eta * eta;
-  const int gspmv = (int)((n / 2 * TPR + NT - 1) / NT);
+  const int gspmv = grid_for(n / 2 * TPR, NT);
   const int ncolv = 2 * (m->nl + 1);
-  const int C = std::max(1, std::min(128, (int)((48 << 10) / (2 * ncolv * (int)sizeof(V)))));
+  const int C = std::max(1, std::min(32, (int)((48 << 10) / (2 * ncolv * (int)sizeof(V)))));
   const size_t smem = 2 * (size_t)C * ncolv * sizeof(V);
   const int gupd = (m->nv + C - 1) / C;
   int k = 0, done = 0;
@@ -722,9 +798,10 @@ int cg_solve(bp_mesh* m, const M* J, double eta, int maxit, int check_every, cud
   while (!done) {
     const int kend = std::min(maxit, k + check_every);
     for (; k < kend; ++k) {
-      k_spmv_pairs<M, V, true><<<gspmv, NT, 0, s>>>(m->rowptr, m->colidx, J, n / 2, p, q, w->scal + 3 * k, w->stop);
-      k_cg_update_staged<V><<<gupd, NT, smem, s>>>(P, k, C, x, r, z, p, q, w->scal, w->stop);
-      k_cg_direction<V><<<grid_for(n, NT), NT, 0, s>>>(k, tol2, n, z, p, w->scal, w->stop);
+      k_spmv_pairs<M, V, true><<<gspmv, NT, 0, s>>>(m->rowptr, m->nbr_ptr, m->nbr_idx, m->nl, J, (int)(n / 2), p,
+                                                     q, w->scal + 3 * k, w->stop);
+      k_cg_update_staged<V, V><<<gupd, UPD_NT, smem, s>>>(P, k, C, x, r, z, p, q, w->scal, w->stop);
+      k_cg_direction<V><<<grid_for(n / 2, NT), NT, 0, s>>>(k, tol2, n / 2, z, p, w->scal, w->stop);
     }
     BP_CUDA_TRY(cudaGetLastError());
     BP_CUDA_TRY(cudaMemcpyAsync(w->host, w->scal, 3 * (size_t)(k + 1) * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -809,13 +886,14 @@ extern "C" int bp_spmv(bp_mesh* m, const void* J, int precision, const double* x
   if (precision != BP_F64 && precision != BP_F32) return BP_EINVAL;
   bp_device_guard g(m->device);
   cudaStream_t s = (cudaStream_t)stream;
-  const int grid = (int)((m->ndof / 2 * TPR + NT - 1) / NT);
+  const int grid = grid_for(m->ndof / 2 * TPR, NT);
+  const int npairs = (int)(m->ndof / 2);
   if (precision == BP_F64)
-    k_spmv_pairs<double, double, false><<<grid, NT, 0, s>>>(m->rowptr, m->colidx, (const double*)J, m->ndof / 2, x,
-                                                            y, nullptr, nullptr);
+    k_spmv_pairs<double, double, false><<<grid, NT, 0, s>>>(m->rowptr, m->nbr_ptr, m->nbr_idx, m->nl,
+                                                            (const double*)J, npairs, x, y, nullptr, nullptr);
   else
-    k_spmv_pairs<float, double, false><<<grid, NT, 0, s>>>(m->rowptr, m->colidx, (const float*)J, m->ndof / 2, x, y,
-                                                           nullptr, nullptr);
+    k_spmv_pairs<float, double, false><<<grid, NT, 0, s>>>(m->rowptr, m->nbr_ptr, m->nbr_idx, m->nl,
+                                                           (const float*)J, npairs, x, y, nullptr, nullptr);
   BP_CUDA_TRY(cudaGetLastError());
   return BP_OK;
 }
@@ -835,7 +913,10 @@ extern "C" int bp_colprec_apply(bp_mesh* m, const double* r, double* z, void* st
   if (!m->ws || !m->ws->has_prec) return BP_EINVAL;
   bp_device_guard g(m->device);
   cudaStream_t s = (cudaStream_t)stream;
-  k_colprec_apply<double><<<(m->nv + 127) / 128, 128, 0, s>>>(prec_of(m), r, z);
+  if (m->ws->prec_f32)
+    k_colprec_apply<double, float><<<(m->nv + 127) / 128, 128, 0, s>>>(prec_of<float>(m), r, z);
+  else
+    k_colprec_apply<double, double><<<(m->nv + 127) / 128, 128, 0, s>>>(prec_of<double>(m), r, z);
   BP_CUDA_TRY(cudaGetLastError());
   return BP_OK;
 }
