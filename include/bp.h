@@ -326,17 +326,24 @@ int bp_mlp_train_step(bp_mlp* mlp, const uint16_t* X_dev, const float* T_dev, in
 int bp_mlp_features(bp_mesh* mesh, uint16_t* X_dev, void* stream);
 /* Replace beta on an uploaded mesh (host array [nv]) and rebuild the basal friction matrices. */
 int bp_mesh_set_beta(bp_mesh* mesh, const double* beta_host, void* stream);
+/* How bp_initial_guess_learned decides between the network's guess and the shallow-ice guess:
+ *   BP_JUDGE_RESIDUAL  keep the guess with the smaller FP64 residual norm;
+ *   BP_JUDGE_ENERGY    keep the guess with the smaller FP64 discrete energy Pi_h (the functional
+ *                      Newton minimises: Pi_h(U) - Pi_h(U*) ~ 1/2 |U - U*|^2 in the Jacobian's norm);
+ *   BP_JUDGE_NONE      always keep the network's guess (evaluation). */
+enum { BP_JUDGE_RESIDUAL = 0, BP_JUDGE_ENERGY = 1, BP_JUDGE_NONE = 2 };
 /*
  * Learned initial guess: per column and component c the network scales the sliding part
  * b_c = u_sia,c(bed) and the deformation part d_c = u_sia,c - b_c of the shallow-ice profile,
  * u_c = (1 + y_2c) b_c + (1 + y_2c+1) d_c, which keeps the vertical profile consistent (vertical
  * shear dominates the stress on thin layers) and reduces to the shallow-ice guess where the network
- * has learned nothing; written in the dof order.  Falls back to the
- * shallow-ice guess when that has the smaller FP64 residual norm (the residual judges the
- * prediction); *used (nullable) receives 1 if the network's prediction was kept, 0 otherwise.
- * Synchronises `stream`.
+ * has learned nothing; written in the dof order.  Falls back to the shallow-ice guess when that one
+ * wins under `judge` (a BP_JUDGE_*; the FP64 residual by default); *used (nullable) receives 1 if the
+ * network's prediction was kept, 0 otherwise.  Synchronises `stream`.
+ * Errors: BP_EINVAL (NULL, misaligned U, unknown judge), BP_EUNSUP (mesh without 10 layers),
+ * BP_ENOMEM, BP_ECUDA.
  */
-int bp_initial_guess_learned(bp_mesh* mesh, bp_mlp* mlp, double* U_dev, int* used, void* stream);
+int bp_initial_guess_learned(bp_mesh* mesh, bp_mlp* mlp, double* U_dev, int judge, int* used, void* stream);
 
 /*
  * Allocation-free variant of bp_assemble_jacobian (R not returned).  The paper has no

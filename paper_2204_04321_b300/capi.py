@@ -22,6 +22,7 @@ BP_SCATTER_AUTO, BP_SCATTER_ATOMIC, BP_SCATTER_COLOR = 0, 1, 2
 BP_JAC_AUTO, BP_JAC_DUAL, BP_JAC_FACTORED = 0, 1, 2
 BP_GUESS_ZERO, BP_GUESS_SIA = 0, 1
 BP_KRYLOV_CG = 0
+BP_JUDGE_RESIDUAL, BP_JUDGE_ENERGY, BP_JUDGE_NONE = 0, 1, 2
 
 
 class BPError(RuntimeError):
@@ -107,7 +108,7 @@ SIGNATURES = {
     "bp_mlp_train_step": (_I, [_P, _P, _P, ctypes.c_int64, ctypes.c_float, _P]),
     "bp_mlp_features": (_I, [_P, _P, _P]),
     "bp_mesh_set_beta": (_I, [_P, _P, _P]),
-    "bp_initial_guess_learned": (_I, [_P, _P, _P, _P, _P]),
+    "bp_initial_guess_learned": (_I, [_P, _P, _P, _I, _P, _P]),
 }
 
 _lock = threading.Lock()
@@ -376,10 +377,11 @@ def bp_mesh_set_beta(handle, beta, stream=None) -> None:
            "bp_mesh_set_beta")
 
 
-def bp_initial_guess_learned(handle, mlp, U, stream=None) -> bool:
+def bp_initial_guess_learned(handle, mlp, U, judge=None, stream=None) -> bool:
     used = ctypes.c_int()
-    _check(lib().bp_initial_guess_learned(handle, mlp.handle, _dptr(U), ctypes.byref(used), _stream_ptr(stream)),
-           "bp_initial_guess_learned")
+    judge = BP_JUDGE_RESIDUAL if judge is None else judge
+    _check(lib().bp_initial_guess_learned(handle, mlp.handle, _dptr(U), judge, ctypes.byref(used),
+                                          _stream_ptr(stream)), "bp_initial_guess_learned")
     return bool(used.value)
 
 

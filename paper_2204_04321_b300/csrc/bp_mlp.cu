@@ -764,8 +764,9 @@ extern "C" int bp_mlp_features(bp_mesh* m, uint16_t* X, void* stream) {
   return BP_OK;
 }
 
-extern "C" int bp_initial_guess_learned(bp_mesh* m, bp_mlp* net, double* U, int* used, void* stream) {
+extern "C" int bp_initial_guess_learned(bp_mesh* m, bp_mlp* net, double* U, int judge, int* used, void* stream) {
   if (!m || !net || !U || !bp_aligned16(U)) return BP_EINVAL;
+  if (judge < BP_JUDGE_RESIDUAL || judge > BP_JUDGE_NONE) return BP_EINVAL;
   if (m->nl != BP_MLP_LEVELS - 1) return BP_EUNSUP;
   bp_device_guard g(m->device);
   cudaStream_t s = (cudaStream_t)stream;
@@ -780,11 +781,18 @@ extern "C" int bp_initial_guess_learned(bp_mesh* m, bp_mlp* net, double* U, int*
   k_scatter_prediction<<<(m->nv + 127) / 128, 128, 0, s>>>(Y, Usia, m->nv, m->nl, U);
   BP_CUDA_TRY(cudaGetLastError());
   if ((rc = check_err(net, s))) return rc;
-  // the FP64 residual judges the prediction against the shallow-ice guess
-  double f_mlp, f_sia;
-  if ((rc = bp_assemble_residual(m, U, R, s)) || (rc = bp_norm2_host(m, R, s, &f_mlp))) return rc;
-  if ((rc = bp_assemble_residual(m, Usia, R, s)) || (rc = bp_norm2_host(m, R, s, &f_sia))) return rc;
-  const bool keep = std::isfinite(f_mlp) && f_mlp <= f_sia;
+  // the FP64 residual norm (or the FP64 energy) judges the prediction against the shallow-ice guess
+  bool keep = true;
+  if (judge != BP_JUDGE_NONE) {
+    double f_mlp, f_sia;
+    if (judge == BP_JUDGE_RESIDUAL) {
+      if ((rc = bp_assemble_residual(m, U, R, s)) || (rc = bp_norm2_host(m, R, s, &f_mlp))) return rc;
+      if ((rc = bp_assemble_residual(m, Usia, R, s)) || (rc = bp_norm2_host(m, R, s, &f_sia))) return rc;
+    } else {
+      if ((rc = bp_energy(m, U, &f_mlp, s)) || (rc = bp_energy(m, Usia, &f_sia, s))) return rc;
+    }
+    keep = std::isfinite(f_mlp) && f_mlp <= f_sia;
+  }
   if (!keep) BP_CUDA_TRY(cudaMemcpyAsync(U, Usia, m->ndof * sizeof(double), cudaMemcpyDeviceToDevice, s));
   BP_CUDA_TRY(cudaStreamSynchronize(s));
   if (used) *used = keep ? 1 : 0;

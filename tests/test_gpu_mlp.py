@@ -189,3 +189,11 @@ def test_learned_guess_falls_back_to_shallow_ice_for_untrained_network():
     c.bp_initial_guess(dm.handle, c.BP_GUESS_SIA, S)
     assert not used  # the untrained network's residual is larger: the shallow-ice guess is returned
     assert float((U - S).abs().max() / S.abs().max()) <= 1e-13  # (its nodal gradient is summed with atomics)
+    # the energy judge rejects it as well; with no judge the network's own guess is returned
+    assert not c.bp_initial_guess_learned(dm.handle, net, U, judge=c.BP_JUDGE_ENERGY)
+    assert float((U - S).abs().max() / S.abs().max()) <= 1e-13
+    assert c.bp_initial_guess_learned(dm.handle, net, U, judge=c.BP_JUDGE_NONE)
+    assert float((U - S).abs().max() / S.abs().max()) > 1e-3
+    with pytest.raises(c.BPError) as e:
+        c.bp_initial_guess_learned(dm.handle, net, U, judge=7)
+    assert e.value.status == c.BP_EINVAL
