@@ -181,6 +181,10 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     dev = torch.device("cuda", local)
+    if args.ensemble_only:
+        print(json.dumps({"ensemble": ensemble_section(capi, synth, dev), "mlp": mlp_section(capi, dev)}),
+              flush=True)
+        return 0
     if args.newton_only:
         mesh = synth.config_medium()
         dm = capi.DeviceMesh(mesh)
@@ -306,6 +310,7 @@ def run_ours(args):
     e2e_value = ws * W * args.steps / e2e_s
 
     newton = newton_section(capi, synth, dm, mesh, dev, skip_large=args.no_large) if not args.no_newton else None
+    mlp = mlp_section(capi, dev) if not args.no_mlp else None
     flops = FLOPS_PER_WEDGE_JAC64 * W
     achieved = flops / (kernel_ms * 1e-3) / 1e12
     peaks = read_peaks()
@@ -317,6 +322,10 @@ def run_ours(args):
         if pj.get("kernel_source_hash") == kernel_hash():
             traffic = pj["bytes_per_wedge"] * W
 
+    if not args.no_ensemble:
+        ensemble = ensemble_section(capi, synth, dev)
+    else:
+        ensemble = None
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -345,6 +354,8 @@ def run_ours(args):
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * dm.ndof,
                     "d2h_bytes_per_step": 8 * dm.ndof + 8 * dm.nnz},
             "newton": newton,
+            "ensemble": ensemble,
+            "mlp": mlp,
             "gpu_launches": args.steps,
             "clocks": clk.summary(),
         }
@@ -381,6 +392,87 @@ def learned_start(capi, dm, dev, reps=3):
     out["judges"] = {"learned": "FP64 residual norm", "learned_energy": "FP64 discrete energy"}
     net.close()
     return out
+
+
+def ensemble_section(capi, synth, dev, reps=5):
+    """64 uneven members (5k-50k triangles, 5-20 layers, H0 1-3 km, own beta) assembled in one
+    persistent launch replayed from a CUDA graph, with the autotuned cells-per-block and scatter.
+    Accuracy: every member's R and J against the same member assembled alone (bp_assemble_jacobian,
+    itself at oracle parity); the per-member oracle comparison is in the GPU tests."""
+    import torch
+    members = synth.ensemble_members()
+    W = sum(m.nwedges for m in members)
+    U = [torch.as_tensor(synth.random_velocity(m, 500 + i), device=dev) for i, m in enumerate(members)]
+    ens = capi.Ensemble(members, U, precision=capi.BP_F64)
+    times, chosen = ens.tune(reps=3)
+    stream = torch.cuda.current_stream()
+    for _ in range(3):
+        ens.assemble()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        ens.assemble()
+        b.record(stream)
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    ms = statistics.median(ts)
+    worst_r = worst_j = 0.0
+    for i, dm in enumerate(ens.dms):
+        J1, R1 = dm.jacobian(U[i])
+        worst_r = max(worst_r, float((ens.R[i] - R1).abs().max() / R1.abs().max()))
+        worst_j = max(worst_j, float((ens.J[i] - J1).abs().max() / J1.abs().max()))
+        del J1, R1
+    out = {"metric": "residual+Jacobian wedge cells/s (ensemble, one persistent launch, CUDA graph)",
+           "value": W / (ms * 1e-3), "unit": "wedges/s", "ms": ms, "members": len(members), "wedges": W,
+           "nnz": int(sum(d.nnz for d in ens.dms)), "dtype": "f64",
+           "chosen": {"cells_per_block": chosen[0],
+                      "scatter": "color" if chosen[1] == capi.BP_SCATTER_COLOR else "atomic"},
+           "tuner_ms": times, "achieved_tflops": FLOPS_PER_WEDGE_JAC64 * W / (ms * 1e-3) / 1e12,
+           "member_vs_single_launch_rel_inf": {"R": worst_r, "J": worst_j}}
+    ens.close()
+    del U
+    torch.cuda.empty_cache()
+    return out
+
+
+def mlp_section(capi, dev, rows=50625, batch=8192, reps=20):
+    """BF16 tcgen05 MLP (16-128-128-128-32): inference over the 1M-wedge dome's 50,625 columns and
+    one Adam training step on a batch of 8,192 rows.  Flops per row: forward 2 x 38,912 MACs;
+    training step (forward + backward for activations and weights) 3x that."""
+    import torch
+    net = capi.Mlp(seed=1)
+    g = torch.Generator(device=dev)
+    g.manual_seed(0)
+    X = torch.randn(rows, 16, device=dev, generator=g).to(torch.bfloat16)
+    T = torch.randn(batch, 32, device=dev, generator=g)
+    Xb = X[:batch].contiguous()
+    Y = torch.empty(rows, 32, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    fwd_ms = timed(lambda: net.forward(X, Y))
+    trn_ms = timed(lambda: net.train_step(Xb, T, 1e-4))
+    flop_fwd = 2 * (16 * 128 + 128 * 128 + 128 * 128 + 128 * 32)
+    net.close()
+    return {"inference": {"rows": rows, "ms": fwd_ms, "tflops": flop_fwd * rows / (fwd_ms * 1e-3) / 1e12},
+            "train_step": {"rows": batch, "ms": trn_ms, "rows_per_s": batch / (trn_ms * 1e-3),
+                           "tflops": 3 * flop_fwd * batch / (trn_ms * 1e-3) / 1e12},
+            "peak_note": "bf16 tensor peak (measured cuBLAS, MEASURED_PEAKS.json): "
+                         + str(read_peaks().get("bf16_tflops")) + " TFLOP/s; these GEMMs (K, N <= 128) "
+                         "are far too small to approach it"}
 
 
 def newton_section(capi, synth, dm, mesh, dev, skip_large=False, reps=3):
@@ -441,6 +533,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-newton", action="store_true", help="skip the Newton-solve measurements")
     ap.add_argument("--no-large", action="store_true", help="skip the 4M-wedge mixed-precision solve")
+    ap.add_argument("--no-ensemble", action="store_true", help="skip the 64-member ensemble measurement")
+    ap.add_argument("--no-mlp", action="store_true", help="skip the MLP kernel timings")
+    ap.add_argument("--ensemble-only", action="store_true", help="only the ensemble and MLP sections")
     ap.add_argument("--newton-only", action="store_true",
                     help="only the Newton-solve section (profiling the solver); prints its JSON")
     ap.add_argument("--newton-reps", type=int, default=3, help="timed repetitions of each Newton solve")
