@@ -467,36 +467,8 @@ __global__ void __launch_bounds__(128) k_energy(const double2* __restrict__ xy, 
   block_add(acc, out);
 }
 
-// Energy change Pi_h(U + alpha d) - Pi_h(U), formed term by term as differences so that it keeps
-// its relative accuracy when it is many orders smaller than Pi_h itself (near convergence):
-//   driving:  alpha load . d;   basal: alpha d^T M u + alpha^2/2 d^T M d;
-//   stress:   x = eps_e^2 + delta is quadratic in the velocity gradient G, so
-//             x1 - x0 = alpha (2 B(G0, Gd)) + alpha^2 Q(Gd) exactly, and
-//             x1^(2/3) - x0^(2/3) = (a - b)(a + b), a - b = (x1 - x0) / (a^2 + a b + b^2), a, b = cube roots.
-template <class T, class A, class B>
-__device__ __forceinline__ void qp_gradient(const A* u0, const A* v0, const A* u1, const A* v1, const B* lx,
-                                            const B* ly, T p0, T p1, int tp, T h, T Gzx, T Gzy, T G[6]) {
-  T GUx = 0, GUy = 0, GVx = 0, GVy = 0, du = 0, dv = 0;
-  for (int a = 0; a < 3; ++a) {
-    const T ua = p0 * (T)u0[a] + p1 * (T)u1[a], va = p0 * (T)v0[a] + p1 * (T)v1[a];
-    GUx += ua * (T)lx[a];
-    GUy += ua * (T)ly[a];
-    GVx += va * (T)lx[a];
-    GVy += va * (T)ly[a];
-    const T la = (a == tp) ? T(2.0 / 3.0) : T(1.0 / 6.0);
-    du += la * ((T)u1[a] - (T)u0[a]);
-    dv += la * ((T)v1[a] - (T)v0[a]);
-  }
-  const T uz = du / h, vz = dv / h;
-  G[0] = GUx - uz * Gzx;  // u_x
-  G[1] = GUy - uz * Gzy;  // u_y
-  G[2] = uz;
-  G[3] = GVx - vz * Gzx;  // v_x
-  G[4] = GVy - vz * Gzy;  // v_y
-  G[5] = vz;
-}
-
-// symmetric bilinear form of eps_e^2: Q(G) = B(G, G)
+// symmetric bilinear form of eps_e^2 on velocity gradients G = (u_x, u_y, u_z, v_x, v_y, v_z):
+// Q(G) = B(G, G) = eps_e^2
 template <class T>
 __device__ __forceinline__ T eps_bilinear(const T* A, const T* B) {
   const T exyA = T(0.5) * (A[1] + A[3]), exyB = T(0.5) * (B[1] + B[3]);
@@ -564,38 +536,91 @@ __global__ void __launch_bounds__(128) k_energy_change(const double2* __restrict
                             0.5 * alpha * alpha * (du * (double)D[ub[b]] + dv * (double)D[ub[b] + 1]));
         }
     }
+    // stress term: the column walk of the assembly kernel (level gradients carried from the wedge
+    // below, one reciprocal of the thickness per triangle point), per point the exact difference
     const T ta = (T)alpha, tdelta = (T)delta;
+    T tlx[3], tly[3], invHq[3];
+    double Hq[3];
+    for (int a = 0; a < 3; ++a) {
+      tlx[a] = (T)lx[a];
+      tly[a] = (T)ly[a];
+      Hq[a] = Hs6 + 0.5 * H[a];
+      invHq[a] = (T)(1.0 / Hq[a]);
+    }
+    T u0[3], v0[3], a0[3], b0[3];
+    for (int a = 0; a < 3; ++a) {
+      u0[a] = (T)U[ub[a]];
+      v0[a] = (T)U[ub[a] + 1];
+      a0[a] = (T)D[ub[a]];
+      b0[a] = (T)D[ub[a] + 1];
+    }
+    auto grad2 = [&](const T* w, T& gx, T& gy) {
+      gx = w[0] * tlx[0] + w[1] * tlx[1] + w[2] * tlx[2];
+      gy = w[0] * tly[0] + w[1] * tly[1] + w[2] * tly[2];
+    };
+    T gU0[2], gV0[2], gA0[2], gB0[2];
+    grad2(u0, gU0[0], gU0[1]);
+    grad2(v0, gV0[0], gV0[1]);
+    grad2(a0, gA0[0], gA0[1]);
+    grad2(b0, gB0[0], gB0[1]);
     double stress = 0.0;
     for (int l = 0; l < L; ++l) {
-      double u0[3], v0[3], u1[3], v1[3];
-      DT a0[3], b0[3], a1[3], b1[3];
+      T u1[3], v1[3], a1[3], b1[3];
       for (int a = 0; a < 3; ++a) {
-        u0[a] = U[ub[a] + 2 * l];
-        v0[a] = U[ub[a] + 2 * l + 1];
-        u1[a] = U[ub[a] + 2 * l + 2];
-        v1[a] = U[ub[a] + 2 * l + 3];
-        a0[a] = D[ub[a] + 2 * l];
-        b0[a] = D[ub[a] + 2 * l + 1];
-        a1[a] = D[ub[a] + 2 * l + 2];
-        b1[a] = D[ub[a] + 2 * l + 3];
+        u1[a] = (T)U[ub[a] + 2 * l + 2];
+        v1[a] = (T)U[ub[a] + 2 * l + 3];
+        a1[a] = (T)D[ub[a] + 2 * l + 2];
+        b1[a] = (T)D[ub[a] + 2 * l + 3];
       }
+      T gU1[2], gV1[2], gA1[2], gB1[2];
+      grad2(u1, gU1[0], gU1[1]);
+      grad2(v1, gV1[0], gV1[1]);
+      grad2(a1, gA1[0], gA1[1]);
+      grad2(b1, gB1[0], gB1[1]);
       const double s_l = sigma[l], ds = sigma[l + 1] - sigma[l];
+      const T invds = (T)(1.0 / ds);
+      const T sixth = T(1.0 / 6.0);
+      const T du6 = (u1[0] - u0[0] + u1[1] - u0[1] + u1[2] - u0[2]) * sixth;
+      const T dv6 = (v1[0] - v0[0] + v1[1] - v0[1] + v1[2] - v0[2]) * sixth;
+      const T da6 = (a1[0] - a0[0] + a1[1] - a0[1] + a1[2] - a0[2]) * sixth;
+      const T db6 = (b1[0] - b0[0] + b1[1] - b0[1] + b1[2] - b0[2]) * sixth;
+      double lstress = 0.0;
       for (int z = 0; z < 2; ++z) {
-        const double p0 = z == 0 ? BP_QP_P : BP_QP_Q, p1 = z == 0 ? BP_QP_Q : BP_QP_P;
-        const double sz = s_l + p1 * ds;
+        const T p0 = (T)(z == 0 ? BP_QP_P : BP_QP_Q), p1 = (T)(z == 0 ? BP_QP_Q : BP_QP_P);
+        const double sz = s_l + (z == 0 ? BP_QP_Q : BP_QP_P) * ds;
         const T Gzx = (T)(gbx + sz * gHx), Gzy = (T)(gby + sz * gHy);
+        const T GUx = p0 * gU0[0] + p1 * gU1[0], GUy = p0 * gU0[1] + p1 * gU1[1];
+        const T GVx = p0 * gV0[0] + p1 * gV1[0], GVy = p0 * gV0[1] + p1 * gV1[1];
+        const T GAx = p0 * gA0[0] + p1 * gA1[0], GAy = p0 * gA0[1] + p1 * gA1[1];
+        const T GBx = p0 * gB0[0] + p1 * gB1[0], GBy = p0 * gB0[1] + p1 * gB1[1];
         for (int tp = 0; tp < 3; ++tp) {
-          const double h = ds * (Hs6 + 0.5 * H[tp]);
-          T G0[6], Gd[6];
-          qp_gradient<T>(u0, v0, u1, v1, lx, ly, (T)p0, (T)p1, tp, (T)h, Gzx, Gzy, G0);
-          qp_gradient<T>(a0, b0, a1, b1, lx, ly, (T)p0, (T)p1, tp, (T)h, Gzx, Gzy, Gd);
+          const T invh = invds * invHq[tp];
+          const T uz = (du6 + T(0.5) * (u1[tp] - u0[tp])) * invh;
+          const T vz = (dv6 + T(0.5) * (v1[tp] - v0[tp])) * invh;
+          const T az = (da6 + T(0.5) * (a1[tp] - a0[tp])) * invh;
+          const T bz = (db6 + T(0.5) * (b1[tp] - b0[tp])) * invh;
+          const T G0[6] = {GUx - uz * Gzx, GUy - uz * Gzy, uz, GVx - vz * Gzx, GVy - vz * Gzy, vz};
+          const T Gd[6] = {GAx - az * Gzx, GAy - az * Gzy, az, GBx - bz * Gzx, GBy - bz * Gzy, bz};
           const T x0 = eps_bilinear(G0, G0) + tdelta;
           const T dx = ta * (T(2) * eps_bilinear(G0, Gd) + ta * eps_bilinear(Gd, Gd));
           const T x1 = x0 + dx;
           const T ca = cube_root(x1), cb = cube_root(x0);
           const T diff23 = dx / (ca * ca + ca * cb + cb * cb) * (ca + cb);
-          stress += (d * h / 12.0) * (double)diff23;
+          lstress += Hq[tp] * (double)diff23;
         }
+      }
+      stress += (d * ds / 12.0) * lstress;
+      for (int a = 0; a < 3; ++a) {
+        u0[a] = u1[a];
+        v0[a] = v1[a];
+        a0[a] = a1[a];
+        b0[a] = b1[a];
+      }
+      for (int c = 0; c < 2; ++c) {
+        gU0[c] = gU1[c];
+        gV0[c] = gV1[c];
+        gA0[c] = gA1[c];
+        gB0[c] = gB1[c];
       }
     }
     acc += 1.5 * cA * stress;
