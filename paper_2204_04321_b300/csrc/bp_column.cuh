@@ -25,6 +25,7 @@
 #pragma once
 
 #include <cmath>
+#include <type_traits>
 
 #include "bp_internal.cuh"
 
@@ -201,6 +202,8 @@ __device__ __forceinline__ void assemble_column(const AsmArgs& A, const int t) {
   }
   const double d12 = d * (1.0 / 12.0);
   const double d6 = d * (1.0 / 6.0);
+  const float cAf = (float)A.cA;
+  const TL d12L = (TL)d12;
   TL clx[3], cly[3];  // grad lambda in lane precision (Jacobian lanes)
   if constexpr (MODE == MODE_FACT) {
 #pragma unroll
@@ -284,6 +287,17 @@ __device__ __forceinline__ void assemble_column(const AsmArgs& A, const int t) {
     double Rl[2][3][2];  // [k][a][c] residual of this wedge
     TL K[78];            // upper triangle of the element matrix
     TL eta_q[2][3];      // 2 mu at the quadrature points (factored Jacobian)
+    // FP32 lanes: the per-point weights in FP32, converted once per wedge (a conversion from
+    // double runs on the FP64 pipe, which the value path already fills)
+    constexpr bool kF32 = std::is_same<TL, float>::value;
+    TL cqL[3], invhL[3];
+    if constexpr (MODE == MODE_FACT) {
+#pragma unroll
+      for (int tp = 0; tp < 3; ++tp) {
+        cqL[tp] = (TL)cq[tp];
+        invhL[tp] = (TL)invh[tp];
+      }
+    }
     if constexpr (MODE != MODE_RES) {
 #pragma unroll
       for (int k = 0; k < 78; ++k) K[k] = TL(0);
@@ -397,10 +411,21 @@ __device__ __forceinline__ void assemble_column(const AsmArgs& A, const int t) {
           TW1[tp] = fma(W6, t1, TW1[tp]);
           TW2[tp] = fma(W6, t2, TW2[tp]);
           if constexpr (MODE == MODE_FACT) {
-            eta_q[z][tp] = (TL)eta;
             // rank-one part eta' p_i p_j with p_{(a,k),c} = psi_k g_c,xy . Lambda_a + lambda_a psi_k' g_c . Z
-            const TL Wp = (TL)(-(1.0 / 3.0) * W * (r * r * r));
-            const TL tau1 = (TL)(2.0 * invh[tp] * t1), tau2 = (TL)(2.0 * invh[tp] * t2);
+            TL Wp, tau1, tau2;
+            if constexpr (kF32) {  // from r, t1, t2 converted once: FP32 arithmetic only
+              const float rf = (float)r;
+              const float ef = cAf * rf;
+              eta_q[z][tp] = ef;
+              Wp = (-1.0f / 3.0f) * cqL[tp] * ef * (rf * rf * rf);
+              tau1 = 2.0f * invhL[tp] * (float)t1;
+              tau2 = 2.0f * invhL[tp] * (float)t2;
+            } else {
+              eta_q[z][tp] = (TL)eta;
+              Wp = (TL)(-(1.0 / 3.0) * W * (r * r * r));
+              tau1 = (TL)(2.0 * invh[tp] * t1);
+              tau2 = (TL)(2.0 * invh[tp] * t2);
+            }
             const TL fg1x = (TL)g1x, fexy = (TL)exy, fg2y = (TL)g2y;
             // p_{(a,k),c} = psi_k alpha_{a,c} -/+ t_{a,c},  alpha = g_c,xy . Lambda_a,  t = lambda_a tau_c / 2
             TL p[12];
@@ -450,13 +475,13 @@ __device__ __forceinline__ void assemble_column(const AsmArgs& A, const int t) {
         for (int z = 0; z < 2; ++z) {
           Qs[z] = TL(0);
 #pragma unroll
-          for (int tp = 0; tp < 3; ++tp) Qs[z] += (TL)cq[tp] * eta_q[z][tp];
+          for (int tp = 0; tp < 3; ++tp) Qs[z] += cqL[tp] * eta_q[z][tp];
           const TL es = (eta_q[z][0] + eta_q[z][1] + eta_q[z][2]) * TL(1.0 / 6.0);
           TL ei[3];
 #pragma unroll
           for (int tp = 0; tp < 3; ++tp) {
             E[z][tp] = es + TL(0.5) * eta_q[z][tp];
-            ei[tp] = eta_q[z][tp] * (TL)invh[tp];
+            ei[tp] = eta_q[z][tp] * invhL[tp];
           }
           // F_ab = sum_tp lambda_a lambda_b eta / h, pairs 00 01 02 11 12 22
           int pr = 0;
@@ -476,9 +501,10 @@ __device__ __forceinline__ void assemble_column(const AsmArgs& A, const int t) {
         Q[0][1] = Q[1][0] = (TL)(BP_QP_P * BP_QP_Q) * (Qs[0] + Qs[1]);
         // V^k_b scaled by 1/2 (the magnitude of psi'): V = -(d/12) sum_z psi_k E_b Gz
         TL Vx[2][3], Vy[2][3];
-        const TL md12 = (TL)(-d * (1.0 / 12.0));
-        const TL gz0x = md12 * (TL)Gzx[0], gz1x = md12 * (TL)Gzx[1];
-        const TL gz0y = md12 * (TL)Gzy[0], gz1y = md12 * (TL)Gzy[1];
+        const TL GzxL[2] = {(TL)Gzx[0], (TL)Gzx[1]}, GzyL[2] = {(TL)Gzy[0], (TL)Gzy[1]};
+        const TL md12 = -d12L;
+        const TL gz0x = md12 * GzxL[0], gz1x = md12 * GzxL[1];
+        const TL gz0y = md12 * GzyL[0], gz1y = md12 * GzyL[1];
 #pragma unroll
         for (int k = 0; k < 2; ++k)
 #pragma unroll
@@ -493,12 +519,12 @@ __device__ __forceinline__ void assemble_column(const AsmArgs& A, const int t) {
           TL Buu[2], Bvv[2], Buv[2];
 #pragma unroll
           for (int z = 0; z < 2; ++z) {
-            const TL gx = (TL)Gzx[z], gy = (TL)Gzy[z];
+            const TL gx = GzxL[z], gy = GzyL[z];
             Buu[z] = TL(2) * gx * gx + TL(0.5) * gy * gy + TL(0.5);
             Bvv[z] = TL(0.5) * gx * gx + TL(2) * gy * gy + TL(0.5);
             Buv[z] = TL(1.5) * gx * gy;
           }
-          const TL s = (TL)(d * (1.0 / 12.0));
+          const TL s = d12L;
 #pragma unroll
           for (int pr = 0; pr < 6; ++pr) {
             Yuu[pr] = s * (F[0][pr] * Buu[0] + F[1][pr] * Buu[1]);

@@ -45,6 +45,10 @@ struct bp_solver_ws {
   int host_cap = 0;
   bool has_prec = false;
   bool prec_f32 = false;      // factors stored as float (set up from an FP32 Jacobian)
+  int* kbase = nullptr;       // CG: first iteration index of the current batch (device)
+  double* cgpar = nullptr;    // CG: [0] tolerance eta^2 on r.r / r0.r0, [1] iteration limit (device)
+  double* hpar = nullptr;     // pinned staging of cgpar
+  void* cg_exec[2] = {nullptr, nullptr};  // instantiated CG batch graphs (FP64, FP32 Krylov)
 };
 
 struct bp_mesh {

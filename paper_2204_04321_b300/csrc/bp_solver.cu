@@ -17,6 +17,7 @@ constexpr int NT = 256;        // threads per block of the vector kernels
 constexpr int SCAL_CAP = 8192; // Krylov iterations per linear solve (scalar history capacity)
 constexpr int GRID_CAP = 148 * 8;  // grid-stride kernels: 8 blocks of NT per SM
 constexpr int UPD_NT = 128;        // threads of the staged CG update (one warp solves the block's columns)
+constexpr int CG_BATCH = 8;        // CG iterations per replay of the captured batch graph
 
 // B300 issues FP64 at ~1/64 of the FP32 rate, so the vector kernels keep per-element reductions in
 // the vector type V and spend FP64 operations only on per-warp / per-block partial sums.
@@ -89,17 +90,19 @@ struct Pair<float> {
 // halves the bytes of an FP32 SpMV), x is read as aligned (u, v) pairs and the values of both rows as
 // aligned pairs.  The two row sums are folded with one add per lane per step (after the first step
 // the lower half of the group carries row 2i, the upper half row 2i + 1).  With DOT, x . y is added
-// to *dot (summed in V per thread, in FP64 across threads, one atomic per block).  Grid-stride over
-// row pairs.
+// to *dot (summed in V per thread, in FP64 across threads, one atomic per block; inside the CG
+// batch graph the target is scal[3 (kbase + j)]).  Grid-stride over row pairs.
 template <class M, class V, bool DOT>
 __global__ void __launch_bounds__(NT) k_spmv_pairs(const int64_t* __restrict__ rowptr,
                                                    const int32_t* __restrict__ nbr_ptr,
                                                    const int32_t* __restrict__ nbr_idx, int L,
                                                    const M* __restrict__ vals, int npairs, const V* __restrict__ x,
-                                                   V* __restrict__ y, double* dot, const int* stop) {
+                                                   V* __restrict__ y, double* dot, const int* stop,
+                                                   const int* kbase, int j) {
   using M2 = typename Pair<M>::type;
   using V2 = typename Pair<V>::type;
   if (stop && *stop) return;
+  if (DOT && kbase) dot += 3 * (*kbase + j);  // CG iteration k = kbase + j writes scal[3k]
   const int lane = threadIdx.x % TPR;
   const bool upper = lane >= TPR / 2;
   V d = V(0);  // this thread's part of x . y (in V; FP64 only across threads)
@@ -300,13 +303,15 @@ __global__ void __launch_bounds__(NT) k_cg_init(const Prec<F> P, const double* _
 // r goes to shared memory, each of the first C threads solves its column there, and z is written back
 // coalesced.  alpha is formed once per block.  Dynamic shared memory: 2 C 2(L+1) values of V.
 template <class V, class F>
-__global__ void __launch_bounds__(UPD_NT) k_cg_update_staged(const Prec<F> P, int k, int C, V* __restrict__ x,
-                                                         V* __restrict__ r, V* __restrict__ z, const V* __restrict__ p,
-                                                         const V* __restrict__ q, double* scal, int* stop) {
+__global__ void __launch_bounds__(UPD_NT) k_cg_update_staged(const Prec<F> P, const int* kbase, int j, int C,
+                                                             V* __restrict__ x, V* __restrict__ r, V* __restrict__ z,
+                                                             const V* __restrict__ p, const V* __restrict__ q,
+                                                             double* scal, int* stop) {
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ V s_alpha;
   __shared__ int s_bad;
   if (*stop) return;
+  const int k = *kbase + j;
   if (threadIdx.x == 0) {
     const double pq = scal[3 * k], rzk = scal[3 * k + 1];
     s_bad = !(pq > 0.0) || !isfinite(rzk);
@@ -344,20 +349,25 @@ __global__ void __launch_bounds__(UPD_NT) k_cg_update_staged(const Prec<F> P, in
   block_add(rr, scal + 3 * (k + 1) + 2);
 }
 
-// beta = r_{k+1}.z_{k+1} / r_k.z_k;  p = z + beta p;  stop once r.r <= tol2 r_0.r_0.  The scalars are
-// formed once per block; the update runs on (u, v) pairs.
+// beta = r_{k+1}.z_{k+1} / r_k.z_k;  p = z + beta p;  stop once r.r <= eta^2 r_0.r_0 (flag 1) or the
+// iteration limit is reached (flag 4).  The scalars are formed once per block; the update runs on
+// (u, v) pairs.
 template <class V>
-__global__ void __launch_bounds__(NT) k_cg_direction(int k, double tol2, int64_t npairs, const V* __restrict__ z,
-                                                     V* __restrict__ p, const double* scal, int* stop) {
+__global__ void __launch_bounds__(NT) k_cg_direction(const int* kbase, int j, const double* cgpar, int64_t npairs,
+                                                     const V* __restrict__ z, V* __restrict__ p, const double* scal,
+                                                     int* stop) {
   using V2 = typename Pair<V>::type;
   __shared__ V s_beta;
   __shared__ int s_done;
   if (*stop) return;
   if (threadIdx.x == 0) {
+    const int k = *kbase + j;
     const double rr = scal[3 * (k + 1) + 2];
-    s_done = rr <= tol2 * scal[2] || !isfinite(rr);
+    const bool conv = rr <= cgpar[0] * scal[2] || !isfinite(rr);
+    const bool limit = (double)(k + 1) >= cgpar[1];
+    s_done = conv || limit;
     s_beta = (V)(scal[3 * (k + 1) + 1] / scal[3 * k + 1]);
-    if (s_done && blockIdx.x == 0) *stop = 1;
+    if (s_done && blockIdx.x == 0) *stop = conv ? 1 : 4;
   }
   __syncthreads();
   if (s_done) return;
@@ -372,6 +382,9 @@ __global__ void __launch_bounds__(NT) k_cg_direction(int k, double tol2, int64_t
     p2[i] = pp;
   }
 }
+
+// end of a CG batch: the next batch starts BATCH iterations later
+__global__ void k_cg_advance(int* kbase, int batch) { *kbase += batch; }
 
 // ------------------------------------------------------------------ energy
 // Pi_h = sum_q c_q (3/2) A^(-1/3) (eps_e^2 + delta)^(2/3) + load . U + 1/2 sum_bed U_b^T M U_b   (n = 3)
@@ -705,8 +718,10 @@ int ensure_ws(bp_mesh* m, cudaStream_t s) {
   WS_ALLOC(w->q, n);
   WS_ALLOC(w->R, n);
   WS_ALLOC(w->Ut, n);
-  WS_ALLOC(w->scal, 3 * (SCAL_CAP + 2));
+  WS_ALLOC(w->scal, 3 * (SCAL_CAP + 2 + CG_BATCH));
   WS_ALLOC(w->stop, 1);
+  WS_ALLOC(w->kbase, 1);
+  WS_ALLOC(w->cgpar, 2);
   WS_ALLOC(w->red, 8);
   WS_ALLOC(w->sia, 3 * nv);
 #undef WS_ALLOC
@@ -716,10 +731,16 @@ int ensure_ws(bp_mesh* m, cudaStream_t s) {
     cudaGetLastError();
     return BP_ENOMEM;
   }
+  if (cudaMallocHost(&w->hpar, 2 * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFreeHost(w->host);
+    return BP_ENOMEM;
+  }
   k_find_dslot<<<(m->nv + 127) / 128, 128, 0, s>>>(m->nbr_ptr, m->nbr_idx, m->nv, w->dslot);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     cudaFreeHost(w->host);
+    cudaFreeHost(w->hpar);
     bp_set_last_cuda_error(e, "k_find_dslot", __LINE__);
     return BP_ECUDA;
   }
@@ -795,49 +816,99 @@ int colprec_setup_t(bp_mesh* m, const M* J, cudaStream_t s) {
   return BP_OK;
 }
 
-// Preconditioned CG on J delta = -R to ||r|| <= eta ||R||.  delta is left in ws->x (type V).
+// One CG batch: CG_BATCH iterations (SpMV + dot, update + preconditioner, direction), then the
+// batch counter advances.  The iteration index, the tolerance and the limit are read from device
+// memory, so one captured graph serves every solve on this mesh and precision.
 template <class M, class V>
-int cg_solve(bp_mesh* m, const M* J, double eta, int maxit, int check_every, cudaStream_t s, int* iters,
-             int* status) {
+void launch_cg_batch(bp_mesh* m, const M* J, cudaStream_t s) {
   bp_solver_ws* w = m->ws;
-  const Prec<V> P = prec_of<V>(m);  // factors set up from the same-precision Jacobian
+  const Prec<V> P = prec_of<V>(m);
   const int64_t n = m->ndof;
-  maxit = std::min(maxit, w->scal_cap);
   V* x = reinterpret_cast<V*>(w->x);
   V* r = reinterpret_cast<V*>(w->r);
   V* z = reinterpret_cast<V*>(w->z);
   V* p = reinterpret_cast<V*>(w->p);
   V* q = reinterpret_cast<V*>(w->q);
-  BP_CUDA_TRY(cudaMemsetAsync(w->scal, 0, 3 * (size_t)(maxit + 2) * sizeof(double), s));
-  BP_CUDA_TRY(cudaMemsetAsync(w->stop, 0, sizeof(int), s));
-  const int gcol = (m->nv + NT - 1) / NT;
-  k_cg_init<V, V><<<gcol, NT, 0, s>>>(P, w->R, x, r, z, p, w->scal);
-  const double tol2 = eta * eta;
   const int gspmv = grid_for(n / 2 * TPR, NT);
   const int ncolv = 2 * (m->nl + 1);
   const int C = std::max(1, std::min(32, (int)((48 << 10) / (2 * ncolv * (int)sizeof(V)))));
   const size_t smem = 2 * (size_t)C * ncolv * sizeof(V);
   const int gupd = (m->nv + C - 1) / C;
+  for (int j = 0; j < CG_BATCH; ++j) {
+    k_spmv_pairs<M, V, true><<<gspmv, NT, 0, s>>>(m->rowptr, m->nbr_ptr, m->nbr_idx, m->nl, J, (int)(n / 2), p, q,
+                                                  w->scal, w->stop, w->kbase, j);
+    k_cg_update_staged<V, V><<<gupd, UPD_NT, smem, s>>>(P, w->kbase, j, C, x, r, z, p, q, w->scal, w->stop);
+    k_cg_direction<V><<<grid_for(n / 2, NT), NT, 0, s>>>(w->kbase, j, w->cgpar, n / 2, z, p, w->scal, w->stop);
+  }
+  k_cg_advance<<<1, 1, 0, s>>>(w->kbase, CG_BATCH);
+}
+
+template <class M, class V>
+int cg_batch_graph(bp_mesh* m, const M* J, cudaGraphExec_t* out) {
+  bp_solver_ws* w = m->ws;
+  const int slot = sizeof(V) == sizeof(float) ? 1 : 0;
+  if (!w->cg_exec[slot]) {
+    cudaStream_t cs;
+    BP_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) launch_cg_batch<M, V>(m, J, cs);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
+    if (e == cudaSuccess) e = e2;
+    cudaGraphExec_t exec = nullptr;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    cudaStreamDestroy(cs);
+    BP_CUDA_TRY(e);
+    w->cg_exec[slot] = exec;
+  }
+  *out = (cudaGraphExec_t)w->cg_exec[slot];
+  return BP_OK;
+}
+
+// Preconditioned CG on J delta = -R to ||r|| <= eta ||R||.  delta is left in ws->x (type V).
+// The iterations run as replays of the captured batch graph; the host reads the device stop flag
+// every check_every iterations (rounded up to whole batches).
+template <class M, class V>
+int cg_solve(bp_mesh* m, const M* J, double eta, int maxit, int check_every, cudaStream_t s, int* iters,
+             int* status) {
+  bp_solver_ws* w = m->ws;
+  const Prec<V> P = prec_of<V>(m);  // factors set up from the same-precision Jacobian
+  maxit = std::min(maxit, w->scal_cap);
+  V* x = reinterpret_cast<V*>(w->x);
+  V* r = reinterpret_cast<V*>(w->r);
+  V* z = reinterpret_cast<V*>(w->z);
+  V* p = reinterpret_cast<V*>(w->p);
+  cudaGraphExec_t exec;
+  int rc = cg_batch_graph<M, V>(m, J, &exec);
+  if (rc) return rc;
+  BP_CUDA_TRY(cudaMemsetAsync(w->scal, 0, 3 * (size_t)(maxit + 2 + CG_BATCH) * sizeof(double), s));
+  BP_CUDA_TRY(cudaMemsetAsync(w->stop, 0, sizeof(int), s));
+  BP_CUDA_TRY(cudaMemsetAsync(w->kbase, 0, sizeof(int), s));
+  // the staging buffer is rewritten only by the next solve, after this one has synchronised
+  w->hpar[0] = eta * eta;
+  w->hpar[1] = (double)maxit;
+  BP_CUDA_TRY(cudaMemcpyAsync(w->cgpar, w->hpar, 2 * sizeof(double), cudaMemcpyHostToDevice, s));
+  const int gcol = (m->nv + NT - 1) / NT;
+  k_cg_init<V, V><<<gcol, NT, 0, s>>>(P, w->R, x, r, z, p, w->scal);
+  BP_CUDA_TRY(cudaGetLastError());
+  const int batches_per_check = std::max(1, (check_every + CG_BATCH - 1) / CG_BATCH);
   int k = 0, done = 0;
   *status = 0;
   while (!done) {
-    const int kend = std::min(maxit, k + check_every);
-    for (; k < kend; ++k) {
-      k_spmv_pairs<M, V, true><<<gspmv, NT, 0, s>>>(m->rowptr, m->nbr_ptr, m->nbr_idx, m->nl, J, (int)(n / 2), p,
-                                                     q, w->scal + 3 * k, w->stop);
-      k_cg_update_staged<V, V><<<gupd, UPD_NT, smem, s>>>(P, k, C, x, r, z, p, q, w->scal, w->stop);
-      k_cg_direction<V><<<grid_for(n / 2, NT), NT, 0, s>>>(k, tol2, n / 2, z, p, w->scal, w->stop);
-    }
-    BP_CUDA_TRY(cudaGetLastError());
-    BP_CUDA_TRY(cudaMemcpyAsync(w->host, w->scal, 3 * (size_t)(k + 1) * sizeof(double), cudaMemcpyDeviceToHost, s));
+    for (int b = 0; b < batches_per_check && k < maxit; ++b, k += CG_BATCH) BP_CUDA_TRY(cudaGraphLaunch(exec, s));
+    const int kk = std::min(k, maxit);
+    BP_CUDA_TRY(cudaMemcpyAsync(w->host, w->scal, 3 * (size_t)(kk + 1) * sizeof(double), cudaMemcpyDeviceToHost, s));
     BP_CUDA_TRY(cudaMemcpyAsync(w->host + w->host_cap - 1, w->stop, sizeof(int), cudaMemcpyDeviceToHost, s));
     BP_CUDA_TRY(cudaStreamSynchronize(s));
     int stopflag;
     std::memcpy(&stopflag, w->host + w->host_cap - 1, sizeof(int));
     if (stopflag || k >= maxit) done = 1;
     if (stopflag == 2) *status = 2;
+    if (done) k = kk;
   }
-  // iterations actually taken: first j with r_j.r_j <= tol2 r_0.r_0
+  // iterations actually taken: first j with r_j.r_j <= eta^2 r_0.r_0
+  const double tol2 = eta * eta;
   const double rr0 = w->host[2];
   int taken = k;
   for (int j = 1; j <= k; ++j) {
@@ -867,6 +938,9 @@ double elapsed(cudaEvent_t a, cudaEvent_t b) {
 void bp_solver_ws_free(bp_mesh* m) {
   if (!m->ws) return;
   if (m->ws->host) cudaFreeHost(m->ws->host);
+  if (m->ws->hpar) cudaFreeHost(m->ws->hpar);
+  for (void* g : m->ws->cg_exec)
+    if (g) cudaGraphExecDestroy((cudaGraphExec_t)g);
   delete m->ws;  // device arrays are in m->allocations
   m->ws = nullptr;
 }
@@ -915,10 +989,12 @@ extern "C" int bp_spmv(bp_mesh* m, const void* J, int precision, const double* x
   const int npairs = (int)(m->ndof / 2);
   if (precision == BP_F64)
     k_spmv_pairs<double, double, false><<<grid, NT, 0, s>>>(m->rowptr, m->nbr_ptr, m->nbr_idx, m->nl,
-                                                            (const double*)J, npairs, x, y, nullptr, nullptr);
+                                                            (const double*)J, npairs, x, y, nullptr, nullptr,
+                                                            nullptr, 0);
   else
     k_spmv_pairs<float, double, false><<<grid, NT, 0, s>>>(m->rowptr, m->nbr_ptr, m->nbr_idx, m->nl,
-                                                           (const float*)J, npairs, x, y, nullptr, nullptr);
+                                                           (const float*)J, npairs, x, y, nullptr, nullptr,
+                                                           nullptr, 0);
   BP_CUDA_TRY(cudaGetLastError());
   return BP_OK;
 }
