@@ -204,6 +204,9 @@ enum { BP_GUESS_ZERO = 0, BP_GUESS_SIA = 1 };
 int bp_initial_guess(bp_mesh* mesh, int kind, double* U_dev, void* stream);
 
 enum { BP_KRYLOV_CG = 0 };
+/* Line search of bp_newton_solve (bp_solve_opts.line_search). */
+enum { BP_LS_OFF = 0, BP_LS_HALVING = 1, BP_LS_QUADRATIC = 2 };
+
 typedef struct {
   double rtol;        /* stop when ||F(U)||_2 <= rtol ||F(0)||_2 (F(0) is the driving-stress load) */
   int max_newton;     /* Newton iteration limit (<= 64) */
@@ -212,7 +215,10 @@ typedef struct {
   int precision;      /* BP_F64: FP64 Jacobian and Krylov; BP_F32: FP32 Jacobian lanes and Krylov
                          (inexact Newton); the residual, viscosity, norms and update stay FP64 */
   int krylov;         /* BP_KRYLOV_CG (the Jacobian is SPD) */
-  int line_search;    /* 1: Armijo backtracking on the energy, alpha = 1, 1/2, ..., 2^-10 */
+  int line_search;    /* Armijo test on the energy change (c = 1e-4, at most 11 trials), a BP_LS_*:
+                         BP_LS_OFF full steps; BP_LS_HALVING alpha = 1, 1/2, ..., 2^-10;
+                         BP_LS_QUADRATIC backtracking by quadratic interpolation of the energy
+                         change, each new alpha kept within [0.1, 0.9] of the rejected one */
   int check_every;    /* Krylov convergence is read back every check_every iterations */
 } bp_solve_opts;
 

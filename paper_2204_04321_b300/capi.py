@@ -23,6 +23,7 @@ BP_JAC_AUTO, BP_JAC_DUAL, BP_JAC_FACTORED = 0, 1, 2
 BP_GUESS_ZERO, BP_GUESS_SIA = 0, 1
 BP_KRYLOV_CG = 0
 BP_JUDGE_RESIDUAL, BP_JUDGE_ENERGY, BP_JUDGE_NONE = 0, 1, 2
+BP_LS_OFF, BP_LS_HALVING, BP_LS_QUADRATIC = 0, 1, 2
 
 
 class BPError(RuntimeError):

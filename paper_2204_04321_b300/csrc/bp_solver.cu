@@ -1077,6 +1077,7 @@ extern "C" int bp_newton_solve(bp_mesh* m, double* U, const bp_solve_opts* opts,
                                void* stream) {
   if (!m || !U || !opts || !rep || !bp_aligned16(U)) return BP_EINVAL;
   const bp_solve_opts o = *opts;
+  if (o.line_search < 0 || o.line_search > BP_LS_QUADRATIC) return BP_EINVAL;
   if (!(o.rtol > 0) || o.max_newton < 0 || o.max_newton > 64 || o.max_krylov < 1 || o.check_every < 1 ||
       (o.precision != BP_F64 && o.precision != BP_F32) || o.krylov != BP_KRYLOV_CG || !(o.eta_max > 0))
     return BP_EINVAL;
@@ -1173,7 +1174,10 @@ extern "C" int bp_newton_solve(bp_mesh* m, double* U, const bp_solve_opts* opts,
     // step without evaluating the energy (the Armijo test is then always met).
     const bool quadratic = k > 0 && rep->alpha[k - 1] == 1.0 && fn <= 0.1 * rep->history[k - 1] * fref;
     if (o.line_search && slope < 0.0 && !quadratic) {
-      // Armijo on the energy: Pi(U + alpha delta) - Pi(U) <= c alpha F . delta, alpha = 1, 1/2, ..., 2^-10.
+      // Armijo on the energy: Pi(U + alpha delta) - Pi(U) <= c alpha F . delta.  Trial steps:
+      // BP_LS_HALVING alpha = 1, 1/2, ..., 2^-10; BP_LS_QUADRATIC the minimiser of the quadratic
+      // through the energy change at 0 (value 0, slope F . delta) and at the rejected alpha,
+      // kept within [0.1, 0.9] of that alpha (backtracking by interpolation).
       const double c = 1e-4;
       for (int h = 0; h <= 10; ++h) {
         double dE;
@@ -1181,7 +1185,14 @@ extern "C" int bp_newton_solve(bp_mesh* m, double* U, const bp_solve_opts* opts,
                  : energy_change_host<double, double>(m, U, w->x, alpha, s, &dE);
         if (rc) return rc;
         if (dE <= c * alpha * slope || h == 10) break;
-        alpha *= 0.5;
+        if (o.line_search == BP_LS_QUADRATIC) {
+          const double curv = dE - slope * alpha;  // > 0 here (Armijo failed)
+          double an = -slope * alpha * alpha / (2.0 * curv);
+          if (!std::isfinite(an)) an = 0.5 * alpha;
+          alpha = std::min(std::max(an, 0.1 * alpha), 0.9 * alpha);
+        } else {
+          alpha *= 0.5;
+        }
       }
     }
     if (f32)

@@ -149,7 +149,8 @@ def test_newton_matches_oracle_newton_on_tiny_mesh():
 
 
 @pytest.mark.parametrize("precision", [0, 1])
-def test_newton_small_dome_converges_from_zero_and_sia_to_same_solution(precision):
+@pytest.mark.parametrize("line_search", [1, 2])
+def test_newton_small_dome_converges_from_zero_and_sia_to_same_solution(precision, line_search):
     c = capi()
     mesh = synth.config_small()
     om = oracle.OracleMesh(mesh)
@@ -158,7 +159,7 @@ def test_newton_small_dome_converges_from_zero_and_sia_to_same_solution(precisio
     for guess in (c.BP_GUESS_ZERO, c.BP_GUESS_SIA):
         U = torch.empty(dm.ndof, dtype=torch.float64, device="cuda")
         c.bp_initial_guess(dm.handle, guess, U)
-        rc, rep = c.bp_newton_solve(dm.handle, U, precision=precision)
+        rc, rep = c.bp_newton_solve(dm.handle, U, precision=precision, line_search=line_search)
         assert rc == c.BP_OK, rep
         assert rep["history"][-1] <= 1e-8
         Uh = U.cpu().numpy()
