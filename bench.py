@@ -109,6 +109,30 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def workload_name(m: int, layers: int) -> str:
+    """The assembly workload: dome on an m x m grid (2 m^2 triangles) extruded to `layers` layers."""
+    ntri = 2 * m * m
+    name = "dome-100k-tri-x10" if (m, layers) == (224, 10) else f"dome-{ntri // 1000}k-tri-x{layers}"
+    return (f"{name}: dome on a {m}x{m} jittered Delaunay grid, {ntri} triangles x {layers} "
+            f"layers = {ntri * layers} wedges, sinusoidal bed, correlated lognormal beta")
+
+
+def max_over_ranks(x: float, ws: int, device=None) -> float:
+    """The largest per-rank value over all ranks (a job takes as long as its slowest rank)."""
+    if ws <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(ws: int, units_per_rank_step: float, steps: int, seconds: float) -> float:
+    """Whole-job throughput of weak-scaled replicas: every rank processes the same units per step."""
+    return ws * units_per_rank_step * steps / seconds
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -160,8 +184,9 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": "dome-100k-tri-x10 (each step a bounded sample: dome-20k-tri-x10, "
-                                   "200,000 wedges, same generators)", "oracle": "CPU FP64, 1 thread"},
+            "config": {"workload": workload_name(args.mesh_m, args.layers),
+                       "sample": "each step: dome-20k-tri-x10, 200,000 wedges, same generators",
+                       "oracle": "CPU FP64, 1 thread"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": "dome-20k-tri-x10, 200,000 wedges per step"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -235,14 +260,9 @@ def run_ours(args):
         clk.window = (t_wall0, t_wall1)
     barrier()
     step_ms = [e0.elapsed_time(e1) for e0, e1 in ev]
-    total_ms = sum(step_ms)
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(step_ms), ws, dev)
     ms_per_step = total_ms / args.steps
-    value = ws * W * args.steps / (total_ms * 1e-3)
+    value = job_throughput(ws, W, args.steps, total_ms * 1e-3)
 
     # zero-initialisation share of a step (memset of J + copy of the memoised load into R), timed alone
     z0, z1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -312,14 +332,9 @@ def run_ours(args):
     for k in range(args.steps):
         e2e_step(k)
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(time.perf_counter() - t0, ws, dev)
     del slots
-    e2e_value = ws * W * args.steps / e2e_s
+    e2e_value = job_throughput(ws, W, args.steps, e2e_s)
 
     newton = newton_section(capi, synth, dm, mesh, dev, skip_large=args.no_large) if not args.no_newton else None
     mlp = mlp_section(capi, dev) if not args.no_mlp else None
@@ -343,9 +358,7 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"{mesh.name}: dome on a {args.mesh_m}x{args.mesh_m} jittered Delaunay grid, "
-                                   f"{mesh.ntri} triangles x {mesh.nlayers} layers = {W} wedges, "
-                                   "sinusoidal bed, correlated lognormal beta",
+            "config": {"workload": workload_name(args.mesh_m, args.layers),
                        "ndof": dm.ndof, "nnz": dm.nnz, "lanes": "f64, sum-factorised",
                        "scatter": "atomic", "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU",
                        "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MB write outside the timed events)"},
