@@ -530,6 +530,17 @@ def newton_section(capi, synth, dm, mesh, dev, skip_large=False, reps=3):
     out[mesh.name] = {"f64": f64, "mixed_f32": f32, "speedup_mixed": f64["s"] / f32["s"],
                       "mixed_vs_f64_solution_rel_inf": float((U32 - U64).abs().max() / U64.abs().max())}
     out[mesh.name]["learned_start_mixed"] = learned_start(capi, dm, dev, reps)
+    # the ocean margin condition (lateral faces of a grounded calving front, partly below sea level)
+    marine = synth.config_marine()
+    dmm = capi.DeviceMesh(marine)
+    m64, W64 = solve(dmm, capi.BP_F64)
+    m32, W32 = solve(dmm, capi.BP_F32)
+    out[marine.name] = {"wedges": marine.nwedges, "margin": "ocean (cryostatic minus sea-water pressure)",
+                        "f64": m64, "mixed_f32": m32, "speedup_mixed": m64["s"] / m32["s"],
+                        "mixed_vs_f64_solution_rel_inf": float((W32 - W64).abs().max() / W64.abs().max()),
+                        "max_speed_m_per_yr": float(torch.hypot(W64[0::2], W64[1::2]).max())}
+    del W64, W32
+    dmm.close()
     if not skip_large:
         big = synth.config_large()
         dmb = capi.DeviceMesh(big)

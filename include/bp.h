@@ -59,8 +59,22 @@ typedef enum {
 
 /* Glen exponent n (must be 3: the kernels use rcbrt), rate factor A [Pa^-n yr^-1],
  * ice density rho [kg m^-3], gravity g [m s^-2], regularisation delta [yr^-2]. */
+/* Lateral margin condition (paper Sec. 2, third boundary condition, on the vertical faces over the
+ * boundary edges of the base triangulation):
+ *   BP_MARGIN_FREE   2 mu eps_c . n = 0 (natural; the default reading for land-terminating margins);
+ *   BP_MARGIN_OCEAN  2 mu eps_c . n = (rho g (s - z) - rho_w g max(-z, 0)) n_c: the cryostatic ice
+ *                    pressure of the first-order model against the ocean's back-pressure below sea
+ *                    level z = 0 (the paper prints max(z, 0), read as the submerged part max(-z, 0)).
+ *                    In weak form R_i gets -int_face (rho g (s - z) - rho_w g max(-z, 0)) n_c N_i, a
+ *                    solution-independent load formed once at upload with a 2 x 2 Gauss rule per face
+ *                    (two points along the edge, two in zeta). */
+enum { BP_MARGIN_FREE = 0, BP_MARGIN_OCEAN = 1 };
+
 typedef struct {
   double n, A, rho, g, delta;
+  double rho_w;      /* sea-water density (kg m^-3), read with BP_MARGIN_OCEAN */
+  int32_t margin;    /* BP_MARGIN_FREE or BP_MARGIN_OCEAN */
+  int32_t reserved;
 } bp_params;
 
 /* Host description of an extruded mesh; all arrays are read during bp_mesh_upload only. */

@@ -42,7 +42,8 @@ class _OMesh(ctypes.Structure):
                 ("xy", ctypes.c_void_p), ("tri", ctypes.c_void_p), ("bed", ctypes.c_void_p),
                 ("thick", ctypes.c_void_p), ("beta", ctypes.c_void_p), ("sigma", ctypes.c_void_p),
                 ("n", ctypes.c_double), ("A", ctypes.c_double), ("rho", ctypes.c_double),
-                ("g", ctypes.c_double), ("delta", ctypes.c_double)]
+                ("g", ctypes.c_double), ("delta", ctypes.c_double), ("rho_w", ctypes.c_double),
+                ("margin", ctypes.c_int32), ("pad2", ctypes.c_int32)]
 
 
 def lib():
@@ -86,7 +87,7 @@ class OracleMesh:
         self.desc = _OMesh(mesh.nv, mesh.ntri, mesh.nlayers, 0, _ptr(self.xy).value,
                            _ptr(self.tri).value, _ptr(self.bed).value, _ptr(self.thick).value,
                            _ptr(self.beta).value, _ptr(self.sigma).value,
-                           p.n, p.A, p.rho, p.g, p.delta)
+                           p.n, p.A, p.rho, p.g, p.delta, p.rho_w, p.margin, 0)
         self.ndof = mesh.ndof
         self._pattern = None
 

@@ -13,7 +13,12 @@
 //    with the effective strain rate eps_e^2 = exx^2 + eyy^2 + exx eyy + exy^2 + exz^2 + eyz^2   Eq. effeps]
 //    (delta regularises U = 0; the paper's form is the delta = 0 limit)
 //  * stress-free upper surface (natural, contributes nothing), linear sliding law
-//    2 mu eps . n + beta u = 0 at the bed (Robin), stress-free vertical margins       [Sec. 2 BCs]
+//    2 mu eps . n + beta u = 0 at the bed (Robin), and on the vertical margins either
+//    stress-free (margin = 0) or the ocean condition (margin = 1)                      [Sec. 2 BCs]
+//    2 mu eps_c . n = (rho g (s - z) - rho_w g max(-z, 0)) n_c  (z = 0 at sea level; the
+//    paper prints max(z, 0), read as the submerged part), whose weak form adds
+//    -int_face (rho g (s - z) - rho_w g max(-z, 0)) n_c N_i to R_i on every vertical face
+//    over a boundary edge of the base triangulation (2 x 2 Gauss rule per face);
 //  * discretised with low-order nodal prismatic (6-node wedge) elements on the mesh
 //    extruded from the base triangulation, residual F(U; {phi_i}, {grad phi_i}, H, beta)  [Sec. 3.1, Eq. residual]
 //  * the Jacobian dF/dU by forward-mode automatic differentiation with a compile-time
@@ -35,6 +40,8 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <map>
+#include <utility>
 #include <vector>
 
 namespace {
@@ -48,6 +55,8 @@ struct Mesh {
   const double* beta;   // [nv]
   const double* sigma;  // [nlayers + 1]
   double n, A, rho, g, delta;
+  double rho_w;         // sea-water density (margin = 1)
+  int32_t margin;       // 0: stress-free vertical margins; 1: ocean condition
 };
 
 // ---------------------------------------------------------------- dual numbers
@@ -289,6 +298,50 @@ void gather_element(const Mesh& m, int l, const int64_t vert[3], const double* U
   for (int j = 0; j < 12; ++j) Ue[j] = U[dofs[j]];
 }
 
+// Load of the ocean margin condition on the vertical faces over the boundary edges (edges a -> b
+// of the counter-clockwise triangles whose reverse b -> a belongs to no triangle; the outward normal
+// times the edge length is (dy, -dx)).  A face over layer l is parametrised by t in [0, 1] along the
+// edge and zeta in [-1, 1]; on it N = (1 - t or t) (1 -/+ zeta) / 2 and n_c dGamma = (dy or -dx)
+// dz/dzeta dt dzeta.  2 x 2 Gauss rule.  F[dof] receives -int f n_c N, f = rho g (s - z) - rho_w g
+// max(-z, 0).  tri_mask (nullable): only edges of masked triangles.
+void lateral_load(const Mesh& m, const uint8_t* tri_mask, double* F) {
+  if (m.margin != 1) return;
+  std::map<std::pair<int, int>, int> owner;  // directed edge -> triangle
+  for (int t = 0; t < m.ntri; ++t)
+    for (int e = 0; e < 3; ++e) owner[{m.tri[3 * t + e], m.tri[3 * t + (e + 1) % 3]}] = t;
+  const double gt[2] = {0.5 - 0.5 / std::sqrt(3.0), 0.5 + 0.5 / std::sqrt(3.0)};  // weights 1/2
+  const double gz[2] = {-1.0 / std::sqrt(3.0), 1.0 / std::sqrt(3.0)};            // weights 1
+  for (const auto& kv : owner) {
+    const int a = kv.first.first, b = kv.first.second;
+    if (owner.count({b, a})) continue;  // interior edge
+    if (tri_mask && !tri_mask[kv.second]) continue;
+    const double dx = m.xy[2 * b] - m.xy[2 * a], dy = m.xy[2 * b + 1] - m.xy[2 * a + 1];
+    const double sa = m.bed[a] + m.thick[a], sb = m.bed[b] + m.thick[b];
+    for (int l = 0; l < m.nlayers; ++l) {
+      const double za0 = m.bed[a] + m.sigma[l] * m.thick[a], za1 = m.bed[a] + m.sigma[l + 1] * m.thick[a];
+      const double zb0 = m.bed[b] + m.sigma[l] * m.thick[b], zb1 = m.bed[b] + m.sigma[l + 1] * m.thick[b];
+      const int64_t lev[2] = {l, l + 1};
+      for (int it = 0; it < 2; ++it)
+        for (int iz = 0; iz < 2; ++iz) {
+          const double t = gt[it], zeta = gz[iz], w = 0.5;
+          const double psi[2] = {0.5 * (1.0 - zeta), 0.5 * (1.0 + zeta)};
+          const double z = (1 - t) * (psi[0] * za0 + psi[1] * za1) + t * (psi[0] * zb0 + psi[1] * zb1);
+          const double s = (1 - t) * sa + t * sb;
+          const double dzdzeta = 0.5 * ((1 - t) * (za1 - za0) + t * (zb1 - zb0));
+          const double f = m.rho * m.g * (s - z) - m.rho_w * m.g * std::max(-z, 0.0);
+          for (int k = 0; k < 2; ++k) {
+            const double Na = (1 - t) * psi[k], Nb = t * psi[k];
+            for (int c = 0; c < 2; ++c) {
+              const double nc = (c == 0 ? dy : -dx) * dzdzeta;
+              F[dof_index(m, a, lev[k], c)] -= w * f * nc * Na;
+              F[dof_index(m, b, lev[k], c)] -= w * f * nc * Nb;
+            }
+          }
+        }
+    }
+  }
+}
+
 bool mesh_ok(const Mesh& m) {
   if (m.nv <= 0 || m.ntri <= 0 || m.nlayers <= 0) return false;
   for (int64_t i = 0; i < 3 * (int64_t)m.ntri; ++i)
@@ -309,6 +362,8 @@ typedef struct {
   const double* beta;
   const double* sigma;
   double n, A, rho, g, delta;
+  double rho_w;
+  int32_t margin, pad2;
 } oracle_mesh;
 
 static Mesh unpack(const oracle_mesh* d) {
@@ -327,6 +382,8 @@ static Mesh unpack(const oracle_mesh* d) {
   m.rho = d->rho;
   m.g = d->g;
   m.delta = d->delta;
+  m.rho_w = d->rho_w;
+  m.margin = d->margin;
   return m;
 }
 
@@ -418,6 +475,7 @@ int oracle_residual(const oracle_mesh* d, const double* U, const uint8_t* tri_ma
       for (int j = 0; j < 12; ++j) R[dofs[j]] += Re[j];
     }
   }
+  lateral_load(m, tri_mask, R);
   return 0;
 }
 
@@ -511,6 +569,7 @@ int oracle_jacobian(const oracle_mesh* d, const double* U, const uint8_t* tri_ma
       }
     }
   }
+  if (R) lateral_load(m, tri_mask, R);
   return 0;
 }
 
@@ -572,6 +631,12 @@ double oracle_energy(const oracle_mesh* d, const double* U) {
         }
       }
     }
+  }
+  if (m.margin == 1) {  // the margin load is constant: its energy is F_lat . U
+    const int64_t ndof = 2 * (int64_t)m.nv * (m.nlayers + 1);
+    std::vector<double> F(ndof, 0.0);
+    lateral_load(m, nullptr, F.data());
+    for (int64_t i = 0; i < ndof; ++i) total += F[i] * U[i];
   }
   return total;
 }

@@ -24,6 +24,7 @@ BP_GUESS_ZERO, BP_GUESS_SIA = 0, 1
 BP_KRYLOV_CG = 0
 BP_JUDGE_RESIDUAL, BP_JUDGE_ENERGY, BP_JUDGE_NONE = 0, 1, 2
 BP_LS_OFF, BP_LS_HALVING, BP_LS_QUADRATIC = 0, 1, 2
+BP_MARGIN_FREE, BP_MARGIN_OCEAN = 0, 1
 
 
 class BPError(RuntimeError):
@@ -34,7 +35,8 @@ class BPError(RuntimeError):
 
 class bp_params(ctypes.Structure):
     _fields_ = [("n", ctypes.c_double), ("A", ctypes.c_double), ("rho", ctypes.c_double),
-                ("g", ctypes.c_double), ("delta", ctypes.c_double)]
+                ("g", ctypes.c_double), ("delta", ctypes.c_double), ("rho_w", ctypes.c_double),
+                ("margin", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class bp_mesh_desc(ctypes.Structure):
@@ -167,7 +169,7 @@ def make_desc(mesh):
     p = mesh.params
     desc = bp_mesh_desc(mesh.nv, mesh.ntri, mesh.nlayers, 0,
                         *[a.ctypes.data for a in keep],
-                        bp_params(p.n, p.A, p.rho, p.g, p.delta))
+                        bp_params(p.n, p.A, p.rho, p.g, p.delta, p.rho_w, p.margin, 0))
     return desc, keep
 
 

@@ -79,7 +79,10 @@ struct bp_mesh {
   // per dof / per entry
   int64_t* rowptr = nullptr;
   int32_t* colidx = nullptr;
-  double* load = nullptr;     // [ndof] driving-stress load rho g grad s . int N_i (solution independent)
+  double* load = nullptr;     // [ndof] solution-independent load: driving stress rho g grad s . int N_i
+                              // (+ the ocean margin load with BP_MARGIN_OCEAN)
+  int2* bedges = nullptr;     // boundary edges a -> b (ocean margin condition only)
+  int nbedges = 0;
   double* rscratch = nullptr; // [ndof] residual scratch for Jacobian calls with R = NULL
   uint16_t* mlp_X = nullptr;  // [nv][16] BF16 features of the learned guess
   float* mlp_Y = nullptr;     // [nv][32] network outputs

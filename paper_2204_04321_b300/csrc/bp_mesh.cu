@@ -77,6 +77,52 @@ __global__ void k_colidx(const int64_t* __restrict__ rowptr, const int32_t* __re
 // Over a wedge with vertical edges int lambda_a psi_k dV = area/24 (h_a + h_0 + h_1 + h_2), which the
 // 6-point rule integrates exactly.  The basal matrix uses the 3-point triangle rule on the true face area
 // (the integrand beta lambda_a lambda_b is cubic, so the rule -- not the exact integral -- defines it).
+// Ocean margin load (Sec. 2, lateral condition 2 mu eps_c . n = (rho g (s - z) - rho_w g max(-z, 0)) n_c):
+// the vertical face over boundary edge a -> b and layer l adds -int f n_c N_i dGamma to the load of its
+// four nodes.  Along the edge t in [0, 1], across the layer zeta in [-1, 1]: N = lambda(t) psi(zeta),
+// n_c dGamma = e_c (dz/dzeta) dt dzeta with e = (dy, -dx) the outward edge normal times the edge length
+// (triangles counter-clockwise).  2 x 2 Gauss points, weights 1/2 (t) x 1 (zeta).  One thread per
+// (edge, layer); atomics because neighbouring faces share nodes.
+__global__ void k_margin_load(const double2* __restrict__ xy, const double* __restrict__ bed,
+                              const double* __restrict__ thick, const double* __restrict__ sigma,
+                              const int2* __restrict__ edges, int nedges, int L, double rg, double rwg,
+                              double* __restrict__ load) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= (int64_t)nedges * L) return;
+  const int e = (int)(i / L), l = (int)(i - (int64_t)e * L);
+  const int v[2] = {edges[e].x, edges[e].y};
+  const double2 pa = xy[v[0]], pb = xy[v[1]];
+  const double en[2] = {pb.y - pa.y, pa.x - pb.x};
+  double zlo[2], zhi[2], sv[2];
+  for (int j = 0; j < 2; ++j) {
+    zlo[j] = bed[v[j]] + sigma[l] * thick[v[j]];
+    zhi[j] = bed[v[j]] + sigma[l + 1] * thick[v[j]];
+    sv[j] = bed[v[j]] + thick[v[j]];
+  }
+  const double gp = 0.5 / sqrt(3.0);
+  double acc[2][2][2] = {{{0, 0}, {0, 0}}, {{0, 0}, {0, 0}}};  // [vertex][level k][component]
+  for (int it = 0; it < 2; ++it)
+    for (int iz = 0; iz < 2; ++iz) {
+      const double t = it == 0 ? 0.5 - gp : 0.5 + gp;
+      const double zeta = iz == 0 ? -2.0 * gp : 2.0 * gp;
+      const double lam[2] = {1.0 - t, t}, psi[2] = {0.5 * (1.0 - zeta), 0.5 * (1.0 + zeta)};
+      double z = 0.0, s = 0.0, dz = 0.0;
+      for (int j = 0; j < 2; ++j) {
+        z += lam[j] * (psi[0] * zlo[j] + psi[1] * zhi[j]);
+        s += lam[j] * sv[j];
+        dz += lam[j] * 0.5 * (zhi[j] - zlo[j]);
+      }
+      const double f = rg * (s - z) - rwg * fmax(-z, 0.0);
+      const double wf = 0.5 * f * dz;
+      for (int j = 0; j < 2; ++j)
+        for (int k = 0; k < 2; ++k)
+          for (int c = 0; c < 2; ++c) acc[j][k][c] += wf * en[c] * lam[j] * psi[k];
+    }
+  for (int j = 0; j < 2; ++j)
+    for (int k = 0; k < 2; ++k)
+      for (int c = 0; c < 2; ++c) atomicAdd(load + bp_dof(v[j], l + k, c, L), -acc[j][k][c]);
+}
+
 __global__ void k_memo(const double2* __restrict__ xy, const double* __restrict__ bed,
                        const double* __restrict__ thick, const double* __restrict__ beta,
                        const double* __restrict__ sigma, const int32_t* __restrict__ tri, int ntri, int L,
@@ -142,6 +188,9 @@ int validate(const bp_mesh_desc* d) {
   if (d->nv < 3 || d->ntri < 1 || d->nlayers < 1) return BP_EINVAL;
   if (d->params.n != 3.0) return BP_EUNSUP;
   if (!(d->params.A > 0) || !(d->params.rho > 0) || !(d->params.g > 0) || !(d->params.delta >= 0))
+    return BP_EINVAL;
+  if (d->params.margin != BP_MARGIN_FREE && d->params.margin != BP_MARGIN_OCEAN) return BP_EINVAL;
+  if (d->params.margin == BP_MARGIN_OCEAN && !(d->params.rho_w >= 0 && std::isfinite(d->params.rho_w)))
     return BP_EINVAL;
   const int L = d->nlayers;
   // ndof must fit the int32 column indices
@@ -313,6 +362,36 @@ extern "C" int bp_mesh_upload(const bp_mesh_desc* d, void* stream_, bp_mesh** ou
   k_colidx<<<grid_rows, threads, 0, stream>>>(m->rowptr, m->nbr_ptr, m->nbr_idx, nv, L, m->colidx);
   k_memo<<<(ntri + 127) / 128, 128, 0, stream>>>(m->xy, m->bed, m->thick, m->beta, m->sigma, m->tri, ntri, L,
                                                  d->params.rho * d->params.g, m->load, m->basal, 1);
+  if (d->params.margin == BP_MARGIN_OCEAN) {
+    // boundary edges: directed edges a -> b of the (counter-clockwise) triangles whose reverse is absent
+    std::vector<int64_t> dir;
+    dir.reserve(3 * (size_t)ntri);
+    for (int t = 0; t < ntri; ++t)
+      for (int k = 0; k < 3; ++k) dir.push_back((int64_t)d->tri[3 * t + k] * nv + d->tri[3 * t + (k + 1) % 3]);
+    std::sort(dir.begin(), dir.end());
+    std::vector<int2> bedges;
+    for (int64_t key : dir) {
+      const int a = (int)(key / nv), b = (int)(key % nv);
+      if (!std::binary_search(dir.begin(), dir.end(), (int64_t)b * nv + a)) bedges.push_back(make_int2(a, b));
+    }
+    m->nbedges = (int)bedges.size();
+    if (m->nbedges > 0) {
+      if ((rc = bp_alloc(m, &m->bedges, bedges.size())) != BP_OK) return fail(rc);
+      if (cudaMemcpyAsync(m->bedges, bedges.data(), bedges.size() * sizeof(int2), cudaMemcpyHostToDevice,
+                          stream) != cudaSuccess)
+        return fail(BP_ECUDA);
+      const int64_t work = (int64_t)m->nbedges * L;
+      k_margin_load<<<(int)((work + 127) / 128), 128, 0, stream>>>(
+          m->xy, m->bed, m->thick, m->sigma, m->bedges, m->nbedges, L, d->params.rho * d->params.g,
+          d->params.rho_w * d->params.g, m->load);
+      // the upload returns only after the stream is synchronised below, so `bedges` outlives the copy
+      cudaError_t ce = cudaStreamSynchronize(stream);
+      if (ce != cudaSuccess) {
+        bp_set_last_cuda_error(ce, "margin load", __LINE__);
+        return fail(BP_ECUDA);
+      }
+    }
+  }
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
   if (e != cudaSuccess) {

@@ -35,6 +35,7 @@ import math
 import numpy as np
 
 RHO_ICE = 910.0       # kg m^-3
+RHO_WATER = 1028.0    # kg m^-3 (sea water)
 GRAVITY = 9.81        # m s^-2
 GLEN_N = 3.0
 RATE_FACTOR = 1e-16   # Pa^-3 yr^-1
@@ -59,6 +60,8 @@ class Params:
     rho: float = RHO_ICE
     g: float = GRAVITY
     delta: float = DELTA
+    rho_w: float = RHO_WATER
+    margin: int = 0       # 0: stress-free lateral margin; 1: cryostatic pressure against the ocean
 
     def as_array(self) -> np.ndarray:
         return np.array([self.n, self.A, self.rho, self.g, self.delta], dtype=np.float64)
@@ -246,6 +249,23 @@ def dome_mesh(m: int, nlayers: int, mesh_seed: int, beta_seed: int, H0: float = 
                 name=name)
 
 
+def marine_mesh(m: int, nlayers: int, mesh_seed: int, beta_seed: int, H0: float = 2000.0, front: float = 60.0,
+                name: str = "") -> Mesh:
+    """Marine-terminating ice cap for the ocean margin condition: the whole square is ice whose
+    surface follows the dome profile from H0 at the centre down to `front` at the distance of the
+    square's half width (and stays at `front` beyond it), on a bed that dips from +200 m at the
+    centre to -300 m there.  The square's boundary is then a grounded calving front 360 m thick with
+    its lower 300 m below sea level, just above flotation (rho_w / rho 300 m = 339 m): the ice and
+    water pressures on the front nearly balance, as at real tidewater fronts."""
+    xy, tri = jittered_grid(m, mesh_seed)
+    r = np.minimum(np.hypot(xy[:, 0], xy[:, 1]) / HALF_WIDTH, 1.0)
+    core = np.clip(1.0 - r ** (4.0 / 3.0), 0.0, None)
+    surface = front + (H0 - front) * core ** (3.0 / 7.0)
+    b = 200.0 - 500.0 * r
+    return Mesh(xy=xy, tri=tri, bed=b, thick=surface - b, beta=lognormal_beta_field(xy, beta_seed),
+                sigma=uniform_sigma(nlayers), params=Params(margin=1), name=name)
+
+
 # ---------------------------------------------------------------- named workloads
 
 def config_small() -> Mesh:
@@ -261,6 +281,11 @@ def config_medium() -> Mesh:
 def config_large() -> Mesh:
     """447 x 447 grid (399,618 triangles) x 10 layers = 3,996,180 wedges, sinusoidal bed."""
     return dome_mesh(447, 10, 301, 302, bed="sinusoidal", beta="field", name="dome-400k-tri-x10")
+
+
+def config_marine() -> Mesh:
+    """Marine ice cap with the ocean margin condition: 224 x 224 grid x 10 layers = 1,003,520 wedges."""
+    return marine_mesh(224, 10, 501, 502, name="marine-100k-tri-x10")
 
 
 def ensemble_members(count: int = 64, seed0: int = 4000, scale: float = 1.0):

@@ -53,6 +53,8 @@ MESHES = {
     "ragged": ragged_mesh,
     "single_layer": lambda: synth.dome_mesh(6, 1, 41, 42, bed="sinusoidal", beta="iid"),
     "two_layers": lambda: synth.dome_mesh(5, 2, 43, 44, bed="sinusoidal", beta="field"),
+    # ocean margin condition on the lateral faces (calving front partly below sea level)
+    "marine": lambda: synth.marine_mesh(12, 4, 45, 46),
 }
 
 

@@ -87,10 +87,11 @@ def test_column_preconditioner_is_exact_block_tridiagonal_solve(precision):
         assert rel_inf(z[idx], zc) <= tol
 
 
-@pytest.mark.parametrize("kind", ["random", "sia"])
+@pytest.mark.parametrize("kind", ["random", "sia", "marine"])
 def test_energy_matches_oracle(kind):
     c = capi()
-    mesh = synth.dome_mesh(20, 5, 61, 62, bed="sinusoidal", beta="field")
+    mesh = (synth.marine_mesh(14, 5, 61, 62) if kind == "marine"
+            else synth.dome_mesh(20, 5, 61, 62, bed="sinusoidal", beta="field"))
     om = oracle.OracleMesh(mesh)
     U = synth.random_velocity(mesh, 5) if kind == "random" else om.sia()
     dm = c.DeviceMesh(mesh)
@@ -133,9 +134,11 @@ def test_shallow_ice_guess_matches_oracle():
     assert float(U.abs().max()) == 0.0
 
 
-def test_newton_matches_oracle_newton_on_tiny_mesh():
+@pytest.mark.parametrize("geometry", ["dome", "marine"])
+def test_newton_matches_oracle_newton_on_tiny_mesh(geometry):
     c = capi()
-    mesh = synth.dome_mesh(4, 3, 71, 72, bed="sinusoidal", beta="iid")
+    mesh = (synth.marine_mesh(6, 3, 71, 72) if geometry == "marine"
+            else synth.dome_mesh(4, 3, 71, 72, bed="sinusoidal", beta="iid"))
     om = oracle.OracleMesh(mesh)
     Uo, info = oracle_newton(om, np.zeros(mesh.ndof), rtol=1e-10)
     assert info["converged"]
@@ -170,13 +173,14 @@ def test_newton_small_dome_converges_from_zero_and_sia_to_same_solution(precisio
 
 
 @pytest.mark.slow
-def test_newton_full_size_dome_reaches_1e8_checked_by_oracle():
+@pytest.mark.parametrize("geometry,precision", [("dome", 0), ("marine", 0), ("marine", 1)])
+def test_newton_full_size_dome_reaches_1e8_checked_by_oracle(geometry, precision):
     c = capi()
-    mesh = synth.config_medium()
+    mesh = synth.config_medium() if geometry == "dome" else synth.config_marine()
     dm = c.DeviceMesh(mesh)
     U = torch.empty(dm.ndof, dtype=torch.float64, device="cuda")
     c.bp_initial_guess(dm.handle, c.BP_GUESS_SIA, U)
-    rc, rep = c.bp_newton_solve(dm.handle, U, max_krylov=4000)
+    rc, rep = c.bp_newton_solve(dm.handle, U, max_krylov=4000, precision=precision)
     assert rc == c.BP_OK, rep
     om = oracle.OracleMesh(mesh)
     Uh = U.cpu().numpy()

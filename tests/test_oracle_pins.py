@@ -462,3 +462,74 @@ def test_oracle_newton_converges_quadratically_to_unique_minimiser():
     h = info1["history"]
     # quadratic tail: the last reduction is at least the square of the previous ratio (loosely)
     assert h[-1] <= 1e-10 and h[-1] <= 10 * h[-2] ** 1.5
+
+
+# ------------------------------------------------------------------ ocean margin condition (Sec. 2, lateral BC)
+
+def _margin(mesh, rho_w):
+    mesh.params.margin = 1
+    mesh.params.rho_w = rho_w
+    return mesh
+
+
+@pytest.mark.parametrize("m,L", [(2, 2), (5, 3)])
+def test_margin_cryostatic_load_balances_driving_stress_on_flat_bed(m, L):
+    """With rho_w = 0 the margin load is -int rho g (s - z) n_c N_i.  At U = 0 (no stress, no
+    friction) the residual is the load, and its sum over nodes is the total force
+    int rho g grad s dV - oint_lateral rho g (s - z) n dGamma, which the divergence theorem sets to
+    zero on a flat bed (s - z vanishes on the surface, n_c on the bed): the pin checks the face
+    geometry, the outward normal, the sign and the rule (exact here) against the volume term."""
+    mesh = _margin(tiny_mesh(m=m, L=L, bed="flat"), 0.0)
+    om = oracle.OracleMesh(mesh)
+    R = om.residual(np.zeros(mesh.ndof))
+    mesh.params.margin = 0
+    drive = oracle.OracleMesh(mesh).residual(np.zeros(mesh.ndof))
+    for c in (0, 1):
+        assert abs(R[c::2].sum()) <= 1e-12 * np.abs(drive[c::2]).sum()
+        assert np.abs(drive[c::2].sum()) > 1e-3 * np.abs(drive[c::2]).sum()  # the driving force is not zero
+
+
+@pytest.mark.parametrize("bed,rho_w", [(100.0, 1028.0), (-1500.0, 1028.0), (-1500.0, 0.0)])
+def test_margin_side_force_of_a_slab_closed_form(bed, rho_w):
+    """Slab of constant thickness on a flat bed at `bed` (all above, or all below sea level): the
+    x-force on the side x = +W is -2W (rho g H^2 / 2 - rho_w g int_b^s max(-z, 0) dz); nodes of that
+    side receive it all (the y-sides have n_x = 0) and the interior none (grad s = 0)."""
+    H = 1000.0
+    mesh = synth.slab_mesh(4, 3, slope=0.0, thickness=H, beta=1e3, half_width=5e3, jitter=0.0)
+    mesh.bed = np.full(mesh.nv, bed)
+    _margin(mesh, rho_w)
+    R = oracle.OracleMesh(mesh).residual(np.zeros(mesh.ndof))
+    s = bed + H
+    rg, wg = mesh.params.rho * mesh.params.g, rho_w * mesh.params.g
+    submerged = (max(-bed, 0.0) ** 2 - max(-s, 0.0) ** 2) / 2.0  # int_b^s max(-z, 0) dz
+    expected = -2 * 5e3 * (rg * H * H / 2.0 - wg * submerged)
+    right = np.abs(mesh.xy[:, 0] - 5e3) < 1e-6
+    rows = np.concatenate([mesh.dof(np.nonzero(right)[0], l, 0) for l in range(mesh.nlayers + 1)])
+    assert R[rows].sum() == pytest.approx(expected, rel=1e-12)
+    left = np.abs(mesh.xy[:, 0] + 5e3) < 1e-6
+    rows_l = np.concatenate([mesh.dof(np.nonzero(left)[0], l, 0) for l in range(mesh.nlayers + 1)])
+    assert R[rows_l].sum() == pytest.approx(-expected, rel=1e-12)   # opposite normal
+    inner = ~(right | left)
+    rows_i = np.concatenate([mesh.dof(np.nonzero(inner)[0], l, 0) for l in range(mesh.nlayers + 1)])
+    assert np.abs(R[rows_i]).max() <= 1e-9 * abs(expected)
+
+
+def test_margin_residual_is_gradient_of_energy():
+    """The margin load is constant, so the margin part of the energy is linear in U: its central
+    differences (energy with the margin minus energy without) equal the residual difference."""
+    mesh = _margin(tiny_mesh(m=2, L=2), 1028.0)
+    mesh.bed = mesh.bed - 500.0   # partly below sea level
+    om = oracle.OracleMesh(mesh)
+    rng = np.random.default_rng(21)
+    U = rng.uniform(-100, 100, mesh.ndof)
+    mesh.params.margin = 0
+    om0 = oracle.OracleMesh(mesh)
+    dR = om.residual(U) - om0.residual(U)
+    assert np.abs(dR).max() > 0
+    for j in rng.choice(mesh.ndof, 12, replace=False):
+        h = 1e-3 * max(1.0, abs(U[j]))
+        Up, Um = U.copy(), U.copy()
+        Up[j] += h
+        Um[j] -= h
+        fd = ((om.energy(Up) - om0.energy(Up)) - (om.energy(Um) - om0.energy(Um))) / (2 * h)
+        assert fd == pytest.approx(dR[j], rel=1e-6, abs=1e-6 * np.abs(dR).max())
