@@ -346,6 +346,17 @@ int bp_mlp_train_step(bp_mlp* mlp, const uint16_t* X_dev, const float* T_dev, in
 int bp_mlp_features(bp_mesh* mesh, uint16_t* X_dev, void* stream);
 /* Replace beta on an uploaded mesh (host array [nv]) and rebuild the basal friction matrices. */
 int bp_mesh_set_beta(bp_mesh* mesh, const double* beta_host, void* stream);
+/*
+ * Temperature-dependent rate factor (Sec. 2, the Arrhenius relation A = A0 exp(-Q / (R T*))):
+ * A_host [nv][L + 1] (node (a, l) at a (L + 1) + l, Pa^-3 yr^-1, > 0), e.g. evaluated from a
+ * pressure-corrected temperature field.  The library keeps the nodal hardness B = A^(-1/3) and
+ * interpolates it at the quadrature points with the wedge basis (2 mu = B (eps_e^2 + delta)^(-1/3));
+ * the residual, the Jacobian, the energy and every solver call use it.  A_host = NULL restores the
+ * uniform A of bp_mesh_upload.  Set it before bp_ensemble_create (an ensemble copies the pointer).
+ * The shallow-ice initial guess keeps the uniform A.  Synchronises `stream`.
+ * Errors: BP_EINVAL (NULL mesh, a value <= 0 or not finite), BP_ENOMEM, BP_ECUDA.
+ */
+int bp_mesh_set_rate_factor(bp_mesh* mesh, const double* A_host, void* stream);
 /* How bp_initial_guess_learned decides between the network's guess and the shallow-ice guess:
  *   BP_JUDGE_RESIDUAL  keep the guess with the smaller FP64 residual norm;
  *   BP_JUDGE_ENERGY    keep the guess with the smaller FP64 discrete energy Pi_h (the functional

@@ -43,7 +43,7 @@ class _OMesh(ctypes.Structure):
                 ("thick", ctypes.c_void_p), ("beta", ctypes.c_void_p), ("sigma", ctypes.c_void_p),
                 ("n", ctypes.c_double), ("A", ctypes.c_double), ("rho", ctypes.c_double),
                 ("g", ctypes.c_double), ("delta", ctypes.c_double), ("rho_w", ctypes.c_double),
-                ("margin", ctypes.c_int32), ("pad2", ctypes.c_int32)]
+                ("margin", ctypes.c_int32), ("pad2", ctypes.c_int32), ("Anode", ctypes.c_void_p)]
 
 
 def lib():
@@ -83,11 +83,14 @@ class OracleMesh:
         self.thick = np.ascontiguousarray(mesh.thick, dtype=np.float64)
         self.beta = np.ascontiguousarray(mesh.beta, dtype=np.float64)
         self.sigma = np.ascontiguousarray(mesh.sigma, dtype=np.float64)
+        rf = getattr(mesh, "rate_factor", None)
+        self.Anode = None if rf is None else np.ascontiguousarray(rf, dtype=np.float64)
         p = mesh.params
         self.desc = _OMesh(mesh.nv, mesh.ntri, mesh.nlayers, 0, _ptr(self.xy).value,
                            _ptr(self.tri).value, _ptr(self.bed).value, _ptr(self.thick).value,
                            _ptr(self.beta).value, _ptr(self.sigma).value,
-                           p.n, p.A, p.rho, p.g, p.delta, p.rho_w, p.margin, 0)
+                           p.n, p.A, p.rho, p.g, p.delta, p.rho_w, p.margin, 0,
+                           None if self.Anode is None else _ptr(self.Anode).value)
         self.ndof = mesh.ndof
         self._pattern = None
 

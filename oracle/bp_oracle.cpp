@@ -32,7 +32,9 @@
 //  * volume quadrature: 3-point triangle rule (points (1/6,1/6), (2/3,1/6), (1/6,2/3),
 //    weights 1/6) x 2-point Gauss-Legendre in zeta (+-1/sqrt 3, weights 1); basal face:
 //    the same triangle rule at zeta = -1;
-//  * s, beta, z nodal; z = b + sigma_l H; s = b + H.
+//  * s, beta, z nodal; z = b + sigma_l H; s = b + H;
+//  * a temperature-dependent rate factor (Arrhenius, Sec. 2) enters as nodal A; its hardness
+//    A^(-1/n) is interpolated with the wedge basis at each quadrature point.
 //
 // Nothing here is blocked, fused or reordered for speed.
 
@@ -57,7 +59,20 @@ struct Mesh {
   double n, A, rho, g, delta;
   double rho_w;         // sea-water density (margin = 1)
   int32_t margin;       // 0: stress-free vertical margins; 1: ocean condition
+  const double* Anode;  // nullable [nv][L + 1] rate factor per node (else the constant A)
 };
+
+// A^(-1/n) at a point with wedge basis values N (nodes: bottom a = 0..2 at level l, top at l + 1):
+// the nodal values of A^(-1/n) interpolated with the basis (reading of the Arrhenius field's
+// per-point evaluation), or the constant A^(-1/n).
+inline double hardness(const Mesh& m, const int64_t vert[3], int l, const double N[6]) {
+  if (!m.Anode) return std::pow(m.A, -1.0 / m.n);
+  double B = 0.0;
+  for (int k = 0; k < 2; ++k)
+    for (int a = 0; a < 3; ++a)
+      B += N[3 * k + a] * std::pow(m.Anode[vert[a] * (m.nlayers + 1) + l + k], -1.0 / m.n);
+  return B;
+}
 
 // ---------------------------------------------------------------- dual numbers
 constexpr int NL = 12;
@@ -232,12 +247,12 @@ void element_residual(const Mesh& m, int t, int l, const S Ue[12], S Re[12]) {
   for (int k = 0; k < 2; ++k)
     for (int a = 0; a < 3; ++a) s_nodal[3 * k + a] = m.bed[vert[a]] + m.thick[vert[a]];
   for (int j = 0; j < 12; ++j) Re[j] = S(dconst_like(Ue[j], 0.0));
-  const double Ainv = std::pow(m.A, -1.0 / m.n);
   const double pexp = (1.0 - m.n) / (2.0 * m.n);
   for (int q = 0; q < 6; ++q) {
     double xi, eta, zeta, w, N[6], gN[6][3], detJ;
     qp_ref(q, &xi, &eta, &zeta, &w);
     phys_basis(X, xi, eta, zeta, N, gN, &detJ);
+    const double Ainv = hardness(m, vert, l, N);
     S gu[3], gv[3];
     for (int r = 0; r < 3; ++r) {
       gu[r] = S(dconst_like(Ue[0], 0.0));
@@ -364,6 +379,7 @@ typedef struct {
   double n, A, rho, g, delta;
   double rho_w;
   int32_t margin, pad2;
+  const double* Anode;
 } oracle_mesh;
 
 static Mesh unpack(const oracle_mesh* d) {
@@ -384,6 +400,7 @@ static Mesh unpack(const oracle_mesh* d) {
   m.delta = d->delta;
   m.rho_w = d->rho_w;
   m.margin = d->margin;
+  m.Anode = d->Anode;
   return m;
 }
 
@@ -421,7 +438,7 @@ int oracle_qp_state(const oracle_mesh* d, const double* U, int t, int l, int q, 
       gs[r] += gN[i][r] * (m.bed[vert[i % 3]] + m.thick[vert[i % 3]]);
     }
   const double e2 = effective_strain2(gu, gv);
-  const double mu = 0.5 * std::pow(m.A, -1.0 / m.n) * std::pow(e2 + m.delta, (1.0 - m.n) / (2.0 * m.n));
+  const double mu = 0.5 * hardness(m, vert, l, N) * std::pow(e2 + m.delta, (1.0 - m.n) / (2.0 * m.n));
   for (int r = 0; r < 3; ++r) {
     out[r] = gu[r];
     out[3 + r] = gv[r];
@@ -581,9 +598,8 @@ int oracle_jacobian(const oracle_mesh* d, const double* U, const uint8_t* tri_ma
 double oracle_energy(const oracle_mesh* d, const double* U) {
   const Mesh m = unpack(d);
   if (!mesh_ok(m)) return NAN;
-  const double Ainv = std::pow(m.A, -1.0 / m.n);
   const double pexp = (m.n + 1.0) / (2.0 * m.n);
-  const double coef = Ainv * 2.0 * m.n / (m.n + 1.0);
+  const double cn = 2.0 * m.n / (m.n + 1.0);
   double total = 0.0;
   for (int t = 0; t < m.ntri; ++t) {
     int64_t vert[3];
@@ -607,6 +623,7 @@ double oracle_energy(const oracle_mesh* d, const double* U) {
           }
         }
         const double e2 = effective_strain2(gu, gv);
+        const double coef = hardness(m, vert, l, N) * cn;
         total += w * detJ * (coef * std::pow(e2 + m.delta, pexp) + m.rho * m.g * (gs[0] * uq + gs[1] * vq));
       }
       if (l == 0) {

@@ -112,6 +112,7 @@ SIGNATURES = {
     "bp_mlp_features": (_I, [_P, _P, _P]),
     "bp_mesh_set_beta": (_I, [_P, _P, _P]),
     "bp_initial_guess_learned": (_I, [_P, _P, _P, _I, _P, _P]),
+    "bp_mesh_set_rate_factor": (_I, [_P, _P, _P]),
 }
 
 _lock = threading.Lock()
@@ -374,6 +375,17 @@ def bp_mlp_features(handle, X, stream=None) -> None:
     _check(lib().bp_mlp_features(handle, _dptr(X), _stream_ptr(stream)), "bp_mlp_features")
 
 
+def bp_mesh_set_rate_factor(handle, A, stream=None) -> None:
+    """Nodal rate factor A [nv * (L + 1)] (host array, node order a (L + 1) + l), or None for the
+    uniform A of the upload."""
+    if A is None:
+        _check(lib().bp_mesh_set_rate_factor(handle, None, _stream_ptr(stream)), "bp_mesh_set_rate_factor")
+        return
+    a = np.ascontiguousarray(A, dtype=np.float64)
+    _check(lib().bp_mesh_set_rate_factor(handle, a.ctypes.data_as(ctypes.c_void_p), _stream_ptr(stream)),
+           "bp_mesh_set_rate_factor")
+
+
 def bp_mesh_set_beta(handle, beta, stream=None) -> None:
     b = np.ascontiguousarray(beta, dtype=np.float64)
     _check(lib().bp_mesh_set_beta(handle, b.ctypes.data_as(ctypes.c_void_p), _stream_ptr(stream)),
@@ -395,6 +407,8 @@ class DeviceMesh:
         import torch
         self.mesh = mesh
         self.handle = bp_mesh_upload(mesh, stream)
+        if getattr(mesh, "rate_factor", None) is not None:
+            bp_mesh_set_rate_factor(self.handle, mesh.rate_factor, stream)
         self.info = bp_mesh_info(self.handle)
         self.ndof = self.info["ndof"]
         self.nnz = self.info["nnz"]

@@ -29,6 +29,7 @@ AsmArgs make_args(const bp_mesh* m, const double* U, double* R, void* J) {
   a.count = m->ntri;
   a.L = m->nl;
   a.cA = m->cA;
+  a.Bn = m->Bnode;
   a.delta = m->p.delta;
   a.U = U;
   a.R = R;

@@ -49,6 +49,7 @@ struct AsmArgs {
   int32_t count;            // columns handled by this launch
   int32_t L;
   double cA, delta;
+  const double* Bn;  // nullable: [nv][L + 1] nodal hardness A^(-1/3) (rate-factor field); else cA
   const double* U;
   double* R;
   void* J;
@@ -202,7 +203,6 @@ __device__ __forceinline__ void assemble_column(const AsmArgs& A, const int t) {
   }
   const double d12 = d * (1.0 / 12.0);
   const double d6 = d * (1.0 / 6.0);
-  const float cAf = (float)A.cA;
   const TL d12L = (TL)d12;
   TL clx[3], cly[3];  // grad lambda in lane precision (Jacobian lanes)
   if constexpr (MODE == MODE_FACT) {
@@ -242,6 +242,16 @@ __device__ __forceinline__ void assemble_column(const AsmArgs& A, const int t) {
   double gvbx = vb[0] * lx[0] + vb[1] * lx[1] + vb[2] * lx[2];
   double gvby = vb[0] * ly[0] + vb[1] * ly[1] + vb[2] * ly[2];
   double carry[3][2] = {{0, 0}, {0, 0}, {0, 0}};  // residual of the current bottom level from the wedge below
+  // rate-factor field: hardness B = A^(-1/3) interpolated at the triangle points of the bottom level
+  double hb[3] = {A.cA, A.cA, A.cA};
+  if (A.Bn) {
+    const double b0 = A.Bn[(int64_t)v[0] * (L + 1)], b1 = A.Bn[(int64_t)v[1] * (L + 1)],
+                 b2 = A.Bn[(int64_t)v[2] * (L + 1)];
+    const double bs = (b0 + b1 + b2) * (1.0 / 6.0);
+    hb[0] = bs + 0.5 * b0;
+    hb[1] = bs + 0.5 * b1;
+    hb[2] = bs + 0.5 * b2;
+  }
 
   for (int l = 0; l < L; ++l) {
     double ut[3], vt[3];
@@ -258,6 +268,15 @@ __device__ __forceinline__ void assemble_column(const AsmArgs& A, const int t) {
     const double s_l = A.sigma[l];
     const double ds = A.sigma[l + 1] - s_l;
     const double invds = 1.0 / ds;
+    double ht[3] = {A.cA, A.cA, A.cA};  // hardness at the triangle points of the top level
+    if (A.Bn) {
+      const double b0 = A.Bn[(int64_t)v[0] * (L + 1) + l + 1], b1 = A.Bn[(int64_t)v[1] * (L + 1) + l + 1],
+                   b2 = A.Bn[(int64_t)v[2] * (L + 1) + l + 1];
+      const double bs = (b0 + b1 + b2) * (1.0 / 6.0);
+      ht[0] = bs + 0.5 * b0;
+      ht[1] = bs + 0.5 * b1;
+      ht[2] = bs + 0.5 * b2;
+    }
 
     // per zeta level: slope of the level surface and the 2D velocity gradients
     double Gzx[2], Gzy[2], GUx[2], GUy[2], GVx[2], GVy[2];
@@ -355,8 +374,8 @@ __device__ __forceinline__ void assemble_column(const AsmArgs& A, const int t) {
           const Dual<TL, 12> e2 = ux * ux + vy * (vy + ux) + exy * exy + exz * exz + eyz * eyz;
           const double xx = e2.v + A.delta;
           const double r = rcbrt(xx);
-          Dual<TL, 12> eta;  // eta = cA (e2 + delta)^(-1/3), d eta / d e2 = -eta / (3 (e2 + delta))
-          eta.v = A.cA * r;
+          Dual<TL, 12> eta;  // eta = B (e2 + delta)^(-1/3), d eta / d e2 = -eta / (3 (e2 + delta))
+          eta.v = (psi(0, z) * hb[tp] + psi(1, z) * ht[tp]) * r;
           const TL detad = (TL)(-(1.0 / 3.0) * eta.v * (r * r * r));
 #pragma unroll
           for (int j = 0; j < 12; ++j) eta.d[j] = detad * e2.d[j];
@@ -398,7 +417,7 @@ __device__ __forceinline__ void assemble_column(const AsmArgs& A, const int t) {
           const double e2 = fma(ux, ux, fma(vy, vy + ux, fma(exy, exy, ez[tp])));
           const double xx = e2 + A.delta;
           const double r = rcbrt(xx);
-          const double eta = A.cA * r;
+          const double eta = (psi(0, z) * hb[tp] + psi(1, z) * ht[tp]) * r;
           const double W = cq[tp] * eta;
           const double g1x = 2.0 * ux + vy, g2y = ux + 2.0 * vy;
           P1x[z] = fma(W, g1x, P1x[z]);
@@ -415,7 +434,7 @@ __device__ __forceinline__ void assemble_column(const AsmArgs& A, const int t) {
             TL Wp, tau1, tau2;
             if constexpr (kF32) {  // from r, t1, t2 converted once: FP32 arithmetic only
               const float rf = (float)r;
-              const float ef = cAf * rf;
+              const float ef = (float)eta;
               eta_q[z][tp] = ef;
               Wp = (-1.0f / 3.0f) * cqL[tp] * ef * (rf * rf * rf);
               tau1 = 2.0f * invhL[tp] * (float)t1;
@@ -648,6 +667,7 @@ __device__ __forceinline__ void assemble_column(const AsmArgs& A, const int t) {
     for (int a = 0; a < 3; ++a) {
       ub[a] = ut[a];
       vb[a] = vt[a];
+      hb[a] = ht[a];
     }
     gubx = gutx;
     guby = guty;

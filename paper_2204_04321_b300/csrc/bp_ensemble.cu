@@ -220,6 +220,7 @@ extern "C" int bp_ensemble_create(bp_mesh* const* members, int count, const doub
     a.count = m->ntri;
     a.L = m->nl;
     a.cA = m->cA;
+    a.Bn = m->Bnode;
     a.delta = m->p.delta;
     a.U = U[i];
     a.R = R[i];

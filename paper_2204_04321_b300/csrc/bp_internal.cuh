@@ -81,6 +81,8 @@ struct bp_mesh {
   int32_t* colidx = nullptr;
   double* load = nullptr;     // [ndof] solution-independent load: driving stress rho g grad s . int N_i
                               // (+ the ocean margin load with BP_MARGIN_OCEAN)
+  double* Bnode = nullptr;    // [nv][L + 1] hardness A^(-1/3) of the rate-factor field (NULL: uniform cA)
+  double* Bnode_buf = nullptr;  // its storage (kept when the field is switched off)
   int2* bedges = nullptr;     // boundary edges a -> b (ocean margin condition only)
   int nbedges = 0;
   double* rscratch = nullptr; // [ndof] residual scratch for Jacobian calls with R = NULL

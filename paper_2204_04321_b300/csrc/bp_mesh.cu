@@ -422,6 +422,30 @@ extern "C" int bp_csr_pattern(const bp_mesh* m, const int64_t** rowptr, const in
   return BP_OK;
 }
 
+extern "C" int bp_mesh_set_rate_factor(bp_mesh* m, const double* A, void* stream) {
+  if (!m) return BP_EINVAL;
+  if (!A) {  // back to the uniform rate factor of the upload parameters
+    m->Bnode = nullptr;
+    return BP_OK;
+  }
+  const int64_t n = (int64_t)m->nv * (m->nl + 1);
+  std::vector<double> B(n);
+  for (int64_t i = 0; i < n; ++i) {
+    if (!(A[i] > 0) || !std::isfinite(A[i])) return BP_EINVAL;
+    B[i] = std::pow(A[i], -1.0 / 3.0);  // hardness, interpolated at the quadrature points
+  }
+  bp_device_guard g(m->device);
+  if (!m->Bnode_buf) {
+    int rc = bp_alloc(m, &m->Bnode_buf, (size_t)n);
+    if (rc) return rc;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  BP_CUDA_TRY(cudaMemcpyAsync(m->Bnode_buf, B.data(), n * sizeof(double), cudaMemcpyHostToDevice, s));
+  BP_CUDA_TRY(cudaStreamSynchronize(s));
+  m->Bnode = m->Bnode_buf;
+  return BP_OK;
+}
+
 extern "C" int bp_mesh_set_beta(bp_mesh* m, const double* beta, void* stream) {
   if (!m || !beta) return BP_EINVAL;
   for (int a = 0; a < m->nv; ++a)

@@ -387,13 +387,26 @@ __global__ void __launch_bounds__(NT) k_cg_direction(const int* kbase, int j, co
 __global__ void k_cg_advance(int* kbase, int batch) { *kbase += batch; }
 
 // ------------------------------------------------------------------ energy
+// Hardness B = A^(-1/3) at the quadrature point (zeta level weights p0, p1 of layer l, triangle point
+// tp): the nodal field interpolated like the velocity, or the uniform value cA.
+__device__ __forceinline__ double hardness_at(const double* __restrict__ Bn, double cA, const int v[3], int L,
+                                              int l, double p0, double p1, int tp) {
+  if (!Bn) return cA;
+  double lo = 0.0, hi = 0.0;
+  for (int a = 0; a < 3; ++a) {
+    const double la = (a == tp) ? 2.0 / 3.0 : 1.0 / 6.0;
+    lo += la * Bn[(int64_t)v[a] * (L + 1) + l];
+    hi += la * Bn[(int64_t)v[a] * (L + 1) + l + 1];
+  }
+  return p0 * lo + p1 * hi;
+}
 // Pi_h = sum_q c_q (3/2) A^(-1/3) (eps_e^2 + delta)^(2/3) + load . U + 1/2 sum_bed U_b^T M U_b   (n = 3)
 __global__ void __launch_bounds__(128) k_energy(const double2* __restrict__ xy, const double* __restrict__ bed,
                                                 const double* __restrict__ thick, const double* __restrict__ sigma,
                                                 const int32_t* __restrict__ tri, const double* __restrict__ basal,
                                                 const double* __restrict__ load, int ntri, int L, int64_t ndof,
-                                                double cA, double delta, const double* __restrict__ U,
-                                                double* out) {
+                                                double cA, const double* __restrict__ Bn, double delta,
+                                                const double* __restrict__ U, double* out) {
   double acc = 0.0;
   // driving-stress part: load . U
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < ndof; i += (int64_t)gridDim.x * blockDim.x)
@@ -472,7 +485,7 @@ __global__ void __launch_bounds__(128) k_energy(const double2* __restrict__ xy, 
           const double exy = 0.5 * (uy + vx);
           const double e2 = ux * ux + vy * vy + ux * vy + exy * exy + 0.25 * (uz * uz + vz * vz);
           const double xx = e2 + delta;
-          acc += (d * h / 12.0) * 1.5 * cA * xx * rcbrt(xx);
+          acc += (d * h / 12.0) * 1.5 * hardness_at(Bn, cA, v, L, l, p0, p1, tp) * xx * rcbrt(xx);
         }
       }
     }
@@ -507,7 +520,8 @@ __global__ void __launch_bounds__(128) k_energy_change(const double2* __restrict
                                                        const int32_t* __restrict__ tri,
                                                        const double* __restrict__ basal,
                                                        const double* __restrict__ load, int ntri, int L,
-                                                       int64_t ndof, double cA, double delta, double alpha,
+                                                       int64_t ndof, double cA, const double* __restrict__ Bn,
+                                                       double delta, double alpha,
                                                        const double* __restrict__ U, const DT* __restrict__ D,
                                                        double* out) {
   double acc = 0.0;
@@ -619,7 +633,7 @@ __global__ void __launch_bounds__(128) k_energy_change(const double2* __restrict
           const T x1 = x0 + dx;
           const T ca = cube_root(x1), cb = cube_root(x0);
           const T diff23 = dx / (ca * ca + ca * cb + cb * cb) * (ca + cb);
-          lstress += Hq[tp] * (double)diff23;
+          lstress += Hq[tp] * hardness_at(Bn, cA, v, L, l, (double)p0, (double)p1, tp) * (double)diff23;
         }
       }
       stress += (d * ds / 12.0) * lstress;
@@ -636,7 +650,7 @@ __global__ void __launch_bounds__(128) k_energy_change(const double2* __restrict
         gB0[c] = gB1[c];
       }
     }
-    acc += 1.5 * cA * stress;
+    acc += 1.5 * stress;
   }
   block_add(acc, out);
 }
@@ -779,7 +793,7 @@ int energy_host(bp_mesh* m, const double* U, cudaStream_t s, double* out) {
   BP_CUDA_TRY(cudaMemsetAsync(w->red + 1, 0, sizeof(double), s));
   const int grid = (int)std::max<int64_t>((m->ntri + 127) / 128, std::min<int64_t>((m->ndof + 127) / 128, 148 * 16));
   k_energy<<<grid, 128, 0, s>>>(m->xy, m->bed, m->thick, m->sigma, m->tri, m->basal, m->load, m->ntri, m->nl,
-                                m->ndof, m->cA, m->p.delta, U, w->red + 1);
+                                m->ndof, m->cA, m->Bnode, m->p.delta, U, w->red + 1);
   BP_CUDA_TRY(cudaGetLastError());
   BP_CUDA_TRY(cudaMemcpyAsync(w->host, w->red + 1, sizeof(double), cudaMemcpyDeviceToHost, s));
   BP_CUDA_TRY(cudaStreamSynchronize(s));
@@ -794,7 +808,8 @@ int energy_change_host(bp_mesh* m, const double* U, const DT* D, double alpha, c
   BP_CUDA_TRY(cudaMemsetAsync(w->red + 2, 0, sizeof(double), s));
   const int grid = (int)std::max<int64_t>((m->ntri + 127) / 128, std::min<int64_t>((m->ndof + 127) / 128, 148 * 16));
   k_energy_change<T, DT><<<grid, 128, 0, s>>>(m->xy, m->bed, m->thick, m->sigma, m->tri, m->basal, m->load, m->ntri,
-                                              m->nl, m->ndof, m->cA, m->p.delta, alpha, U, D, w->red + 2);
+                                              m->nl, m->ndof, m->cA, m->Bnode, m->p.delta, alpha, U, D,
+                                              w->red + 2);
   BP_CUDA_TRY(cudaGetLastError());
   BP_CUDA_TRY(cudaMemcpyAsync(w->host, w->red + 2, sizeof(double), cudaMemcpyDeviceToHost, s));
   BP_CUDA_TRY(cudaStreamSynchronize(s));

@@ -79,6 +79,7 @@ class Mesh:
     sigma: np.ndarray   # [nlayers + 1] float64, 0 = bed ... 1 = surface
     params: Params = dataclasses.field(default_factory=Params)
     name: str = ""
+    rate_factor: np.ndarray | None = None  # [nv * (L + 1)] nodal A (Pa^-3 yr^-1), node a (L + 1) + l
 
     @property
     def nv(self) -> int:
@@ -264,6 +265,30 @@ def marine_mesh(m: int, nlayers: int, mesh_seed: int, beta_seed: int, H0: float 
     b = 200.0 - 500.0 * r
     return Mesh(xy=xy, tri=tri, bed=b, thick=surface - b, beta=lognormal_beta_field(xy, beta_seed),
                 sigma=uniform_sigma(nlayers), params=Params(margin=1), name=name)
+
+
+SECONDS_PER_YEAR = 365.25 * 86400.0
+GAS_CONSTANT = 8.314         # J mol^-1 K^-1
+
+
+def arrhenius_rate_factor(mesh: Mesh, T_centre: float = -30.0, T_margin: float = -15.0,
+                          T_bed: float = -2.0) -> np.ndarray:
+    """Nodal rate factor A [nv * (L + 1)] (Pa^-3 yr^-1) from a synthetic pressure-corrected
+    temperature field by the Arrhenius relation A = A0 exp(-Q / (R T*)): the surface temperature
+    rises linearly with the distance from the centre (T_centre to T_margin at the dome radius), the
+    bed is at T_bed, and T* is linear in sigma between them.  Constants: the two-regime values of
+    Cuffey and Paterson (2010), A(-10 C) = 3.5e-25 s^-1 Pa^-3, Q = 60 kJ/mol below -10 C and
+    115 kJ/mol above, with A0 = A(-10 C) exp(Q / (R 263.15 K)) in each regime."""
+    r = np.minimum(np.hypot(mesh.xy[:, 0], mesh.xy[:, 1]) / DOME_RADIUS, 1.0)
+    Ts = T_centre + (T_margin - T_centre) * r
+    L = mesh.nlayers
+    T = np.empty((mesh.nv, L + 1))
+    for l in range(L + 1):
+        T[:, l] = T_bed + (Ts - T_bed) * mesh.sigma[l]
+    Tk = 273.15 + T
+    Q = np.where(Tk < 263.15, 6.0e4, 1.15e5)
+    A0 = 3.5e-25 * np.exp(Q / (GAS_CONSTANT * 263.15))
+    return (A0 * np.exp(-Q / (GAS_CONSTANT * Tk)) * SECONDS_PER_YEAR).reshape(-1)
 
 
 # ---------------------------------------------------------------- named workloads

@@ -48,6 +48,13 @@ def ragged_mesh(m=23, L=4, seed=31):
     return mesh
 
 
+def arrhenius_mesh():
+    """Temperature-dependent rate factor (nodal field, 35x range of A)."""
+    mesh = synth.dome_mesh(10, 4, 47, 48, bed="sinusoidal", beta="field")
+    mesh.rate_factor = synth.arrhenius_rate_factor(mesh)
+    return mesh
+
+
 MESHES = {
     "small": synth.config_small,
     "ragged": ragged_mesh,
@@ -55,6 +62,7 @@ MESHES = {
     "two_layers": lambda: synth.dome_mesh(5, 2, 43, 44, bed="sinusoidal", beta="field"),
     # ocean margin condition on the lateral faces (calving front partly below sea level)
     "marine": lambda: synth.marine_mesh(12, 4, 45, 46),
+    "arrhenius": arrhenius_mesh,
 }
 
 

@@ -87,11 +87,13 @@ def test_column_preconditioner_is_exact_block_tridiagonal_solve(precision):
         assert rel_inf(z[idx], zc) <= tol
 
 
-@pytest.mark.parametrize("kind", ["random", "sia", "marine"])
+@pytest.mark.parametrize("kind", ["random", "sia", "marine", "arrhenius"])
 def test_energy_matches_oracle(kind):
     c = capi()
     mesh = (synth.marine_mesh(14, 5, 61, 62) if kind == "marine"
             else synth.dome_mesh(20, 5, 61, 62, bed="sinusoidal", beta="field"))
+    if kind == "arrhenius":
+        mesh.rate_factor = synth.arrhenius_rate_factor(mesh)
     om = oracle.OracleMesh(mesh)
     U = synth.random_velocity(mesh, 5) if kind == "random" else om.sia()
     dm = c.DeviceMesh(mesh)
@@ -134,11 +136,13 @@ def test_shallow_ice_guess_matches_oracle():
     assert float(U.abs().max()) == 0.0
 
 
-@pytest.mark.parametrize("geometry", ["dome", "marine"])
+@pytest.mark.parametrize("geometry", ["dome", "marine", "arrhenius"])
 def test_newton_matches_oracle_newton_on_tiny_mesh(geometry):
     c = capi()
     mesh = (synth.marine_mesh(6, 3, 71, 72) if geometry == "marine"
             else synth.dome_mesh(4, 3, 71, 72, bed="sinusoidal", beta="iid"))
+    if geometry == "arrhenius":
+        mesh.rate_factor = synth.arrhenius_rate_factor(mesh)
     om = oracle.OracleMesh(mesh)
     Uo, info = oracle_newton(om, np.zeros(mesh.ndof), rtol=1e-10)
     assert info["converged"]
@@ -186,3 +190,21 @@ def test_newton_full_size_dome_reaches_1e8_checked_by_oracle(geometry, precision
     Uh = U.cpu().numpy()
     f = np.linalg.norm(om.residual(Uh)) / np.linalg.norm(om.residual(np.zeros_like(Uh)))
     assert f <= 1.1e-8, f
+
+
+def test_rate_factor_entry_validates_and_resets():
+    c = capi()
+    mesh = synth.config_small()
+    dm = c.DeviceMesh(mesh)
+    U = dev(synth.random_velocity(mesh, 3))
+    R0 = dm.residual(U).cpu().numpy()
+    bad = np.full(mesh.nv * (mesh.nlayers + 1), mesh.params.A)
+    bad[7] = -1.0
+    with pytest.raises(c.BPError) as e:
+        c.bp_mesh_set_rate_factor(dm.handle, bad)
+    assert e.value.status == c.BP_EINVAL
+    c.bp_mesh_set_rate_factor(dm.handle, np.full(mesh.nv * (mesh.nlayers + 1), 8 * mesh.params.A))
+    R8 = dm.residual(U).cpu().numpy()
+    c.bp_mesh_set_rate_factor(dm.handle, None)
+    assert rel_inf(dm.residual(U).cpu().numpy(), R0) <= 1e-14
+    assert rel_inf(R8, R0) > 1e-3   # an 8x softer ice halves the stress term

@@ -533,3 +533,82 @@ def test_margin_residual_is_gradient_of_energy():
         Um[j] -= h
         fd = ((om.energy(Up) - om0.energy(Up)) - (om.energy(Um) - om0.energy(Um))) / (2 * h)
         assert fd == pytest.approx(dR[j], rel=1e-6, abs=1e-6 * np.abs(dR).max())
+
+
+# ------------------------------------------------------------------ temperature-dependent rate factor (Sec. 2, Arrhenius)
+
+def test_uniform_rate_factor_field_equals_the_constant():
+    mesh = tiny_mesh(m=3, L=2)
+    rng = np.random.default_rng(31)
+    U = rng.uniform(-100, 100, mesh.ndof)
+    om0 = oracle.OracleMesh(mesh)
+    R0, E0 = om0.residual(U), om0.energy(U)
+    _, _, J0, _ = om0.jacobian(U)
+    mesh.rate_factor = np.full(mesh.nv * (mesh.nlayers + 1), mesh.params.A)
+    om = oracle.OracleMesh(mesh)
+    _, _, J1, _ = om.jacobian(U)
+    assert np.abs(om.residual(U) - R0).max() <= 1e-13 * np.abs(R0).max()
+    assert np.abs(J1 - J0).max() <= 1e-13 * np.abs(J0).max()
+    assert om.energy(U) == pytest.approx(E0, rel=1e-13)
+
+
+def test_affine_hardness_field_is_reproduced_at_the_quadrature_points():
+    """Nodal A = (b0 + g . x)^-3 makes the hardness A^(-1/3) affine in x; interpolated with the wedge
+    basis it must equal b0 + g . x_q at every quadrature point (a wrong node or level index of the
+    field, or a wrong exponent, breaks this)."""
+    mesh = tiny_mesh(m=3, L=3)
+    b0, g = 2.0e5, np.array([3.0, -2.0, 40.0])
+    L = mesh.nlayers
+    A = np.empty((mesh.nv, L + 1))
+    for l in range(L + 1):
+        X = np.stack([mesh.xy[:, 0], mesh.xy[:, 1], mesh.bed + mesh.sigma[l] * mesh.thick], 1)
+        A[:, l] = (b0 + X @ g) ** -3.0
+    mesh.rate_factor = A.reshape(-1)
+    om = oracle.OracleMesh(mesh)
+    rng = np.random.default_rng(32)
+    U = rng.uniform(-100, 100, mesh.ndof)
+    for t in range(0, mesh.ntri, 3):
+        for l in range(L):
+            vert = mesh.tri[t]
+            Xw = np.array([[mesh.xy[v, 0], mesh.xy[v, 1], mesh.bed[v] + mesh.sigma[l + k] * mesh.thick[v]]
+                           for k in (0, 1) for v in vert])
+            for q in range(6):
+                xi, eta, zeta, _ = oracle.quadrature_point(q)
+                N, _, _ = oracle.basis_at(Xw, xi, eta, zeta)
+                xq = N @ Xw
+                st = om.qp_state(U, t, l, q)
+                B = 2 * st["mu"] * (st["eps2"] + mesh.params.delta) ** (1.0 / 3.0)
+                assert B == pytest.approx(b0 + xq @ g, rel=1e-12)
+
+
+def test_rate_factor_field_residual_is_gradient_of_energy():
+    mesh = tiny_mesh(m=2, L=2)
+    mesh.rate_factor = synth.arrhenius_rate_factor(mesh)
+    om = oracle.OracleMesh(mesh)
+    rng = np.random.default_rng(33)
+    U = rng.uniform(-100, 100, mesh.ndof)
+    R = om.residual(U)
+    J, _ = om.jacobian_scipy(U)
+    for j in rng.choice(mesh.ndof, 12, replace=False):
+        h = 1e-3 * max(1.0, abs(U[j]))
+        Up, Um = U.copy(), U.copy()
+        Up[j] += h
+        Um[j] -= h
+        fd = (om.energy(Up) - om.energy(Um)) / (2 * h)
+        assert fd == pytest.approx(R[j], rel=1e-6, abs=1e-9 * np.abs(R).max())
+        fdJ = (om.residual(Up) - om.residual(Um)) / (2 * h)
+        col = J[:, j].toarray().ravel()
+        assert np.abs(fdJ - col).max() <= 1e-6 * np.abs(col).max()
+
+
+def test_arrhenius_rate_factor_values():
+    """The generator's A at -10 C is the reference 3.5e-25 s^-1 Pa^-3 in both regimes, and A rises
+    with temperature (and steeply above -10 C)."""
+    mesh = tiny_mesh(m=2, L=2)
+    A = synth.arrhenius_rate_factor(mesh, T_centre=-10.0, T_margin=-10.0, T_bed=-10.0)
+    assert np.allclose(A, 3.5e-25 * synth.SECONDS_PER_YEAR, rtol=1e-12)
+    warm = synth.arrhenius_rate_factor(mesh, T_centre=-2.0, T_margin=-2.0, T_bed=-2.0)[0]
+    cold = synth.arrhenius_rate_factor(mesh, T_centre=-30.0, T_margin=-30.0, T_bed=-30.0)[0]
+    assert cold < A[0] < warm
+    # Q = 115 kJ/mol above -10 C: A(-2 C) / A(-10 C) = exp(Q/R (1/263.15 - 1/271.15))
+    assert warm / A[0] == pytest.approx(math.exp(1.15e5 / 8.314 * (1 / 263.15 - 1 / 271.15)), rel=1e-12)
