@@ -234,6 +234,9 @@ typedef struct {
                          BP_LS_QUADRATIC backtracking by quadratic interpolation of the energy
                          change, each new alpha kept within [0.1, 0.9] of the rejected one */
   int check_every;    /* Krylov convergence is read back every check_every iterations */
+  double picard_rtol; /* > 0: while ||F|| > picard_rtol ||F(0)|| take Picard steps (the Jacobian
+                         without the eta' rank-one part: the fixed-viscosity matrix, SPD, cheaper
+                         to assemble), then Newton steps; 0: Newton from the first step */
 } bp_solve_opts;
 
 typedef struct {
@@ -250,7 +253,8 @@ typedef struct {
   double t_total, t_assemble, t_precond, t_krylov, t_linesearch; /* seconds (CUDA events) */
 } bp_solve_report;
 
-/* Defaults: rtol 1e-8, 50 Newton, 1000 Krylov, eta_max 0.1, BP_F64, CG, line search on, check 8. */
+/* Defaults: rtol 1e-8, 50 Newton, 1000 Krylov, eta_max 0.1, BP_F64, CG, line search on, check 8,
+ * picard_rtol 0. */
 void bp_solve_opts_default(bp_solve_opts* opts);
 
 /*

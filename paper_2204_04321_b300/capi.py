@@ -55,7 +55,7 @@ class bp_mesh_info_t(ctypes.Structure):
 class bp_solve_opts(ctypes.Structure):
     _fields_ = [("rtol", ctypes.c_double), ("max_newton", ctypes.c_int), ("max_krylov", ctypes.c_int),
                 ("eta_max", ctypes.c_double), ("precision", ctypes.c_int), ("krylov", ctypes.c_int),
-                ("line_search", ctypes.c_int), ("check_every", ctypes.c_int)]
+                ("line_search", ctypes.c_int), ("check_every", ctypes.c_int), ("picard_rtol", ctypes.c_double)]
 
 
 class bp_solve_report(ctypes.Structure):

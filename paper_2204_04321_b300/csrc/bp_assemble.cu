@@ -7,11 +7,11 @@
 
 namespace {
 
-template <int MODE, class TL, bool ATOMIC>
+template <int MODE, class TL, bool ATOMIC, bool PICARD = false>
 __global__ void __launch_bounds__(128) k_assemble(const AsmArgs A) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= A.count) return;
-  assemble_column<MODE, TL, ATOMIC>(A, A.tri_list ? A.tri_list[idx] : idx);
+  assemble_column<MODE, TL, ATOMIC, PICARD>(A, A.tri_list ? A.tri_list[idx] : idx);
 }
 
 AsmArgs make_args(const bp_mesh* m, const double* U, double* R, void* J) {
@@ -37,17 +37,17 @@ AsmArgs make_args(const bp_mesh* m, const double* U, double* R, void* J) {
   return a;
 }
 
-template <int MODE, class TL>
+template <int MODE, class TL, bool PICARD = false>
 int launch(const bp_mesh* m, AsmArgs a, int scatter, cudaStream_t s) {
   constexpr int TPB = 128;
   if (scatter == BP_SCATTER_COLOR) {
     for (int c = 0; c < m->ncolors; ++c) {
       a.tri_list = m->color_tris + m->color_off[c];
       a.count = m->color_off[c + 1] - m->color_off[c];
-      k_assemble<MODE, TL, false><<<(a.count + TPB - 1) / TPB, TPB, 0, s>>>(a);
+      k_assemble<MODE, TL, false, PICARD><<<(a.count + TPB - 1) / TPB, TPB, 0, s>>>(a);
     }
   } else {
-    k_assemble<MODE, TL, true><<<(a.count + TPB - 1) / TPB, TPB, 0, s>>>(a);
+    k_assemble<MODE, TL, true, PICARD><<<(a.count + TPB - 1) / TPB, TPB, 0, s>>>(a);
   }
   BP_CUDA_TRY(cudaGetLastError());
   return BP_OK;
@@ -63,8 +63,8 @@ extern "C" int bp_assemble_residual(bp_mesh* m, const double* U, double* R, void
   return launch<MODE_RES, double>(m, make_args(m, U, R, nullptr), BP_SCATTER_ATOMIC, s);
 }
 
-extern "C" int bp_assemble_jacobian(bp_mesh* m, const double* U, double* R, void* J, int precision,
-                                    int scatter, int method, void* stream) {
+int bp_assemble_jacobian_ex(bp_mesh* m, const double* U, double* R, void* J, int precision, int scatter, int method,
+                            int picard, void* stream) {
   if (!m || !U || !J || !bp_aligned16(U)) return BP_EINVAL;
   if (precision != BP_F64 && precision != BP_F32 && precision != BP_F64X2) return BP_EINVAL;
   if (precision == BP_F64X2 && method == BP_JAC_DUAL) return BP_EUNSUP;
@@ -85,12 +85,22 @@ extern "C" int bp_assemble_jacobian(bp_mesh* m, const double* U, double* R, void
   BP_CUDA_TRY(cudaMemcpyAsync(Rw, m->load, m->ndof * sizeof(double), cudaMemcpyDeviceToDevice, s));
   BP_CUDA_TRY(cudaMemsetAsync(J, 0, m->nnz * (precision == BP_F32 ? sizeof(float) : sizeof(double)), s));
   const AsmArgs a = make_args(m, U, Rw, J);
+  if (picard) {  // fixed-viscosity matrix (Newton solver's Picard steps): factored method, FP64 or FP32
+    if (method != BP_JAC_FACTORED || precision == BP_F64X2) return BP_EUNSUP;
+    return precision == BP_F64 ? launch<MODE_FACT, double, true>(m, a, scatter, s)
+                               : launch<MODE_FACT, float, true>(m, a, scatter, s);
+  }
   if (precision == BP_F64X2) return launch<MODE_FACT, f64x2>(m, a, scatter, s);
   if (precision == BP_F64)
     return method == BP_JAC_DUAL ? launch<MODE_DUAL, double>(m, a, scatter, s)
                                  : launch<MODE_FACT, double>(m, a, scatter, s);
   return method == BP_JAC_DUAL ? launch<MODE_DUAL, float>(m, a, scatter, s)
                                : launch<MODE_FACT, float>(m, a, scatter, s);
+}
+
+extern "C" int bp_assemble_jacobian(bp_mesh* m, const double* U, double* R, void* J, int precision,
+                                    int scatter, int method, void* stream) {
+  return bp_assemble_jacobian_ex(m, U, R, J, precision, scatter, method, 0, stream);
 }
 
 // ---------------------------------------------------------------------------------------------

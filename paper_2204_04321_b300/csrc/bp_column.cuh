@@ -166,7 +166,9 @@ __device__ __forceinline__ Dual<TL, NL> operator*(double s, const Dual<TL, NL>& 
 
 // ------------------------------------------------------------------ the column kernel
 // Assembles every wedge of the column above base triangle t (one thread).
-template <int MODE, class TL, bool ATOMIC>
+// PICARD (factored method only): leave out the eta' rank-one part, i.e. assemble the fixed-viscosity
+// (Picard) matrix instead of the Jacobian; the residual is unchanged.
+template <int MODE, class TL, bool ATOMIC, bool PICARD = false>
 __device__ __forceinline__ void assemble_column(const AsmArgs& A, const int t) {
   const int L = A.L;
 
@@ -445,6 +447,7 @@ __device__ __forceinline__ void assemble_column(const AsmArgs& A, const int t) {
               tau1 = (TL)(2.0 * invh[tp] * t1);
               tau2 = (TL)(2.0 * invh[tp] * t2);
             }
+            if constexpr (!PICARD) {
             const TL fg1x = (TL)g1x, fexy = (TL)exy, fg2y = (TL)g2y;
             // p_{(a,k),c} = psi_k alpha_{a,c} -/+ t_{a,c},  alpha = g_c,xy . Lambda_a,  t = lambda_a tau_c / 2
             TL p[12];
@@ -465,6 +468,7 @@ __device__ __forceinline__ void assemble_column(const AsmArgs& A, const int t) {
 #pragma unroll
               for (int j = i; j < 12; ++j) K[uidx(i, j)] += pw * p[j];
             }
+            }  // !PICARD
           }
         }
       }

@@ -101,6 +101,10 @@ int bp_nodal_surface_gradient(bp_mesh* m, double** acc, cudaStream_t s);
 // ||v||_2 of an ndof vector (synchronous)
 int bp_norm2_host(bp_mesh* m, const double* v, cudaStream_t s, double* out);
 // scratch of the learned guess: features, outputs, a shallow-ice guess, a residual
+// bp_assemble_jacobian with the option to leave out the eta' rank-one part of the sum-factorised
+// Jacobian (picard = 1: the fixed-viscosity matrix of a Picard step).
+int bp_assemble_jacobian_ex(bp_mesh* m, const double* U, double* R, void* J, int precision, int scatter, int method,
+                            int picard, void* stream);
 int bp_learned_scratch(bp_mesh* m, uint16_t** X, float** Y, double** Usia, double** R, double** red);
 
 // Allocation helper that records the pointer in the mesh (freed by bp_mesh_free).

@@ -1086,6 +1086,7 @@ extern "C" void bp_solve_opts_default(bp_solve_opts* o) {
   o->krylov = BP_KRYLOV_CG;
   o->line_search = 1;
   o->check_every = 8;
+  o->picard_rtol = 0.0;
 }
 
 extern "C" int bp_newton_solve(bp_mesh* m, double* U, const bp_solve_opts* opts, bp_solve_report* rep,
@@ -1093,6 +1094,7 @@ extern "C" int bp_newton_solve(bp_mesh* m, double* U, const bp_solve_opts* opts,
   if (!m || !U || !opts || !rep || !bp_aligned16(U)) return BP_EINVAL;
   const bp_solve_opts o = *opts;
   if (o.line_search < 0 || o.line_search > BP_LS_QUADRATIC) return BP_EINVAL;
+  if (!(o.picard_rtol >= 0)) return BP_EINVAL;
   if (!(o.rtol > 0) || o.max_newton < 0 || o.max_newton > 64 || o.max_krylov < 1 || o.check_every < 1 ||
       (o.precision != BP_F64 && o.precision != BP_F32) || o.krylov != BP_KRYLOV_CG || !(o.eta_max > 0))
     return BP_EINVAL;
@@ -1123,7 +1125,11 @@ extern "C" int bp_newton_solve(bp_mesh* m, double* U, const bp_solve_opts* opts,
   for (int k = 0;; ++k) {
     // assemble J and F at U
     BP_CUDA_TRY(cudaEventRecord(ev[1], s));
-    if ((rc = bp_assemble_jacobian(m, U, w->R, w->J, o.precision, BP_SCATTER_ATOMIC, BP_JAC_FACTORED, s)))
+    // Picard (fixed-viscosity) matrix while far from the solution, if asked for: the residual of the
+    // previous step decides (the first step uses the initial residual, unknown yet: Picard if on)
+    const bool picard = o.picard_rtol > 0 && (k == 0 || rep->history[k - 1] > o.picard_rtol);
+    if ((rc = bp_assemble_jacobian_ex(m, U, w->R, w->J, o.precision, BP_SCATTER_ATOMIC, BP_JAC_FACTORED,
+                                      picard ? 1 : 0, s)))
       return rc;
     BP_CUDA_TRY(cudaEventRecord(ev[2], s));
     double fn;

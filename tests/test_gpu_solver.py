@@ -208,3 +208,25 @@ def test_rate_factor_entry_validates_and_resets():
     c.bp_mesh_set_rate_factor(dm.handle, None)
     assert rel_inf(dm.residual(U).cpu().numpy(), R0) <= 1e-14
     assert rel_inf(R8, R0) > 1e-3   # an 8x softer ice halves the stress term
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_picard_then_newton_reaches_the_same_solution(precision):
+    """Picard steps (the Jacobian without the eta' rank-one part) while far from the solution, then
+    Newton: the same minimiser as pure Newton, and the final FP64 residual checked by the oracle."""
+    c = capi()
+    mesh = synth.config_small()
+    om = oracle.OracleMesh(mesh)
+    dm = c.DeviceMesh(mesh)
+    sols = []
+    for pr in (0.0, 0.05):
+        U = torch.empty(dm.ndof, dtype=torch.float64, device="cuda")
+        c.bp_initial_guess(dm.handle, c.BP_GUESS_SIA, U)
+        rc, rep = c.bp_newton_solve(dm.handle, U, precision=precision, picard_rtol=pr)
+        assert rc == c.BP_OK, rep
+        Uh = U.cpu().numpy()
+        assert np.linalg.norm(om.residual(Uh)) <= 1.1e-8 * np.linalg.norm(om.residual(np.zeros_like(Uh)))
+        sols.append(Uh)
+    assert rel_inf(sols[0], sols[1]) <= 1e-6
+    with pytest.raises(c.BPError):
+        c.bp_newton_solve(dm.handle, U, picard_rtol=-1.0)
