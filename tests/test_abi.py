@@ -56,6 +56,12 @@ def tiny():
     (lambda m: m.sigma.__setitem__(1, m.sigma[2]), capi.BP_EMESH),           # sigma not increasing
     (lambda m: setattr(m.params, "n", 4.0), capi.BP_EUNSUP),                 # only n = 3
     (lambda m: m.xy.__setitem__((4, 0), np.nan), capi.BP_EMESH),             # non-finite coordinate
+    (lambda m: m.tri.__setitem__((0, 2), m.tri[0, 1]), capi.BP_EMESH),        # repeated vertex
+    (lambda m: m.xy.__setitem__(m.tri[0, 2], 0.5 * (m.xy[m.tri[0, 0]] + m.xy[m.tri[0, 1]])),
+     capi.BP_EMESH),                                                          # collinear (zero area)
+    (lambda m: setattr(m.params, "margin", 2), capi.BP_EINVAL),              # unknown margin condition
+    (lambda m: (setattr(m.params, "margin", 1), setattr(m.params, "rho_w", -1.0)), capi.BP_EINVAL),
+    (lambda m: setattr(m.params, "A", 0.0), capi.BP_EINVAL),                 # rate factor must be > 0
 ])
 def test_invalid_mesh_rejected_on_host(corrupt, status):
     m = tiny()
@@ -75,3 +81,18 @@ def test_null_arguments_rejected():
     assert L.bp_assemble_residual(None, None, None, None) == capi.BP_EINVAL
     assert L.bp_assemble_jacobian(None, None, None, None, 0, 0, 0, None) == capi.BP_EINVAL
     L.bp_mesh_free(None)  # no-op
+
+
+def test_empty_and_oversized_meshes_rejected_before_any_device_work():
+    import ctypes
+    m = tiny()
+    desc, keep = capi.make_desc(m)
+    out = ctypes.c_void_p(1)
+    desc.ntri = 0                                   # no triangles
+    assert capi.lib().bp_mesh_upload(ctypes.byref(desc), None, ctypes.byref(out)) == capi.BP_EINVAL
+    desc, keep = capi.make_desc(m)
+    desc.nv = 1 << 30                               # 2 nv (L + 1) dofs beyond the int32 column indices
+    assert capi.lib().bp_mesh_upload(ctypes.byref(desc), None, ctypes.byref(out)) == capi.BP_EINVAL
+    desc, keep = capi.make_desc(m)
+    desc.nlayers = 0
+    assert capi.lib().bp_mesh_upload(ctypes.byref(desc), None, ctypes.byref(out)) == capi.BP_EINVAL
