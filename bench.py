@@ -34,7 +34,9 @@ UNIT = "wedges/s"
 FP64_PEAK_TFLOPS = 148 * 2 * 2 * 2.032e9 / 1e12
 FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12   # 148 SMs x 128 FP32 lanes x FMA x max clock
 # FP64 flops per wedge of the residual + Jacobian assembly (factored formulation), counted with
-# ncu on 450,000 wedges: (2 x DFMA + DADD + DMUL) / wedges.  Fixed as the algorithm's work figure.
+# ncu on 450,000 wedges: (2 x DFMA + DADD + DMUL) / wedges, with the library inverse cube root.
+# Fixed as the algorithm's work figure (the kernel now executes 2,962: its inverse cube root is an
+# FP32 seed plus one FP64 correction).
 FLOPS_PER_WEDGE_JAC64 = 3002  # ncu: (2 DFMA + DADD + DMUL) per wedge of the factored kernel
 L2_FLUSH_BYTES = 512 << 20
 

@@ -7,8 +7,12 @@
 
 namespace {
 
+#ifndef BP_ASM_MIN_BLOCKS
+#define BP_ASM_MIN_BLOCKS 1  // minimum resident blocks of 128 threads per SM asked of the register allocator
+#endif
+
 template <int MODE, class TL, bool ATOMIC, bool PICARD = false>
-__global__ void __launch_bounds__(128) k_assemble(const AsmArgs A) {
+__global__ void __launch_bounds__(128, BP_ASM_MIN_BLOCKS) k_assemble(const AsmArgs A) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= A.count) return;
   assemble_column<MODE, TL, ATOMIC, PICARD>(A, A.tri_list ? A.tri_list[idx] : idx);

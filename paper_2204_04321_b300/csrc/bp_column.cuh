@@ -375,7 +375,7 @@ __device__ __forceinline__ void assemble_column(const AsmArgs& A, const int t) {
           const Dual<TL, 12> eyz = 0.5 * vzd;
           const Dual<TL, 12> e2 = ux * ux + vy * (vy + ux) + exy * exy + exz * exz + eyz * eyz;
           const double xx = e2.v + A.delta;
-          const double r = rcbrt(xx);
+          const double r = inv_cbrt(xx);
           Dual<TL, 12> eta;  // eta = B (e2 + delta)^(-1/3), d eta / d e2 = -eta / (3 (e2 + delta))
           eta.v = (psi(0, z) * hb[tp] + psi(1, z) * ht[tp]) * r;
           const TL detad = (TL)(-(1.0 / 3.0) * eta.v * (r * r * r));
@@ -418,7 +418,7 @@ __device__ __forceinline__ void assemble_column(const AsmArgs& A, const int t) {
           const double exy = 0.5 * (uy + vx);
           const double e2 = fma(ux, ux, fma(vy, vy + ux, fma(exy, exy, ez[tp])));
           const double xx = e2 + A.delta;
-          const double r = rcbrt(xx);
+          const double r = inv_cbrt(xx);
           const double eta = (psi(0, z) * hb[tp] + psi(1, z) * ht[tp]) * r;
           const double W = cq[tp] * eta;
           const double g1x = 2.0 * ux + vy, g2y = ux + 2.0 * vy;

@@ -143,6 +143,18 @@ __host__ __device__ inline bool bp_aligned16(const void* p) { return (reinterpre
 // Node level helpers of the extruded CSR pattern.
 __host__ __device__ inline int bp_nlev(int level, int L) { return (level == 0 || level == L) ? 2 : 3; }
 __host__ __device__ inline int bp_levels_before(int level) { return level == 0 ? 0 : 3 * level - 1; }
+// x^(-1/3) for the viscosity, FP64-accurate with little FP64 work: an FP32 seed y (rcbrtf, relative
+// error ~1e-7) refined once with the binomial series of (1 - e)^(-1/3), e = 1 - x y^3:
+//   x^(-1/3) = y (1 - e)^(-1/3) = y (1 + e/3 + 2 e^2/9 + O(e^3)),
+// a third-order correction whose truncation error (~e^3 / 6 ~ 1e-21) is far below FP64 rounding;
+// 6 FP64 operations and 2 conversions.  Outside the FP32 normal range the library rcbrt is used.
+__device__ __forceinline__ double inv_cbrt(double x) {
+  if (!(x > 1e-30 && x < 1e30)) return rcbrt(x);
+  const double y = (double)rcbrtf((float)x);
+  const double e = fma(-x * y, y * y, 1.0);
+  return fma(y * e, fma(2.0 / 9.0, e, 1.0 / 3.0), y);
+}
+
 __host__ __device__ inline int64_t bp_dof(int64_t a, int l, int c, int L) {
   return 2 * (a * (L + 1) + l) + c;
 }

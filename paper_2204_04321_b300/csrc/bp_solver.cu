@@ -485,7 +485,7 @@ __global__ void __launch_bounds__(128) k_energy(const double2* __restrict__ xy, 
           const double exy = 0.5 * (uy + vx);
           const double e2 = ux * ux + vy * vy + ux * vy + exy * exy + 0.25 * (uz * uz + vz * vz);
           const double xx = e2 + delta;
-          acc += (d * h / 12.0) * 1.5 * hardness_at(Bn, cA, v, L, l, p0, p1, tp) * xx * rcbrt(xx);
+          acc += (d * h / 12.0) * 1.5 * hardness_at(Bn, cA, v, L, l, p0, p1, tp) * xx * inv_cbrt(xx);
         }
       }
     }
@@ -502,7 +502,10 @@ __device__ __forceinline__ T eps_bilinear(const T* A, const T* B) {
          T(0.25) * (A[2] * B[2] + A[5] * B[5]);
 }
 
-__device__ __forceinline__ double cube_root(double x) { return cbrt(x); }
+__device__ __forceinline__ double cube_root(double x) {  // x^(1/3) = x (x^(-1/3))^2
+  const double r = inv_cbrt(x);
+  return x * r * r;
+}
 __device__ __forceinline__ float cube_root(float x) { return cbrtf(x); }
 
 // Energy change Pi_h(U + alpha D) - Pi_h(U), formed term by term as differences so that it keeps
