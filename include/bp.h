@@ -8,7 +8,8 @@
  *       -div(2 mu eps_1) + rho g ds/dx = 0,  -div(2 mu eps_2) + rho g ds/dy = 0,
  *     Glen viscosity mu = 1/2 A^(-1/n) (eps_e^2 + delta)^((1-n)/(2n)) (delta regularises U = 0),
  *     a stress-free surface, the linear sliding (Robin) law 2 mu eps . n + beta u = 0 at the bed
- *     and stress-free vertical margins;
+ *     and, on the vertical margins, either stress-free or the ocean condition (bp_params.margin);
+ *     A constant or a nodal field (Arrhenius relation, bp_mesh_set_rate_factor);
  *   - Sec. 3.1, Eq. residual: low-order nodal prismatic (6-node wedge) finite elements on the
  *     3D mesh extruded from a base triangulation give the residual F(U; {phi_i}, {grad phi_i}, H, beta);
  *   - Sec. 3.1, Eq. linearsystem: damped Newton J delta = -F, U <- U + alpha delta;
@@ -57,8 +58,6 @@ typedef enum {
   BP_ESIZE = 8      /* the problem exceeds a fixed capacity of the call (see BP_NOALLOC_MAX_NDOF) */
 } bp_status;
 
-/* Glen exponent n (must be 3: the kernels use rcbrt), rate factor A [Pa^-n yr^-1],
- * ice density rho [kg m^-3], gravity g [m s^-2], regularisation delta [yr^-2]. */
 /* Lateral margin condition (paper Sec. 2, third boundary condition, on the vertical faces over the
  * boundary edges of the base triangulation):
  *   BP_MARGIN_FREE   2 mu eps_c . n = 0 (natural; the default reading for land-terminating margins);
@@ -70,6 +69,9 @@ typedef enum {
  *                    (two points along the edge, two in zeta). */
 enum { BP_MARGIN_FREE = 0, BP_MARGIN_OCEAN = 1 };
 
+/* Glen exponent n (must be 3: the kernels take the cube root of eps_e^2 + delta), rate factor
+ * A [Pa^-n yr^-1] (> 0; see bp_mesh_set_rate_factor for a field), ice density rho [kg m^-3],
+ * gravity g [m s^-2], regularisation delta [yr^-2]. */
 typedef struct {
   double n, A, rho, g, delta;
   double rho_w;      /* sea-water density (kg m^-3), read with BP_MARGIN_OCEAN */
@@ -107,8 +109,9 @@ typedef struct {
  *   BP_F32   FP32 lanes (J values are float);
  *   BP_F64X2 FP64-accurate lanes built from pairs of FP32 numbers (hi + lo, error-free sum and
  *            product transformations, relative error ~2^-46 per operation); J values are double;
- *            Jacobian assembly only, sum-factorised method only.  FP32 throughput on B300 is
- *            ~60x its FP64 throughput, which makes this the fast route to an FP64-accurate J. */
+ *            Jacobian assembly only, sum-factorised method only.  It moves the lane arithmetic to
+ *            the FP32 pipe (~60x the FP64 rate on B300), but the doubled register footprint of the
+ *            element matrix spills, and on B300 it measures slower than BP_F64 lanes. */
 enum { BP_F64 = 0, BP_F32 = 1, BP_F64X2 = 2 };
 /* Scatter of element contributions: atomics, or colour by colour with plain read-modify-write. */
 enum { BP_SCATTER_AUTO = 0, BP_SCATTER_ATOMIC = 1, BP_SCATTER_COLOR = 2 };
@@ -259,10 +262,13 @@ void bp_solve_opts_default(bp_solve_opts* opts);
 
 /*
  * Damped Newton (Eq. linearsystem) from the guess in U_dev to ||F|| <= rtol ||F(0)||: per step
- * the Jacobian and residual are assembled (bp_assemble_jacobian), the column preconditioner is
- * factorised, J delta = -F is solved by preconditioned CG to the Eisenstat-Walker tolerance, and
- * alpha is the first of 1, 1/2, ..., 2^-10 with bp_energy_change(U, delta, alpha) <= 1e-4 alpha F . delta
- * (Armijo on the energy).  U_dev holds the last iterate on return.
+ * the Jacobian and residual are assembled (bp_assemble_jacobian; the Picard matrix instead while
+ * opts->picard_rtol asks for it), the column preconditioner is factorised, J delta = -F is solved
+ * by preconditioned CG to the Eisenstat-Walker tolerance, and the step length alpha is the first
+ * trial of opts->line_search with bp_energy_change(U, delta, alpha) <= 1e-4 alpha F . delta
+ * (Armijo on the energy; the last trial is taken if none passes).  After a full step that reduced
+ * the residual tenfold (the quadratic regime) the next full step is taken without the test.
+ * U_dev holds the last iterate on return.
  * Synchronises `stream`.  Errors: BP_EINVAL, BP_ENOMEM, BP_ECUDA, BP_ENAN (non-finite residual),
  * BP_ENOCONV (max_newton reached; the report is filled either way).
  */
