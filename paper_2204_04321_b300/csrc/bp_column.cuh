@@ -112,6 +112,17 @@ __device__ __forceinline__ f64x2& operator+=(f64x2& a, const f64x2 b) {
   return a;
 }
 
+// FP64 value -> lane type.  FP32 lanes convert on the integer pipe (f32_of): the FP64 pipe, which
+// would otherwise run the conversions, is the one the value path fills.
+template <class TL>
+__device__ __forceinline__ TL to_lane(const double x) {
+  return TL(x);
+}
+template <>
+__device__ __forceinline__ float to_lane<float>(const double x) {
+  return f32_of(x);
+}
+
 // storage type of a lane type in the Jacobian array, and the conversion
 template <class TL>
 struct LaneStore {
@@ -149,7 +160,7 @@ template <class TL, int NL>
 __device__ __forceinline__ Dual<TL, NL> operator*(const Dual<TL, NL>& a, const Dual<TL, NL>& b) {
   Dual<TL, NL> r;
   r.v = a.v * b.v;
-  const TL av = (TL)a.v, bv = (TL)b.v;
+  const TL av = to_lane<TL>(a.v), bv = to_lane<TL>(b.v);
 #pragma unroll
   for (int k = 0; k < NL; ++k) r.d[k] = a.d[k] * bv + av * b.d[k];
   return r;
@@ -158,7 +169,7 @@ template <class TL, int NL>
 __device__ __forceinline__ Dual<TL, NL> operator*(double s, const Dual<TL, NL>& a) {
   Dual<TL, NL> r;
   r.v = s * a.v;
-  const TL ts = (TL)s;
+  const TL ts = to_lane<TL>(s);
 #pragma unroll
   for (int k = 0; k < NL; ++k) r.d[k] = ts * a.d[k];
   return r;
@@ -205,13 +216,13 @@ __device__ __forceinline__ void assemble_column(const AsmArgs& A, const int t) {
   }
   const double d12 = d * (1.0 / 12.0);
   const double d6 = d * (1.0 / 6.0);
-  const TL d12L = (TL)d12;
+  const TL d12L = to_lane<TL>(d12);
   TL clx[3], cly[3];  // grad lambda in lane precision (Jacobian lanes)
   if constexpr (MODE == MODE_FACT) {
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      clx[a] = (TL)lx[a];
-      cly[a] = (TL)ly[a];
+      clx[a] = to_lane<TL>(lx[a]);
+      cly[a] = to_lane<TL>(ly[a]);
     }
   }
 
@@ -308,15 +319,14 @@ __device__ __forceinline__ void assemble_column(const AsmArgs& A, const int t) {
     double Rl[2][3][2];  // [k][a][c] residual of this wedge
     TL K[78];            // upper triangle of the element matrix
     TL eta_q[2][3];      // 2 mu at the quadrature points (factored Jacobian)
-    // FP32 lanes: the per-point weights in FP32, converted once per wedge (a conversion from
-    // double runs on the FP64 pipe, which the value path already fills)
+    // FP32 lanes: the per-point weights in FP32, converted once per wedge
     constexpr bool kF32 = std::is_same<TL, float>::value;
     TL cqL[3], invhL[3];
     if constexpr (MODE == MODE_FACT) {
 #pragma unroll
       for (int tp = 0; tp < 3; ++tp) {
-        cqL[tp] = (TL)cq[tp];
-        invhL[tp] = (TL)invh[tp];
+        cqL[tp] = to_lane<TL>(cq[tp]);
+        invhL[tp] = to_lane<TL>(invh[tp]);
       }
     }
     if constexpr (MODE != MODE_RES) {
@@ -346,7 +356,7 @@ __device__ __forceinline__ void assemble_column(const AsmArgs& A, const int t) {
               gNd[3 * k + a][1] = psi(k, z) * ly[a] + c * Zy;
               gNd[3 * k + a][2] = c * Zz;
 #pragma unroll
-              for (int r = 0; r < 3; ++r) gN[3 * k + a][r] = (TL)gNd[3 * k + a][r];
+              for (int r = 0; r < 3; ++r) gN[3 * k + a][r] = to_lane<TL>(gNd[3 * k + a][r]);
             }
           Dual<TL, 12> ux, uy, uzd, vx, vy, vzd;
           ux.v = GUx[z] - uz[tp] * Gzx[z];
@@ -378,11 +388,12 @@ __device__ __forceinline__ void assemble_column(const AsmArgs& A, const int t) {
           const double r = inv_cbrt(xx);
           Dual<TL, 12> eta;  // eta = B (e2 + delta)^(-1/3), d eta / d e2 = -eta / (3 (e2 + delta))
           eta.v = (psi(0, z) * hb[tp] + psi(1, z) * ht[tp]) * r;
-          const TL detad = (TL)(-(1.0 / 3.0) * eta.v * (r * r * r));
+          const TL detad = to_lane<TL>(-(1.0 / 3.0) * eta.v * (r * r * r));
 #pragma unroll
           for (int j = 0; j < 12; ++j) eta.d[j] = detad * e2.d[j];
           const Dual<TL, 12> g1x = 2.0 * ux + vy, g2y = ux + 2.0 * vy;
           const double c = cq[tp];
+          const TL cL = to_lane<TL>(c);
 #pragma unroll
           for (int n = 0; n < 6; ++n) {
 #pragma unroll
@@ -398,7 +409,7 @@ __device__ __forceinline__ void assemble_column(const AsmArgs& A, const int t) {
               const Dual<TL, 12> ri = eta * pi;
               Rl[n / 3][n % 3][comp] += c * ri.v;
 #pragma unroll
-              for (int j = i; j < 12; ++j) K[uidx(i, j)] += (TL)c * ri.d[j];
+              for (int j = i; j < 12; ++j) K[uidx(i, j)] += cL * ri.d[j];
             }
           }
         }
@@ -435,12 +446,12 @@ __device__ __forceinline__ void assemble_column(const AsmArgs& A, const int t) {
             // rank-one part eta' p_i p_j with p_{(a,k),c} = psi_k g_c,xy . Lambda_a + lambda_a psi_k' g_c . Z
             TL Wp, tau1, tau2;
             if constexpr (kF32) {  // from r, t1, t2 converted once: FP32 arithmetic only
-              const float rf = (float)r;
-              const float ef = (float)eta;
+              const float rf = f32_of(r);
+              const float ef = f32_of(eta);
               eta_q[z][tp] = ef;
               Wp = (-1.0f / 3.0f) * cqL[tp] * ef * (rf * rf * rf);
-              tau1 = 2.0f * invhL[tp] * (float)t1;
-              tau2 = 2.0f * invhL[tp] * (float)t2;
+              tau1 = 2.0f * invhL[tp] * f32_of(t1);
+              tau2 = 2.0f * invhL[tp] * f32_of(t2);
             } else {
               eta_q[z][tp] = (TL)eta;
               Wp = (TL)(-(1.0 / 3.0) * W * (r * r * r));
@@ -448,7 +459,7 @@ __device__ __forceinline__ void assemble_column(const AsmArgs& A, const int t) {
               tau2 = (TL)(2.0 * invh[tp] * t2);
             }
             if constexpr (!PICARD) {
-            const TL fg1x = (TL)g1x, fexy = (TL)exy, fg2y = (TL)g2y;
+            const TL fg1x = to_lane<TL>(g1x), fexy = to_lane<TL>(exy), fg2y = to_lane<TL>(g2y);
             // p_{(a,k),c} = psi_k alpha_{a,c} -/+ t_{a,c},  alpha = g_c,xy . Lambda_a,  t = lambda_a tau_c / 2
             TL p[12];
 #pragma unroll
@@ -524,7 +535,8 @@ __device__ __forceinline__ void assemble_column(const AsmArgs& A, const int t) {
         Q[0][1] = Q[1][0] = (TL)(BP_QP_P * BP_QP_Q) * (Qs[0] + Qs[1]);
         // V^k_b scaled by 1/2 (the magnitude of psi'): V = -(d/12) sum_z psi_k E_b Gz
         TL Vx[2][3], Vy[2][3];
-        const TL GzxL[2] = {(TL)Gzx[0], (TL)Gzx[1]}, GzyL[2] = {(TL)Gzy[0], (TL)Gzy[1]};
+        const TL GzxL[2] = {to_lane<TL>(Gzx[0]), to_lane<TL>(Gzx[1])};
+        const TL GzyL[2] = {to_lane<TL>(Gzy[0]), to_lane<TL>(Gzy[1])};
         const TL md12 = -d12L;
         const TL gz0x = md12 * GzxL[0], gz1x = md12 * GzxL[1];
         const TL gz0y = md12 * GzyL[0], gz1y = md12 * GzyL[1];
@@ -620,7 +632,7 @@ __device__ __forceinline__ void assemble_column(const AsmArgs& A, const int t) {
 #pragma unroll
           for (int b = a; b < 3; ++b)
 #pragma unroll
-            for (int c = 0; c < 2; ++c) K[uidx(2 * a + c, 2 * b + c)] += (TL)M[a][b];
+            for (int c = 0; c < 2; ++c) K[uidx(2 * a + c, 2 * b + c)] += to_lane<TL>(M[a][b]);
       }
     }
 

@@ -143,14 +143,42 @@ __host__ __device__ inline bool bp_aligned16(const void* p) { return (reinterpre
 // Node level helpers of the extruded CSR pattern.
 __host__ __device__ inline int bp_nlev(int level, int L) { return (level == 0 || level == L) ? 2 : 3; }
 __host__ __device__ inline int bp_levels_before(int level) { return level == 0 ? 0 : 3 * level - 1; }
+// Binary64 <-> binary32 conversions done on the integer pipe by repacking the IEEE 754 fields
+// (sign; exponent rebiased between 1023 and 127; fraction cut from 52 to 23 bits or widened).
+// B300 runs conversions from or to FP64 on its narrow FP64 pipe, which the kernels that use these
+// keep busy with FP64 arithmetic; the integer pipe is otherwise idle there.
+//   f32_of: rounds to nearest with ties away from zero (IEEE rounds ties to even: the two differ
+//   only when the 29 dropped bits are exactly 1000...0).  Magnitudes below the FP32 normal range
+//   give a signed zero, above it an infinity; NaN stays NaN.
+__device__ __forceinline__ float f32_of(const double x) {
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  const unsigned e = (hi >> 20) & 0x7FFu;
+  unsigned m = ((e - 896u) << 23) | ((hi & 0xFFFFFu) << 3) | (lo >> 29);
+  m += (lo >> 28) & 1u;  // the first dropped bit; a carry moves into the exponent
+  m = e <= 896u ? 0u : m;
+  const unsigned big = (e == 0x7FFu && ((hi & 0xFFFFFu) | lo) != 0u) ? 0x7FC00000u : 0x7F800000u;
+  m = e >= 1151u ? big : m;
+  return __uint_as_float((hi & 0x80000000u) | m);
+}
+//   f64_of: exact for normal FP32 numbers, zeros, infinities and NaN; subnormals give a signed zero.
+__device__ __forceinline__ double f64_of(const float f) {
+  const unsigned b = __float_as_uint(f);
+  const unsigned e = (b >> 23) & 0xFFu;
+  const unsigned frac = e == 0u ? 0u : (b & 0x7FFFFFu);
+  const unsigned E = e == 0u ? 0u : (e == 0xFFu ? 0x7FFu : e + 896u);
+  const unsigned hi = (b & 0x80000000u) | (E << 20) | (frac >> 3);
+  return __hiloint2double((int)hi, (int)(frac << 29));
+}
+
 // x^(-1/3) for the viscosity, FP64-accurate with little FP64 work: an FP32 seed y (rcbrtf, relative
 // error ~1e-7) refined once with the binomial series of (1 - e)^(-1/3), e = 1 - x y^3:
 //   x^(-1/3) = y (1 - e)^(-1/3) = y (1 + e/3 + 2 e^2/9 + O(e^3)),
 // a third-order correction whose truncation error (~e^3 / 6 ~ 1e-21) is far below FP64 rounding;
-// 6 FP64 operations and 2 conversions.  Outside the FP32 normal range the library rcbrt is used.
+// 6 FP64 operations, the two conversions on the integer pipe.  Outside the FP32 normal range the
+// library rcbrt is used.
 __device__ __forceinline__ double inv_cbrt(double x) {
   if (!(x > 1e-30 && x < 1e30)) return rcbrt(x);
-  const double y = (double)rcbrtf((float)x);
+  const double y = f64_of(rcbrtf(f32_of(x)));
   const double e = fma(-x * y, y * y, 1.0);
   return fma(y * e, fma(2.0 / 9.0, e, 1.0 / 3.0), y);
 }

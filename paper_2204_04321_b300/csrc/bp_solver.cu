@@ -502,6 +502,19 @@ __device__ __forceinline__ T eps_bilinear(const T* A, const T* B) {
          T(0.25) * (A[2] * B[2] + A[5] * B[5]);
 }
 
+// FP64 <-> arithmetic type T of the energy change; FP32 converts on the integer pipe (f32_of,
+// f64_of), which leaves the FP64 pipe to the FP64 part of the kernel.
+template <class T>
+__device__ __forceinline__ T to_T(const double x) {
+  return T(x);
+}
+template <>
+__device__ __forceinline__ float to_T<float>(const double x) {
+  return f32_of(x);
+}
+__device__ __forceinline__ double from_T(const double x) { return x; }
+__device__ __forceinline__ double from_T(const float x) { return f64_of(x); }
+
 __device__ __forceinline__ double cube_root(double x) {  // x^(1/3) = x (x^(-1/3))^2
   const double r = inv_cbrt(x);
   return x * r * r;
@@ -572,15 +585,15 @@ __global__ void __launch_bounds__(128) k_energy_change(const double2* __restrict
     T tlx[3], tly[3], invHq[3];
     double Hq[3];
     for (int a = 0; a < 3; ++a) {
-      tlx[a] = (T)lx[a];
-      tly[a] = (T)ly[a];
+      tlx[a] = to_T<T>(lx[a]);
+      tly[a] = to_T<T>(ly[a]);
       Hq[a] = Hs6 + 0.5 * H[a];
-      invHq[a] = (T)(1.0 / Hq[a]);
+      invHq[a] = to_T<T>(1.0 / Hq[a]);
     }
     T u0[3], v0[3], a0[3], b0[3];
     for (int a = 0; a < 3; ++a) {
-      u0[a] = (T)U[ub[a]];
-      v0[a] = (T)U[ub[a] + 1];
+      u0[a] = to_T<T>(U[ub[a]]);
+      v0[a] = to_T<T>(U[ub[a] + 1]);
       a0[a] = (T)D[ub[a]];
       b0[a] = (T)D[ub[a] + 1];
     }
@@ -597,8 +610,8 @@ __global__ void __launch_bounds__(128) k_energy_change(const double2* __restrict
     for (int l = 0; l < L; ++l) {
       T u1[3], v1[3], a1[3], b1[3];
       for (int a = 0; a < 3; ++a) {
-        u1[a] = (T)U[ub[a] + 2 * l + 2];
-        v1[a] = (T)U[ub[a] + 2 * l + 3];
+        u1[a] = to_T<T>(U[ub[a] + 2 * l + 2]);
+        v1[a] = to_T<T>(U[ub[a] + 2 * l + 3]);
         a1[a] = (T)D[ub[a] + 2 * l + 2];
         b1[a] = (T)D[ub[a] + 2 * l + 3];
       }
@@ -608,7 +621,7 @@ __global__ void __launch_bounds__(128) k_energy_change(const double2* __restrict
       grad2(a1, gA1[0], gA1[1]);
       grad2(b1, gB1[0], gB1[1]);
       const double s_l = sigma[l], ds = sigma[l + 1] - sigma[l];
-      const T invds = (T)(1.0 / ds);
+      const T invds = to_T<T>(1.0 / ds);
       const T sixth = T(1.0 / 6.0);
       const T du6 = (u1[0] - u0[0] + u1[1] - u0[1] + u1[2] - u0[2]) * sixth;
       const T dv6 = (v1[0] - v0[0] + v1[1] - v0[1] + v1[2] - v0[2]) * sixth;
@@ -618,7 +631,7 @@ __global__ void __launch_bounds__(128) k_energy_change(const double2* __restrict
       for (int z = 0; z < 2; ++z) {
         const T p0 = (T)(z == 0 ? BP_QP_P : BP_QP_Q), p1 = (T)(z == 0 ? BP_QP_Q : BP_QP_P);
         const double sz = s_l + (z == 0 ? BP_QP_Q : BP_QP_P) * ds;
-        const T Gzx = (T)(gbx + sz * gHx), Gzy = (T)(gby + sz * gHy);
+        const T Gzx = to_T<T>(gbx + sz * gHx), Gzy = to_T<T>(gby + sz * gHy);
         const T GUx = p0 * gU0[0] + p1 * gU1[0], GUy = p0 * gU0[1] + p1 * gU1[1];
         const T GVx = p0 * gV0[0] + p1 * gV1[0], GVy = p0 * gV0[1] + p1 * gV1[1];
         const T GAx = p0 * gA0[0] + p1 * gA1[0], GAy = p0 * gA0[1] + p1 * gA1[1];
@@ -636,7 +649,8 @@ __global__ void __launch_bounds__(128) k_energy_change(const double2* __restrict
           const T x1 = x0 + dx;
           const T ca = cube_root(x1), cb = cube_root(x0);
           const T diff23 = dx / (ca * ca + ca * cb + cb * cb) * (ca + cb);
-          lstress += Hq[tp] * hardness_at(Bn, cA, v, L, l, (double)p0, (double)p1, tp) * (double)diff23;
+          lstress += Hq[tp] * hardness_at(Bn, cA, v, L, l, z == 0 ? BP_QP_P : BP_QP_Q, z == 0 ? BP_QP_Q : BP_QP_P, tp) *
+                     from_T(diff23);
         }
       }
       stress += (d * ds / 12.0) * lstress;

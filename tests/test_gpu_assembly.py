@@ -120,6 +120,25 @@ def test_jacobian_parity(name, method, scatter, precision):
     assert err <= (TOL32 if precision == "f32" else TOL64), err
 
 
+@pytest.mark.parametrize("name", ["small", "marine", "arrhenius"])
+@pytest.mark.parametrize("kind", ["zero", "sia"])
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+def test_jacobian_parity_at_zero_and_shallow_ice_velocities(name, kind, precision):
+    """U = 0 makes every strain-rate lane exactly zero (the FP32 lane conversion's zero case);
+    the shallow-ice guess is the usual starting point of the Newton solve."""
+    c = capi()
+    mesh = MESHES[name]()
+    om = oracle.OracleMesh(mesh)
+    U = velocities(mesh, kind, om)
+    dm = c.DeviceMesh(mesh)
+    prec = c.BP_F64 if precision == "f64" else c.BP_F32
+    J, R = dm.jacobian(dev(U), precision=prec)
+    _, _, Jc, Rc = om.jacobian(U)
+    assert rel_inf(R.cpu().numpy(), Rc) <= TOL64
+    err = rel_inf(J.cpu().numpy().astype(np.float64), Jc)
+    assert err <= (TOL32 if precision == "f32" else TOL64), err
+
+
 def test_jacobian_without_residual_and_repeat_calls_overwrite():
     c = capi()
     mesh = synth.config_small()
