@@ -587,12 +587,16 @@ def newton_section(capi, synth, dm, mesh, dev, skip_large=False, reps=3):
 
 
 def kernel_hash():
-    """Hash of the assembly kernel's source text (the per-column body and its helpers)."""
+    """Hash of the assembly kernel's source text: the per-column body and the shared device helpers
+    (conversions, inverse cube root, pattern helpers) it calls."""
     import hashlib
-    with open(os.path.join(ROOT, "paper_2204_04321_b300", "csrc", "bp_column.cuh")) as f:
+    csrc = os.path.join(ROOT, "paper_2204_04321_b300", "csrc")
+    with open(os.path.join(csrc, "bp_column.cuh")) as f:
         src = f.read()
-    a = src.index("constexpr int MODE_RES")
-    return hashlib.sha256(src[a:].encode()).hexdigest()[:16]
+    src = src[src.index("constexpr int MODE_RES"):]
+    with open(os.path.join(csrc, "bp_internal.cuh")) as f:
+        src += f.read()
+    return hashlib.sha256(src.encode()).hexdigest()[:16]
 
 
 def main():

@@ -569,23 +569,9 @@ __device__ __forceinline__ void assemble_column(const AsmArgs& A, const int t) {
         }
         const TL* flx = clx;
         const TL* fly = cly;
-        // BV[a][k][b] = B(Lambda_a, V^k_b) for the four component pairs (uu, uv, vu, vv)
-        TL BV[3][2][3][4];
-#pragma unroll
-        for (int a = 0; a < 3; ++a)
-#pragma unroll
-          for (int k = 0; k < 2; ++k)
-#pragma unroll
-            for (int b = 0; b < 3; ++b) {
-              const TL xx = flx[a] * Vx[k][b], yy = fly[a] * Vy[k][b];
-              const TL xy = flx[a] * Vy[k][b], yx = fly[a] * Vx[k][b];
-              BV[a][k][b][0] = TL(2) * xx + TL(0.5) * yy;
-              BV[a][k][b][1] = xy + TL(0.5) * yx;
-              BV[a][k][b][2] = TL(0.5) * xy + yx;
-              BV[a][k][b][3] = TL(0.5) * xx + TL(2) * yy;
-            }
-        // per node pair (n1 = (a,k) <= n2 = (b,m)): the in-plane B(Lambda_a, Lambda_b) once, then
-        // K += Q_km BL + s_m BV[a][k][b] + s_k BV[b][m][a]^T + s_k s_m Y_ab   (s = sign of psi')
+        // per node pair (n1 = (a,k) <= n2 = (b,m)), s = sign of psi':
+        //   K += Q_km B(Lambda_a, Lambda_b) + s_k s_m Y_ab + s_m BV[a][k][b] + s_k BV[b][m][a]^T,
+        // with BV[a][k][b] = B(Lambda_a, V^k_b).  First the in-plane and Y terms pair by pair ...
 #pragma unroll
         for (int n1 = 0; n1 < 6; ++n1) {
 #pragma unroll
@@ -599,18 +585,56 @@ __device__ __forceinline__ void assemble_column(const AsmArgs& A, const int t) {
             const int pr = lo * 3 - (lo * (lo - 1)) / 2 + (hi - lo);
             const TL Yc[4] = {Yuu[pr], Yuv[pr], Yuv[pr], Yvv[pr]};
             const TL q = Q[ki][kj];
-            const bool nm = (kj == 0), nk = (ki == 0);  // psi_m' < 0, psi_k' < 0
+            const bool neg = (ki == 0) != (kj == 0);
 #pragma unroll
             for (int ci = 0; ci < 2; ++ci)
 #pragma unroll
               for (int cj = 0; cj < 2; ++cj) {
                 const int i = 2 * n1 + ci, j = 2 * n2 + cj;
                 if (i > j) continue;
-                const int cd = 2 * ci + cj, dc = 2 * cj + ci;
-                // s_k s_m Y + s_k BV[b][m][a]^T + s_m BV[a][k][b]  (signs by negation and add/sub only)
-                const TL y = (nk != nm) ? -Yc[cd] : Yc[cd];
-                const TL u = add_signed(add_signed(y, BV[bj][kj][ai][dc], nk), BV[ai][ki][bj][cd], nm);
-                K[uidx(i, j)] += q * BL[cd] + u;
+                const int cd = 2 * ci + cj;
+                K[uidx(i, j)] = add_signed(K[uidx(i, j)] + q * BL[cd], Yc[cd], neg);
+              }
+          }
+        }
+        // ... then the BV terms node by node: the 12 values BV[a][k][.] of node n = (a, k) go to the
+        // pairs where n is the first node (the s_m term) and where it is the second (the transposed
+        // s_k term), so that only one node's values are live at a time.
+#pragma unroll
+        for (int n = 0; n < 6; ++n) {
+          const int kn = n / 3, an = n % 3;
+          TL BVn[3][4];
+#pragma unroll
+          for (int b = 0; b < 3; ++b) {
+            const TL xx = flx[an] * Vx[kn][b], yy = fly[an] * Vy[kn][b];
+            const TL xy = flx[an] * Vy[kn][b], yx = fly[an] * Vx[kn][b];
+            BVn[b][0] = TL(2) * xx + TL(0.5) * yy;
+            BVn[b][1] = xy + TL(0.5) * yx;
+            BVn[b][2] = TL(0.5) * xy + yx;
+            BVn[b][3] = TL(0.5) * xx + TL(2) * yy;
+          }
+#pragma unroll
+          for (int n2 = n; n2 < 6; ++n2) {  // n first: + s_m BV[a][k][b][cd], n2 = (b, m)
+            const int kj = n2 / 3, bj = n2 % 3;
+#pragma unroll
+            for (int ci = 0; ci < 2; ++ci)
+#pragma unroll
+              for (int cj = 0; cj < 2; ++cj) {
+                const int i = 2 * n + ci, j = 2 * n2 + cj;
+                if (i > j) continue;
+                K[uidx(i, j)] = add_signed(K[uidx(i, j)], BVn[bj][2 * ci + cj], kj == 0);
+              }
+          }
+#pragma unroll
+          for (int n1 = 0; n1 <= n; ++n1) {  // n second: + s_k BV[b][m][a][dc], n1 = (a, k)
+            const int ki = n1 / 3, ai = n1 % 3;
+#pragma unroll
+            for (int ci = 0; ci < 2; ++ci)
+#pragma unroll
+              for (int cj = 0; cj < 2; ++cj) {
+                const int i = 2 * n1 + ci, j = 2 * n + cj;
+                if (i > j) continue;
+                K[uidx(i, j)] = add_signed(K[uidx(i, j)], BVn[ai][2 * cj + ci], ki == 0);
               }
           }
         }

@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <type_traits>
 
 #include "bp_internal.cuh"
 
@@ -345,6 +346,108 @@ __global__ void __launch_bounds__(UPD_NT) k_cg_update_staged(const Prec<F> P, co
   }
   __syncthreads();
   for (int i = threadIdx.x; i < cnt; i += blockDim.x) z[base + i] = sz[i];
+  block_add(rz, scal + 3 * (k + 1) + 1);
+  block_add(rr, scal + 3 * (k + 1) + 2);
+}
+
+// The same step for FP32 vectors and factors when the column has NLEV = L + 1 levels known at compile
+// time: one warp per 32 consecutive columns and every lane solves one column.  Each lane first loads its
+// column's factors (NLEV - 1 lower, NLEV - 1 upper and NLEV inverse diagonal 2 x 2 blocks) into
+// registers, so that the loads are all in flight together and the substitution does no global load
+// (the staged kernel's single solving warp waits on one factor load after another).  The warp then runs
+// x += alpha p, r -= alpha q over its columns' contiguous range, stages r in shared memory (column
+// stride padded to an odd count against bank conflicts), each lane solves its column in place, and z
+// is written back coalesced.
+template <int NLEV>
+__global__ void __launch_bounds__(UPD_NT) k_cg_update_cols(const Prec<float> P, const int* kbase, int j,
+                                                           float* __restrict__ x, float* __restrict__ r,
+                                                           float* __restrict__ z, const float* __restrict__ p,
+                                                           const float* __restrict__ q, double* scal, int* stop) {
+  constexpr int N = 2 * NLEV;     // values per column
+  constexpr int SN = N | 1;       // shared-memory stride per column
+  __shared__ float sbuf[UPD_NT / 32][32 * SN];
+  __shared__ float s_alpha;
+  __shared__ int s_bad;
+  if (*stop) return;
+  const int k = *kbase + j;
+  if (threadIdx.x == 0) {
+    const double pq = scal[3 * k], rzk = scal[3 * k + 1];
+    s_bad = !(pq > 0.0) || !isfinite(rzk);
+    s_alpha = s_bad ? 0.f : (float)(rzk / pq);
+    if (s_bad && blockIdx.x == 0) *stop = 2;
+  }
+  __syncthreads();
+  if (s_bad) return;
+  const float alpha = s_alpha;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nv = P.nv;
+  const int a0 = (blockIdx.x * (UPD_NT / 32) + warp) * 32;
+  const int a = a0 + lane;
+  const bool own = a < nv;
+  float Lf[NLEV - 1][4], Uf[NLEV - 1][4], Gf[NLEV][4];
+  if (own) {
+#pragma unroll
+    for (int l = 0; l < NLEV; ++l)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int64_t o = ((int64_t)l * 4 + e) * nv + a;
+        Gf[l][e] = P.Ginv[o];
+        if (l < NLEV - 1) {
+          Lf[l][e] = P.Lm[o];
+          Uf[l][e] = P.Fu[o];
+        }
+      }
+  }
+  float* sr = sbuf[warp];
+  const int ncol = min(32, nv - a0);  // <= 0 for a warp past the last column
+  const int64_t base = (int64_t)a0 * N;
+  float rr = 0.f;
+  for (int i = lane; i < ncol * N; i += 32) {
+    const float xv = x[base + i] + alpha * p[base + i];
+    const float rv = r[base + i] - alpha * q[base + i];
+    x[base + i] = xv;
+    r[base + i] = rv;
+    sr[(i / N) * SN + i % N] = rv;
+    rr += rv * rv;
+  }
+  __syncwarp();
+  double rz = 0.0;
+  if (own) {
+    float* c = sr + lane * SN;
+    float rv[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) rv[i] = c[i];
+    // forward: y_0 = r_0, y_l = r_l - Lm_l y_{l-1}
+    float y[N];
+    y[0] = rv[0];
+    y[1] = rv[1];
+#pragma unroll
+    for (int l = 1; l < NLEV; ++l) {
+      const float* Lp = Lf[l - 1];
+      y[2 * l] = rv[2 * l] - (Lp[0] * y[2 * l - 2] + Lp[1] * y[2 * l - 1]);
+      y[2 * l + 1] = rv[2 * l + 1] - (Lp[2] * y[2 * l - 2] + Lp[3] * y[2 * l - 1]);
+    }
+    // backward: z_L = G_L^-1 y_L, z_l = G_l^-1 (y_l - F_l z_{l+1})
+    float srz = 0.f, z0 = 0.f, z1 = 0.f;
+#pragma unroll
+    for (int l = NLEV - 1; l >= 0; --l) {
+      float t0 = y[2 * l], t1 = y[2 * l + 1];
+      if (l < NLEV - 1) {
+        const float* Fp = Uf[l];
+        t0 -= Fp[0] * z0 + Fp[1] * z1;
+        t1 -= Fp[2] * z0 + Fp[3] * z1;
+      }
+      const float* Gp = Gf[l];
+      z0 = Gp[0] * t0 + Gp[1] * t1;
+      z1 = Gp[2] * t0 + Gp[3] * t1;
+      c[2 * l] = z0;
+      c[2 * l + 1] = z1;
+      srz += rv[2 * l] * z0 + rv[2 * l + 1] * z1;
+    }
+    rz = (double)srz;
+  }
+  __syncwarp();
+  for (int i = lane; i < ncol * N; i += 32) z[base + i] = sr[(i / N) * SN + i % N];
   block_add(rz, scal + 3 * (k + 1) + 1);
   block_add(rr, scal + 3 * (k + 1) + 2);
 }
@@ -851,6 +954,24 @@ int colprec_setup_t(bp_mesh* m, const M* J, cudaStream_t s) {
 // One CG batch: CG_BATCH iterations (SpMV + dot, update + preconditioner, direction), then the
 // batch counter advances.  The iteration index, the tolerance and the limit are read from device
 // memory, so one captured graph serves every solve on this mesh and precision.
+// FP32 CG with 5 or 10 layers: the register-resident update; returns false where it does not apply.
+template <class V>
+bool update_cols(const Prec<V>& P, bp_solver_ws* w, int j, V* x, V* r, V* z, const V* p, const V* q, int L,
+                 cudaStream_t s) {
+  if constexpr (std::is_same<V, float>::value) {
+    const int grid = (P.nv + UPD_NT - 1) / UPD_NT;
+    if (L == 10) {
+      k_cg_update_cols<11><<<grid, UPD_NT, 0, s>>>(P, w->kbase, j, x, r, z, p, q, w->scal, w->stop);
+      return true;
+    }
+    if (L == 5) {
+      k_cg_update_cols<6><<<grid, UPD_NT, 0, s>>>(P, w->kbase, j, x, r, z, p, q, w->scal, w->stop);
+      return true;
+    }
+  }
+  return false;
+}
+
 template <class M, class V>
 void launch_cg_batch(bp_mesh* m, const M* J, cudaStream_t s) {
   bp_solver_ws* w = m->ws;
@@ -869,7 +990,8 @@ void launch_cg_batch(bp_mesh* m, const M* J, cudaStream_t s) {
   for (int j = 0; j < CG_BATCH; ++j) {
     k_spmv_pairs<M, V, true><<<gspmv, NT, 0, s>>>(m->rowptr, m->nbr_ptr, m->nbr_idx, m->nl, J, (int)(n / 2), p, q,
                                                   w->scal, w->stop, w->kbase, j);
-    k_cg_update_staged<V, V><<<gupd, UPD_NT, smem, s>>>(P, w->kbase, j, C, x, r, z, p, q, w->scal, w->stop);
+    if (!update_cols<V>(P, w, j, x, r, z, p, q, m->nl, s))
+      k_cg_update_staged<V, V><<<gupd, UPD_NT, smem, s>>>(P, w->kbase, j, C, x, r, z, p, q, w->scal, w->stop);
     k_cg_direction<V><<<grid_for(n / 2, NT), NT, 0, s>>>(w->kbase, j, w->cgpar, n / 2, z, p, w->scal, w->stop);
   }
   k_cg_advance<<<1, 1, 0, s>>>(w->kbase, CG_BATCH);
