@@ -300,6 +300,12 @@ def run_ours(args):
     J32 = torch.empty(dm.nnz, dtype=torch.float32, device=dev)
     jac32_ms = timed(lambda: capi.bp_assemble_jacobian(dm.handle, U, R, J32, capi.BP_F32,
                                                        capi.BP_SCATTER_ATOMIC, capi.BP_JAC_FACTORED, stream))
+    jac32c_ms = timed(lambda: capi.bp_assemble_jacobian(dm.handle, U, R, J32, capi.BP_F32,
+                                                        capi.BP_SCATTER_COLOR, capi.BP_JAC_FACTORED, stream))
+    all32_ms = timed(lambda: capi.bp_assemble_jacobian(dm.handle, U, R, J32, capi.BP_F32_ALL,
+                                                       capi.BP_SCATTER_ATOMIC, capi.BP_JAC_FACTORED, stream))
+    all32c_ms = timed(lambda: capi.bp_assemble_jacobian(dm.handle, U, R, J32, capi.BP_F32_ALL,
+                                                        capi.BP_SCATTER_COLOR, capi.BP_JAC_FACTORED, stream))
     dual_ms = timed(lambda: capi.bp_assemble_jacobian(dm.handle, U, R, J, capi.BP_F64,
                                                       capi.BP_SCATTER_ATOMIC, capi.BP_JAC_DUAL, stream), reps=5)
     pair_ms = timed(lambda: capi.bp_assemble_jacobian(dm.handle, U, R, J, capi.BP_F64X2,
@@ -380,6 +386,10 @@ def run_ours(args):
             "secondary": {
                 "residual_only": {"value": W / (res_ms * 1e-3), "unit": UNIT, "ms": res_ms},
                 "jacobian_f32_lanes": {"value": W / (jac32_ms * 1e-3), "unit": UNIT, "ms": jac32_ms},
+                "jacobian_f32_lanes_colored": {"value": W / (jac32c_ms * 1e-3), "unit": UNIT, "ms": jac32c_ms},
+                "jacobian_f32_all": {"value": W / (all32_ms * 1e-3), "unit": UNIT, "ms": all32_ms,
+                                     "note": "FP32 value path and lanes (residual with FP32 rounding)"},
+                "jacobian_f32_all_colored": {"value": W / (all32c_ms * 1e-3), "unit": UNIT, "ms": all32c_ms},
                 "jacobian_f64_dual12": {"value": W / (dual_ms * 1e-3), "unit": UNIT, "ms": dual_ms},
                 "jacobian_paired_f32_lanes": {"value": W / (pair_ms * 1e-3), "unit": UNIT, "ms": pair_ms,
                                               "note": "FP64-accurate (1e-12 parity) lanes of hi+lo FP32 pairs"},
@@ -553,13 +563,18 @@ def newton_section(capi, synth, dm, mesh, dev, skip_large=False, reps=3):
         return {"s": statistics.median(times), "converged": rep["converged"], "newton_iters": rep["newton_iters"],
                 "krylov_iters": rep["krylov_iters"], "final_rel_residual": rep["history"][-1],
                 "t_assemble": rep["t_assemble"], "t_precond": rep["t_precond"], "t_krylov": rep["t_krylov"],
-                "t_linesearch": rep["t_linesearch"]}, U
+                "t_linesearch": rep["t_linesearch"], "value32_steps": rep["value32_steps"]}, U
 
     out = {"metric": "time to 1e-8 rel. FP64 residual Newton solve", "unit": "s", "start": "shallow-ice guess"}
     f64, U64 = solve(dm, capi.BP_F64)
     f32, U32 = solve(dm, capi.BP_F32)
     out[mesh.name] = {"f64": f64, "mixed_f32": f32, "speedup_mixed": f64["s"] / f32["s"],
                       "mixed_vs_f64_solution_rel_inf": float((U32 - U64).abs().max() / U64.abs().max())}
+    # early steps with the FP32 value path (inexact residual) until ||F|| <= tau ||F(0)||
+    for tau in (1e-2, 1e-3, 1e-4):
+        v, Uv = solve(dm, capi.BP_F32, value32_rtol=tau)
+        v["vs_f64_solution_rel_inf"] = float((Uv - U64).abs().max() / U64.abs().max())
+        out[mesh.name][f"mixed_f32_value32_until_{tau:g}"] = v
     out[mesh.name]["learned_start_mixed"] = learned_start(capi, dm, dev, reps)
     # the ocean margin condition (lateral faces of a grounded calving front, partly below sea level)
     marine = synth.config_marine()
@@ -567,9 +582,11 @@ def newton_section(capi, synth, dm, mesh, dev, skip_large=False, reps=3):
     m64, W64 = solve(dmm, capi.BP_F64)
     m32, W32 = solve(dmm, capi.BP_F32)
     mp, _ = solve(dmm, capi.BP_F32, picard_rtol=0.01)
+    mpv, _ = solve(dmm, capi.BP_F32, picard_rtol=0.01, value32_rtol=1e-3)
     out[marine.name] = {"wedges": marine.nwedges, "margin": "ocean (cryostatic minus sea-water pressure)",
                         "f64": m64, "mixed_f32": m32, "speedup_mixed": m64["s"] / m32["s"],
                         "mixed_f32_picard_until_1e-2": mp,
+                        "mixed_f32_picard_until_1e-2_value32_until_1e-3": mpv,
                         "mixed_vs_f64_solution_rel_inf": float((W32 - W64).abs().max() / W64.abs().max()),
                         "max_speed_m_per_yr": float(torch.hypot(W64[0::2], W64[1::2]).max())}
     del W64, W32
@@ -579,7 +596,9 @@ def newton_section(capi, synth, dm, mesh, dev, skip_large=False, reps=3):
         dmb = capi.DeviceMesh(big)
         b64, V64 = solve(dmb, capi.BP_F64, reps=1)
         b32, V32 = solve(dmb, capi.BP_F32, reps=1)
+        bv, _ = solve(dmb, capi.BP_F32, reps=1, value32_rtol=1e-3)
         out[big.name] = {"wedges": big.nwedges, "f64": b64, "mixed_f32": b32, "speedup_mixed": b64["s"] / b32["s"],
+                         "mixed_f32_value32_until_1e-3": bv,
                          "mixed_vs_f64_solution_rel_inf": float((V32 - V64).abs().max() / V64.abs().max())}
         del V64, V32
         dmb.close()

@@ -104,15 +104,22 @@ typedef struct {
   int64_t device_bytes; /* device memory held by the mesh object */
 } bp_mesh_info_t;
 
-/* Jacobian precision of the derivative lanes (the residual is always FP64):
+/* Jacobian precision of the derivative lanes (the residual is FP64 except with BP_F32_ALL):
  *   BP_F64   native FP64 lanes;
  *   BP_F32   FP32 lanes (J values are float);
  *   BP_F64X2 FP64-accurate lanes built from pairs of FP32 numbers (hi + lo, error-free sum and
  *            product transformations, relative error ~2^-46 per operation); J values are double;
  *            Jacobian assembly only, sum-factorised method only.  It moves the lane arithmetic to
  *            the FP32 pipe (~60x the FP64 rate on B300), but the doubled register footprint of the
- *            element matrix spills, and on B300 it measures slower than BP_F64 lanes. */
-enum { BP_F64 = 0, BP_F32 = 1, BP_F64X2 = 2 };
+ *            element matrix spills, and on B300 it measures slower than BP_F64 lanes.
+ *   BP_F32_ALL  FP32 lanes and an FP32 value path: the geometry, the 2D velocity gradients and the
+ *            vertical velocity differences are formed in FP64 and rounded once, everything at the
+ *            quadrature points (strain rates, viscosity, stresses, element residual) runs in FP32.
+ *            J values are float; R is still a double array but carries FP32 rounding (relative
+ *            ~1e-7 of the element contributions).  Sum-factorised method only.  Meant for the
+ *            early steps of an inexact Newton solve (bp_solve_opts.value32_rtol), where the
+ *            residual is far above that rounding. */
+enum { BP_F64 = 0, BP_F32 = 1, BP_F64X2 = 2, BP_F32_ALL = 3 };
 /* Scatter of element contributions: atomics, or colour by colour with plain read-modify-write. */
 enum { BP_SCATTER_AUTO = 0, BP_SCATTER_ATOMIC = 1, BP_SCATTER_COLOR = 2 };
 /* How the element Jacobian is formed: forward-mode dual numbers with 12 lanes (one per
@@ -155,13 +162,13 @@ int bp_assemble_residual(bp_mesh* mesh, const double* U_dev, double* R_dev, void
 
 /*
  * Jacobian dR/dU at U (Sec. 3.2) into J_vals_dev ([nnz] values on the bp_csr_pattern
- * pattern: double for BP_F64 and BP_F64X2, float for BP_F32) and, if R_dev != NULL, the FP64
- * residual.
+ * pattern: double for BP_F64 and BP_F64X2, float for BP_F32 and BP_F32_ALL) and, if R_dev != NULL,
+ * the residual (FP64; FP32-accurate with BP_F32_ALL).
  * Both outputs are overwritten (zeroing is part of the call).  `scatter` is a BP_SCATTER_*,
  * `method` a BP_JAC_*.  Asynchronous on `stream`.
- * Errors: BP_EINVAL (NULL U/J, unknown precision/scatter/method), BP_EUNSUP (BP_F64X2 with
- * BP_JAC_DUAL), BP_ENOMEM (first call with R_dev == NULL allocates a residual scratch in the mesh
- * object), BP_ECUDA.
+ * Errors: BP_EINVAL (NULL U/J, unknown precision/scatter/method), BP_EUNSUP (BP_F64X2 or
+ * BP_F32_ALL with BP_JAC_DUAL), BP_ENOMEM (first call with R_dev == NULL allocates a residual
+ * scratch in the mesh object), BP_ECUDA.
  */
 int bp_assemble_jacobian(bp_mesh* mesh, const double* U_dev, double* R_dev, void* J_vals_dev,
                          int precision, int scatter, int method, void* stream);
@@ -173,7 +180,7 @@ int bp_assemble_jacobian(bp_mesh* mesh, const double* U_dev, double* R_dev, void
 
 /*
  * y = J x for a Jacobian on the bp_csr_pattern pattern (J_vals_dev: double for BP_F64, float for
- * BP_F32; products and sums in FP64).  The operator application "Op*x" of the linear solve.
+ * BP_F32 or BP_F32_ALL; products and sums in FP64).  The operator application "Op*x" of the linear solve.
  * J, x and y must be 16-byte aligned (u and v rows are processed as pairs).  Asynchronous.
  * Errors: BP_EINVAL (NULL, misaligned, unknown precision), BP_ECUDA.
  */
@@ -240,13 +247,17 @@ typedef struct {
   double picard_rtol; /* > 0: while ||F|| > picard_rtol ||F(0)|| take Picard steps (the Jacobian
                          without the eta' rank-one part: the fixed-viscosity matrix, SPD, cheaper
                          to assemble), then Newton steps; 0: Newton from the first step */
+  double value32_rtol; /* BP_F32 only, > 0: while ||F|| > value32_rtol ||F(0)|| assemble with
+                          BP_F32_ALL (FP32 value path: an inexact residual, rounding ~1e-7 of the
+                          element contributions), then with the FP64 value path; convergence is
+                          always tested on an FP64 residual.  0: FP64 value path throughout */
 } bp_solve_opts;
 
 typedef struct {
   int newton_iters;          /* Newton steps taken */
   int krylov_iters;          /* total Krylov iterations */
   int converged;             /* 1 if ||F|| <= rtol ||F(0)|| */
-  int pad;
+  int value32_steps;         /* steps assembled with the FP32 value path (bp_solve_opts.value32_rtol) */
   double fnorm_ref;          /* ||F(0)||_2 */
   double fnorm_initial;      /* ||F(U_0)||_2 */
   double fnorm_final;        /* ||F(U)||_2 at return */
@@ -257,7 +268,7 @@ typedef struct {
 } bp_solve_report;
 
 /* Defaults: rtol 1e-8, 50 Newton, 1000 Krylov, eta_max 0.1, BP_F64, CG, line search on, check 8,
- * picard_rtol 0. */
+ * picard_rtol 0, value32_rtol 0. */
 void bp_solve_opts_default(bp_solve_opts* opts);
 
 /*

@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(HERE, "libbp.so")
 
 BP_OK, BP_EINVAL, BP_EMESH, BP_ENOMEM, BP_ECUDA, BP_ENAN, BP_ENOCONV, BP_EUNSUP, BP_ESIZE = range(9)
 BP_NOALLOC_MAX_NDOF = 1048576
-BP_F64, BP_F32, BP_F64X2 = 0, 1, 2
+BP_F64, BP_F32, BP_F64X2, BP_F32_ALL = 0, 1, 2, 3
 BP_SCATTER_AUTO, BP_SCATTER_ATOMIC, BP_SCATTER_COLOR = 0, 1, 2
 BP_JAC_AUTO, BP_JAC_DUAL, BP_JAC_FACTORED = 0, 1, 2
 BP_GUESS_ZERO, BP_GUESS_SIA = 0, 1
@@ -25,6 +25,7 @@ BP_KRYLOV_CG = 0
 BP_JUDGE_RESIDUAL, BP_JUDGE_ENERGY, BP_JUDGE_NONE = 0, 1, 2
 BP_LS_OFF, BP_LS_HALVING, BP_LS_QUADRATIC = 0, 1, 2
 BP_MARGIN_FREE, BP_MARGIN_OCEAN = 0, 1
+BP_MLP_IN, BP_MLP_HIDDEN, BP_MLP_OUT, BP_MLP_OUT_USED, BP_MLP_LEVELS = 16, 128, 32, 22, 11
 
 
 class BPError(RuntimeError):
@@ -55,12 +56,13 @@ class bp_mesh_info_t(ctypes.Structure):
 class bp_solve_opts(ctypes.Structure):
     _fields_ = [("rtol", ctypes.c_double), ("max_newton", ctypes.c_int), ("max_krylov", ctypes.c_int),
                 ("eta_max", ctypes.c_double), ("precision", ctypes.c_int), ("krylov", ctypes.c_int),
-                ("line_search", ctypes.c_int), ("check_every", ctypes.c_int), ("picard_rtol", ctypes.c_double)]
+                ("line_search", ctypes.c_int), ("check_every", ctypes.c_int), ("picard_rtol", ctypes.c_double),
+                ("value32_rtol", ctypes.c_double)]
 
 
 class bp_solve_report(ctypes.Structure):
     _fields_ = [("newton_iters", ctypes.c_int), ("krylov_iters", ctypes.c_int), ("converged", ctypes.c_int),
-                ("pad", ctypes.c_int), ("fnorm_ref", ctypes.c_double), ("fnorm_initial", ctypes.c_double),
+                ("value32_steps", ctypes.c_int), ("fnorm_ref", ctypes.c_double), ("fnorm_initial", ctypes.c_double),
                 ("fnorm_final", ctypes.c_double), ("history", ctypes.c_double * 65),
                 ("krylov_per_newton", ctypes.c_int * 64), ("alpha", ctypes.c_double * 64),
                 ("t_total", ctypes.c_double), ("t_assemble", ctypes.c_double), ("t_precond", ctypes.c_double),
@@ -69,6 +71,7 @@ class bp_solve_report(ctypes.Structure):
     def as_dict(self) -> dict:
         k = self.newton_iters
         return {"newton_iters": k, "krylov_iters": self.krylov_iters, "converged": bool(self.converged),
+                "value32_steps": self.value32_steps,
                 "fnorm_ref": self.fnorm_ref, "fnorm_initial": self.fnorm_initial, "fnorm_final": self.fnorm_final,
                 "history": list(self.history[:k + 1]), "krylov_per_newton": list(self.krylov_per_newton[:k]),
                 "alpha": list(self.alpha[:k]), "t_total": self.t_total, "t_assemble": self.t_assemble,
@@ -430,7 +433,7 @@ class DeviceMesh:
                  R=None, J=None, want_residual=True, stream=None):
         import torch
         if J is None:
-            J = torch.empty(self.nnz, dtype=torch.float32 if precision == BP_F32 else torch.float64,
+            J = torch.empty(self.nnz, dtype=torch.float32 if precision in (BP_F32, BP_F32_ALL) else torch.float64,
                             device=self.device)
         if R is None and want_residual:
             R = torch.empty(self.ndof, dtype=torch.float64, device=self.device)

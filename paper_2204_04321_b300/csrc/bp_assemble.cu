@@ -11,11 +11,23 @@ namespace {
 #define BP_ASM_MIN_BLOCKS 1  // minimum resident blocks of 128 threads per SM asked of the register allocator
 #endif
 
-template <int MODE, class TL, bool ATOMIC, bool PICARD = false>
-__global__ void __launch_bounds__(128, BP_ASM_MIN_BLOCKS) k_assemble(const AsmArgs A) {
+#ifndef BP_ASM_MIN_BLOCKS_F32
+#define BP_ASM_MIN_BLOCKS_F32 1
+#endif
+#ifndef BP_ASM_MIN_BLOCKS_F32ALL
+#define BP_ASM_MIN_BLOCKS_F32ALL 1
+#endif
+template <class TL, class TV>
+constexpr int min_blocks() {
+  return std::is_same<TV, float>::value ? BP_ASM_MIN_BLOCKS_F32ALL
+                                        : (std::is_same<TL, float>::value ? BP_ASM_MIN_BLOCKS_F32 : BP_ASM_MIN_BLOCKS);
+}
+
+template <int MODE, class TL, bool ATOMIC, bool PICARD = false, class TV = double>
+__global__ void __launch_bounds__(128, min_blocks<TL, TV>()) k_assemble(const AsmArgs A) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= A.count) return;
-  assemble_column<MODE, TL, ATOMIC, PICARD>(A, A.tri_list ? A.tri_list[idx] : idx);
+  assemble_column<MODE, TL, ATOMIC, PICARD, TV>(A, A.tri_list ? A.tri_list[idx] : idx);
 }
 
 AsmArgs make_args(const bp_mesh* m, const double* U, double* R, void* J) {
@@ -41,20 +53,50 @@ AsmArgs make_args(const bp_mesh* m, const double* U, double* R, void* J) {
   return a;
 }
 
-template <int MODE, class TL, bool PICARD = false>
+template <int MODE, class TL, bool PICARD = false, class TV = double>
 int launch(const bp_mesh* m, AsmArgs a, int scatter, cudaStream_t s) {
   constexpr int TPB = 128;
   if (scatter == BP_SCATTER_COLOR) {
     for (int c = 0; c < m->ncolors; ++c) {
       a.tri_list = m->color_tris + m->color_off[c];
       a.count = m->color_off[c + 1] - m->color_off[c];
-      k_assemble<MODE, TL, false, PICARD><<<(a.count + TPB - 1) / TPB, TPB, 0, s>>>(a);
+      k_assemble<MODE, TL, false, PICARD, TV><<<(a.count + TPB - 1) / TPB, TPB, 0, s>>>(a);
     }
   } else {
-    k_assemble<MODE, TL, true, PICARD><<<(a.count + TPB - 1) / TPB, TPB, 0, s>>>(a);
+    k_assemble<MODE, TL, true, PICARD, TV><<<(a.count + TPB - 1) / TPB, TPB, 0, s>>>(a);
   }
   BP_CUDA_TRY(cudaGetLastError());
   return BP_OK;
+}
+
+// Argument checks shared by the Jacobian entry points.
+int check_jacobian_args(int precision, int scatter, int method) {
+  if (precision != BP_F64 && precision != BP_F32 && precision != BP_F64X2 && precision != BP_F32_ALL)
+    return BP_EINVAL;
+  if (scatter < BP_SCATTER_AUTO || scatter > BP_SCATTER_COLOR) return BP_EINVAL;
+  if (method < BP_JAC_AUTO || method > BP_JAC_FACTORED) return BP_EINVAL;
+  if ((precision == BP_F64X2 || precision == BP_F32_ALL) && method == BP_JAC_DUAL) return BP_EUNSUP;
+  return BP_OK;
+}
+
+size_t jacobian_value_bytes(int precision) {
+  return (precision == BP_F32 || precision == BP_F32_ALL) ? sizeof(float) : sizeof(double);
+}
+
+// Launch of the Jacobian kernel for checked arguments (scatter and method resolved).
+int launch_jacobian(const bp_mesh* m, const AsmArgs& a, int precision, int scatter, int method, cudaStream_t s) {
+  switch (precision) {
+    case BP_F64X2:
+      return launch<MODE_FACT, f64x2>(m, a, scatter, s);
+    case BP_F32_ALL:
+      return launch<MODE_FACT, float, false, float>(m, a, scatter, s);
+    case BP_F64:
+      return method == BP_JAC_DUAL ? launch<MODE_DUAL, double>(m, a, scatter, s)
+                                   : launch<MODE_FACT, double>(m, a, scatter, s);
+    default:
+      return method == BP_JAC_DUAL ? launch<MODE_DUAL, float>(m, a, scatter, s)
+                                   : launch<MODE_FACT, float>(m, a, scatter, s);
+  }
 }
 
 }  // namespace
@@ -70,10 +112,8 @@ extern "C" int bp_assemble_residual(bp_mesh* m, const double* U, double* R, void
 int bp_assemble_jacobian_ex(bp_mesh* m, const double* U, double* R, void* J, int precision, int scatter, int method,
                             int picard, void* stream) {
   if (!m || !U || !J || !bp_aligned16(U)) return BP_EINVAL;
-  if (precision != BP_F64 && precision != BP_F32 && precision != BP_F64X2) return BP_EINVAL;
-  if (precision == BP_F64X2 && method == BP_JAC_DUAL) return BP_EUNSUP;
-  if (scatter < BP_SCATTER_AUTO || scatter > BP_SCATTER_COLOR) return BP_EINVAL;
-  if (method < BP_JAC_AUTO || method > BP_JAC_FACTORED) return BP_EINVAL;
+  int rc0 = check_jacobian_args(precision, scatter, method);
+  if (rc0) return rc0;
   bp_device_guard g(m->device);
   cudaStream_t s = (cudaStream_t)stream;
   if (scatter == BP_SCATTER_AUTO) scatter = BP_SCATTER_ATOMIC;
@@ -87,19 +127,20 @@ int bp_assemble_jacobian_ex(bp_mesh* m, const double* U, double* R, void* J, int
     Rw = m->rscratch;
   }
   BP_CUDA_TRY(cudaMemcpyAsync(Rw, m->load, m->ndof * sizeof(double), cudaMemcpyDeviceToDevice, s));
-  BP_CUDA_TRY(cudaMemsetAsync(J, 0, m->nnz * (precision == BP_F32 ? sizeof(float) : sizeof(double)), s));
+  BP_CUDA_TRY(cudaMemsetAsync(J, 0, m->nnz * jacobian_value_bytes(precision), s));
   const AsmArgs a = make_args(m, U, Rw, J);
   if (picard) {  // fixed-viscosity matrix (Newton solver's Picard steps): factored method, FP64 or FP32
     if (method != BP_JAC_FACTORED || precision == BP_F64X2) return BP_EUNSUP;
-    return precision == BP_F64 ? launch<MODE_FACT, double, true>(m, a, scatter, s)
-                               : launch<MODE_FACT, float, true>(m, a, scatter, s);
+    switch (precision) {
+      case BP_F64:
+        return launch<MODE_FACT, double, true>(m, a, scatter, s);
+      case BP_F32_ALL:
+        return launch<MODE_FACT, float, true, float>(m, a, scatter, s);
+      default:
+        return launch<MODE_FACT, float, true>(m, a, scatter, s);
+    }
   }
-  if (precision == BP_F64X2) return launch<MODE_FACT, f64x2>(m, a, scatter, s);
-  if (precision == BP_F64)
-    return method == BP_JAC_DUAL ? launch<MODE_DUAL, double>(m, a, scatter, s)
-                                 : launch<MODE_FACT, double>(m, a, scatter, s);
-  return method == BP_JAC_DUAL ? launch<MODE_DUAL, float>(m, a, scatter, s)
-                               : launch<MODE_FACT, float>(m, a, scatter, s);
+  return launch_jacobian(m, a, precision, scatter, method, s);
 }
 
 extern "C" int bp_assemble_jacobian(bp_mesh* m, const double* U, double* R, void* J, int precision,
@@ -145,10 +186,8 @@ int noalloc_scratch(int device, double** out) {
 extern "C" int bp_assemble_jacobian_noalloc(bp_mesh* m, const double* U, void* J, int precision,
                                             int scatter, int method, void* stream) {
   if (!m || !U || !J || !bp_aligned16(U)) return BP_EINVAL;
-  if (precision != BP_F64 && precision != BP_F32 && precision != BP_F64X2) return BP_EINVAL;
-  if (precision == BP_F64X2 && method == BP_JAC_DUAL) return BP_EUNSUP;
-  if (scatter < BP_SCATTER_AUTO || scatter > BP_SCATTER_COLOR) return BP_EINVAL;
-  if (method < BP_JAC_AUTO || method > BP_JAC_FACTORED) return BP_EINVAL;
+  int rc0 = check_jacobian_args(precision, scatter, method);
+  if (rc0) return rc0;
   if (m->ndof > BP_NOALLOC_MAX_NDOF) return BP_ESIZE;
   bp_device_guard g(m->device);
   double* Rw = nullptr;
@@ -159,12 +198,6 @@ extern "C" int bp_assemble_jacobian_noalloc(bp_mesh* m, const double* U, void* J
   if (method == BP_JAC_AUTO) method = BP_JAC_FACTORED;
   // the scratch keeps the previous call's residual: start it again from the memoised load
   BP_CUDA_TRY(cudaMemcpyAsync(Rw, m->load, m->ndof * sizeof(double), cudaMemcpyDeviceToDevice, s));
-  BP_CUDA_TRY(cudaMemsetAsync(J, 0, m->nnz * (precision == BP_F32 ? sizeof(float) : sizeof(double)), s));
-  const AsmArgs a = make_args(m, U, Rw, J);
-  if (precision == BP_F64X2) return launch<MODE_FACT, f64x2>(m, a, scatter, s);
-  if (precision == BP_F64)
-    return method == BP_JAC_DUAL ? launch<MODE_DUAL, double>(m, a, scatter, s)
-                                 : launch<MODE_FACT, double>(m, a, scatter, s);
-  return method == BP_JAC_DUAL ? launch<MODE_DUAL, float>(m, a, scatter, s)
-                               : launch<MODE_FACT, float>(m, a, scatter, s);
+  BP_CUDA_TRY(cudaMemsetAsync(J, 0, m->nnz * jacobian_value_bytes(precision), s));
+  return launch_jacobian(m, make_args(m, U, Rw, J), precision, scatter, method, s);
 }

@@ -123,6 +123,23 @@ __device__ __forceinline__ float to_lane<float>(const double x) {
   return f32_of(x);
 }
 
+// A value-path quantity (type TV) as a lane (type TL): no conversion when the types agree.
+template <class TL, class TV>
+__device__ __forceinline__ TL lane_from(const TV x) {
+  if constexpr (std::is_same<TL, TV>::value) {
+    return x;
+  } else {
+    return to_lane<TL>(x);
+  }
+}
+// Value-path helpers for TV = double (FP64 value path) and TV = float (the all-FP32 variant).
+__device__ __forceinline__ double inv_cbrt_t(const double x) { return inv_cbrt(x); }
+__device__ __forceinline__ float inv_cbrt_t(const float x) { return rcbrtf(x); }
+__device__ __forceinline__ double fma_t(const double a, const double b, const double c) { return fma(a, b, c); }
+__device__ __forceinline__ float fma_t(const float a, const float b, const float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double to_r(const double x) { return x; }
+__device__ __forceinline__ double to_r(const float x) { return f64_of(x); }
+
 // storage type of a lane type in the Jacobian array, and the conversion
 template <class TL>
 struct LaneStore {
@@ -179,8 +196,14 @@ __device__ __forceinline__ Dual<TL, NL> operator*(double s, const Dual<TL, NL>& 
 // Assembles every wedge of the column above base triangle t (one thread).
 // PICARD (factored method only): leave out the eta' rank-one part, i.e. assemble the fixed-viscosity
 // (Picard) matrix instead of the Jacobian; the residual is unchanged.
-template <int MODE, class TL, bool ATOMIC, bool PICARD = false>
+// TV is the value-path type: double (the residual in FP64), or float for the all-FP32 variant
+// (factored method, FP32 lanes) whose residual carries FP32 rounding: per-column and per-level
+// geometry, the 2D velocity gradients and the vertical velocity differences are still formed in
+// FP64 and rounded once, everything per quadrature point runs in FP32.
+template <int MODE, class TL, bool ATOMIC, bool PICARD = false, class TV = double>
 __device__ __forceinline__ void assemble_column(const AsmArgs& A, const int t) {
+  static_assert(std::is_same<TV, double>::value || (MODE == MODE_FACT && std::is_same<TL, float>::value),
+                "the FP32 value path exists for the factored method with FP32 lanes only");
   const int L = A.L;
 
   // ---- column geometry (per base triangle)
@@ -217,6 +240,13 @@ __device__ __forceinline__ void assemble_column(const AsmArgs& A, const int t) {
   const double d12 = d * (1.0 / 12.0);
   const double d6 = d * (1.0 / 6.0);
   const TL d12L = to_lane<TL>(d12);
+  const TV d6V = to_lane<TV>(d6), deltaV = to_lane<TV>(A.delta), cAV = to_lane<TV>(A.cA);
+  TV lxV[3], lyV[3];  // grad lambda in value-path precision
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    lxV[a] = to_lane<TV>(lx[a]);
+    lyV[a] = to_lane<TV>(ly[a]);
+  }
   TL clx[3], cly[3];  // grad lambda in lane precision (Jacobian lanes)
   if constexpr (MODE == MODE_FACT) {
 #pragma unroll
@@ -254,16 +284,16 @@ __device__ __forceinline__ void assemble_column(const AsmArgs& A, const int t) {
   double guby = ub[0] * ly[0] + ub[1] * ly[1] + ub[2] * ly[2];
   double gvbx = vb[0] * lx[0] + vb[1] * lx[1] + vb[2] * lx[2];
   double gvby = vb[0] * ly[0] + vb[1] * ly[1] + vb[2] * ly[2];
-  double carry[3][2] = {{0, 0}, {0, 0}, {0, 0}};  // residual of the current bottom level from the wedge below
+  TV carry[3][2] = {{0, 0}, {0, 0}, {0, 0}};  // residual of the current bottom level from the wedge below
   // rate-factor field: hardness B = A^(-1/3) interpolated at the triangle points of the bottom level
-  double hb[3] = {A.cA, A.cA, A.cA};
+  TV hb[3] = {cAV, cAV, cAV};
   if (A.Bn) {
     const double b0 = A.Bn[(int64_t)v[0] * (L + 1)], b1 = A.Bn[(int64_t)v[1] * (L + 1)],
                  b2 = A.Bn[(int64_t)v[2] * (L + 1)];
     const double bs = (b0 + b1 + b2) * (1.0 / 6.0);
-    hb[0] = bs + 0.5 * b0;
-    hb[1] = bs + 0.5 * b1;
-    hb[2] = bs + 0.5 * b2;
+    hb[0] = to_lane<TV>(bs + 0.5 * b0);
+    hb[1] = to_lane<TV>(bs + 0.5 * b1);
+    hb[2] = to_lane<TV>(bs + 0.5 * b2);
   }
 
   for (int l = 0; l < L; ++l) {
@@ -281,42 +311,50 @@ __device__ __forceinline__ void assemble_column(const AsmArgs& A, const int t) {
     const double s_l = A.sigma[l];
     const double ds = A.sigma[l + 1] - s_l;
     const double invds = 1.0 / ds;
-    double ht[3] = {A.cA, A.cA, A.cA};  // hardness at the triangle points of the top level
+    TV ht[3] = {cAV, cAV, cAV};  // hardness at the triangle points of the top level
     if (A.Bn) {
       const double b0 = A.Bn[(int64_t)v[0] * (L + 1) + l + 1], b1 = A.Bn[(int64_t)v[1] * (L + 1) + l + 1],
                    b2 = A.Bn[(int64_t)v[2] * (L + 1) + l + 1];
       const double bs = (b0 + b1 + b2) * (1.0 / 6.0);
-      ht[0] = bs + 0.5 * b0;
-      ht[1] = bs + 0.5 * b1;
-      ht[2] = bs + 0.5 * b2;
+      ht[0] = to_lane<TV>(bs + 0.5 * b0);
+      ht[1] = to_lane<TV>(bs + 0.5 * b1);
+      ht[2] = to_lane<TV>(bs + 0.5 * b2);
     }
 
     // per zeta level: slope of the level surface and the 2D velocity gradients
-    double Gzx[2], Gzy[2], GUx[2], GUy[2], GVx[2], GVy[2];
+    double Gzx[2], Gzy[2];
+    TV GzxV[2], GzyV[2], GUx[2], GUy[2], GVx[2], GVy[2];
+    const TV gUb[2] = {to_lane<TV>(gubx), to_lane<TV>(guby)}, gUt[2] = {to_lane<TV>(gutx), to_lane<TV>(guty)};
+    const TV gVb[2] = {to_lane<TV>(gvbx), to_lane<TV>(gvby)}, gVt[2] = {to_lane<TV>(gvtx), to_lane<TV>(gvty)};
 #pragma unroll
     for (int z = 0; z < 2; ++z) {
       const double sz = s_l + psi(1, z) * ds;
       Gzx[z] = gbx + sz * gHx;
       Gzy[z] = gby + sz * gHy;
-      GUx[z] = psi(0, z) * gubx + psi(1, z) * gutx;
-      GUy[z] = psi(0, z) * guby + psi(1, z) * guty;
-      GVx[z] = psi(0, z) * gvbx + psi(1, z) * gvtx;
-      GVy[z] = psi(0, z) * gvby + psi(1, z) * gvty;
+      GzxV[z] = to_lane<TV>(Gzx[z]);
+      GzyV[z] = to_lane<TV>(Gzy[z]);
+      GUx[z] = TV(psi(0, z)) * gUb[0] + TV(psi(1, z)) * gUt[0];
+      GUy[z] = TV(psi(0, z)) * gUb[1] + TV(psi(1, z)) * gUt[1];
+      GVx[z] = TV(psi(0, z)) * gVb[0] + TV(psi(1, z)) * gVt[0];
+      GVy[z] = TV(psi(0, z)) * gVb[1] + TV(psi(1, z)) * gVt[1];
     }
     // per triangle point: vertical shear, weights
     const double dus6 = (ut[0] - ub[0] + ut[1] - ub[1] + ut[2] - ub[2]) * (1.0 / 6.0);
     const double dvs6 = (vt[0] - vb[0] + vt[1] - vb[1] + vt[2] - vb[2]) * (1.0 / 6.0);
-    double uz[3], vz[3], cq[3], ez[3], invh[3];
+    double cq[3], invh[3];
+    TV uz[3], vz[3], ez[3], cqV[3];
 #pragma unroll
     for (int tp = 0; tp < 3; ++tp) {
       invh[tp] = invds * invHq[tp];
-      uz[tp] = (dus6 + 0.5 * (ut[tp] - ub[tp])) * invh[tp];
-      vz[tp] = (dvs6 + 0.5 * (vt[tp] - vb[tp])) * invh[tp];
-      ez[tp] = 0.25 * (uz[tp] * uz[tp] + vz[tp] * vz[tp]);
+      const TV invhV = to_lane<TV>(invh[tp]);
+      uz[tp] = to_lane<TV>(dus6 + 0.5 * (ut[tp] - ub[tp])) * invhV;
+      vz[tp] = to_lane<TV>(dvs6 + 0.5 * (vt[tp] - vb[tp])) * invhV;
+      ez[tp] = TV(0.25) * (uz[tp] * uz[tp] + vz[tp] * vz[tp]);
       cq[tp] = d12 * ds * Hq[tp];
+      cqV[tp] = to_lane<TV>(cq[tp]);
     }
 
-    double Rl[2][3][2];  // [k][a][c] residual of this wedge
+    TV Rl[2][3][2];  // [k][a][c] residual of this wedge
     TL K[78];            // upper triangle of the element matrix
     TL eta_q[2][3];      // 2 mu at the quadrature points (factored Jacobian)
     // FP32 lanes: the per-point weights in FP32, converted once per wedge
@@ -416,42 +454,42 @@ __device__ __forceinline__ void assemble_column(const AsmArgs& A, const int t) {
       }
     } else {
       // ---- structured value path (+ sum-factorised Jacobian lanes)
-      double P1x[2] = {0, 0}, P1y[2] = {0, 0}, P2x[2] = {0, 0}, P2y[2] = {0, 0};
-      double TW1[3] = {0, 0, 0}, TW2[3] = {0, 0, 0};
+      TV P1x[2] = {0, 0}, P1y[2] = {0, 0}, P2x[2] = {0, 0}, P2y[2] = {0, 0};
+      TV TW1[3] = {0, 0, 0}, TW2[3] = {0, 0, 0};
 #pragma unroll
       for (int z = 0; z < 2; ++z) {
 #pragma unroll
         for (int tp = 0; tp < 3; ++tp) {
-          const double ux = GUx[z] - uz[tp] * Gzx[z];
-          const double uy = GUy[z] - uz[tp] * Gzy[z];
-          const double vx = GVx[z] - vz[tp] * Gzx[z];
-          const double vy = GVy[z] - vz[tp] * Gzy[z];
-          const double exy = 0.5 * (uy + vx);
-          const double e2 = fma(ux, ux, fma(vy, vy + ux, fma(exy, exy, ez[tp])));
-          const double xx = e2 + A.delta;
-          const double r = inv_cbrt(xx);
-          const double eta = (psi(0, z) * hb[tp] + psi(1, z) * ht[tp]) * r;
-          const double W = cq[tp] * eta;
-          const double g1x = 2.0 * ux + vy, g2y = ux + 2.0 * vy;
-          P1x[z] = fma(W, g1x, P1x[z]);
-          P1y[z] = fma(W, exy, P1y[z]);
-          P2x[z] = fma(W, exy, P2x[z]);
-          P2y[z] = fma(W, g2y, P2y[z]);
-          const double t1 = 0.5 * uz[tp] - g1x * Gzx[z] - exy * Gzy[z];
-          const double t2 = 0.5 * vz[tp] - exy * Gzx[z] - g2y * Gzy[z];
-          const double W6 = d6 * eta;
-          TW1[tp] = fma(W6, t1, TW1[tp]);
-          TW2[tp] = fma(W6, t2, TW2[tp]);
+          const TV ux = GUx[z] - uz[tp] * GzxV[z];
+          const TV uy = GUy[z] - uz[tp] * GzyV[z];
+          const TV vx = GVx[z] - vz[tp] * GzxV[z];
+          const TV vy = GVy[z] - vz[tp] * GzyV[z];
+          const TV exy = TV(0.5) * (uy + vx);
+          const TV e2 = fma_t(ux, ux, fma_t(vy, vy + ux, fma_t(exy, exy, ez[tp])));
+          const TV xx = e2 + deltaV;
+          const TV r = inv_cbrt_t(xx);
+          const TV eta = (TV(psi(0, z)) * hb[tp] + TV(psi(1, z)) * ht[tp]) * r;
+          const TV W = cqV[tp] * eta;
+          const TV g1x = TV(2.0) * ux + vy, g2y = ux + TV(2.0) * vy;
+          P1x[z] = fma_t(W, g1x, P1x[z]);
+          P1y[z] = fma_t(W, exy, P1y[z]);
+          P2x[z] = fma_t(W, exy, P2x[z]);
+          P2y[z] = fma_t(W, g2y, P2y[z]);
+          const TV t1 = TV(0.5) * uz[tp] - g1x * GzxV[z] - exy * GzyV[z];
+          const TV t2 = TV(0.5) * vz[tp] - exy * GzxV[z] - g2y * GzyV[z];
+          const TV W6 = d6V * eta;
+          TW1[tp] = fma_t(W6, t1, TW1[tp]);
+          TW2[tp] = fma_t(W6, t2, TW2[tp]);
           if constexpr (MODE == MODE_FACT) {
             // rank-one part eta' p_i p_j with p_{(a,k),c} = psi_k g_c,xy . Lambda_a + lambda_a psi_k' g_c . Z
             TL Wp, tau1, tau2;
             if constexpr (kF32) {  // from r, t1, t2 converted once: FP32 arithmetic only
-              const float rf = f32_of(r);
-              const float ef = f32_of(eta);
+              const float rf = lane_from<float>(r);
+              const float ef = lane_from<float>(eta);
               eta_q[z][tp] = ef;
               Wp = (-1.0f / 3.0f) * cqL[tp] * ef * (rf * rf * rf);
-              tau1 = 2.0f * invhL[tp] * f32_of(t1);
-              tau2 = 2.0f * invhL[tp] * f32_of(t2);
+              tau1 = 2.0f * invhL[tp] * lane_from<float>(t1);
+              tau2 = 2.0f * invhL[tp] * lane_from<float>(t2);
             } else {
               eta_q[z][tp] = (TL)eta;
               Wp = (TL)(-(1.0 / 3.0) * W * (r * r * r));
@@ -459,7 +497,7 @@ __device__ __forceinline__ void assemble_column(const AsmArgs& A, const int t) {
               tau2 = (TL)(2.0 * invh[tp] * t2);
             }
             if constexpr (!PICARD) {
-            const TL fg1x = to_lane<TL>(g1x), fexy = to_lane<TL>(exy), fg2y = to_lane<TL>(g2y);
+            const TL fg1x = lane_from<TL>(g1x), fexy = lane_from<TL>(exy), fg2y = lane_from<TL>(g2y);
             // p_{(a,k),c} = psi_k alpha_{a,c} -/+ t_{a,c},  alpha = g_c,xy . Lambda_a,  t = lambda_a tau_c / 2
             TL p[12];
 #pragma unroll
@@ -484,18 +522,18 @@ __device__ __forceinline__ void assemble_column(const AsmArgs& A, const int t) {
         }
       }
       // residual: R_{a,k,c} = Lambda_a . sum_z psi_k(z) P_c(z) + psi_k' sum_tp lambda_a(tp) TW_c(tp)
-      const double T1s = (TW1[0] + TW1[1] + TW1[2]) * (1.0 / 6.0);
-      const double T2s = (TW2[0] + TW2[1] + TW2[2]) * (1.0 / 6.0);
+      const TV T1s = (TW1[0] + TW1[1] + TW1[2]) * TV(1.0 / 6.0);
+      const TV T2s = (TW2[0] + TW2[1] + TW2[2]) * TV(1.0 / 6.0);
 #pragma unroll
       for (int k = 0; k < 2; ++k) {
-        const double A1x = psi(k, 0) * P1x[0] + psi(k, 1) * P1x[1];
-        const double A1y = psi(k, 0) * P1y[0] + psi(k, 1) * P1y[1];
-        const double A2x = psi(k, 0) * P2x[0] + psi(k, 1) * P2x[1];
-        const double A2y = psi(k, 0) * P2y[0] + psi(k, 1) * P2y[1];
+        const TV A1x = TV(psi(k, 0)) * P1x[0] + TV(psi(k, 1)) * P1x[1];
+        const TV A1y = TV(psi(k, 0)) * P1y[0] + TV(psi(k, 1)) * P1y[1];
+        const TV A2x = TV(psi(k, 0)) * P2x[0] + TV(psi(k, 1)) * P2x[1];
+        const TV A2y = TV(psi(k, 0)) * P2y[0] + TV(psi(k, 1)) * P2y[1];
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-          Rl[k][a][0] = lx[a] * A1x + ly[a] * A1y + dpsi(k) * (T1s + 0.5 * TW1[a]);
-          Rl[k][a][1] = lx[a] * A2x + ly[a] * A2y + dpsi(k) * (T2s + 0.5 * TW2[a]);
+          Rl[k][a][0] = lxV[a] * A1x + lyV[a] * A1y + TV(dpsi(k)) * (T1s + TV(0.5) * TW1[a]);
+          Rl[k][a][1] = lxV[a] * A2x + lyV[a] * A2y + TV(dpsi(k)) * (T2s + TV(0.5) * TW2[a]);
         }
       }
       if constexpr (MODE == MODE_FACT) {
@@ -647,8 +685,8 @@ __device__ __forceinline__ void assemble_column(const AsmArgs& A, const int t) {
       const double M[3][3] = {{Mb[0], Mb[1], Mb[2]}, {Mb[1], Mb[3], Mb[4]}, {Mb[2], Mb[4], Mb[5]}};
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
-        Rl[0][a][0] += M[a][0] * ub[0] + M[a][1] * ub[1] + M[a][2] * ub[2];
-        Rl[0][a][1] += M[a][0] * vb[0] + M[a][1] * vb[1] + M[a][2] * vb[2];
+        Rl[0][a][0] += to_lane<TV>(M[a][0] * ub[0] + M[a][1] * ub[1] + M[a][2] * ub[2]);
+        Rl[0][a][1] += to_lane<TV>(M[a][0] * vb[0] + M[a][1] * vb[1] + M[a][2] * vb[2]);
       }
       if constexpr (MODE != MODE_RES) {
 #pragma unroll
@@ -663,8 +701,8 @@ __device__ __forceinline__ void assemble_column(const AsmArgs& A, const int t) {
     // ---- scatter: residual of the bottom level is complete now; the top level is carried
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      scatter_add<ATOMIC>(A.R + ubase[a] + 2 * l, Rl[0][a][0] + carry[a][0]);
-      scatter_add<ATOMIC>(A.R + ubase[a] + 2 * l + 1, Rl[0][a][1] + carry[a][1]);
+      scatter_add<ATOMIC>(A.R + ubase[a] + 2 * l, to_r(Rl[0][a][0] + carry[a][0]));
+      scatter_add<ATOMIC>(A.R + ubase[a] + 2 * l + 1, to_r(Rl[0][a][1] + carry[a][1]));
       carry[a][0] = Rl[1][a][0];
       carry[a][1] = Rl[1][a][1];
     }
@@ -716,8 +754,8 @@ __device__ __forceinline__ void assemble_column(const AsmArgs& A, const int t) {
   }
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    scatter_add<ATOMIC>(A.R + ubase[a] + 2 * L, carry[a][0]);
-    scatter_add<ATOMIC>(A.R + ubase[a] + 2 * L + 1, carry[a][1]);
+    scatter_add<ATOMIC>(A.R + ubase[a] + 2 * L, to_r(carry[a][0]));
+    scatter_add<ATOMIC>(A.R + ubase[a] + 2 * L + 1, to_r(carry[a][1]));
   }
 }
 

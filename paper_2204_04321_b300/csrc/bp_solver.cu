@@ -1136,7 +1136,7 @@ int bp_learned_scratch(bp_mesh* m, uint16_t** X, float** Y, double** Usia, doubl
 
 extern "C" int bp_spmv(bp_mesh* m, const void* J, int precision, const double* x, double* y, void* stream) {
   if (!m || !J || !x || !y || !bp_aligned16(x) || !bp_aligned16(y) || !bp_aligned16(J)) return BP_EINVAL;
-  if (precision != BP_F64 && precision != BP_F32) return BP_EINVAL;
+  if (precision != BP_F64 && precision != BP_F32 && precision != BP_F32_ALL) return BP_EINVAL;
   bp_device_guard g(m->device);
   cudaStream_t s = (cudaStream_t)stream;
   const int grid = grid_for(m->ndof / 2 * TPR, NT);
@@ -1155,7 +1155,7 @@ extern "C" int bp_spmv(bp_mesh* m, const void* J, int precision, const double* x
 
 extern "C" int bp_colprec_setup(bp_mesh* m, const void* J, int precision, void* stream) {
   if (!m || !J) return BP_EINVAL;
-  if (precision != BP_F64 && precision != BP_F32) return BP_EINVAL;
+  if (precision != BP_F64 && precision != BP_F32 && precision != BP_F32_ALL) return BP_EINVAL;
   bp_device_guard g(m->device);
   cudaStream_t s = (cudaStream_t)stream;
   int rc = ensure_ws(m, s);
@@ -1226,6 +1226,7 @@ extern "C" void bp_solve_opts_default(bp_solve_opts* o) {
   o->line_search = 1;
   o->check_every = 8;
   o->picard_rtol = 0.0;
+  o->value32_rtol = 0.0;
 }
 
 extern "C" int bp_newton_solve(bp_mesh* m, double* U, const bp_solve_opts* opts, bp_solve_report* rep,
@@ -1233,7 +1234,7 @@ extern "C" int bp_newton_solve(bp_mesh* m, double* U, const bp_solve_opts* opts,
   if (!m || !U || !opts || !rep || !bp_aligned16(U)) return BP_EINVAL;
   const bp_solve_opts o = *opts;
   if (o.line_search < 0 || o.line_search > BP_LS_QUADRATIC) return BP_EINVAL;
-  if (!(o.picard_rtol >= 0)) return BP_EINVAL;
+  if (!(o.picard_rtol >= 0) || !(o.value32_rtol >= 0)) return BP_EINVAL;
   if (!(o.rtol > 0) || o.max_newton < 0 || o.max_newton > 64 || o.max_krylov < 1 || o.check_every < 1 ||
       (o.precision != BP_F64 && o.precision != BP_F32) || o.krylov != BP_KRYLOV_CG || !(o.eta_max > 0))
     return BP_EINVAL;
@@ -1267,13 +1268,26 @@ extern "C" int bp_newton_solve(bp_mesh* m, double* U, const bp_solve_opts* opts,
     // Picard (fixed-viscosity) matrix while far from the solution, if asked for: the residual of the
     // previous step decides (the first step uses the initial residual, unknown yet: Picard if on)
     const bool picard = o.picard_rtol > 0 && (k == 0 || rep->history[k - 1] > o.picard_rtol);
-    if ((rc = bp_assemble_jacobian_ex(m, U, w->R, w->J, o.precision, BP_SCATTER_ATOMIC, BP_JAC_FACTORED,
-                                      picard ? 1 : 0, s)))
-      return rc;
-    BP_CUDA_TRY(cudaEventRecord(ev[2], s));
+    // FP32 value path (inexact residual) while the previous residual was above value32_rtol; a
+    // residual that comes out below it is assembled again with the FP64 value path before it is
+    // tested or used, so that convergence is always judged on the FP64 residual
+    bool v32 = f32 && o.value32_rtol > 0 && (k == 0 || rep->history[k - 1] > o.value32_rtol);
     double fn;
-    if ((rc = dot_host(m, w->R, w->R, m->ndof, s, &fn))) return rc;
-    fn = std::sqrt(fn);
+    for (;;) {
+      if ((rc = bp_assemble_jacobian_ex(m, U, w->R, w->J, v32 ? BP_F32_ALL : o.precision, BP_SCATTER_ATOMIC,
+                                        BP_JAC_FACTORED, picard ? 1 : 0, s)))
+        return rc;
+      if ((rc = dot_host(m, w->R, w->R, m->ndof, s, &fn))) return rc;
+      fn = std::sqrt(fn);
+      if (v32 && std::isfinite(fn) && fn <= o.value32_rtol * fref) {
+        v32 = false;
+        continue;
+      }
+      break;
+    }
+    if (v32) ++rep->value32_steps;
+    BP_CUDA_TRY(cudaEventRecord(ev[2], s));
+    BP_CUDA_TRY(cudaEventSynchronize(ev[2]));
     rep->t_assemble += elapsed(ev[1], ev[2]);
     if (!std::isfinite(fn)) {
       status = BP_ENAN;

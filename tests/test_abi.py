@@ -30,6 +30,64 @@ def test_library_exports_every_declared_symbol():
     assert set(capi.SIGNATURES) == names
 
 
+C_TYPES = {"double": 8, "int": 4, "int32_t": 4, "int64_t": 8, "float": 4}
+
+
+def header_structs():
+    """{struct name: [(field, size in bytes)]} of the typedef'd structs of include/bp.h, in order."""
+    src = open(os.path.join(ROOT, "include", "bp.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    out = {}
+    for body, name in re.findall(r"typedef struct \{(.*?)\}\s*(\w+);", src, flags=re.S):
+        fields = []
+        for decl in body.split(";"):
+            decl = decl.strip()
+            if not decl:
+                continue
+            m = re.match(r"(?:const\s+)?(\w+)\s*(\**)\s*(.*)", decl)
+            ctype, star, names = m.groups()
+            for n in names.split(","):
+                n = n.strip()
+                ptr = star or n.startswith("*")
+                n = n.lstrip("*").strip()
+                count = 1
+                arr = re.match(r"(\w+)\[(\d+)\]", n)
+                if arr:
+                    n, count = arr.group(1), int(arr.group(2))
+                size = 8 if ptr else (C_TYPES[ctype] if ctype in C_TYPES else sum(z for _, z in out[ctype]))
+                fields.append((n, size * count))
+        out[name] = fields
+    return out
+
+
+@pytest.mark.parametrize("name", ["bp_params", "bp_mesh_desc", "bp_mesh_info_t", "bp_solve_opts",
+                                  "bp_solve_report"])
+def test_binding_structs_match_the_header(name):
+    """Field names, order and sizes of the ctypes mirrors equal the C declarations."""
+    import ctypes
+    fields = header_structs()[name]
+    cls = getattr(capi, name)
+    assert [f for f, _ in cls._fields_] == [f for f, _ in fields]
+    for (f, t), (_, size) in zip(cls._fields_, fields):
+        assert ctypes.sizeof(t) == size, f
+
+
+def test_binding_constants_match_the_header():
+    src = open(os.path.join(ROOT, "include", "bp.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    consts = {}
+    for body in re.findall(r"enum\s*\{(.*?)\}", src, flags=re.S):
+        for n, v in re.findall(r"(BP_\w+)\s*=\s*(-?\d+)", body):
+            consts[n] = int(v)
+    consts.update({n: int(v) for n, v in re.findall(r"#define\s+(BP_\w+)\s+(\d+)\b", src)})
+    assert consts["BP_F32_ALL"] == 3 and len(consts) > 30
+    for n, v in consts.items():
+        if hasattr(capi, n):
+            assert getattr(capi, n) == v, n
+    missing = [n for n in consts if not hasattr(capi, n)]
+    assert not missing, missing
+
+
 def test_version_and_strerror():
     assert "sm_103a" in capi.bp_version()
     assert capi.bp_strerror(capi.BP_EMESH) == "invalid mesh"

@@ -139,6 +139,43 @@ def test_jacobian_parity_at_zero_and_shallow_ice_velocities(name, kind, precisio
     assert err <= (TOL32 if precision == "f32" else TOL64), err
 
 
+# FP32 value path: the element work at the quadrature points runs in FP32, so R carries FP32
+# rounding of the element contributions (unit roundoff 6e-8) amplified by the cancellations of the
+# velocity gradient (level-surface gradient minus shear times slope) and of the assembly; the bar
+# is normwise, like the FP32-lane Jacobian's.
+TOL32_VALUES = 1e-5
+
+
+@pytest.mark.parametrize("name", list(MESHES))
+@pytest.mark.parametrize("kind", ["random", "zero", "sia"])
+@pytest.mark.parametrize("scatter", ["atomic", "color"])
+def test_fp32_value_path_parity(name, kind, scatter):
+    c = capi()
+    mesh = MESHES[name]()
+    om = oracle.OracleMesh(mesh)
+    U = velocities(mesh, kind, om)
+    dm = c.DeviceMesh(mesh)
+    J, R = dm.jacobian(dev(U), precision=c.BP_F32_ALL,
+                       scatter=c.BP_SCATTER_ATOMIC if scatter == "atomic" else c.BP_SCATTER_COLOR)
+    assert J.dtype == torch.float32
+    _, _, Jc, Rc = om.jacobian(U)
+    errR = rel_inf(R.cpu().numpy(), Rc)
+    errJ = rel_inf(J.cpu().numpy().astype(np.float64), Jc)
+    assert errR <= TOL32_VALUES, errR
+    assert errJ <= TOL32, errJ
+    if kind != "zero":    # at U = 0 the stress terms vanish and R is the memoised load exactly
+        assert errR > 1e-13   # the value path did run in FP32
+
+
+def test_fp32_value_path_rejects_dual_numbers():
+    c = capi()
+    mesh = synth.config_small()
+    dm = c.DeviceMesh(mesh)
+    with pytest.raises(c.BPError) as e:
+        dm.jacobian(dev(np.zeros(mesh.ndof)), precision=c.BP_F32_ALL, method=c.BP_JAC_DUAL)
+    assert e.value.status == c.BP_EUNSUP
+
+
 def test_jacobian_without_residual_and_repeat_calls_overwrite():
     c = capi()
     mesh = synth.config_small()

@@ -230,3 +230,27 @@ def test_picard_then_newton_reaches_the_same_solution(precision):
     assert rel_inf(sols[0], sols[1]) <= 1e-6
     with pytest.raises(c.BPError):
         c.bp_newton_solve(dm.handle, U, picard_rtol=-1.0)
+
+
+@pytest.mark.parametrize("geometry", ["dome", "marine"])
+def test_fp32_value_path_steps_then_fp64_reach_the_same_solution(geometry):
+    """Mixed-precision Newton whose early steps assemble with the FP32 value path (inexact residual):
+    the same minimiser, and the final residual (always FP64) checked by the oracle."""
+    c = capi()
+    mesh = synth.config_small() if geometry == "dome" else synth.marine_mesh(12, 5, 45, 46)
+    om = oracle.OracleMesh(mesh)
+    dm = c.DeviceMesh(mesh)
+    sols, steps = [], []
+    for v32 in (0.0, 1e-3):
+        U = torch.empty(dm.ndof, dtype=torch.float64, device="cuda")
+        c.bp_initial_guess(dm.handle, c.BP_GUESS_SIA, U)
+        rc, rep = c.bp_newton_solve(dm.handle, U, precision=c.BP_F32, value32_rtol=v32)
+        assert rc == c.BP_OK, rep
+        Uh = U.cpu().numpy()
+        assert np.linalg.norm(om.residual(Uh)) <= 1.1e-8 * np.linalg.norm(om.residual(np.zeros_like(Uh)))
+        sols.append(Uh)
+        steps.append(rep["value32_steps"])
+    assert steps[0] == 0 and steps[1] >= 1
+    assert rel_inf(sols[0], sols[1]) <= 1e-6
+    with pytest.raises(c.BPError):
+        c.bp_newton_solve(dm.handle, U, precision=c.BP_F32, value32_rtol=-1.0)
