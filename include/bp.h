@@ -192,9 +192,9 @@ int bp_spmv(bp_mesh* mesh, const void* J_vals_dev, int precision, const double* 
  * couples the (L + 1) levels of its column (2 x 2 blocks) is factorised by block Thomas elimination
  * without pivoting (J is symmetric positive definite), one thread per column -- the per-vertical-line
  * batched LU of the paper's semicoarsening prolongation (Sec. 4.4).  bp_colprec_setup factorises
- * in FP64 arithmetic and keeps the factors in the mesh: FP64 factors for a BP_F64 Jacobian, FP32
- * factors for a BP_F32 Jacobian (the mixed-precision Krylov path), which bp_colprec_apply then
- * applies in FP32 arithmetic.  bp_colprec_apply computes z = P^-1 r.  Asynchronous.
+ * and keeps the factors in the mesh: FP64 arithmetic and factors for a BP_F64 Jacobian, FP32
+ * arithmetic and factors for a BP_F32 (or BP_F32_ALL) Jacobian (the mixed-precision Krylov path),
+ * which bp_colprec_apply then applies in FP32 arithmetic.  bp_colprec_apply computes z = P^-1 r.  Asynchronous.
  * Errors: BP_EINVAL, BP_ENOMEM (workspace), BP_ECUDA.
  */
 int bp_colprec_setup(bp_mesh* mesh, const void* J_vals_dev, int precision, void* stream);

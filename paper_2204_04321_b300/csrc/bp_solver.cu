@@ -167,8 +167,9 @@ __device__ __forceinline__ int64_t col_entry(int64_t vs, int dg, int ds, int l, 
   return vs + (int64_t)dg * (4 * bp_levels_before(l) + 2 * c * nl) + 2 * (ds * nl + lp - lmin) + cp;
 }
 
-// Block Thomas elimination of the column's block-tridiagonal part of J (2 x 2 blocks, FP64 arithmetic,
-// factors stored as F):
+// Block Thomas elimination of the column's block-tridiagonal part of J (2 x 2 blocks; arithmetic and
+// factors in F: FP64 for the FP64 path, FP32 for the mixed-precision path, whose factors are FP32
+// anyway and whose elimination would otherwise run on the narrow FP64 pipe, divisions included):
 //   G_0 = D_0,  Lm_l = E_l G_{l-1}^-1,  G_l = D_l - Lm_l F_{l-1},  store Lm_l, G_l^-1, F_l.
 template <class M, class F>
 __global__ void __launch_bounds__(128) k_colprec_setup(const M* __restrict__ J, const int64_t* __restrict__ vstart,
@@ -180,16 +181,17 @@ __global__ void __launch_bounds__(128) k_colprec_setup(const M* __restrict__ J, 
   if (a >= nv) return;
   const int64_t vs = vstart[a];
   const int dg = vdeg[a], ds = dslot[a];
-  auto at = [&](int l, int c, int lp, int cp) -> double {
-    return (double)J[col_entry(vs, dg, ds, l, c, lp, cp, L)];
+  using A = F;  // arithmetic type
+  auto at = [&](int l, int c, int lp, int cp) -> A {
+    return (A)J[col_entry(vs, dg, ds, l, c, lp, cp, L)];
   };
-  double Gp[4] = {0, 0, 0, 0}, Fp[4] = {0, 0, 0, 0};
+  A Gp[4] = {0, 0, 0, 0}, Fp[4] = {0, 0, 0, 0};
   for (int l = 0; l <= L; ++l) {
-    double G[4] = {at(l, 0, l, 0), at(l, 0, l, 1), at(l, 1, l, 0), at(l, 1, l, 1)};
+    A G[4] = {at(l, 0, l, 0), at(l, 0, l, 1), at(l, 1, l, 0), at(l, 1, l, 1)};
     if (l > 0) {
-      const double E[4] = {at(l, 0, l - 1, 0), at(l, 0, l - 1, 1), at(l, 1, l - 1, 0), at(l, 1, l - 1, 1)};
-      const double Lmat[4] = {E[0] * Gp[0] + E[1] * Gp[2], E[0] * Gp[1] + E[1] * Gp[3],
-                              E[2] * Gp[0] + E[3] * Gp[2], E[2] * Gp[1] + E[3] * Gp[3]};
+      const A E[4] = {at(l, 0, l - 1, 0), at(l, 0, l - 1, 1), at(l, 1, l - 1, 0), at(l, 1, l - 1, 1)};
+      const A Lmat[4] = {E[0] * Gp[0] + E[1] * Gp[2], E[0] * Gp[1] + E[1] * Gp[3],
+                         E[2] * Gp[0] + E[3] * Gp[2], E[2] * Gp[1] + E[3] * Gp[3]};
       G[0] -= Lmat[0] * Fp[0] + Lmat[1] * Fp[2];
       G[1] -= Lmat[0] * Fp[1] + Lmat[1] * Fp[3];
       G[2] -= Lmat[2] * Fp[0] + Lmat[3] * Fp[2];
@@ -197,7 +199,7 @@ __global__ void __launch_bounds__(128) k_colprec_setup(const M* __restrict__ J, 
 #pragma unroll
       for (int e = 0; e < 4; ++e) Lm[((int64_t)(l - 1) * 4 + e) * nv + a] = (F)Lmat[e];
     }
-    const double idet = 1.0 / (G[0] * G[3] - G[1] * G[2]);
+    const A idet = A(1) / (G[0] * G[3] - G[1] * G[2]);
     Gp[0] = G[3] * idet;
     Gp[1] = -G[1] * idet;
     Gp[2] = -G[2] * idet;
@@ -350,42 +352,19 @@ __global__ void __launch_bounds__(UPD_NT) k_cg_update_staged(const Prec<F> P, co
   block_add(rr, scal + 3 * (k + 1) + 2);
 }
 
-// The same step for FP32 vectors and factors when the column has NLEV = L + 1 levels known at compile
-// time: one warp per 32 consecutive columns and every lane solves one column.  Each lane first loads its
+// FP32 columns with NLEV = L + 1 levels known at compile time (the CG step and its start below):
+// one warp per 32 consecutive columns, every lane solves one column.  Each lane first loads its
 // column's factors (NLEV - 1 lower, NLEV - 1 upper and NLEV inverse diagonal 2 x 2 blocks) into
 // registers, so that the loads are all in flight together and the substitution does no global load
-// (the staged kernel's single solving warp waits on one factor load after another).  The warp then runs
-// x += alpha p, r -= alpha q over its columns' contiguous range, stages r in shared memory (column
-// stride padded to an odd count against bank conflicts), each lane solves its column in place, and z
-// is written back coalesced.
+// (a single solving warp per block would wait on one factor load after another).  The warp's columns
+// are one contiguous range of the dof-ordered vectors: the element-wise work runs coalesced, r is
+// staged in shared memory (column stride padded to an odd count against bank conflicts), each lane
+// solves its column in place, and z is written back coalesced.
 template <int NLEV>
-__global__ void __launch_bounds__(UPD_NT) k_cg_update_cols(const Prec<float> P, const int* kbase, int j,
-                                                           float* __restrict__ x, float* __restrict__ r,
-                                                           float* __restrict__ z, const float* __restrict__ p,
-                                                           const float* __restrict__ q, double* scal, int* stop) {
-  constexpr int N = 2 * NLEV;     // values per column
-  constexpr int SN = N | 1;       // shared-memory stride per column
-  __shared__ float sbuf[UPD_NT / 32][32 * SN];
-  __shared__ float s_alpha;
-  __shared__ int s_bad;
-  if (*stop) return;
-  const int k = *kbase + j;
-  if (threadIdx.x == 0) {
-    const double pq = scal[3 * k], rzk = scal[3 * k + 1];
-    s_bad = !(pq > 0.0) || !isfinite(rzk);
-    s_alpha = s_bad ? 0.f : (float)(rzk / pq);
-    if (s_bad && blockIdx.x == 0) *stop = 2;
-  }
-  __syncthreads();
-  if (s_bad) return;
-  const float alpha = s_alpha;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int nv = P.nv;
-  const int a0 = (blockIdx.x * (UPD_NT / 32) + warp) * 32;
-  const int a = a0 + lane;
-  const bool own = a < nv;
+struct ColFactors {
   float Lf[NLEV - 1][4], Uf[NLEV - 1][4], Gf[NLEV][4];
-  if (own) {
+  __device__ __forceinline__ void load(const Prec<float>& P, int a) {
+    const int nv = P.nv;
 #pragma unroll
     for (int l = 0; l < NLEV; ++l)
 #pragma unroll
@@ -398,22 +377,9 @@ __global__ void __launch_bounds__(UPD_NT) k_cg_update_cols(const Prec<float> P, 
         }
       }
   }
-  float* sr = sbuf[warp];
-  const int ncol = min(32, nv - a0);  // <= 0 for a warp past the last column
-  const int64_t base = (int64_t)a0 * N;
-  float rr = 0.f;
-  for (int i = lane; i < ncol * N; i += 32) {
-    const float xv = x[base + i] + alpha * p[base + i];
-    const float rv = r[base + i] - alpha * q[base + i];
-    x[base + i] = xv;
-    r[base + i] = rv;
-    sr[(i / N) * SN + i % N] = rv;
-    rr += rv * rv;
-  }
-  __syncwarp();
-  double rz = 0.0;
-  if (own) {
-    float* c = sr + lane * SN;
+  // z = P^-1 r for the column at c[0 .. 2 NLEV) (overwritten with z); returns r . z
+  __device__ __forceinline__ float solve(float* c) const {
+    constexpr int N = 2 * NLEV;
     float rv[N];
 #pragma unroll
     for (int i = 0; i < N; ++i) rv[i] = c[i];
@@ -444,12 +410,94 @@ __global__ void __launch_bounds__(UPD_NT) k_cg_update_cols(const Prec<float> P, 
       c[2 * l + 1] = z1;
       srz += rv[2 * l] * z0 + rv[2 * l + 1] * z1;
     }
-    rz = (double)srz;
+    return srz;
   }
+};
+
+// CG step: alpha = r.z / p.Ap, x += alpha p, r -= alpha q, z = P^-1 r, and r.z, r.r of step k + 1.
+template <int NLEV>
+__global__ void __launch_bounds__(UPD_NT) k_cg_update_cols(const Prec<float> P, const int* kbase, int j,
+                                                           float* __restrict__ x, float* __restrict__ r,
+                                                           float* __restrict__ z, const float* __restrict__ p,
+                                                           const float* __restrict__ q, double* scal, int* stop) {
+  constexpr int N = 2 * NLEV;     // values per column
+  constexpr int SN = N | 1;       // shared-memory stride per column
+  __shared__ float sbuf[UPD_NT / 32][32 * SN];
+  __shared__ float s_alpha;
+  __shared__ int s_bad;
+  if (*stop) return;
+  const int k = *kbase + j;
+  if (threadIdx.x == 0) {
+    const double pq = scal[3 * k], rzk = scal[3 * k + 1];
+    s_bad = !(pq > 0.0) || !isfinite(rzk);
+    s_alpha = s_bad ? 0.f : (float)(rzk / pq);
+    if (s_bad && blockIdx.x == 0) *stop = 2;
+  }
+  __syncthreads();
+  if (s_bad) return;
+  const float alpha = s_alpha;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int a0 = (blockIdx.x * (UPD_NT / 32) + warp) * 32;
+  const bool own = a0 + lane < P.nv;
+  ColFactors<NLEV> f;
+  if (own) f.load(P, a0 + lane);
+  float* sr = sbuf[warp];
+  const int ncol = min(32, P.nv - a0);  // <= 0 for a warp past the last column
+  const int64_t base = (int64_t)a0 * N;
+  float rr = 0.f;
+  for (int i = lane; i < ncol * N; i += 32) {
+    const float xv = x[base + i] + alpha * p[base + i];
+    const float rv = r[base + i] - alpha * q[base + i];
+    x[base + i] = xv;
+    r[base + i] = rv;
+    sr[(i / N) * SN + i % N] = rv;
+    rr += rv * rv;
+  }
+  __syncwarp();
+  double rz = 0.0;
+  if (own) rz = (double)f.solve(sr + lane * SN);
   __syncwarp();
   for (int i = lane; i < ncol * N; i += 32) z[base + i] = sr[(i / N) * SN + i % N];
   block_add(rz, scal + 3 * (k + 1) + 1);
   block_add(rr, scal + 3 * (k + 1) + 2);
+}
+
+// CG start: x = 0, r = -R, z = P^-1 r, p = z, and r.z, r.r of step 0.
+template <int NLEV>
+__global__ void __launch_bounds__(UPD_NT) k_cg_init_cols(const Prec<float> P, const double* __restrict__ R,
+                                                         float* __restrict__ x, float* __restrict__ r,
+                                                         float* __restrict__ z, float* __restrict__ p,
+                                                         double* scal) {
+  constexpr int N = 2 * NLEV;
+  constexpr int SN = N | 1;
+  __shared__ float sbuf[UPD_NT / 32][32 * SN];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int a0 = (blockIdx.x * (UPD_NT / 32) + warp) * 32;
+  const bool own = a0 + lane < P.nv;
+  ColFactors<NLEV> f;
+  if (own) f.load(P, a0 + lane);
+  float* sr = sbuf[warp];
+  const int ncol = min(32, P.nv - a0);
+  const int64_t base = (int64_t)a0 * N;
+  float rr = 0.f;
+  for (int i = lane; i < ncol * N; i += 32) {
+    const float rv = -f32_of(R[base + i]);
+    x[base + i] = 0.f;
+    r[base + i] = rv;
+    sr[(i / N) * SN + i % N] = rv;
+    rr += rv * rv;
+  }
+  __syncwarp();
+  double rz = 0.0;
+  if (own) rz = (double)f.solve(sr + lane * SN);
+  __syncwarp();
+  for (int i = lane; i < ncol * N; i += 32) {
+    const float zv = sr[(i / N) * SN + i % N];
+    z[base + i] = zv;
+    p[base + i] = zv;
+  }
+  block_add(rz, scal + 1);
+  block_add(rr, scal + 2);
 }
 
 // beta = r_{k+1}.z_{k+1} / r_k.z_k;  p = z + beta p;  stop once r.r <= eta^2 r_0.r_0 (flag 1) or the
@@ -490,6 +538,19 @@ __global__ void __launch_bounds__(NT) k_cg_direction(const int* kbase, int j, co
 __global__ void k_cg_advance(int* kbase, int batch) { *kbase += batch; }
 
 // ------------------------------------------------------------------ energy
+// FP64 <-> arithmetic type T of the energy change; FP32 converts on the integer pipe (f32_of,
+// f64_of), which leaves the FP64 pipe to the FP64 part of the kernel.
+template <class T>
+__device__ __forceinline__ T to_T(const double x) {
+  return T(x);
+}
+template <>
+__device__ __forceinline__ float to_T<float>(const double x) {
+  return f32_of(x);
+}
+__device__ __forceinline__ double from_T(const double x) { return x; }
+__device__ __forceinline__ double from_T(const float x) { return f64_of(x); }
+
 // Hardness B = A^(-1/3) at the quadrature point (zeta level weights p0, p1 of layer l, triangle point
 // tp): the nodal field interpolated like the velocity, or the uniform value cA.
 __device__ __forceinline__ double hardness_at(const double* __restrict__ Bn, double cA, const int v[3], int L,
@@ -500,6 +561,20 @@ __device__ __forceinline__ double hardness_at(const double* __restrict__ Bn, dou
     const double la = (a == tp) ? 2.0 / 3.0 : 1.0 / 6.0;
     lo += la * Bn[(int64_t)v[a] * (L + 1) + l];
     hi += la * Bn[(int64_t)v[a] * (L + 1) + l + 1];
+  }
+  return p0 * lo + p1 * hi;
+}
+// The same in arithmetic T (FP32 for the mixed-precision energy change: the nodal values are rounded
+// once and interpolated in FP32).
+template <class T>
+__device__ __forceinline__ T hardness_at_t(const double* __restrict__ Bn, T cA, const int v[3], int L, int l, T p0,
+                                           T p1, int tp) {
+  if (!Bn) return cA;
+  T lo = T(0), hi = T(0);
+  for (int a = 0; a < 3; ++a) {
+    const T la = T((a == tp) ? 2.0 / 3.0 : 1.0 / 6.0);
+    lo += la * to_T<T>(Bn[(int64_t)v[a] * (L + 1) + l]);
+    hi += la * to_T<T>(Bn[(int64_t)v[a] * (L + 1) + l + 1]);
   }
   return p0 * lo + p1 * hi;
 }
@@ -605,18 +680,6 @@ __device__ __forceinline__ T eps_bilinear(const T* A, const T* B) {
          T(0.25) * (A[2] * B[2] + A[5] * B[5]);
 }
 
-// FP64 <-> arithmetic type T of the energy change; FP32 converts on the integer pipe (f32_of,
-// f64_of), which leaves the FP64 pipe to the FP64 part of the kernel.
-template <class T>
-__device__ __forceinline__ T to_T(const double x) {
-  return T(x);
-}
-template <>
-__device__ __forceinline__ float to_T<float>(const double x) {
-  return f32_of(x);
-}
-__device__ __forceinline__ double from_T(const double x) { return x; }
-__device__ __forceinline__ double from_T(const float x) { return f64_of(x); }
 
 __device__ __forceinline__ double cube_root(double x) {  // x^(1/3) = x (x^(-1/3))^2
   const double r = inv_cbrt(x);
@@ -684,14 +747,16 @@ __global__ void __launch_bounds__(128) k_energy_change(const double2* __restrict
     }
     // stress term: the column walk of the assembly kernel (level gradients carried from the wedge
     // below, one reciprocal of the thickness per triangle point), per point the exact difference
-    const T ta = (T)alpha, tdelta = (T)delta;
-    T tlx[3], tly[3], invHq[3];
-    double Hq[3];
+    // per column in FP64, rounded once to T; below, everything per level and point runs in T
+    const T ta = to_T<T>(alpha), tdelta = to_T<T>(delta), tcA = to_T<T>(cA);
+    const T tgbx = to_T<T>(gbx), tgby = to_T<T>(gby), tgHx = to_T<T>(gHx), tgHy = to_T<T>(gHy);
+    T tlx[3], tly[3], invHq[3], Hq[3];
     for (int a = 0; a < 3; ++a) {
       tlx[a] = to_T<T>(lx[a]);
       tly[a] = to_T<T>(ly[a]);
-      Hq[a] = Hs6 + 0.5 * H[a];
-      invHq[a] = to_T<T>(1.0 / Hq[a]);
+      const double hq = Hs6 + 0.5 * H[a];
+      Hq[a] = to_T<T>(hq);
+      invHq[a] = to_T<T>(1.0 / hq);
     }
     T u0[3], v0[3], a0[3], b0[3];
     for (int a = 0; a < 3; ++a) {
@@ -723,18 +788,18 @@ __global__ void __launch_bounds__(128) k_energy_change(const double2* __restrict
       grad2(v1, gV1[0], gV1[1]);
       grad2(a1, gA1[0], gA1[1]);
       grad2(b1, gB1[0], gB1[1]);
-      const double s_l = sigma[l], ds = sigma[l + 1] - sigma[l];
-      const T invds = to_T<T>(1.0 / ds);
+      const T s_l = to_T<T>(sigma[l]), ds = to_T<T>(sigma[l + 1] - sigma[l]);
+      const T invds = T(1) / ds;
       const T sixth = T(1.0 / 6.0);
       const T du6 = (u1[0] - u0[0] + u1[1] - u0[1] + u1[2] - u0[2]) * sixth;
       const T dv6 = (v1[0] - v0[0] + v1[1] - v0[1] + v1[2] - v0[2]) * sixth;
       const T da6 = (a1[0] - a0[0] + a1[1] - a0[1] + a1[2] - a0[2]) * sixth;
       const T db6 = (b1[0] - b0[0] + b1[1] - b0[1] + b1[2] - b0[2]) * sixth;
-      double lstress = 0.0;
+      T lstress = T(0);
       for (int z = 0; z < 2; ++z) {
         const T p0 = (T)(z == 0 ? BP_QP_P : BP_QP_Q), p1 = (T)(z == 0 ? BP_QP_Q : BP_QP_P);
-        const double sz = s_l + (z == 0 ? BP_QP_Q : BP_QP_P) * ds;
-        const T Gzx = to_T<T>(gbx + sz * gHx), Gzy = to_T<T>(gby + sz * gHy);
+        const T sz = s_l + T(z == 0 ? BP_QP_Q : BP_QP_P) * ds;
+        const T Gzx = tgbx + sz * tgHx, Gzy = tgby + sz * tgHy;
         const T GUx = p0 * gU0[0] + p1 * gU1[0], GUy = p0 * gU0[1] + p1 * gU1[1];
         const T GVx = p0 * gV0[0] + p1 * gV1[0], GVy = p0 * gV0[1] + p1 * gV1[1];
         const T GAx = p0 * gA0[0] + p1 * gA1[0], GAy = p0 * gA0[1] + p1 * gA1[1];
@@ -752,11 +817,10 @@ __global__ void __launch_bounds__(128) k_energy_change(const double2* __restrict
           const T x1 = x0 + dx;
           const T ca = cube_root(x1), cb = cube_root(x0);
           const T diff23 = dx / (ca * ca + ca * cb + cb * cb) * (ca + cb);
-          lstress += Hq[tp] * hardness_at(Bn, cA, v, L, l, z == 0 ? BP_QP_P : BP_QP_Q, z == 0 ? BP_QP_Q : BP_QP_P, tp) *
-                     from_T(diff23);
+          lstress += Hq[tp] * hardness_at_t<T>(Bn, tcA, v, L, l, p0, p1, tp) * diff23;
         }
       }
-      stress += (d * ds / 12.0) * lstress;
+      stress += (d * (sigma[l + 1] - sigma[l]) / 12.0) * from_T(lstress);
       for (int a = 0; a < 3; ++a) {
         u0[a] = u1[a];
         v0[a] = v1[a];
@@ -954,7 +1018,23 @@ int colprec_setup_t(bp_mesh* m, const M* J, cudaStream_t s) {
 // One CG batch: CG_BATCH iterations (SpMV + dot, update + preconditioner, direction), then the
 // batch counter advances.  The iteration index, the tolerance and the limit are read from device
 // memory, so one captured graph serves every solve on this mesh and precision.
-// FP32 CG with 5 or 10 layers: the register-resident update; returns false where it does not apply.
+// FP32 CG with 5 or 10 layers: the register-resident start and update; false where they do not apply.
+template <class V>
+bool init_cols(const Prec<V>& P, const double* R, V* x, V* r, V* z, V* p, double* scal, int L, cudaStream_t s) {
+  if constexpr (std::is_same<V, float>::value) {
+    const int grid = (P.nv + UPD_NT - 1) / UPD_NT;
+    if (L == 10) {
+      k_cg_init_cols<11><<<grid, UPD_NT, 0, s>>>(P, R, x, r, z, p, scal);
+      return true;
+    }
+    if (L == 5) {
+      k_cg_init_cols<6><<<grid, UPD_NT, 0, s>>>(P, R, x, r, z, p, scal);
+      return true;
+    }
+  }
+  return false;
+}
+
 template <class V>
 bool update_cols(const Prec<V>& P, bp_solver_ws* w, int j, V* x, V* r, V* z, const V* p, const V* q, int L,
                  cudaStream_t s) {
@@ -1044,7 +1124,8 @@ int cg_solve(bp_mesh* m, const M* J, double eta, int maxit, int check_every, cud
   w->hpar[1] = (double)maxit;
   BP_CUDA_TRY(cudaMemcpyAsync(w->cgpar, w->hpar, 2 * sizeof(double), cudaMemcpyHostToDevice, s));
   const int gcol = (m->nv + NT - 1) / NT;
-  k_cg_init<V, V><<<gcol, NT, 0, s>>>(P, w->R, x, r, z, p, w->scal);
+  if (!init_cols<V>(P, w->R, x, r, z, p, w->scal, m->nl, s))
+    k_cg_init<V, V><<<gcol, NT, 0, s>>>(P, w->R, x, r, z, p, w->scal);
   BP_CUDA_TRY(cudaGetLastError());
   const int batches_per_check = std::max(1, (check_every + CG_BATCH - 1) / CG_BATCH);
   int k = 0, done = 0;
