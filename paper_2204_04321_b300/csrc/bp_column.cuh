@@ -65,6 +65,9 @@ __device__ __forceinline__ constexpr double lam(int a, int tp) {  // lambda_a at
 __device__ __forceinline__ constexpr int uidx(int i, int j) {  // upper-triangle index, i <= j < 12
   return i * 12 - (i * (i - 1)) / 2 + (j - i);
 }
+__device__ __forceinline__ constexpr int uidx6(int i, int j) {  // upper-triangle index, i <= j < 6
+  return i * 6 - (i * (i - 1)) / 2 + (j - i);
+}
 
 template <bool ATOMIC, class T>
 __device__ __forceinline__ void scatter_add(T* p, T v) {
@@ -296,13 +299,37 @@ __device__ __forceinline__ void assemble_column(const AsmArgs& A, const int t) {
     hb[2] = to_lane<TV>(bs + 0.5 * b2);
   }
 
+  // FP32 lanes (a narrower value path or lighter registers): the next level's velocities are loaded
+  // one wedge ahead, and the element-matrix block of the top level is carried to the next wedge
+  // (where it is the bottom block of the same J entries) instead of being scattered twice.
+  constexpr bool kAhead = std::is_same<TL, float>::value && MODE == MODE_FACT;
+  double2 nxt[3];
+  TL Kc[21];  // carried top-top block (upper triangle of local dofs 6..11)
+  if constexpr (kAhead) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) nxt[a] = *reinterpret_cast<const double2*>(A.U + ubase[a] + 2);
+#pragma unroll
+    for (int k = 0; k < 21; ++k) Kc[k] = TL(0);
+  }
+
   for (int l = 0; l < L; ++l) {
     double ut[3], vt[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      const double2 w = *reinterpret_cast<const double2*>(A.U + ubase[a] + 2 * (l + 1));
+      double2 w;
+      if constexpr (kAhead) {
+        w = nxt[a];
+      } else {
+        w = *reinterpret_cast<const double2*>(A.U + ubase[a] + 2 * (l + 1));
+      }
       ut[a] = w.x;
       vt[a] = w.y;
+    }
+    if constexpr (kAhead) {
+      if (l + 2 <= L) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) nxt[a] = *reinterpret_cast<const double2*>(A.U + ubase[a] + 2 * (l + 2));
+      }
     }
     const double gutx = ut[0] * lx[0] + ut[1] * lx[1] + ut[2] * lx[2];
     const double guty = ut[0] * ly[0] + ut[1] * ly[1] + ut[2] * ly[2];
@@ -370,6 +397,12 @@ __device__ __forceinline__ void assemble_column(const AsmArgs& A, const int t) {
     if constexpr (MODE != MODE_RES) {
 #pragma unroll
       for (int k = 0; k < 78; ++k) K[k] = TL(0);
+    }
+    if constexpr (kAhead) {  // the previous wedge's top-top block starts this wedge's bottom-bottom block
+#pragma unroll
+      for (int i = 0; i < 6; ++i)
+#pragma unroll
+        for (int j = i; j < 6; ++j) K[uidx(i, j)] = Kc[uidx6(i, j)];
     }
 
     if constexpr (MODE == MODE_DUAL) {
@@ -729,6 +762,12 @@ __device__ __forceinline__ void assemble_column(const AsmArgs& A, const int t) {
 #pragma unroll
         for (int j = i; j < 12; ++j) {
           const int nj = j >> 1, cj = j & 1, kj = nj / 3, bj = nj % 3;
+          if constexpr (kAhead) {
+            if (i >= 6 && l + 1 < L) {  // top-top block: carried to the next wedge
+              Kc[uidx6(i - 6, j - 6)] = K[uidx(i, j)];
+              continue;
+            }
+          }
           const ST val = LaneStore<TL>::cast(K[uidx(i, j)]);
           const int64_t pij = rowbase[ni] + ci * rowhalf[ni] + 2 * (sl[3 * ai + bj] * nlev[ki] + off[ki][kj]) + cj;
           scatter_add<ATOMIC>(J + pij, val);
