@@ -161,6 +161,38 @@ __device__ __forceinline__ TL add_signed(const TL acc, const TL x, const bool ne
   return negative ? acc - x : acc + x;
 }
 
+// Accumulation into the element matrix: K += a b and K +/- x.  With paired-FP32 lanes the accumulator
+// stays unnormalised: hi carries the FP32 sum and lo the exact rounding errors of the additions
+// (TwoSum) plus the low-order parts of the products (TwoProd through fmaf), so each update skips the
+// renormalisation of a full pair addition; the scatter sums hi and lo in FP64.
+template <class TL>
+__device__ __forceinline__ void acc_fma(TL& K, const TL a, const TL b) {
+  K += a * b;
+}
+template <class TL>
+__device__ __forceinline__ void acc_add(TL& K, const TL x, const bool negative) {
+  K = add_signed(K, x, negative);
+}
+template <>
+__device__ __forceinline__ void acc_fma<f64x2>(f64x2& K, const f64x2 a, const f64x2 b) {
+  const float p = a.hi * b.hi;
+  float e = fmaf(a.hi, b.hi, -p);
+  e = fmaf(a.hi, b.lo, e);
+  e = fmaf(a.lo, b.hi, e);
+  const float s = K.hi + p;
+  const float bb = s - K.hi;
+  K.lo += ((K.hi - (s - bb)) + (p - bb)) + e;
+  K.hi = s;
+}
+template <>
+__device__ __forceinline__ void acc_add<f64x2>(f64x2& K, const f64x2 x0, const bool negative) {
+  const f64x2 x = negative ? -x0 : x0;
+  const float s = K.hi + x.hi;
+  const float bb = s - K.hi;
+  K.lo += ((K.hi - (s - bb)) + (x.hi - bb)) + x.lo;
+  K.hi = s;
+}
+
 // ------------------------------------------------------------------ dual numbers
 // Forward-mode dual number with an FP64 value and NL derivative lanes of type TL.
 template <class TL, int NL>
@@ -480,7 +512,7 @@ __device__ __forceinline__ void assemble_column(const AsmArgs& A, const int t) {
               const Dual<TL, 12> ri = eta * pi;
               Rl[n / 3][n % 3][comp] += c * ri.v;
 #pragma unroll
-              for (int j = i; j < 12; ++j) K[uidx(i, j)] += cL * ri.d[j];
+              for (int j = i; j < 12; ++j) acc_fma(K[uidx(i, j)], cL, ri.d[j]);
             }
           }
         }
@@ -548,7 +580,7 @@ __device__ __forceinline__ void assemble_column(const AsmArgs& A, const int t) {
             for (int i = 0; i < 12; ++i) {
               const TL pw = Wp * p[i];
 #pragma unroll
-              for (int j = i; j < 12; ++j) K[uidx(i, j)] += pw * p[j];
+              for (int j = i; j < 12; ++j) acc_fma(K[uidx(i, j)], pw, p[j]);
             }
             }  // !PICARD
           }
@@ -664,7 +696,8 @@ __device__ __forceinline__ void assemble_column(const AsmArgs& A, const int t) {
                 const int i = 2 * n1 + ci, j = 2 * n2 + cj;
                 if (i > j) continue;
                 const int cd = 2 * ci + cj;
-                K[uidx(i, j)] = add_signed(K[uidx(i, j)] + q * BL[cd], Yc[cd], neg);
+                acc_fma(K[uidx(i, j)], q, BL[cd]);
+                acc_add(K[uidx(i, j)], Yc[cd], neg);
               }
           }
         }
@@ -693,7 +726,7 @@ __device__ __forceinline__ void assemble_column(const AsmArgs& A, const int t) {
               for (int cj = 0; cj < 2; ++cj) {
                 const int i = 2 * n + ci, j = 2 * n2 + cj;
                 if (i > j) continue;
-                K[uidx(i, j)] = add_signed(K[uidx(i, j)], BVn[bj][2 * ci + cj], kj == 0);
+                acc_add(K[uidx(i, j)], BVn[bj][2 * ci + cj], kj == 0);
               }
           }
 #pragma unroll
@@ -705,7 +738,7 @@ __device__ __forceinline__ void assemble_column(const AsmArgs& A, const int t) {
               for (int cj = 0; cj < 2; ++cj) {
                 const int i = 2 * n1 + ci, j = 2 * n + cj;
                 if (i > j) continue;
-                K[uidx(i, j)] = add_signed(K[uidx(i, j)], BVn[ai][2 * cj + ci], ki == 0);
+                acc_add(K[uidx(i, j)], BVn[ai][2 * cj + ci], ki == 0);
               }
           }
         }
@@ -727,7 +760,7 @@ __device__ __forceinline__ void assemble_column(const AsmArgs& A, const int t) {
 #pragma unroll
           for (int b = a; b < 3; ++b)
 #pragma unroll
-            for (int c = 0; c < 2; ++c) K[uidx(2 * a + c, 2 * b + c)] += to_lane<TL>(M[a][b]);
+            for (int c = 0; c < 2; ++c) acc_add(K[uidx(2 * a + c, 2 * b + c)], to_lane<TL>(M[a][b]), false);
       }
     }
 
