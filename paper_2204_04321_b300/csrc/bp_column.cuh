@@ -125,6 +125,11 @@ template <>
 __device__ __forceinline__ float to_lane<float>(const double x) {
   return f32_of(x);
 }
+template <>
+__device__ __forceinline__ f64x2 to_lane<f64x2>(const double x) {  // hi + lo, both split on the integer pipe
+  const float h = f32_of(x);
+  return f64x2(h, f32_of(x - f64_of(h)));
+}
 
 // A value-path quantity (type TV) as a lane (type TL): no conversion when the types agree.
 template <class TL, class TV>
@@ -556,10 +561,10 @@ __device__ __forceinline__ void assemble_column(const AsmArgs& A, const int t) {
               tau1 = 2.0f * invhL[tp] * lane_from<float>(t1);
               tau2 = 2.0f * invhL[tp] * lane_from<float>(t2);
             } else {
-              eta_q[z][tp] = (TL)eta;
-              Wp = (TL)(-(1.0 / 3.0) * W * (r * r * r));
-              tau1 = (TL)(2.0 * invh[tp] * t1);
-              tau2 = (TL)(2.0 * invh[tp] * t2);
+              eta_q[z][tp] = to_lane<TL>(eta);
+              Wp = to_lane<TL>(-(1.0 / 3.0) * W * (r * r * r));
+              tau1 = to_lane<TL>(2.0 * invh[tp] * t1);
+              tau2 = to_lane<TL>(2.0 * invh[tp] * t2);
             }
             if constexpr (!PICARD) {
             const TL fg1x = lane_from<TL>(g1x), fexy = lane_from<TL>(exy), fg2y = lane_from<TL>(g2y);
