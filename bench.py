@@ -607,14 +607,15 @@ def newton_section(capi, synth, dm, mesh, dev, skip_large=False, reps=3):
 
 def kernel_hash():
     """Hash of the assembly kernel's source text: the per-column body and the shared device helpers
-    (conversions, inverse cube root, pattern helpers) it calls."""
+    it calls (pattern helpers, conversions, inverse cube root: the tail of the internal header)."""
     import hashlib
     csrc = os.path.join(ROOT, "paper_2204_04321_b300", "csrc")
     with open(os.path.join(csrc, "bp_column.cuh")) as f:
         src = f.read()
     src = src[src.index("constexpr int MODE_RES"):]
     with open(os.path.join(csrc, "bp_internal.cuh")) as f:
-        src += f.read()
+        helpers = f.read()
+    src += helpers[helpers.index("// The kernels read velocity pairs"):]
     return hashlib.sha256(src.encode()).hexdigest()[:16]
 
 

@@ -243,7 +243,8 @@ typedef struct {
                          BP_LS_OFF full steps; BP_LS_HALVING alpha = 1, 1/2, ..., 2^-10;
                          BP_LS_QUADRATIC backtracking by quadratic interpolation of the energy
                          change, each new alpha kept within [0.1, 0.9] of the rejected one */
-  int check_every;    /* Krylov convergence is read back every check_every iterations */
+  int check_every;    /* batch replays (device_loop 0, or no conditional graph nodes): convergence
+                         is read back every check_every iterations */
   double picard_rtol; /* > 0: while ||F|| > picard_rtol ||F(0)|| take Picard steps (the Jacobian
                          without the eta' rank-one part: the fixed-viscosity matrix, SPD, cheaper
                          to assemble), then Newton steps; 0: Newton from the first step */
@@ -251,6 +252,11 @@ typedef struct {
                           BP_F32_ALL (FP32 value path: an inexact residual, rounding ~1e-7 of the
                           element contributions), then with the FP64 value path; convergence is
                           always tested on an FP64 residual.  0: FP64 value path throughout */
+  int device_loop;    /* 1: the CG iterations run as a device-driven loop (a conditional WHILE graph
+                         node, 4 iterations per pass, programmatic launches): the device stops the
+                         loop, no host check in between; 0: replays of a captured 8-iteration batch
+                         with a host check every check_every iterations */
+  int reserved;       /* must be 0 */
 } bp_solve_opts;
 
 typedef struct {
@@ -268,7 +274,7 @@ typedef struct {
 } bp_solve_report;
 
 /* Defaults: rtol 1e-8, 50 Newton, 1000 Krylov, eta_max 0.1, BP_F64, CG, line search on, check 8,
- * picard_rtol 0, value32_rtol 0. */
+ * picard_rtol 0, value32_rtol 0, device_loop 1. */
 void bp_solve_opts_default(bp_solve_opts* opts);
 
 /*

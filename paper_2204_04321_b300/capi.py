@@ -57,7 +57,7 @@ class bp_solve_opts(ctypes.Structure):
     _fields_ = [("rtol", ctypes.c_double), ("max_newton", ctypes.c_int), ("max_krylov", ctypes.c_int),
                 ("eta_max", ctypes.c_double), ("precision", ctypes.c_int), ("krylov", ctypes.c_int),
                 ("line_search", ctypes.c_int), ("check_every", ctypes.c_int), ("picard_rtol", ctypes.c_double),
-                ("value32_rtol", ctypes.c_double)]
+                ("value32_rtol", ctypes.c_double), ("device_loop", ctypes.c_int), ("reserved", ctypes.c_int)]
 
 
 class bp_solve_report(ctypes.Structure):

@@ -49,6 +49,8 @@ struct bp_solver_ws {
   double* cgpar = nullptr;    // CG: [0] tolerance eta^2 on r.r / r0.r0, [1] iteration limit (device)
   double* hpar = nullptr;     // pinned staging of cgpar
   void* cg_exec[2] = {nullptr, nullptr};  // instantiated CG batch graphs (FP64, FP32 Krylov)
+  void* cg_loop[2] = {nullptr, nullptr};  // instantiated device-driven CG loops (conditional WHILE node)
+  bool cg_loop_failed[2] = {false, false};  // the loop graph could not be built: use the batches
 };
 
 struct bp_mesh {

@@ -19,6 +19,14 @@ constexpr int SCAL_CAP = 8192; // Krylov iterations per linear solve (scalar his
 constexpr int GRID_CAP = 148 * 8;  // grid-stride kernels: 8 blocks of NT per SM
 constexpr int UPD_NT = 128;        // threads of the staged CG update (one warp solves the block's columns)
 constexpr int CG_BATCH = 8;        // CG iterations per replay of the captured batch graph
+constexpr int LOOP_BODY = 4;       // CG iterations per pass of the device-driven loop
+
+// Programmatic dependent launch inside the CG loop: each kernel lets the next one be scheduled at
+// once (its blocks then wait on the SM instead of behind the launch latency) and waits for the
+// previous kernel's completion and memory before it touches data the previous kernels produce or
+// still read.  Both instructions do nothing in a launch without the programmatic attribute.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
 // B300 issues FP64 at ~1/64 of the FP32 rate, so the vector kernels keep per-element reductions in
 // the vector type V and spend FP64 operations only on per-warp / per-block partial sums.
@@ -102,6 +110,8 @@ __global__ void __launch_bounds__(NT) k_spmv_pairs(const int64_t* __restrict__ r
                                                    const int* kbase, int j) {
   using M2 = typename Pair<M>::type;
   using V2 = typename Pair<V>::type;
+  pdl_trigger();
+  pdl_wait();
   if (stop && *stop) return;
   if (DOT && kbase) dot += 3 * (*kbase + j);  // CG iteration k = kbase + j writes scal[3k]
   const int lane = threadIdx.x % TPR;
@@ -313,6 +323,8 @@ __global__ void __launch_bounds__(UPD_NT) k_cg_update_staged(const Prec<F> P, co
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ V s_alpha;
   __shared__ int s_bad;
+  pdl_trigger();
+  pdl_wait();
   if (*stop) return;
   const int k = *kbase + j;
   if (threadIdx.x == 0) {
@@ -425,6 +437,13 @@ __global__ void __launch_bounds__(UPD_NT) k_cg_update_cols(const Prec<float> P, 
   __shared__ float sbuf[UPD_NT / 32][32 * SN];
   __shared__ float s_alpha;
   __shared__ int s_bad;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int a0 = (blockIdx.x * (UPD_NT / 32) + warp) * 32;
+  const bool own = a0 + lane < P.nv;
+  pdl_trigger();
+  ColFactors<NLEV> f;  // the factors do not depend on the previous kernels: load them before waiting
+  if (own) f.load(P, a0 + lane);
+  pdl_wait();
   if (*stop) return;
   const int k = *kbase + j;
   if (threadIdx.x == 0) {
@@ -436,11 +455,6 @@ __global__ void __launch_bounds__(UPD_NT) k_cg_update_cols(const Prec<float> P, 
   __syncthreads();
   if (s_bad) return;
   const float alpha = s_alpha;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int a0 = (blockIdx.x * (UPD_NT / 32) + warp) * 32;
-  const bool own = a0 + lane < P.nv;
-  ColFactors<NLEV> f;
-  if (own) f.load(P, a0 + lane);
   float* sr = sbuf[warp];
   const int ncol = min(32, P.nv - a0);  // <= 0 for a warp past the last column
   const int64_t base = (int64_t)a0 * N;
@@ -503,22 +517,31 @@ __global__ void __launch_bounds__(UPD_NT) k_cg_init_cols(const Prec<float> P, co
 // beta = r_{k+1}.z_{k+1} / r_k.z_k;  p = z + beta p;  stop once r.r <= eta^2 r_0.r_0 (flag 1) or the
 // iteration limit is reached (flag 4).  The scalars are formed once per block; the update runs on
 // (u, v) pairs.
+// Inside the device-driven loop (set_loop != 0) the first thread of block 0 also sets the loop's
+// condition on every path: 1 only when no stop flag is up after this iteration, so the loop ends at
+// convergence, at the iteration limit, or after a breakdown flagged by the update.
 template <class V>
 __global__ void __launch_bounds__(NT) k_cg_direction(const int* kbase, int j, const double* cgpar, int64_t npairs,
                                                      const V* __restrict__ z, V* __restrict__ p, const double* scal,
-                                                     int* stop) {
+                                                     int* stop, cudaGraphConditionalHandle loop, int set_loop) {
   using V2 = typename Pair<V>::type;
   __shared__ V s_beta;
   __shared__ int s_done;
-  if (*stop) return;
+  pdl_trigger();
+  pdl_wait();
   if (threadIdx.x == 0) {
-    const int k = *kbase + j;
-    const double rr = scal[3 * (k + 1) + 2];
-    const bool conv = rr <= cgpar[0] * scal[2] || !isfinite(rr);
-    const bool limit = (double)(k + 1) >= cgpar[1];
-    s_done = conv || limit;
-    s_beta = (V)(scal[3 * (k + 1) + 1] / scal[3 * k + 1]);
-    if (s_done && blockIdx.x == 0) *stop = conv ? 1 : 4;
+    int done = *stop != 0;
+    if (!done) {
+      const int k = *kbase + j;
+      const double rr = scal[3 * (k + 1) + 2];
+      const bool conv = rr <= cgpar[0] * scal[2] || !isfinite(rr);
+      const bool limit = (double)(k + 1) >= cgpar[1];
+      done = conv || limit;
+      s_beta = (V)(scal[3 * (k + 1) + 1] / scal[3 * k + 1]);
+      if (done && blockIdx.x == 0) *stop = conv ? 1 : 4;
+    }
+    s_done = done;
+    if (set_loop && blockIdx.x == 0) cudaGraphSetConditional(loop, done ? 0u : 1u);
   }
   __syncthreads();
   if (s_done) return;
@@ -535,7 +558,10 @@ __global__ void __launch_bounds__(NT) k_cg_direction(const int* kbase, int j, co
 }
 
 // end of a CG batch: the next batch starts BATCH iterations later
-__global__ void k_cg_advance(int* kbase, int batch) { *kbase += batch; }
+__global__ void k_cg_advance(int* kbase, int batch) {
+  pdl_wait();
+  *kbase += batch;
+}
 
 // ------------------------------------------------------------------ energy
 // FP64 <-> arithmetic type T of the energy change; FP32 converts on the integer pipe (f32_of,
@@ -1018,6 +1044,22 @@ int colprec_setup_t(bp_mesh* m, const M* J, cudaStream_t s) {
 // One CG batch: CG_BATCH iterations (SpMV + dot, update + preconditioner, direction), then the
 // batch counter advances.  The iteration index, the tolerance and the limit are read from device
 // memory, so one captured graph serves every solve on this mesh and precision.
+// Launch with the programmatic-stream-serialisation attribute (captured as a programmatic edge).
+template <class... Args, class... Act>
+void launch_pdl(void (*kern)(Args...), int grid, int block, size_t smem, cudaStream_t s, Act... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 // FP32 CG with 5 or 10 layers: the register-resident start and update; false where they do not apply.
 template <class V>
 bool init_cols(const Prec<V>& P, const double* R, V* x, V* r, V* z, V* p, double* scal, int L, cudaStream_t s) {
@@ -1037,15 +1079,15 @@ bool init_cols(const Prec<V>& P, const double* R, V* x, V* r, V* z, V* p, double
 
 template <class V>
 bool update_cols(const Prec<V>& P, bp_solver_ws* w, int j, V* x, V* r, V* z, const V* p, const V* q, int L,
-                 cudaStream_t s) {
+                 cudaStream_t s, bool pdl = false) {
   if constexpr (std::is_same<V, float>::value) {
     const int grid = (P.nv + UPD_NT - 1) / UPD_NT;
-    if (L == 10) {
-      k_cg_update_cols<11><<<grid, UPD_NT, 0, s>>>(P, w->kbase, j, x, r, z, p, q, w->scal, w->stop);
-      return true;
-    }
-    if (L == 5) {
-      k_cg_update_cols<6><<<grid, UPD_NT, 0, s>>>(P, w->kbase, j, x, r, z, p, q, w->scal, w->stop);
+    if (L == 10 || L == 5) {
+      auto kern = L == 10 ? k_cg_update_cols<11> : k_cg_update_cols<6>;
+      if (pdl)
+        launch_pdl(kern, grid, UPD_NT, 0, s, P, (const int*)w->kbase, j, x, r, z, p, q, w->scal, w->stop);
+      else
+        kern<<<grid, UPD_NT, 0, s>>>(P, w->kbase, j, x, r, z, p, q, w->scal, w->stop);
       return true;
     }
   }
@@ -1072,9 +1114,89 @@ void launch_cg_batch(bp_mesh* m, const M* J, cudaStream_t s) {
                                                   w->scal, w->stop, w->kbase, j);
     if (!update_cols<V>(P, w, j, x, r, z, p, q, m->nl, s))
       k_cg_update_staged<V, V><<<gupd, UPD_NT, smem, s>>>(P, w->kbase, j, C, x, r, z, p, q, w->scal, w->stop);
-    k_cg_direction<V><<<grid_for(n / 2, NT), NT, 0, s>>>(w->kbase, j, w->cgpar, n / 2, z, p, w->scal, w->stop);
+    k_cg_direction<V><<<grid_for(n / 2, NT), NT, 0, s>>>(w->kbase, j, w->cgpar, n / 2, z, p, w->scal, w->stop,
+                                                         cudaGraphConditionalHandle{}, 0);
   }
   k_cg_advance<<<1, 1, 0, s>>>(w->kbase, CG_BATCH);
+}
+
+// LOOP_BODY CG iterations as the body of the device-driven loop: per iteration SpMV + dot, update +
+// preconditioner, direction (which sets the loop condition); then the iteration counter advances.
+// Launches after the stopping iteration exit at once.
+template <class M, class V>
+void launch_cg_iteration(bp_mesh* m, const M* J, cudaStream_t s, cudaGraphConditionalHandle loop) {
+  bp_solver_ws* w = m->ws;
+  const Prec<V> P = prec_of<V>(m);
+  const int64_t n = m->ndof;
+  V* x = reinterpret_cast<V*>(w->x);
+  V* r = reinterpret_cast<V*>(w->r);
+  V* z = reinterpret_cast<V*>(w->z);
+  V* p = reinterpret_cast<V*>(w->p);
+  V* q = reinterpret_cast<V*>(w->q);
+  const int gspmv = grid_for(n / 2 * TPR, NT);
+  const int ncolv = 2 * (m->nl + 1);
+  const int C = std::max(1, std::min(32, (int)((48 << 10) / (2 * ncolv * (int)sizeof(V)))));
+  const size_t smem = 2 * (size_t)C * ncolv * sizeof(V);
+  const int gupd = (m->nv + C - 1) / C;
+  for (int j = 0; j < LOOP_BODY; ++j) {
+    launch_pdl(k_spmv_pairs<M, V, true>, gspmv, NT, 0, s, m->rowptr, m->nbr_ptr, m->nbr_idx, m->nl, J, (int)(n / 2),
+               (const V*)p, q, w->scal, (const int*)w->stop, (const int*)w->kbase, j);
+    if (!update_cols<V>(P, w, j, x, r, z, p, q, m->nl, s, true))
+      launch_pdl(k_cg_update_staged<V, V>, gupd, UPD_NT, smem, s, P, (const int*)w->kbase, j, C, x, r, z, (const V*)p,
+                 (const V*)q, w->scal, w->stop);
+    launch_pdl(k_cg_direction<V>, grid_for(n / 2, NT), NT, 0, s, (const int*)w->kbase, j, (const double*)w->cgpar,
+               (int64_t)(n / 2), (const V*)z, p, (const double*)w->scal, w->stop, loop, 1);
+  }
+  launch_pdl(k_cg_advance, 1, 1, 0, s, w->kbase, LOOP_BODY);
+}
+
+// The whole CG iteration loop as one graph: a conditional WHILE node whose body is one iteration
+// (captured once per mesh and precision).  The device decides when to stop, so a solve needs no host
+// check between iterations and launches no iteration past the last.  Returns exec = NULL (and the
+// caller replays batches instead) where conditional nodes are not available.
+template <class M, class V>
+int cg_loop_graph(bp_mesh* m, const M* J, cudaGraphExec_t* out) {
+  bp_solver_ws* w = m->ws;
+  const int slot = sizeof(V) == sizeof(float) ? 1 : 0;
+  *out = nullptr;
+  if (w->cg_loop_failed[slot]) return BP_OK;
+  if (!w->cg_loop[slot]) {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t cs = nullptr;
+    cudaGraphConditionalHandle h{};
+    cudaGraphNodeParams cp{};
+    cudaGraphNode_t node = nullptr;
+    cudaError_t e = cudaGraphCreate(&graph, 0);
+    if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault);
+    if (e == cudaSuccess) {
+      cp.type = cudaGraphNodeTypeConditional;
+      cp.conditional.handle = h;
+      cp.conditional.type = cudaGraphCondTypeWhile;
+      cp.conditional.size = 1;
+      e = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp);
+    }
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e == cudaSuccess)
+      e = cudaStreamBeginCaptureToGraph(cs, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                        cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      launch_cg_iteration<M, V>(m, J, cs, h);
+      cudaGraph_t body = nullptr;
+      e = cudaStreamEndCapture(cs, &body);
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+    if (cs) cudaStreamDestroy(cs);
+    if (graph) cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      cudaGetLastError();  // not sticky: fall back to the batch graphs
+      w->cg_loop_failed[slot] = true;
+      return BP_OK;
+    }
+    w->cg_loop[slot] = exec;
+  }
+  *out = (cudaGraphExec_t)w->cg_loop[slot];
+  return BP_OK;
 }
 
 template <class M, class V>
@@ -1104,8 +1226,8 @@ int cg_batch_graph(bp_mesh* m, const M* J, cudaGraphExec_t* out) {
 // The iterations run as replays of the captured batch graph; the host reads the device stop flag
 // every check_every iterations (rounded up to whole batches).
 template <class M, class V>
-int cg_solve(bp_mesh* m, const M* J, double eta, int maxit, int check_every, cudaStream_t s, int* iters,
-             int* status) {
+int cg_solve(bp_mesh* m, const M* J, double eta, int maxit, int check_every, bool device_loop, cudaStream_t s,
+             int* iters, int* status) {
   bp_solver_ws* w = m->ws;
   const Prec<V> P = prec_of<V>(m);  // factors set up from the same-precision Jacobian
   maxit = std::min(maxit, w->scal_cap);
@@ -1113,9 +1235,10 @@ int cg_solve(bp_mesh* m, const M* J, double eta, int maxit, int check_every, cud
   V* r = reinterpret_cast<V*>(w->r);
   V* z = reinterpret_cast<V*>(w->z);
   V* p = reinterpret_cast<V*>(w->p);
-  cudaGraphExec_t exec;
-  int rc = cg_batch_graph<M, V>(m, J, &exec);
+  cudaGraphExec_t loop = nullptr, exec = nullptr;
+  int rc = device_loop ? cg_loop_graph<M, V>(m, J, &loop) : BP_OK;
   if (rc) return rc;
+  if (!loop && (rc = cg_batch_graph<M, V>(m, J, &exec))) return rc;
   BP_CUDA_TRY(cudaMemsetAsync(w->scal, 0, 3 * (size_t)(maxit + 2 + CG_BATCH) * sizeof(double), s));
   BP_CUDA_TRY(cudaMemsetAsync(w->stop, 0, sizeof(int), s));
   BP_CUDA_TRY(cudaMemsetAsync(w->kbase, 0, sizeof(int), s));
@@ -1130,6 +1253,20 @@ int cg_solve(bp_mesh* m, const M* J, double eta, int maxit, int check_every, cud
   const int batches_per_check = std::max(1, (check_every + CG_BATCH - 1) / CG_BATCH);
   int k = 0, done = 0;
   *status = 0;
+  if (loop) {  // one launch runs the whole solve; then read the iteration count and the history
+    BP_CUDA_TRY(cudaGraphLaunch(loop, s));
+    int* hk = reinterpret_cast<int*>(w->host + w->host_cap - 2);
+    BP_CUDA_TRY(cudaMemcpyAsync(hk, w->kbase, sizeof(int), cudaMemcpyDeviceToHost, s));
+    BP_CUDA_TRY(cudaMemcpyAsync(w->host + w->host_cap - 1, w->stop, sizeof(int), cudaMemcpyDeviceToHost, s));
+    BP_CUDA_TRY(cudaStreamSynchronize(s));
+    k = std::min(std::max(*hk, 0), maxit);
+    BP_CUDA_TRY(cudaMemcpyAsync(w->host, w->scal, 3 * (size_t)(k + 2) * sizeof(double), cudaMemcpyDeviceToHost, s));
+    BP_CUDA_TRY(cudaStreamSynchronize(s));
+    int stopflag;
+    std::memcpy(&stopflag, w->host + w->host_cap - 1, sizeof(int));
+    if (stopflag == 2) *status = 2;
+    done = 1;
+  }
   while (!done) {
     for (int b = 0; b < batches_per_check && k < maxit; ++b, k += CG_BATCH) BP_CUDA_TRY(cudaGraphLaunch(exec, s));
     const int kk = std::min(k, maxit);
@@ -1175,6 +1312,8 @@ void bp_solver_ws_free(bp_mesh* m) {
   if (m->ws->host) cudaFreeHost(m->ws->host);
   if (m->ws->hpar) cudaFreeHost(m->ws->hpar);
   for (void* g : m->ws->cg_exec)
+    if (g) cudaGraphExecDestroy((cudaGraphExec_t)g);
+  for (void* g : m->ws->cg_loop)
     if (g) cudaGraphExecDestroy((cudaGraphExec_t)g);
   delete m->ws;  // device arrays are in m->allocations
   m->ws = nullptr;
@@ -1308,6 +1447,8 @@ extern "C" void bp_solve_opts_default(bp_solve_opts* o) {
   o->check_every = 8;
   o->picard_rtol = 0.0;
   o->value32_rtol = 0.0;
+  o->device_loop = 1;
+  o->reserved = 0;
 }
 
 extern "C" int bp_newton_solve(bp_mesh* m, double* U, const bp_solve_opts* opts, bp_solve_report* rep,
@@ -1316,6 +1457,7 @@ extern "C" int bp_newton_solve(bp_mesh* m, double* U, const bp_solve_opts* opts,
   const bp_solve_opts o = *opts;
   if (o.line_search < 0 || o.line_search > BP_LS_QUADRATIC) return BP_EINVAL;
   if (!(o.picard_rtol >= 0) || !(o.value32_rtol >= 0)) return BP_EINVAL;
+  if ((o.device_loop != 0 && o.device_loop != 1) || o.reserved != 0) return BP_EINVAL;
   if (!(o.rtol > 0) || o.max_newton < 0 || o.max_newton > 64 || o.max_krylov < 1 || o.check_every < 1 ||
       (o.precision != BP_F64 && o.precision != BP_F32) || o.krylov != BP_KRYLOV_CG || !(o.eta_max > 0))
     return BP_EINVAL;
@@ -1401,10 +1543,10 @@ extern "C" int bp_newton_solve(bp_mesh* m, double* U, const bp_solve_opts* opts,
     BP_CUDA_TRY(cudaEventRecord(ev[4], s));
     int its = 0, kst = 0;
     if (f32)
-      rc = cg_solve<float, float>(m, reinterpret_cast<const float*>(w->J), eta, o.max_krylov, o.check_every, s,
-                                  &its, &kst);
+      rc = cg_solve<float, float>(m, reinterpret_cast<const float*>(w->J), eta, o.max_krylov, o.check_every,
+                                  o.device_loop != 0, s, &its, &kst);
     else
-      rc = cg_solve<double, double>(m, w->J, eta, o.max_krylov, o.check_every, s, &its, &kst);
+      rc = cg_solve<double, double>(m, w->J, eta, o.max_krylov, o.check_every, o.device_loop != 0, s, &its, &kst);
     if (rc) return rc;
     BP_CUDA_TRY(cudaEventRecord(ev[5], s));
     BP_CUDA_TRY(cudaEventSynchronize(ev[5]));

@@ -255,3 +255,29 @@ def test_fp32_value_path_steps_then_fp64_reach_the_same_solution(geometry):
     assert rel_inf(sols[0], sols[1]) <= 1e-6
     with pytest.raises(c.BPError):
         c.bp_newton_solve(dm.handle, U, precision=c.BP_F32, value32_rtol=-1.0)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("layers", [3, 5])
+def test_device_driven_cg_loop_matches_host_checked_batches(precision, layers):
+    """The CG iterations as a conditional-graph loop stopped by the device, against replays of the
+    captured batch checked by the host: the same iterations, the same Newton path and solution
+    (5 layers take the register-resident column update, 3 the staged one)."""
+    c = capi()
+    mesh = synth.dome_mesh(16, layers, 81, 82, bed="sinusoidal", beta="field")
+    dm = c.DeviceMesh(mesh)
+    out = []
+    for loop in (1, 0):
+        U = torch.empty(dm.ndof, dtype=torch.float64, device="cuda")
+        c.bp_initial_guess(dm.handle, c.BP_GUESS_SIA, U)
+        rc, rep = c.bp_newton_solve(dm.handle, U, precision=precision, device_loop=loop)
+        assert rc == c.BP_OK, rep
+        out.append((U.cpu().numpy(), rep))
+    (U1, r1), (U0, r0) = out
+    assert r1["krylov_per_newton"] == r0["krylov_per_newton"]
+    assert r1["newton_iters"] == r0["newton_iters"]
+    # the two runs differ only in the order of the atomic additions of the dot products (as two
+    # runs of either mode do); both stop at 1e-8 relative residual
+    assert rel_inf(U1, U0) <= 1e-9
+    with pytest.raises(c.BPError):
+        c.bp_newton_solve(dm.handle, U, device_loop=2)
