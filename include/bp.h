@@ -201,6 +201,27 @@ int bp_colprec_setup(bp_mesh* mesh, const void* J_vals_dev, int precision, void*
 int bp_colprec_apply(bp_mesh* mesh, const double* r_dev, double* z_dev, void* stream);
 
 /*
+ * Matrix-dependent semicoarsening (MDSC) two-level preconditioner (Sec. 4.4: the vertical-line
+ * prolongation of the paper's multigrid, then a 2D solve of the plane problem), one symmetric cycle:
+ *   P      semicoarsening to the top level: in each column the top value is extended downwards by
+ *          the harmonic extension of the column's block-tridiagonal part T of J (the column rows
+ *          below the top satisfied with zero right-hand side), from T's block-Thomas factors;
+ *   A_c    = P^T J P on the base vertices (2 x 2 blocks over the closed neighbourhoods);
+ *   B_c    8 steps of Chebyshev acceleration of block-Jacobi on A_c over [lam / 30, lam], lam the
+ *          Gershgorin bound of D^-1 A_c (D its diagonal blocks);
+ *   S      = 0.7 T^-1 (the damped vertical-line solve);
+ *   z1 = S r;  z2 = z1 + P B_c P^T (r - J z1);  z = z2 + S (r - J z2)  (symmetric positive definite).
+ * bp_mdsc_setup also sets up the column factors (as bp_colprec_setup) and reads the Gershgorin
+ * bound back (synchronises `stream`); precision as for bp_colprec_setup (FP32 arithmetic for an
+ * FP32 Jacobian).  bp_mdsc_apply computes z = M^-1 r (device arrays of ndof doubles, 16-byte
+ * aligned) with the Jacobian values J_vals_dev that bp_mdsc_setup saw (the cycle multiplies by J);
+ * asynchronous.  Errors: BP_EINVAL (NULL, misaligned, unknown precision, no setup), BP_ENOMEM,
+ * BP_ENAN (non-finite plane operator), BP_ECUDA.
+ */
+int bp_mdsc_setup(bp_mesh* mesh, const void* J_vals_dev, int precision, void* stream);
+int bp_mdsc_apply(bp_mesh* mesh, const void* J_vals_dev, const double* r_dev, double* z_dev, void* stream);
+
+/*
  * Discrete energy Pi_h(U) = sum_q w det J A^(-1/n) 2n/(n+1) (eps_e^2 + delta)^((n+1)/(2n))
  * + sum_i load_i U_i + 1/2 sum_bed U_b^T M_beta U_b, whose gradient is the residual (same
  * quadrature).  Not written in the paper: it follows from Eq. effvisc / effeps and is the merit
@@ -228,6 +249,8 @@ enum { BP_GUESS_ZERO = 0, BP_GUESS_SIA = 1 };
 int bp_initial_guess(bp_mesh* mesh, int kind, double* U_dev, void* stream);
 
 enum { BP_KRYLOV_CG = 0 };
+/* Preconditioner of the Newton solve's CG (bp_solve_opts.preconditioner). */
+enum { BP_PREC_COLUMN = 0, BP_PREC_MDSC = 1 };
 /* Line search of bp_newton_solve (bp_solve_opts.line_search). */
 enum { BP_LS_OFF = 0, BP_LS_HALVING = 1, BP_LS_QUADRATIC = 2 };
 
@@ -256,7 +279,9 @@ typedef struct {
                          node, 4 iterations per pass, programmatic launches): the device stops the
                          loop, no host check in between; 0: replays of a captured 8-iteration batch
                          with a host check every check_every iterations */
-  int reserved;       /* must be 0 */
+  int preconditioner; /* BP_PREC_COLUMN: the vertical-line block solve; BP_PREC_MDSC: the two-level
+                         semicoarsening cycle (bp_mdsc_setup), always iterated by a device-driven
+                         loop where conditional graph nodes exist */
 } bp_solve_opts;
 
 typedef struct {
@@ -274,7 +299,7 @@ typedef struct {
 } bp_solve_report;
 
 /* Defaults: rtol 1e-8, 50 Newton, 1000 Krylov, eta_max 0.1, BP_F64, CG, line search on, check 8,
- * picard_rtol 0, value32_rtol 0, device_loop 1. */
+ * picard_rtol 0, value32_rtol 0, device_loop 1, BP_PREC_COLUMN. */
 void bp_solve_opts_default(bp_solve_opts* opts);
 
 /*

@@ -22,6 +22,7 @@ BP_SCATTER_AUTO, BP_SCATTER_ATOMIC, BP_SCATTER_COLOR = 0, 1, 2
 BP_JAC_AUTO, BP_JAC_DUAL, BP_JAC_FACTORED = 0, 1, 2
 BP_GUESS_ZERO, BP_GUESS_SIA = 0, 1
 BP_KRYLOV_CG = 0
+BP_PREC_COLUMN, BP_PREC_MDSC = 0, 1
 BP_JUDGE_RESIDUAL, BP_JUDGE_ENERGY, BP_JUDGE_NONE = 0, 1, 2
 BP_LS_OFF, BP_LS_HALVING, BP_LS_QUADRATIC = 0, 1, 2
 BP_MARGIN_FREE, BP_MARGIN_OCEAN = 0, 1
@@ -57,7 +58,7 @@ class bp_solve_opts(ctypes.Structure):
     _fields_ = [("rtol", ctypes.c_double), ("max_newton", ctypes.c_int), ("max_krylov", ctypes.c_int),
                 ("eta_max", ctypes.c_double), ("precision", ctypes.c_int), ("krylov", ctypes.c_int),
                 ("line_search", ctypes.c_int), ("check_every", ctypes.c_int), ("picard_rtol", ctypes.c_double),
-                ("value32_rtol", ctypes.c_double), ("device_loop", ctypes.c_int), ("reserved", ctypes.c_int)]
+                ("value32_rtol", ctypes.c_double), ("device_loop", ctypes.c_int), ("preconditioner", ctypes.c_int)]
 
 
 class bp_solve_report(ctypes.Structure):
@@ -94,6 +95,8 @@ SIGNATURES = {
     "bp_spmv": (_I, [_P, _P, _I, _P, _P, _P]),
     "bp_colprec_setup": (_I, [_P, _P, _I, _P]),
     "bp_colprec_apply": (_I, [_P, _P, _P, _P]),
+    "bp_mdsc_setup": (_I, [_P, _P, _I, _P]),
+    "bp_mdsc_apply": (_I, [_P, _P, _P, _P, _P]),
     "bp_energy": (_I, [_P, _P, _P, _P]),
     "bp_energy_change": (_I, [_P, _P, _P, ctypes.c_double, _P, _P]),
     "bp_initial_guess": (_I, [_P, _I, _P, _P]),
@@ -232,6 +235,14 @@ def bp_colprec_setup(handle, J, precision=BP_F64, stream=None) -> None:
 
 def bp_colprec_apply(handle, r, z, stream=None) -> None:
     _check(lib().bp_colprec_apply(handle, _dptr(r), _dptr(z), _stream_ptr(stream)), "bp_colprec_apply")
+
+
+def bp_mdsc_setup(handle, J, precision=BP_F64, stream=None) -> None:
+    _check(lib().bp_mdsc_setup(handle, _dptr(J), precision, _stream_ptr(stream)), "bp_mdsc_setup")
+
+
+def bp_mdsc_apply(handle, J, r, z, stream=None) -> None:
+    _check(lib().bp_mdsc_apply(handle, _dptr(J), _dptr(r), _dptr(z), _stream_ptr(stream)), "bp_mdsc_apply")
 
 
 def bp_energy(handle, U, stream=None) -> float:

@@ -51,6 +51,17 @@ struct bp_solver_ws {
   void* cg_exec[2] = {nullptr, nullptr};  // instantiated CG batch graphs (FP64, FP32 Krylov)
   void* cg_loop[2] = {nullptr, nullptr};  // instantiated device-driven CG loops (conditional WHILE node)
   bool cg_loop_failed[2] = {false, false};  // the loop graph could not be built: use the batches
+  // MDSC two-level preconditioner (allocated on first use); arrays typed like the column factors
+  double* mP = nullptr;     // [L][4][nv] semicoarsening prolongation blocks of levels 0..L-1 (top = I)
+  double* mAc = nullptr;    // [nbr][4] plane operator P^T J P, 2 x 2 blocks on the vertex neighbourhoods
+  double* mDinv = nullptr;  // [nv][4] inverses of its diagonal blocks
+  double* mcheb = nullptr;  // Chebyshev coefficients: [0] 1/theta, then per step (rho' rho, 2 rho' / delta)
+  double* mlam = nullptr;   // Gershgorin bound of D^-1 A_c (device)
+  double *mz1 = nullptr, *mt = nullptr, *ms = nullptr;  // [ndof] fine scratch
+  double *mrc = nullptr, *mec = nullptr, *mrr = nullptr, *md0 = nullptr, *md1 = nullptr;  // [2 nv]
+  int64_t nbr_total = 0;
+  bool has_mdsc = false, mdsc_f32 = false;
+  void* mdsc_loop[2] = {nullptr, nullptr};  // device-driven PCG loops with the MDSC cycle
 };
 
 struct bp_mesh {

@@ -1299,6 +1299,565 @@ int cg_solve(bp_mesh* m, const M* J, double eta, int maxit, int check_every, boo
   return BP_OK;
 }
 
+// ------------------------------------------------------------------ MDSC two-level preconditioner
+// Paper Sec. 4.4: the multigrid preconditioner coarsens the extruded mesh vertically first, with a
+// prolongation built from per-vertical-line solves, and solves the resulting plane problem by a 2D
+// method.  Here, one symmetric two-level cycle:
+//   P: semicoarsening to the top level; in column a, P_a(L) = I and, below, the harmonic extension
+//      of the top value down the column, from the block-Thomas factors of the column part T of J:
+//      P_a(L-1) = -G_{L-1}^-1 F_{L-1},  P_a(l) = -G_l^-1 F_l P_a(l+1);
+//   A_c = P^T J P on the base vertices (2 x 2 blocks over the closed neighbourhoods);
+//   B_c: MDSC_STEPS steps of Chebyshev acceleration of block-Jacobi on A_c over
+//        [lam / MDSC_RATIO, lam], lam the Gershgorin bound of D^-1 A_c;
+//   S = omega T^-1 (the column solve, damped);
+//   z1 = S r;  z2 = z1 + P B_c P^T (r - J z1);  z = z2 + S (r - J z2).
+// Symmetric (S and B_c are), positive definite for omega < 2 / lambda_max(T^-1 J).
+constexpr double MDSC_OMEGA = 0.7;
+constexpr int MDSC_STEPS = 8;
+constexpr double MDSC_RATIO = 30.0;
+
+template <class F>
+__device__ __forceinline__ void load2x2(const F* base, int64_t stride, F* out) {
+#pragma unroll
+  for (int e = 0; e < 4; ++e) out[e] = base[e * stride];
+}
+
+// Prolongation blocks of levels L-1 .. 0, one thread per column.
+template <class F>
+__global__ void __launch_bounds__(128) k_mdsc_prolong(const Prec<F> Pr, F* __restrict__ P) {
+  const int a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= Pr.nv) return;
+  const int64_t nv = Pr.nv;
+  F cur[4] = {F(1), F(0), F(0), F(1)};  // P(L) = I
+  for (int l = Pr.L - 1; l >= 0; --l) {
+    F G[4], Fl[4], t[4];
+    load2x2(Pr.Ginv + (int64_t)l * 4 * nv + a, nv, G);
+    load2x2(Pr.Fu + (int64_t)l * 4 * nv + a, nv, Fl);
+    // t = F_l P(l+1), P(l) = -G_l^-1 t
+    t[0] = Fl[0] * cur[0] + Fl[1] * cur[2];
+    t[1] = Fl[0] * cur[1] + Fl[1] * cur[3];
+    t[2] = Fl[2] * cur[0] + Fl[3] * cur[2];
+    t[3] = Fl[2] * cur[1] + Fl[3] * cur[3];
+    cur[0] = -(G[0] * t[0] + G[1] * t[2]);
+    cur[1] = -(G[0] * t[1] + G[1] * t[3]);
+    cur[2] = -(G[2] * t[0] + G[3] * t[2]);
+    cur[3] = -(G[2] * t[1] + G[3] * t[3]);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) P[((int64_t)l * 4 + e) * nv + a] = cur[e];
+  }
+}
+
+// Plane operator A_c = P^T J P (one thread per base vertex: its row of 2 x 2 blocks), the inverses
+// of its diagonal blocks, and the Gershgorin bound of D^-1 A_c (atomic maximum over the rows).
+template <class M, class F>
+__global__ void __launch_bounds__(128) k_mdsc_plane(const M* __restrict__ J, const int64_t* __restrict__ vstart,
+                                                    const int32_t* __restrict__ vdeg,
+                                                    const int32_t* __restrict__ dslot,
+                                                    const int32_t* __restrict__ nbr_ptr,
+                                                    const int32_t* __restrict__ nbr_idx, const F* __restrict__ P,
+                                                    int nv, int L, F* __restrict__ Ac, F* __restrict__ Dinv,
+                                                    double* lam) {
+  const int a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= nv) return;
+  const int64_t vs = vstart[a];
+  const int dg = vdeg[a], p0 = nbr_ptr[a];
+  auto pblk = [&](int l, int v, F* out) {
+    if (l == L) {
+      out[0] = F(1), out[1] = F(0), out[2] = F(0), out[3] = F(1);
+    } else {
+      load2x2(P + (int64_t)l * 4 * nv + v, nv, out);
+    }
+  };
+  for (int s = 0; s < dg; ++s) {
+    const int b = nbr_idx[p0 + s];
+    F acc[4] = {F(0), F(0), F(0), F(0)};
+    for (int l = 0; l <= L; ++l) {
+      F Pa[4];
+      pblk(l, a, Pa);
+      const int nl = bp_nlev(l, L), lmin = l > 0 ? l - 1 : 0;
+      for (int d = 0; d < nl; ++d) {
+        const int lp = lmin + d;
+        F A[4], Pb[4], t[4];
+#pragma unroll
+        for (int c = 0; c < 2; ++c)
+#pragma unroll
+          for (int cp = 0; cp < 2; ++cp) A[2 * c + cp] = (F)J[col_entry(vs, dg, s, l, c, lp, cp, L)];
+        pblk(lp, b, Pb);
+        // t = A Pb;  acc += Pa^T t
+        t[0] = A[0] * Pb[0] + A[1] * Pb[2];
+        t[1] = A[0] * Pb[1] + A[1] * Pb[3];
+        t[2] = A[2] * Pb[0] + A[3] * Pb[2];
+        t[3] = A[2] * Pb[1] + A[3] * Pb[3];
+        acc[0] += Pa[0] * t[0] + Pa[2] * t[2];
+        acc[1] += Pa[0] * t[1] + Pa[2] * t[3];
+        acc[2] += Pa[1] * t[0] + Pa[3] * t[2];
+        acc[3] += Pa[1] * t[1] + Pa[3] * t[3];
+      }
+    }
+#pragma unroll
+    for (int e = 0; e < 4; ++e) Ac[(int64_t)(p0 + s) * 4 + e] = acc[e];
+  }
+  F D[4], Di[4];
+  load2x2(Ac + (int64_t)(p0 + dslot[a]) * 4, 1, D);
+  const F idet = F(1) / (D[0] * D[3] - D[1] * D[2]);
+  Di[0] = D[3] * idet, Di[1] = -D[1] * idet, Di[2] = -D[2] * idet, Di[3] = D[0] * idet;
+#pragma unroll
+  for (int e = 0; e < 4; ++e) Dinv[(int64_t)a * 4 + e] = Di[e];
+  F s0 = F(0), s1 = F(0);
+  for (int s = 0; s < dg; ++s) {
+    F B[4];
+    load2x2(Ac + (int64_t)(p0 + s) * 4, 1, B);
+    s0 += fabs(Di[0] * B[0] + Di[1] * B[2]) + fabs(Di[0] * B[1] + Di[1] * B[3]);
+    s1 += fabs(Di[2] * B[0] + Di[3] * B[2]) + fabs(Di[2] * B[1] + Di[3] * B[3]);
+  }
+  const double g = (double)(s0 > s1 ? s0 : s1);
+  // non-negative doubles order like their bit patterns
+  atomicMax(reinterpret_cast<unsigned long long*>(lam), (unsigned long long)__double_as_longlong(g));
+}
+
+// out = (base ? base : 0) + omega T^-1 r, one thread per column (sb: scratch for T^-1 r).
+template <class V, class F>
+__global__ void __launch_bounds__(128) k_mdsc_smooth(const Prec<F> Pr, const V* __restrict__ r, V* __restrict__ sb,
+                                                     const V* base, V* out, F omega) {
+  const int a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= Pr.nv) return;
+  const int64_t off = 2LL * a * (Pr.L + 1);
+  double rz, rr;
+  colprec_apply(Pr, a, r, sb, &rz, &rr, off);
+  for (int i = 0; i < 2 * (Pr.L + 1); ++i) {
+    const V v = (V)(omega * (F)sb[off + i]);
+    out[off + i] = base ? base[off + i] + v : v;
+  }
+}
+
+// The same for FP32 columns of NLEV levels: one warp per 32 columns, factors in registers, r staged
+// in shared memory (as in the CG update).
+template <int NLEV>
+__global__ void __launch_bounds__(UPD_NT) k_mdsc_smooth_cols(const Prec<float> Pr, const float* __restrict__ r,
+                                                             const float* base, float* out, float omega) {
+  constexpr int N = 2 * NLEV;
+  constexpr int SN = N | 1;
+  __shared__ float sbuf[UPD_NT / 32][32 * SN];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int a0 = (blockIdx.x * (UPD_NT / 32) + warp) * 32;
+  const bool own = a0 + lane < Pr.nv;
+  ColFactors<NLEV> f;
+  if (own) f.load(Pr, a0 + lane);
+  float* sr = sbuf[warp];
+  const int ncol = min(32, Pr.nv - a0);
+  const int64_t b0 = (int64_t)a0 * N;
+  for (int i = lane; i < ncol * N; i += 32) sr[(i / N) * SN + i % N] = r[b0 + i];
+  __syncwarp();
+  if (own) f.solve(sr + lane * SN);
+  __syncwarp();
+  for (int i = lane; i < ncol * N; i += 32) {
+    const float v = omega * sr[(i / N) * SN + i % N];
+    out[b0 + i] = base ? base[b0 + i] + v : v;
+  }
+}
+
+// out = base + omega T^-1 r with the fastest applicable kernel
+template <class V, class F>
+void mdsc_smooth(const Prec<F>& Pr, const V* r, V* sb, const V* base, V* out, F omega, cudaStream_t s) {
+  if constexpr (std::is_same<V, float>::value && std::is_same<F, float>::value) {
+    const int grid = (Pr.nv + UPD_NT - 1) / UPD_NT;
+    if (Pr.L == 10) {
+      k_mdsc_smooth_cols<11><<<grid, UPD_NT, 0, s>>>(Pr, r, base, out, omega);
+      return;
+    }
+    if (Pr.L == 5) {
+      k_mdsc_smooth_cols<6><<<grid, UPD_NT, 0, s>>>(Pr, r, base, out, omega);
+      return;
+    }
+  }
+  k_mdsc_smooth<V, F><<<(Pr.nv + 127) / 128, 128, 0, s>>>(Pr, r, sb, base, out, omega);
+}
+
+// t = r - t (element-wise)
+template <class V>
+__global__ void __launch_bounds__(NT) k_mdsc_sub(const V* __restrict__ r, V* __restrict__ t, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    t[i] = r[i] - t[i];
+}
+
+// rc = P^T t, one thread per column
+template <class V, class F>
+__global__ void __launch_bounds__(128) k_mdsc_restrict(const F* __restrict__ P, const V* __restrict__ t,
+                                                       F* __restrict__ rc, int nv, int L) {
+  const int a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= nv) return;
+  const int64_t base = 2LL * a * (L + 1);
+  F r0 = (F)t[base + 2 * L], r1 = (F)t[base + 2 * L + 1];
+  for (int l = 0; l < L; ++l) {
+    F Pl[4];
+    load2x2(P + (int64_t)l * 4 * nv + a, nv, Pl);
+    const F v0 = (F)t[base + 2 * l], v1 = (F)t[base + 2 * l + 1];
+    r0 += Pl[0] * v0 + Pl[2] * v1;
+    r1 += Pl[1] * v0 + Pl[3] * v1;
+  }
+  rc[2 * a] = r0;
+  rc[2 * a + 1] = r1;
+}
+
+// z += P ec, one thread per column
+template <class V, class F>
+__global__ void __launch_bounds__(128) k_mdsc_prolong_add(const F* __restrict__ P, const F* __restrict__ ec,
+                                                          V* __restrict__ z, int nv, int L) {
+  const int a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= nv) return;
+  const int64_t base = 2LL * a * (L + 1);
+  const F e0 = ec[2 * a], e1 = ec[2 * a + 1];
+  for (int l = 0; l < L; ++l) {
+    F Pl[4];
+    load2x2(P + (int64_t)l * 4 * nv + a, nv, Pl);
+    z[base + 2 * l] += (V)(Pl[0] * e0 + Pl[1] * e1);
+    z[base + 2 * l + 1] += (V)(Pl[2] * e0 + Pl[3] * e1);
+  }
+  z[base + 2 * L] += (V)e0;
+  z[base + 2 * L + 1] += (V)e1;
+}
+
+// Chebyshev acceleration (Saad, Sec. 12.3) of block-Jacobi on A_c from x = 0:
+//   start  x = 0, r = b, d = D^-1 r / theta;
+//   step   x += d, r -= A_c d, d = rho' rho d + (2 rho' / delta) D^-1 r   (coefficients in cheb).
+template <class F>
+__global__ void __launch_bounds__(NT) k_mdsc_cheb_init(const F* __restrict__ Dinv, const double* __restrict__ cheb,
+                                                       const F* __restrict__ b, F* __restrict__ x, F* __restrict__ r,
+                                                       F* __restrict__ d, int nv) {
+  const int a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= nv) return;
+  const F it = (F)cheb[0];
+  const F b0 = b[2 * a], b1 = b[2 * a + 1];
+  F Di[4];
+  load2x2(Dinv + (int64_t)a * 4, 1, Di);
+  x[2 * a] = F(0);
+  x[2 * a + 1] = F(0);
+  r[2 * a] = b0;
+  r[2 * a + 1] = b1;
+  d[2 * a] = it * (Di[0] * b0 + Di[1] * b1);
+  d[2 * a + 1] = it * (Di[2] * b0 + Di[3] * b1);
+}
+
+template <class F>
+__global__ void __launch_bounds__(NT) k_mdsc_cheb_step(const F* __restrict__ Ac, const F* __restrict__ Dinv,
+                                                       const int32_t* __restrict__ nbr_ptr,
+                                                       const int32_t* __restrict__ nbr_idx,
+                                                       const double* __restrict__ cheb, int k,
+                                                       const F* __restrict__ d, F* __restrict__ dn,
+                                                       F* __restrict__ x, F* __restrict__ r, int nv) {
+  const int a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= nv) return;
+  F q0 = F(0), q1 = F(0);
+  for (int i = nbr_ptr[a]; i < nbr_ptr[a + 1]; ++i) {
+    const int b = nbr_idx[i];
+    F B[4];
+    load2x2(Ac + (int64_t)i * 4, 1, B);
+    const F d0 = d[2 * b], d1 = d[2 * b + 1];
+    q0 += B[0] * d0 + B[1] * d1;
+    q1 += B[2] * d0 + B[3] * d1;
+  }
+  const F da0 = d[2 * a], da1 = d[2 * a + 1];
+  x[2 * a] += da0;
+  x[2 * a + 1] += da1;
+  const F r0 = r[2 * a] - q0, r1 = r[2 * a + 1] - q1;
+  r[2 * a] = r0;
+  r[2 * a + 1] = r1;
+  F Di[4];
+  load2x2(Dinv + (int64_t)a * 4, 1, Di);
+  const F c1 = (F)cheb[1 + 2 * k], c2 = (F)cheb[2 + 2 * k];
+  dn[2 * a] = c1 * da0 + c2 * (Di[0] * r0 + Di[1] * r1);
+  dn[2 * a + 1] = c1 * da1 + c2 * (Di[2] * r0 + Di[3] * r1);
+}
+
+template <class F>
+int mdsc_alloc(bp_mesh* m) {
+  bp_solver_ws* w = m->ws;
+  if (w->mP) return BP_OK;
+  int rc;
+  const int64_t n = m->ndof, nv = m->nv, L = m->nl;
+  w->nbr_total = m->nnz / (4 * (3 * L + 1));  // nv + 2 E: the closed-neighbourhood entries
+#define MD_ALLOC(ptr, cnt) \
+  if ((rc = bp_alloc(m, &(ptr), (cnt))) != BP_OK) return rc
+  MD_ALLOC(w->mP, 4 * std::max<int64_t>(L, 1) * nv);
+  MD_ALLOC(w->mAc, 4 * w->nbr_total);
+  MD_ALLOC(w->mDinv, 4 * nv);
+  MD_ALLOC(w->mcheb, 2 * MDSC_STEPS + 2);
+  MD_ALLOC(w->mlam, 1);
+  MD_ALLOC(w->mz1, n);
+  MD_ALLOC(w->mt, n);
+  MD_ALLOC(w->ms, n);
+  MD_ALLOC(w->mrc, 2 * nv);
+  MD_ALLOC(w->mec, 2 * nv);
+  MD_ALLOC(w->mrr, 2 * nv);
+  MD_ALLOC(w->md0, 2 * nv);
+  MD_ALLOC(w->md1, 2 * nv);
+#undef MD_ALLOC
+  return BP_OK;
+}
+
+// Setup from the same-precision Jacobian (the column factors are set up first): P, A_c, D^-1, the
+// Gershgorin bound (read back once) and the Chebyshev coefficients.  F: factor / plane type.
+template <class M>
+int mdsc_setup_t(bp_mesh* m, const M* J, cudaStream_t s) {
+  using F = M;
+  int rc = colprec_setup_t(m, J, s);
+  if (rc) return rc;
+  if ((rc = mdsc_alloc<F>(m))) return rc;
+  bp_solver_ws* w = m->ws;
+  const int gcol = (m->nv + 127) / 128;
+  F* P = reinterpret_cast<F*>(w->mP);
+  k_mdsc_prolong<F><<<gcol, 128, 0, s>>>(prec_of<F>(m), P);
+  BP_CUDA_TRY(cudaMemsetAsync(w->mlam, 0, sizeof(double), s));
+  k_mdsc_plane<M, F><<<gcol, 128, 0, s>>>(J, m->vstart, m->vdeg, w->dslot, m->nbr_ptr, m->nbr_idx, P, m->nv, m->nl,
+                                          reinterpret_cast<F*>(w->mAc), reinterpret_cast<F*>(w->mDinv), w->mlam);
+  BP_CUDA_TRY(cudaGetLastError());
+  BP_CUDA_TRY(cudaMemcpyAsync(w->host, w->mlam, sizeof(double), cudaMemcpyDeviceToHost, s));
+  BP_CUDA_TRY(cudaStreamSynchronize(s));
+  const double lam_hi = w->host[0];
+  if (!(lam_hi > 0) || !std::isfinite(lam_hi)) return BP_ENAN;
+  const double lam_lo = lam_hi / MDSC_RATIO;
+  const double theta = 0.5 * (lam_hi + lam_lo), delta = 0.5 * (lam_hi - lam_lo), sigma = theta / delta;
+  double* c = w->host;  // staged in the pinned mirror (synchronised below)
+  c[0] = 1.0 / theta;
+  double rho = 1.0 / sigma;
+  for (int k = 0; k < MDSC_STEPS; ++k) {
+    const double rn = 1.0 / (2.0 * sigma - rho);
+    c[1 + 2 * k] = rn * rho;
+    c[2 + 2 * k] = 2.0 * rn / delta;
+    rho = rn;
+  }
+  BP_CUDA_TRY(cudaMemcpyAsync(w->mcheb, c, (2 * MDSC_STEPS + 1) * sizeof(double), cudaMemcpyHostToDevice, s));
+  BP_CUDA_TRY(cudaStreamSynchronize(s));
+  w->has_mdsc = true;
+  w->mdsc_f32 = sizeof(F) == sizeof(float);
+  return BP_OK;
+}
+
+// z = M^-1 r (the cycle above) for vectors V, Jacobian values M, factors and plane data F.
+template <class M, class V, class F>
+void mdsc_apply_launch(bp_mesh* m, const M* J, const V* r, V* z, cudaStream_t s) {
+  bp_solver_ws* w = m->ws;
+  const Prec<F> Pr = prec_of<F>(m);
+  const F* P = reinterpret_cast<const F*>(w->mP);
+  const F* Ac = reinterpret_cast<const F*>(w->mAc);
+  const F* Dinv = reinterpret_cast<const F*>(w->mDinv);
+  F* rc = reinterpret_cast<F*>(w->mrc);
+  F* ec = reinterpret_cast<F*>(w->mec);
+  F* rr = reinterpret_cast<F*>(w->mrr);
+  F* d[2] = {reinterpret_cast<F*>(w->md0), reinterpret_cast<F*>(w->md1)};
+  V* z1 = reinterpret_cast<V*>(w->mz1);
+  V* t = reinterpret_cast<V*>(w->mt);
+  V* sb = reinterpret_cast<V*>(w->ms);
+  const int64_t n = m->ndof;
+  const int gcol = (m->nv + 127) / 128, gv = (m->nv + NT - 1) / NT;
+  const int gspmv = grid_for(n / 2 * TPR, NT), gvec = grid_for(n, NT);
+  const F omega = (F)MDSC_OMEGA;
+  // z1 = S r
+  mdsc_smooth<V, F>(Pr, r, sb, nullptr, z1, omega, s);
+  // rc = P^T (r - J z1)
+  k_spmv_pairs<M, V, false><<<gspmv, NT, 0, s>>>(m->rowptr, m->nbr_ptr, m->nbr_idx, m->nl, J, (int)(n / 2), z1, t,
+                                                 nullptr, nullptr, nullptr, 0);
+  k_mdsc_sub<V><<<gvec, NT, 0, s>>>(r, t, n);
+  k_mdsc_restrict<V, F><<<gcol, 128, 0, s>>>(P, t, rc, m->nv, m->nl);
+  // ec = B_c rc
+  k_mdsc_cheb_init<F><<<gv, NT, 0, s>>>(Dinv, w->mcheb, rc, ec, rr, d[0], m->nv);
+  for (int k = 0; k < MDSC_STEPS; ++k)
+    k_mdsc_cheb_step<F><<<gv, NT, 0, s>>>(Ac, Dinv, m->nbr_ptr, m->nbr_idx, w->mcheb, k, d[k & 1], d[(k + 1) & 1],
+                                          ec, rr, m->nv);
+  // z2 = z1 + P ec (in z1);  z = z2 + S (r - J z2)
+  k_mdsc_prolong_add<V, F><<<gcol, 128, 0, s>>>(P, ec, z1, m->nv, m->nl);
+  k_spmv_pairs<M, V, false><<<gspmv, NT, 0, s>>>(m->rowptr, m->nbr_ptr, m->nbr_idx, m->nl, J, (int)(n / 2), z1, t,
+                                                 nullptr, nullptr, nullptr, 0);
+  k_mdsc_sub<V><<<gvec, NT, 0, s>>>(r, t, n);
+  mdsc_smooth<V, F>(Pr, t, sb, z1, z, omega, s);
+}
+
+// ---- preconditioned CG with the MDSC cycle (device scalars as in cg_solve)
+// x = 0, r = -R, and r.r of step 0
+template <class V>
+__global__ void __launch_bounds__(NT) k_pcg_init(const double* __restrict__ R, V* __restrict__ x, V* __restrict__ r,
+                                                 int64_t n, double* scal) {
+  V rr = V(0);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const V v = (V)(-R[i]);
+    x[i] = V(0);
+    r[i] = v;
+    rr += v * v;
+  }
+  block_add(rr, scal + 2);
+}
+
+// alpha = r.z / p.Ap, x += alpha p, r -= alpha q, and r.r of step k + 1
+template <class V>
+__global__ void __launch_bounds__(NT) k_pcg_update(const int* kbase, int j, V* __restrict__ x, V* __restrict__ r,
+                                                   const V* __restrict__ p, const V* __restrict__ q, int64_t n,
+                                                   double* scal, int* stop) {
+  __shared__ V s_alpha;
+  __shared__ int s_bad;
+  if (*stop) return;
+  const int k = *kbase + j;
+  if (threadIdx.x == 0) {
+    const double pq = scal[3 * k], rzk = scal[3 * k + 1];
+    s_bad = !(pq > 0.0) || !isfinite(rzk);
+    s_alpha = s_bad ? V(0) : (V)(rzk / pq);
+    if (s_bad && blockIdx.x == 0) *stop = 2;
+  }
+  __syncthreads();
+  if (s_bad) return;
+  const V alpha = s_alpha;
+  V rr = V(0);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    x[i] += alpha * p[i];
+    const V v = r[i] - alpha * q[i];
+    r[i] = v;
+    rr += v * v;
+  }
+  block_add(rr, scal + 3 * (k + 1) + 2);
+}
+
+// r.z into scal[3 (kbase + j + shift) + 1]
+template <class V>
+__global__ void __launch_bounds__(NT) k_pcg_rz(const int* kbase, int j, int shift, const V* __restrict__ r,
+                                               const V* __restrict__ z, int64_t n, double* scal, const int* stop) {
+  if (*stop) return;
+  V acc = V(0);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    acc += r[i] * z[i];
+  block_add(acc, scal + 3 * (*kbase + j + shift) + 1);
+}
+
+// One MDSC-preconditioned CG iteration (the loop body when `loop` is set).
+template <class M, class V>
+void launch_mdsc_iteration(bp_mesh* m, const M* J, cudaStream_t s, cudaGraphConditionalHandle loop, int set_loop) {
+  bp_solver_ws* w = m->ws;
+  const int64_t n = m->ndof;
+  V* x = reinterpret_cast<V*>(w->x);
+  V* r = reinterpret_cast<V*>(w->r);
+  V* z = reinterpret_cast<V*>(w->z);
+  V* p = reinterpret_cast<V*>(w->p);
+  V* q = reinterpret_cast<V*>(w->q);
+  const int gspmv = grid_for(n / 2 * TPR, NT), gvec = grid_for(n, NT);
+  k_spmv_pairs<M, V, true><<<gspmv, NT, 0, s>>>(m->rowptr, m->nbr_ptr, m->nbr_idx, m->nl, J, (int)(n / 2), p, q,
+                                                w->scal, w->stop, w->kbase, 0);
+  k_pcg_update<V><<<gvec, NT, 0, s>>>(w->kbase, 0, x, r, p, q, n, w->scal, w->stop);
+  mdsc_apply_launch<M, V, V>(m, J, r, z, s);
+  k_pcg_rz<V><<<gvec, NT, 0, s>>>(w->kbase, 0, 1, r, z, n, w->scal, w->stop);
+  k_cg_direction<V><<<grid_for(n / 2, NT), NT, 0, s>>>(w->kbase, 0, w->cgpar, n / 2, z, p, w->scal, w->stop, loop,
+                                                       set_loop);
+  k_cg_advance<<<1, 1, 0, s>>>(w->kbase, 1);
+}
+
+template <class M, class V>
+int mdsc_loop_graph(bp_mesh* m, const M* J, cudaGraphExec_t* out) {
+  bp_solver_ws* w = m->ws;
+  const int slot = sizeof(V) == sizeof(float) ? 1 : 0;
+  *out = nullptr;
+  if (w->cg_loop_failed[slot]) return BP_OK;
+  if (!w->mdsc_loop[slot]) {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t cs = nullptr;
+    cudaGraphConditionalHandle h{};
+    cudaGraphNodeParams cp{};
+    cudaGraphNode_t node = nullptr;
+    cudaError_t e = cudaGraphCreate(&graph, 0);
+    if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault);
+    if (e == cudaSuccess) {
+      cp.type = cudaGraphNodeTypeConditional;
+      cp.conditional.handle = h;
+      cp.conditional.type = cudaGraphCondTypeWhile;
+      cp.conditional.size = 1;
+      e = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp);
+    }
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e == cudaSuccess)
+      e = cudaStreamBeginCaptureToGraph(cs, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                        cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      launch_mdsc_iteration<M, V>(m, J, cs, h, 1);
+      cudaGraph_t body = nullptr;
+      e = cudaStreamEndCapture(cs, &body);
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+    if (cs) cudaStreamDestroy(cs);
+    if (graph) cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return BP_OK;  // the caller iterates from the host
+    }
+    w->mdsc_loop[slot] = exec;
+  }
+  *out = (cudaGraphExec_t)w->mdsc_loop[slot];
+  return BP_OK;
+}
+
+// MDSC-preconditioned CG on J delta = -R to ||r|| <= eta ||R||; delta in ws->x (type V).  The
+// Jacobian J must be the one mdsc_setup_t saw (captured in the loop graph by address).
+template <class M, class V>
+int mdsc_cg_solve(bp_mesh* m, const M* J, double eta, int maxit, cudaStream_t s, int* iters, int* status) {
+  bp_solver_ws* w = m->ws;
+  maxit = std::min(maxit, w->scal_cap);
+  const int64_t n = m->ndof;
+  V* r = reinterpret_cast<V*>(w->r);
+  V* z = reinterpret_cast<V*>(w->z);
+  V* p = reinterpret_cast<V*>(w->p);
+  cudaGraphExec_t loop = nullptr;
+  int rc = mdsc_loop_graph<M, V>(m, J, &loop);
+  if (rc) return rc;
+  BP_CUDA_TRY(cudaMemsetAsync(w->scal, 0, 3 * (size_t)(maxit + 2 + CG_BATCH) * sizeof(double), s));
+  BP_CUDA_TRY(cudaMemsetAsync(w->stop, 0, sizeof(int), s));
+  BP_CUDA_TRY(cudaMemsetAsync(w->kbase, 0, sizeof(int), s));
+  w->hpar[0] = eta * eta;
+  w->hpar[1] = (double)maxit;
+  BP_CUDA_TRY(cudaMemcpyAsync(w->cgpar, w->hpar, 2 * sizeof(double), cudaMemcpyHostToDevice, s));
+  const int gvec = grid_for(n, NT);
+  k_pcg_init<V><<<gvec, NT, 0, s>>>(w->R, reinterpret_cast<V*>(w->x), r, n, w->scal);
+  mdsc_apply_launch<M, V, V>(m, J, r, z, s);
+  k_pcg_rz<V><<<gvec, NT, 0, s>>>(w->kbase, 0, 0, r, z, n, w->scal, w->stop);
+  BP_CUDA_TRY(cudaMemcpyAsync(p, z, n * sizeof(V), cudaMemcpyDeviceToDevice, s));
+  BP_CUDA_TRY(cudaGetLastError());
+  int k = 0;
+  *status = 0;
+  int* hk = reinterpret_cast<int*>(w->host + w->host_cap - 2);
+  int stopflag = 0;
+  if (loop) {
+    BP_CUDA_TRY(cudaGraphLaunch(loop, s));
+    BP_CUDA_TRY(cudaMemcpyAsync(hk, w->kbase, sizeof(int), cudaMemcpyDeviceToHost, s));
+    BP_CUDA_TRY(cudaMemcpyAsync(w->host + w->host_cap - 1, w->stop, sizeof(int), cudaMemcpyDeviceToHost, s));
+    BP_CUDA_TRY(cudaStreamSynchronize(s));
+    k = std::min(std::max(*hk, 0), maxit);
+    std::memcpy(&stopflag, w->host + w->host_cap - 1, sizeof(int));
+  } else {  // no conditional nodes: one iteration per host check
+    while (!stopflag && k < maxit) {
+      launch_mdsc_iteration<M, V>(m, J, s, cudaGraphConditionalHandle{}, 0);
+      BP_CUDA_TRY(cudaGetLastError());
+      BP_CUDA_TRY(cudaMemcpyAsync(w->host + w->host_cap - 1, w->stop, sizeof(int), cudaMemcpyDeviceToHost, s));
+      BP_CUDA_TRY(cudaStreamSynchronize(s));
+      std::memcpy(&stopflag, w->host + w->host_cap - 1, sizeof(int));
+      ++k;
+    }
+  }
+  BP_CUDA_TRY(cudaMemcpyAsync(w->host, w->scal, 3 * (size_t)(k + 2) * sizeof(double), cudaMemcpyDeviceToHost, s));
+  BP_CUDA_TRY(cudaStreamSynchronize(s));
+  if (stopflag == 2) *status = 2;
+  const double tol2 = eta * eta, rr0 = w->host[2];
+  int taken = k;
+  for (int j = 1; j <= k; ++j) {
+    const double rr = w->host[3 * j + 2];
+    if (rr <= tol2 * rr0 || !std::isfinite(rr)) {
+      taken = j;
+      break;
+    }
+    if (w->host[3 * j + 2] == 0.0 && w->host[3 * j + 1] == 0.0) {
+      taken = j - 1;
+      break;
+    }
+  }
+  *iters = taken;
+  if (!std::isfinite(rr0)) *status = 3;
+  return BP_OK;
+}
+
 double elapsed(cudaEvent_t a, cudaEvent_t b) {
   float ms = 0.f;
   cudaEventElapsedTime(&ms, a, b);
@@ -1314,6 +1873,8 @@ void bp_solver_ws_free(bp_mesh* m) {
   for (void* g : m->ws->cg_exec)
     if (g) cudaGraphExecDestroy((cudaGraphExec_t)g);
   for (void* g : m->ws->cg_loop)
+    if (g) cudaGraphExecDestroy((cudaGraphExec_t)g);
+  for (void* g : m->ws->mdsc_loop)
     if (g) cudaGraphExecDestroy((cudaGraphExec_t)g);
   delete m->ws;  // device arrays are in m->allocations
   m->ws = nullptr;
@@ -1396,6 +1957,29 @@ extern "C" int bp_colprec_apply(bp_mesh* m, const double* r, double* z, void* st
   return BP_OK;
 }
 
+extern "C" int bp_mdsc_setup(bp_mesh* m, const void* J, int precision, void* stream) {
+  if (!m || !J) return BP_EINVAL;
+  if (precision != BP_F64 && precision != BP_F32 && precision != BP_F32_ALL) return BP_EINVAL;
+  bp_device_guard g(m->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc = ensure_ws(m, s);
+  if (rc) return rc;
+  return precision == BP_F64 ? mdsc_setup_t(m, (const double*)J, s) : mdsc_setup_t(m, (const float*)J, s);
+}
+
+extern "C" int bp_mdsc_apply(bp_mesh* m, const void* J, const double* r, double* z, void* stream) {
+  if (!m || !J || !r || !z || !bp_aligned16(r) || !bp_aligned16(z) || !bp_aligned16(J)) return BP_EINVAL;
+  if (!m->ws || !m->ws->has_mdsc) return BP_EINVAL;
+  bp_device_guard g(m->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (m->ws->mdsc_f32)
+    mdsc_apply_launch<float, double, float>(m, (const float*)J, r, z, s);
+  else
+    mdsc_apply_launch<double, double, double>(m, (const double*)J, r, z, s);
+  BP_CUDA_TRY(cudaGetLastError());
+  return BP_OK;
+}
+
 extern "C" int bp_energy(bp_mesh* m, const double* U, double* out, void* stream) {
   if (!m || !U || !out) return BP_EINVAL;
   bp_device_guard g(m->device);
@@ -1448,7 +2032,7 @@ extern "C" void bp_solve_opts_default(bp_solve_opts* o) {
   o->picard_rtol = 0.0;
   o->value32_rtol = 0.0;
   o->device_loop = 1;
-  o->reserved = 0;
+  o->preconditioner = BP_PREC_COLUMN;
 }
 
 extern "C" int bp_newton_solve(bp_mesh* m, double* U, const bp_solve_opts* opts, bp_solve_report* rep,
@@ -1457,7 +2041,9 @@ extern "C" int bp_newton_solve(bp_mesh* m, double* U, const bp_solve_opts* opts,
   const bp_solve_opts o = *opts;
   if (o.line_search < 0 || o.line_search > BP_LS_QUADRATIC) return BP_EINVAL;
   if (!(o.picard_rtol >= 0) || !(o.value32_rtol >= 0)) return BP_EINVAL;
-  if ((o.device_loop != 0 && o.device_loop != 1) || o.reserved != 0) return BP_EINVAL;
+  if ((o.device_loop != 0 && o.device_loop != 1) ||
+      (o.preconditioner != BP_PREC_COLUMN && o.preconditioner != BP_PREC_MDSC))
+    return BP_EINVAL;
   if (!(o.rtol > 0) || o.max_newton < 0 || o.max_newton > 64 || o.max_krylov < 1 || o.check_every < 1 ||
       (o.precision != BP_F64 && o.precision != BP_F32) || o.krylov != BP_KRYLOV_CG || !(o.eta_max > 0))
     return BP_EINVAL;
@@ -1537,12 +2123,20 @@ extern "C" int bp_newton_solve(bp_mesh* m, double* U, const bp_solve_opts* opts,
     eta = std::max(eta, eta_floor);
     fprev = fn;
     // preconditioner + Krylov
+    const bool mdsc = o.preconditioner == BP_PREC_MDSC;
     BP_CUDA_TRY(cudaEventRecord(ev[3], s));
-    if ((rc = f32 ? colprec_setup_t(m, reinterpret_cast<const float*>(w->J), s) : colprec_setup_t(m, w->J, s)))
-      return rc;
+    if (mdsc)
+      rc = f32 ? mdsc_setup_t(m, reinterpret_cast<const float*>(w->J), s) : mdsc_setup_t(m, w->J, s);
+    else
+      rc = f32 ? colprec_setup_t(m, reinterpret_cast<const float*>(w->J), s) : colprec_setup_t(m, w->J, s);
+    if (rc) return rc;
     BP_CUDA_TRY(cudaEventRecord(ev[4], s));
     int its = 0, kst = 0;
-    if (f32)
+    if (mdsc && f32)
+      rc = mdsc_cg_solve<float, float>(m, reinterpret_cast<const float*>(w->J), eta, o.max_krylov, s, &its, &kst);
+    else if (mdsc)
+      rc = mdsc_cg_solve<double, double>(m, w->J, eta, o.max_krylov, s, &its, &kst);
+    else if (f32)
       rc = cg_solve<float, float>(m, reinterpret_cast<const float*>(w->J), eta, o.max_krylov, o.check_every,
                                   o.device_loop != 0, s, &its, &kst);
     else
