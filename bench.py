@@ -543,6 +543,9 @@ def mlp_section(capi, dev, rows=50625, batch=8192, reps=20):
                          "are far too small to approach it"}
 
 
+SOLVE_KW = {}  # options added to every timed Newton solve (--cg-host-loop)
+
+
 def newton_section(capi, synth, dm, mesh, dev, skip_large=False, reps=3):
     """Time to ||F(U)|| <= 1e-8 ||F(0)|| from the shallow-ice guess: plain FP64 path and the
     mixed-precision path (FP32 Jacobian lanes and Krylov, FP64 residual/viscosity/update)."""
@@ -555,7 +558,7 @@ def newton_section(capi, synth, dm, mesh, dev, skip_large=False, reps=3):
             capi.bp_initial_guess(dmx.handle, capi.BP_GUESS_SIA, U)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            rc, rep = capi.bp_newton_solve(dmx.handle, U, precision=prec, max_krylov=4000, **kw)
+            rc, rep = capi.bp_newton_solve(dmx.handle, U, precision=prec, max_krylov=4000, **SOLVE_KW, **kw)
             torch.cuda.synchronize()
             times.append(time.perf_counter() - t0)
             if rc != capi.BP_OK:
@@ -641,9 +644,14 @@ def main():
     ap.add_argument("--newton-only", action="store_true",
                     help="only the Newton-solve section (profiling the solver); prints its JSON")
     ap.add_argument("--newton-reps", type=int, default=3, help="timed repetitions of each Newton solve")
+    ap.add_argument("--cg-host-loop", action="store_true",
+                    help="iterate CG from the host (device_loop 0) so that a kernel profiler lists every "
+                         "CG launch (the device-driven loop launches its kernels from the device)")
     ap.add_argument("--mesh-m", type=int, default=224, help="base grid size (224: the 1M-wedge workload)")
     ap.add_argument("--layers", type=int, default=10)
     args = ap.parse_args()
+    if args.cg_host_loop:
+        SOLVE_KW["device_loop"] = 0
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -280,8 +280,8 @@ typedef struct {
                          loop, no host check in between; 0: replays of a captured 8-iteration batch
                          with a host check every check_every iterations */
   int preconditioner; /* BP_PREC_COLUMN: the vertical-line block solve; BP_PREC_MDSC: the two-level
-                         semicoarsening cycle (bp_mdsc_setup), always iterated by a device-driven
-                         loop where conditional graph nodes exist */
+                         semicoarsening cycle (bp_mdsc_setup); with device_loop 0 its iterations are
+                         launched from the host, one host check each */
 } bp_solve_opts;
 
 typedef struct {

@@ -1794,7 +1794,8 @@ int mdsc_loop_graph(bp_mesh* m, const M* J, cudaGraphExec_t* out) {
 // MDSC-preconditioned CG on J delta = -R to ||r|| <= eta ||R||; delta in ws->x (type V).  The
 // Jacobian J must be the one mdsc_setup_t saw (captured in the loop graph by address).
 template <class M, class V>
-int mdsc_cg_solve(bp_mesh* m, const M* J, double eta, int maxit, cudaStream_t s, int* iters, int* status) {
+int mdsc_cg_solve(bp_mesh* m, const M* J, double eta, int maxit, bool device_loop, cudaStream_t s, int* iters,
+                  int* status) {
   bp_solver_ws* w = m->ws;
   maxit = std::min(maxit, w->scal_cap);
   const int64_t n = m->ndof;
@@ -1802,7 +1803,7 @@ int mdsc_cg_solve(bp_mesh* m, const M* J, double eta, int maxit, cudaStream_t s,
   V* z = reinterpret_cast<V*>(w->z);
   V* p = reinterpret_cast<V*>(w->p);
   cudaGraphExec_t loop = nullptr;
-  int rc = mdsc_loop_graph<M, V>(m, J, &loop);
+  int rc = device_loop ? mdsc_loop_graph<M, V>(m, J, &loop) : BP_OK;
   if (rc) return rc;
   BP_CUDA_TRY(cudaMemsetAsync(w->scal, 0, 3 * (size_t)(maxit + 2 + CG_BATCH) * sizeof(double), s));
   BP_CUDA_TRY(cudaMemsetAsync(w->stop, 0, sizeof(int), s));
@@ -2133,9 +2134,10 @@ extern "C" int bp_newton_solve(bp_mesh* m, double* U, const bp_solve_opts* opts,
     BP_CUDA_TRY(cudaEventRecord(ev[4], s));
     int its = 0, kst = 0;
     if (mdsc && f32)
-      rc = mdsc_cg_solve<float, float>(m, reinterpret_cast<const float*>(w->J), eta, o.max_krylov, s, &its, &kst);
+      rc = mdsc_cg_solve<float, float>(m, reinterpret_cast<const float*>(w->J), eta, o.max_krylov,
+                                       o.device_loop != 0, s, &its, &kst);
     else if (mdsc)
-      rc = mdsc_cg_solve<double, double>(m, w->J, eta, o.max_krylov, s, &its, &kst);
+      rc = mdsc_cg_solve<double, double>(m, w->J, eta, o.max_krylov, o.device_loop != 0, s, &its, &kst);
     else if (f32)
       rc = cg_solve<float, float>(m, reinterpret_cast<const float*>(w->J), eta, o.max_krylov, o.check_every,
                                   o.device_loop != 0, s, &its, &kst);
