@@ -440,6 +440,14 @@ def learned_start(capi, dm, dev, reps=3, seeds=10):
                      "initial_rel_residual": rep["history"][0]}
         if name != "sia":
             out[name]["network_guess_kept"] = rep["learned_used"]
+    # the same two starts with FP32 value-path steps until 1e-3 (the fastest mixed configuration)
+    for name in ("sia", "learned_picard"):
+        times, rep = [], None
+        for _ in range(reps):
+            _, rep = learned.solve(dm, capi.BP_F32, name, mlp=net, value32_rtol=1e-3)
+            times.append(rep["wall_s"])
+        out[name + "_value32_until_1e-3"] = {"s": statistics.median(times), "newton_iters": rep["newton_iters"],
+                                             "converged": rep["converged"]}
     out["judges"] = {"learned": "FP64 residual norm", "learned_energy": "FP64 discrete energy",
                      "learned_picard": f"FP64 energy, then Picard steps until ||F|| <= {learned.PICARD_RTOL} ||F(0)||"}
     mesh = dm.mesh

@@ -43,11 +43,11 @@ JUDGES = {"learned": capi.BP_JUDGE_RESIDUAL, "learned_energy": capi.BP_JUDGE_ENE
 PICARD_RTOL = 0.1
 
 
-def solve(dm, precision=capi.BP_F32, guess="sia", mlp=None, max_krylov=4000):
+def solve(dm, precision=capi.BP_F32, guess="sia", mlp=None, max_krylov=4000, **opts):
     """Newton solve from the named initial guess ("zero", "sia", or a learned guess: "learned" judged
     by the FP64 residual, "learned_energy" judged by the FP64 energy, "learned_raw" unjudged,
     "learned_picard" energy-judged and followed by Picard steps).  The wall time covers the guess
-    and the solve; rep["guess_rel_err"] is |U0 - U*| / |U*|."""
+    and the solve; rep["guess_rel_err"] is |U0 - U*| / |U*|.  opts: further bp_solve_opts fields."""
     import torch
     U = torch.empty(dm.ndof, dtype=torch.float64, device=dm.device)
     used = None
@@ -62,7 +62,9 @@ def solve(dm, precision=capi.BP_F32, guess="sia", mlp=None, max_krylov=4000):
     U0 = U.clone()  # (not timed)
     torch.cuda.synchronize()
     t1 = time.perf_counter()
-    kw = {"picard_rtol": PICARD_RTOL} if guess == "learned_picard" else {}
+    kw = dict(opts)
+    if guess == "learned_picard":
+        kw["picard_rtol"] = PICARD_RTOL
     rc, rep = capi.bp_newton_solve(dm.handle, U, precision=precision, max_krylov=max_krylov, **kw)
     torch.cuda.synchronize()
     rep["wall_s"] = t_guess + (time.perf_counter() - t1)
