@@ -300,17 +300,6 @@ __device__ __forceinline__ void assemble_column(const AsmArgs& A, const int t) {
 #pragma unroll
   for (int a = 0; a < 3; ++a) ubase[a] = 2LL * v[a] * (L + 1);
 
-  int64_t vs[3];
-  int dg[3], sl[9];
-  if constexpr (MODE != MODE_RES) {
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      vs[a] = A.vstart[v[a]];
-      dg[a] = A.vdeg[v[a]];
-    }
-#pragma unroll
-    for (int k = 0; k < 9; ++k) sl[k] = A.slots[9 * t + k];
-  }
 
   // ---- bottom level
   double ub[3], vb[3];
@@ -780,6 +769,18 @@ __device__ __forceinline__ void assemble_column(const AsmArgs& A, const int t) {
     if constexpr (MODE != MODE_RES) {
       using ST = typename LaneStore<TL>::type;
       ST* J = static_cast<ST*>(A.J);
+      // scatter positions: the vertices' row blocks and the triangle's slots are read here, per
+      // wedge, from the (L1-resident) mesh arrays rather than kept live across the level loop,
+      // whose registers the element matrix needs
+      int64_t vs[3];
+      int dg[3], sl[9];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        vs[a] = __ldg(A.vstart + v[a]);
+        dg[a] = __ldg(A.vdeg + v[a]);
+      }
+#pragma unroll
+      for (int k = 0; k < 9; ++k) sl[k] = __ldg(A.slots + 9 * t + k);
       int64_t rowbase[6], rowhalf[6];
       int nlev[2], off[2][2];
 #pragma unroll
