@@ -1045,6 +1045,7 @@ int colprec_setup_t(bp_mesh* m, const M* J, cudaStream_t s) {
 // batch counter advances.  The iteration index, the tolerance and the limit are read from device
 // memory, so one captured graph serves every solve on this mesh and precision.
 // Launch with the programmatic-stream-serialisation attribute (captured as a programmatic edge).
+// Used only while capturing the loop body; a refused launch is picked up after the capture.
 template <class... Args, class... Act>
 void launch_pdl(void (*kern)(Args...), int grid, int block, size_t smem, cudaStream_t s, Act... args) {
   cudaLaunchConfig_t cfg = {};
@@ -1182,8 +1183,10 @@ int cg_loop_graph(bp_mesh* m, const M* J, cudaGraphExec_t* out) {
                                         cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
       launch_cg_iteration<M, V>(m, J, cs, h);
+      const cudaError_t le = cudaGetLastError();  // a launch the capture refused
       cudaGraph_t body = nullptr;
       e = cudaStreamEndCapture(cs, &body);
+      if (e == cudaSuccess) e = le;
     }
     if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
     if (cs) cudaStreamDestroy(cs);
@@ -1775,8 +1778,10 @@ int mdsc_loop_graph(bp_mesh* m, const M* J, cudaGraphExec_t* out) {
                                         cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
       launch_mdsc_iteration<M, V>(m, J, cs, h, 1);
+      const cudaError_t le = cudaGetLastError();  // a launch the capture refused
       cudaGraph_t body = nullptr;
       e = cudaStreamEndCapture(cs, &body);
+      if (e == cudaSuccess) e = le;
     }
     if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
     if (cs) cudaStreamDestroy(cs);

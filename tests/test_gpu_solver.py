@@ -43,7 +43,7 @@ def _host_csr(dm, J):
                          shape=(dm.ndof, dm.ndof))
 
 
-@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("precision", [0, 1, 3])   # FP64, FP32 and FP32-value-path (float) values
 def test_spmv_matches_scipy(precision):
     c = capi()
     mesh = synth.dome_mesh(23, 4, 31, 32, bed="sinusoidal")
@@ -65,7 +65,7 @@ def _column_blocks(A, mesh, a):
     return idx, B
 
 
-@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("precision", [0, 1, 3])
 def test_column_preconditioner_is_exact_block_tridiagonal_solve(precision):
     c = capi()
     mesh = synth.dome_mesh(12, 6, 51, 52, bed="sinusoidal")
