@@ -31,6 +31,7 @@
  *   - device buffers U, R, J are owned by the caller; the mesh object owns the mesh arrays,
  *     the sparsity pattern and all scratch it needs, all on the device current at upload;
  *   - velocity arrays U_dev must be 16-byte aligned (the kernels load (u, v) pairs together);
+ *   - Jacobian value arrays must be 8-byte aligned (FP32 values are scattered as (u, v) pairs);
  *   - calls that take a stream are asynchronous on that stream (a cudaStream_t passed as
  *     void*, NULL = legacy default stream) unless documented as synchronising;
  *   - residual / Jacobian outputs are overwritten, never accumulated;
@@ -166,7 +167,7 @@ int bp_assemble_residual(bp_mesh* mesh, const double* U_dev, double* R_dev, void
  * the residual (FP64; FP32-accurate with BP_F32_ALL).
  * Both outputs are overwritten (zeroing is part of the call).  `scatter` is a BP_SCATTER_*,
  * `method` a BP_JAC_*.  Asynchronous on `stream`.
- * Errors: BP_EINVAL (NULL U/J, unknown precision/scatter/method), BP_EUNSUP (BP_F64X2 or
+ * Errors: BP_EINVAL (NULL U/J, misaligned U/J, unknown precision/scatter/method), BP_EUNSUP (BP_F64X2 or
  * BP_F32_ALL with BP_JAC_DUAL), BP_ENOMEM (first call with R_dev == NULL allocates a residual
  * scratch in the mesh object), BP_ECUDA.
  */

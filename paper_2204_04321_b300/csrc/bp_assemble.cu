@@ -111,7 +111,7 @@ extern "C" int bp_assemble_residual(bp_mesh* m, const double* U, double* R, void
 
 int bp_assemble_jacobian_ex(bp_mesh* m, const double* U, double* R, void* J, int precision, int scatter, int method,
                             int picard, void* stream) {
-  if (!m || !U || !J || !bp_aligned16(U)) return BP_EINVAL;
+  if (!m || !U || !J || !bp_aligned16(U) || !bp_aligned8(J)) return BP_EINVAL;
   int rc0 = check_jacobian_args(precision, scatter, method);
   if (rc0) return rc0;
   bp_device_guard g(m->device);
@@ -185,7 +185,7 @@ int noalloc_scratch(int device, double** out) {
 
 extern "C" int bp_assemble_jacobian_noalloc(bp_mesh* m, const double* U, void* J, int precision,
                                             int scatter, int method, void* stream) {
-  if (!m || !U || !J || !bp_aligned16(U)) return BP_EINVAL;
+  if (!m || !U || !J || !bp_aligned16(U) || !bp_aligned8(J)) return BP_EINVAL;
   int rc0 = check_jacobian_args(precision, scatter, method);
   if (rc0) return rc0;
   if (m->ndof > BP_NOALLOC_MAX_NDOF) return BP_ESIZE;

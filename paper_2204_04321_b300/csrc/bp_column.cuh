@@ -795,24 +795,54 @@ __device__ __forceinline__ void assemble_column(const AsmArgs& A, const int t) {
           rowhalf[3 * k + a] = 2LL * nlev[k] * dg[a];
         }
       }
+      if constexpr (ATOMIC && std::is_same<ST, float>::value) {
+        // FP32 values: the (u, v) column pair of a row and a column node is one aligned float2 in
+        // the pattern, added by one vector atomic: 72 per wedge (54 with the carry) instead of 144
+        // scalar ones.  The entry points require 8-byte aligned FP32 values.
+        if constexpr (kAhead) {
+          if (l + 1 < L) {  // top-top block: carried to the next wedge
 #pragma unroll
-      for (int i = 0; i < 12; ++i) {
-        const int ni = i >> 1, ci = i & 1, ki = ni / 3, ai = ni % 3;
+            for (int i = 6; i < 12; ++i)
 #pragma unroll
-        for (int j = i; j < 12; ++j) {
-          const int nj = j >> 1, cj = j & 1, kj = nj / 3, bj = nj % 3;
-          if constexpr (kAhead) {
-            if (i >= 6 && l + 1 < L) {  // top-top block: carried to the next wedge
-              Kc[uidx6(i - 6, j - 6)] = K[uidx(i, j)];
-              continue;
-            }
+              for (int j = i; j < 12; ++j) Kc[uidx6(i - 6, j - 6)] = K[uidx(i, j)];
           }
-          const ST val = LaneStore<TL>::cast(K[uidx(i, j)]);
-          const int64_t pij = rowbase[ni] + ci * rowhalf[ni] + 2 * (sl[3 * ai + bj] * nlev[ki] + off[ki][kj]) + cj;
-          scatter_add<ATOMIC>(J + pij, val);
-          if (i != j) {
-            const int64_t pji = rowbase[nj] + cj * rowhalf[nj] + 2 * (sl[3 * bj + ai] * nlev[kj] + off[kj][ki]) + ci;
-            scatter_add<ATOMIC>(J + pji, val);
+        }
+#pragma unroll
+        for (int i = 0; i < 12; ++i) {
+          const int ni = i >> 1, ci = i & 1, ki = ni / 3, ai = ni % 3;
+#pragma unroll
+          for (int nj = 0; nj < 6; ++nj) {
+            const int kj = nj / 3, bj = nj % 3;
+            if constexpr (kAhead) {
+              if (ni >= 3 && nj >= 3 && l + 1 < L) continue;  // carried
+            }
+            const int j0 = 2 * nj, j1 = 2 * nj + 1;
+            const float v0 = LaneStore<TL>::cast(K[i <= j0 ? uidx(i, j0) : uidx(j0, i)]);
+            const float v1 = LaneStore<TL>::cast(K[i <= j1 ? uidx(i, j1) : uidx(j1, i)]);
+            const int64_t p = rowbase[ni] + ci * rowhalf[ni] + 2 * (sl[3 * ai + bj] * nlev[ki] + off[ki][kj]);
+            atomicAdd(reinterpret_cast<float2*>(J + p), make_float2(v0, v1));
+          }
+        }
+      } else {
+#pragma unroll
+        for (int i = 0; i < 12; ++i) {
+          const int ni = i >> 1, ci = i & 1, ki = ni / 3, ai = ni % 3;
+#pragma unroll
+          for (int j = i; j < 12; ++j) {
+            const int nj = j >> 1, cj = j & 1, kj = nj / 3, bj = nj % 3;
+            if constexpr (kAhead) {
+              if (i >= 6 && l + 1 < L) {  // top-top block: carried to the next wedge
+                Kc[uidx6(i - 6, j - 6)] = K[uidx(i, j)];
+                continue;
+              }
+            }
+            const ST val = LaneStore<TL>::cast(K[uidx(i, j)]);
+            const int64_t pij = rowbase[ni] + ci * rowhalf[ni] + 2 * (sl[3 * ai + bj] * nlev[ki] + off[ki][kj]) + cj;
+            scatter_add<ATOMIC>(J + pij, val);
+            if (i != j) {
+              const int64_t pji = rowbase[nj] + cj * rowhalf[nj] + 2 * (sl[3 * bj + ai] * nlev[kj] + off[kj][ki]) + ci;
+              scatter_add<ATOMIC>(J + pji, val);
+            }
           }
         }
       }

@@ -194,7 +194,7 @@ extern "C" int bp_ensemble_create(bp_mesh* const* members, int count, const doub
   BP_CUDA_TRY(cudaGetDevice(&dev));
   for (int i = 0; i < count; ++i)
     if (!members[i] || !U[i] || !R[i] || !J[i] || members[i]->device != dev || !bp_aligned16(U[i]) ||
-        ((reinterpret_cast<uintptr_t>(J[i]) & 3u) != 0))
+        !bp_aligned8(J[i]))
       return BP_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
   auto* e = new bp_ensemble();

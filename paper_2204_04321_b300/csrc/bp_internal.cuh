@@ -152,6 +152,7 @@ struct bp_device_guard {
 
 // The kernels read velocity pairs (u, v) as one 16-byte load.
 __host__ __device__ inline bool bp_aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+__host__ __device__ inline bool bp_aligned8(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 7u) == 0; }
 
 // Node level helpers of the extruded CSR pattern.
 __host__ __device__ inline int bp_nlev(int level, int L) { return (level == 0 || level == L) ? 2 : 3; }

@@ -68,3 +68,15 @@ def test_misaligned_velocity_is_rejected():
     with pytest.raises(capi.BPError) as e:
         capi.bp_assemble_residual(dm.handle, buf[1:], R)   # 8-byte, not 16-byte aligned
     assert e.value.status == capi.BP_EINVAL
+
+
+def test_misaligned_fp32_jacobian_is_rejected():
+    from paper_2204_04321_b300 import capi
+    m = synth.dome_mesh(4, 2, 1, 2)
+    dm = capi.DeviceMesh(m)
+    U = torch.zeros(dm.ndof, dtype=torch.float64, device="cuda")
+    Jbuf = torch.zeros(dm.nnz + 1, dtype=torch.float32, device="cuda")
+    for prec in (capi.BP_F32, capi.BP_F32_ALL):
+        with pytest.raises(capi.BPError) as e:
+            capi.bp_assemble_jacobian(dm.handle, U, None, Jbuf[1:], prec)   # 4-byte, not 8-byte aligned
+        assert e.value.status == capi.BP_EINVAL
