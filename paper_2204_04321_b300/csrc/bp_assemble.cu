@@ -27,7 +27,13 @@ template <int MODE, class TL, bool ATOMIC, bool PICARD = false, class TV = doubl
 __global__ void __launch_bounds__(128, min_blocks<TL, TV>()) k_assemble(const AsmArgs A) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= A.count) return;
-  assemble_column<MODE, TL, ATOMIC, PICARD, TV>(A, A.tri_list ? A.tri_list[idx] : idx);
+  const int t = A.tri_list ? A.tri_list[idx] : idx;
+  if constexpr (MODE == MODE_FACT) {  // per-column in-plane coefficients: 24 lanes per thread
+    __shared__ __align__(16) unsigned char sraw[24 * 128 * sizeof(TL)];
+    assemble_column<MODE, TL, ATOMIC, PICARD, TV, true>(A, t, reinterpret_cast<TL*>(sraw) + threadIdx.x);
+  } else {
+    assemble_column<MODE, TL, ATOMIC, PICARD, TV>(A, t);
+  }
 }
 
 AsmArgs make_args(const bp_mesh* m, const double* U, double* R, void* J) {

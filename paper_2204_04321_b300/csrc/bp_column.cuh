@@ -240,8 +240,11 @@ __device__ __forceinline__ Dual<TL, NL> operator*(double s, const Dual<TL, NL>& 
 // (factored method, FP32 lanes) whose residual carries FP32 rounding: per-column and per-level
 // geometry, the 2D velocity gradients and the vertical velocity differences are still formed in
 // FP64 and rounded once, everything per quadrature point runs in FP32.
-template <int MODE, class TL, bool ATOMIC, bool PICARD = false, class TV = double>
-__device__ __forceinline__ void assemble_column(const AsmArgs& A, const int t) {
+// SBL (factored method): the in-plane coefficients B(Lambda_a, Lambda_b) depend on the triangle only;
+// they are formed once per column into shared memory (sbl: this thread's first slot, consecutive
+// slots blockDim.x apart) and read per wedge instead of being formed again at every level.
+template <int MODE, class TL, bool ATOMIC, bool PICARD = false, class TV = double, bool SBL = false>
+__device__ __forceinline__ void assemble_column(const AsmArgs& A, const int t, TL* sbl = nullptr) {
   static_assert(std::is_same<TV, double>::value || (MODE == MODE_FACT && std::is_same<TL, float>::value),
                 "the FP32 value path exists for the factored method with FP32 lanes only");
   const int L = A.L;
@@ -294,6 +297,21 @@ __device__ __forceinline__ void assemble_column(const AsmArgs& A, const int t) {
       clx[a] = to_lane<TL>(lx[a]);
       cly[a] = to_lane<TL>(ly[a]);
     }
+  }
+  if constexpr (SBL) {  // B(Lambda_a, Lambda_b) for the vertex pairs a <= b (pairs 00 01 02 11 12 22)
+    const int bs = blockDim.x;
+    int pr = 0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = a; b < 3; ++b, ++pr) {
+        const TL xx = clx[a] * clx[b], yy = cly[a] * cly[b];
+        const TL xy = clx[a] * cly[b], yx = cly[a] * clx[b];
+        sbl[(4 * pr + 0) * bs] = TL(2) * xx + TL(0.5) * yy;
+        sbl[(4 * pr + 1) * bs] = xy + TL(0.5) * yx;
+        sbl[(4 * pr + 2) * bs] = TL(0.5) * xy + yx;
+        sbl[(4 * pr + 3) * bs] = TL(0.5) * xx + TL(2) * yy;
+      }
   }
 
   int64_t ubase[3];
@@ -674,12 +692,23 @@ __device__ __forceinline__ void assemble_column(const AsmArgs& A, const int t) {
 #pragma unroll
           for (int n2 = n1; n2 < 6; ++n2) {
             const int ki = n1 / 3, ai = n1 % 3, kj = n2 / 3, bj = n2 % 3;
-            const TL xx = flx[ai] * flx[bj], yy = fly[ai] * fly[bj];
-            const TL xy = flx[ai] * fly[bj], yx = fly[ai] * flx[bj];
-            const TL BL[4] = {TL(2) * xx + TL(0.5) * yy, xy + TL(0.5) * yx, TL(0.5) * xy + yx,
-                              TL(0.5) * xx + TL(2) * yy};
             const int lo = ai < bj ? ai : bj, hi = ai < bj ? bj : ai;
             const int pr = lo * 3 - (lo * (lo - 1)) / 2 + (hi - lo);
+            TL BL[4];
+            if constexpr (SBL) {  // B(Lambda_b, Lambda_a) is B(Lambda_a, Lambda_b) with the uv / vu terms swapped
+              const int bs = blockDim.x;
+              BL[0] = sbl[(4 * pr + 0) * bs];
+              BL[1] = sbl[(4 * pr + (ai <= bj ? 1 : 2)) * bs];
+              BL[2] = sbl[(4 * pr + (ai <= bj ? 2 : 1)) * bs];
+              BL[3] = sbl[(4 * pr + 3) * bs];
+            } else {
+              const TL xx = flx[ai] * flx[bj], yy = fly[ai] * fly[bj];
+              const TL xy = flx[ai] * fly[bj], yx = fly[ai] * flx[bj];
+              BL[0] = TL(2) * xx + TL(0.5) * yy;
+              BL[1] = xy + TL(0.5) * yx;
+              BL[2] = TL(0.5) * xy + yx;
+              BL[3] = TL(0.5) * xx + TL(2) * yy;
+            }
             const TL Yc[4] = {Yuu[pr], Yuv[pr], Yuv[pr], Yvv[pr]};
             const TL q = Q[ki][kj];
             const bool neg = (ki == 0) != (kj == 0);
