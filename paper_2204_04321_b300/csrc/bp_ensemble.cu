@@ -44,9 +44,16 @@ __global__ void k_ens_init(const InitItem* __restrict__ items, int count, int* _
   }
 }
 
+// dynamic shared memory of a block: the per-column in-plane coefficients, 24 lanes per thread
+template <class TL>
+size_t ens_smem(int cpb) {
+  return 24 * (size_t)cpb * sizeof(TL);
+}
+
 template <class TL, bool ATOMIC>
 __global__ void __launch_bounds__(256) k_ensemble(const AsmArgs* __restrict__ args, const Tile* __restrict__ tiles,
                                                   int ntiles, int* counter) {
+  extern __shared__ __align__(16) unsigned char ens_sbl[];
   __shared__ int s_tile;
   for (;;) {
     if (threadIdx.x == 0) s_tile = atomicAdd(counter, 1);
@@ -58,7 +65,8 @@ __global__ void __launch_bounds__(256) k_ensemble(const AsmArgs* __restrict__ ar
     if ((int)threadIdx.x < T.count) {
       const AsmArgs a = args[T.member];
       const int idx = T.first + threadIdx.x;
-      assemble_column<MODE_FACT, TL, ATOMIC>(a, a.tri_list ? a.tri_list[idx] : idx);
+      assemble_column<MODE_FACT, TL, ATOMIC, false, double, true>(a, a.tri_list ? a.tri_list[idx] : idx,
+                                                                  reinterpret_cast<TL*>(ens_sbl) + threadIdx.x);
     }
   }
 }
@@ -137,11 +145,11 @@ int build_candidate(bp_ensemble* e, int cpb, int colored, cudaStream_t s, Candid
   if (e->precision == BP_F64)
     BP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm,
                                                               colored ? k_ensemble<double, false> : k_ensemble<double, true>,
-                                                              cpb, 0));
+                                                              cpb, ens_smem<double>(cpb)));
   else
     BP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm,
                                                               colored ? k_ensemble<float, false> : k_ensemble<float, true>,
-                                                              cpb, 0));
+                                                              cpb, ens_smem<float>(cpb)));
   BP_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, e->device));
   c->grid = std::max(1, per_sm) * nsm;
   return BP_OK;
@@ -157,15 +165,17 @@ int launch_candidate(bp_ensemble* e, const Candidate& c, cudaStream_t s) {
     const int grid = std::min(c.grid, nt);
     int* ctr = e->counters + 1 + k;
     if (e->precision == BP_F64) {
+      const size_t sm = ens_smem<double>(c.cpb);
       if (c.colored)
-        k_ensemble<double, false><<<grid, c.cpb, 0, s>>>(e->args_color, tl, nt, ctr);
+        k_ensemble<double, false><<<grid, c.cpb, sm, s>>>(e->args_color, tl, nt, ctr);
       else
-        k_ensemble<double, true><<<grid, c.cpb, 0, s>>>(e->args_atomic, tl, nt, ctr);
+        k_ensemble<double, true><<<grid, c.cpb, sm, s>>>(e->args_atomic, tl, nt, ctr);
     } else {
+      const size_t sm = ens_smem<float>(c.cpb);
       if (c.colored)
-        k_ensemble<float, false><<<grid, c.cpb, 0, s>>>(e->args_color, tl, nt, ctr);
+        k_ensemble<float, false><<<grid, c.cpb, sm, s>>>(e->args_color, tl, nt, ctr);
       else
-        k_ensemble<float, true><<<grid, c.cpb, 0, s>>>(e->args_atomic, tl, nt, ctr);
+        k_ensemble<float, true><<<grid, c.cpb, sm, s>>>(e->args_atomic, tl, nt, ctr);
     }
   }
   BP_CUDA_TRY(cudaGetLastError());
@@ -242,6 +252,16 @@ extern "C" int bp_ensemble_create(bp_mesh* const* members, int count, const doub
   if (cudaMemcpyAsync(e->args_atomic, aa.data(), count * sizeof(AsmArgs), cudaMemcpyHostToDevice, s) ||
       cudaMemcpyAsync(e->args_color, ac.data(), count * sizeof(AsmArgs), cudaMemcpyHostToDevice, s) ||
       cudaMemcpyAsync(e->init, it.data(), count * sizeof(InitItem), cudaMemcpyHostToDevice, s))
+    return fail(BP_ECUDA);
+  // 256 columns per block need 48 KiB of dynamic shared memory besides the static tile index: opt in
+  if (cudaFuncSetAttribute(k_ensemble<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)ens_smem<double>(256)) ||
+      cudaFuncSetAttribute(k_ensemble<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)ens_smem<double>(256)) ||
+      cudaFuncSetAttribute(k_ensemble<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)ens_smem<float>(256)) ||
+      cudaFuncSetAttribute(k_ensemble<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)ens_smem<float>(256)))
     return fail(BP_ECUDA);
   for (int cpb : {32, 64, 128, 256})
     for (int colored : {0, 1}) {
