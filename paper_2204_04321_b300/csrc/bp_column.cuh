@@ -242,7 +242,8 @@ __device__ __forceinline__ Dual<TL, NL> operator*(double s, const Dual<TL, NL>& 
 // FP64 and rounded once, everything per quadrature point runs in FP32.
 // SBL (factored method): the in-plane coefficients B(Lambda_a, Lambda_b) depend on the triangle only;
 // they are formed once per column into shared memory (sbl: this thread's first slot, consecutive
-// slots blockDim.x apart) and read per wedge instead of being formed again at every level.
+// slots blockDim.x apart; 24 slots) and read per wedge instead of being formed again at every
+// level.  With FP64 or FP32 lanes the carried element block takes 21 more slots there.
 template <int MODE, class TL, bool ATOMIC, bool PICARD = false, class TV = double, bool SBL = false>
 __device__ __forceinline__ void assemble_column(const AsmArgs& A, const int t, TL* sbl = nullptr) {
   static_assert(std::is_same<TV, double>::value || (MODE == MODE_FACT && std::is_same<TL, float>::value),
@@ -348,12 +349,17 @@ __device__ __forceinline__ void assemble_column(const AsmArgs& A, const int t, T
   // block of the same J entries) instead of being scattered twice: 108 atomics per wedge, not 144.
   constexpr bool kAhead = (std::is_same<TL, float>::value || std::is_same<TL, double>::value) && MODE == MODE_FACT;
   double2 nxt[3];
-  TL Kc[21];  // carried top-top block (upper triangle of local dofs 6..11)
+  // carried top-top block (upper triangle of local dofs 6..11): in shared memory after the in-plane
+  // coefficients with SBL (slots 24..44), else in registers
+  TL Kc_r[SBL ? 1 : 21];
+  const int kcs = SBL ? (int)blockDim.x : 1;
+  TL* const Kc0 = SBL ? sbl + 24 * kcs : Kc_r;
+#define KC(k) Kc0[(k) * kcs]
   if constexpr (kAhead) {
 #pragma unroll
     for (int a = 0; a < 3; ++a) nxt[a] = *reinterpret_cast<const double2*>(A.U + ubase[a] + 2);
 #pragma unroll
-    for (int k = 0; k < 21; ++k) Kc[k] = TL(0);
+    for (int k = 0; k < 21; ++k) KC(k) = TL(0);
   }
 
   for (int l = 0; l < L; ++l) {
@@ -446,7 +452,7 @@ __device__ __forceinline__ void assemble_column(const AsmArgs& A, const int t, T
 #pragma unroll
       for (int i = 0; i < 6; ++i)
 #pragma unroll
-        for (int j = i; j < 6; ++j) K[uidx(i, j)] = Kc[uidx6(i, j)];
+        for (int j = i; j < 6; ++j) K[uidx(i, j)] = KC(uidx6(i, j));
     }
 
     if constexpr (MODE == MODE_DUAL) {
@@ -833,7 +839,7 @@ __device__ __forceinline__ void assemble_column(const AsmArgs& A, const int t, T
 #pragma unroll
             for (int i = 6; i < 12; ++i)
 #pragma unroll
-              for (int j = i; j < 12; ++j) Kc[uidx6(i - 6, j - 6)] = K[uidx(i, j)];
+              for (int j = i; j < 12; ++j) KC(uidx6(i - 6, j - 6)) = K[uidx(i, j)];
           }
         }
 #pragma unroll
@@ -861,7 +867,7 @@ __device__ __forceinline__ void assemble_column(const AsmArgs& A, const int t, T
             const int nj = j >> 1, cj = j & 1, kj = nj / 3, bj = nj % 3;
             if constexpr (kAhead) {
               if (i >= 6 && l + 1 < L) {  // top-top block: carried to the next wedge
-                Kc[uidx6(i - 6, j - 6)] = K[uidx(i, j)];
+                KC(uidx6(i - 6, j - 6)) = K[uidx(i, j)];
                 continue;
               }
             }
@@ -894,6 +900,7 @@ __device__ __forceinline__ void assemble_column(const AsmArgs& A, const int t, T
     scatter_add<ATOMIC>(A.R + ubase[a] + 2 * L, to_r(carry[a][0]));
     scatter_add<ATOMIC>(A.R + ubase[a] + 2 * L + 1, to_r(carry[a][1]));
   }
+#undef KC
 }
 
 }  // namespace

@@ -44,10 +44,11 @@ __global__ void k_ens_init(const InitItem* __restrict__ items, int count, int* _
   }
 }
 
-// dynamic shared memory of a block: the per-column in-plane coefficients, 24 lanes per thread
+// dynamic shared memory of a block: the per-column in-plane coefficients and the carried element
+// block, 45 lanes per thread
 template <class TL>
 size_t ens_smem(int cpb) {
-  return 24 * (size_t)cpb * sizeof(TL);
+  return 45 * (size_t)cpb * sizeof(TL);
 }
 
 template <class TL, bool ATOMIC>
@@ -253,7 +254,7 @@ extern "C" int bp_ensemble_create(bp_mesh* const* members, int count, const doub
       cudaMemcpyAsync(e->args_color, ac.data(), count * sizeof(AsmArgs), cudaMemcpyHostToDevice, s) ||
       cudaMemcpyAsync(e->init, it.data(), count * sizeof(InitItem), cudaMemcpyHostToDevice, s))
     return fail(BP_ECUDA);
-  // 256 columns per block need 48 KiB of dynamic shared memory besides the static tile index: opt in
+  // 256 columns per block need 90 KiB of dynamic shared memory: opt in
   if (cudaFuncSetAttribute(k_ensemble<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)ens_smem<double>(256)) ||
       cudaFuncSetAttribute(k_ensemble<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
