@@ -28,9 +28,8 @@ __global__ void __launch_bounds__(128, min_blocks<TL, TV>()) k_assemble(const As
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= A.count) return;
   const int t = A.tri_list ? A.tri_list[idx] : idx;
-  if constexpr (MODE == MODE_FACT) {  // in-plane coefficients (24 lanes) and carried block (21; not paired lanes)
-    constexpr int kSlots = std::is_same<TL, f64x2>::value ? 24 : 45;
-    __shared__ __align__(16) unsigned char sraw[kSlots * 128 * sizeof(TL)];
+  if constexpr (MODE == MODE_FACT) {  // in-plane coefficients (24 lanes) and carried block (21)
+    __shared__ __align__(16) unsigned char sraw[45 * 128 * sizeof(TL)];
     assemble_column<MODE, TL, ATOMIC, PICARD, TV, true>(A, t, reinterpret_cast<TL*>(sraw) + threadIdx.x);
   } else {
     assemble_column<MODE, TL, ATOMIC, PICARD, TV>(A, t);

@@ -347,7 +347,9 @@ __device__ __forceinline__ void assemble_column(const AsmArgs& A, const int t, T
   // Sum-factorised FP64 and FP32 lanes: the next level's velocities are loaded one wedge ahead, and
   // the element-matrix block of the top level is carried to the next wedge (where it is the bottom
   // block of the same J entries) instead of being scattered twice: 108 atomics per wedge, not 144.
-  constexpr bool kAhead = (std::is_same<TL, float>::value || std::is_same<TL, double>::value) && MODE == MODE_FACT;
+  constexpr bool kAhead =
+      (std::is_same<TL, float>::value || std::is_same<TL, double>::value || (SBL && std::is_same<TL, f64x2>::value)) &&
+      MODE == MODE_FACT;
   double2 nxt[3];
   // carried top-top block (upper triangle of local dofs 6..11): in shared memory after the in-plane
   // coefficients with SBL (slots 24..44), else in registers
