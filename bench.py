@@ -624,9 +624,11 @@ def newton_section(capi, synth, dm, mesh, dev, skip_large=False, reps=3):
 
 
 def kernel_hash():
-    """Hash of the assembly kernel's source text: the per-column body and the shared device helpers
-    it calls (pattern helpers, conversions, inverse cube root: the tail of the internal header)."""
+    """Hash of the assembly kernel's source code: the per-column body and the shared device helpers
+    it calls (pattern helpers, conversions, inverse cube root: the tail of the internal header),
+    with comments and blank lines removed (a comment edit does not change the kernel)."""
     import hashlib
+    import re
     csrc = os.path.join(ROOT, "paper_2204_04321_b300", "csrc")
     with open(os.path.join(csrc, "bp_column.cuh")) as f:
         src = f.read()
@@ -634,6 +636,9 @@ def kernel_hash():
     with open(os.path.join(csrc, "bp_internal.cuh")) as f:
         helpers = f.read()
     src += helpers[helpers.index("// The kernels read velocity pairs"):]
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", "", src)
+    src = "\n".join(line.rstrip() for line in src.splitlines() if line.strip())
     return hashlib.sha256(src.encode()).hexdigest()[:16]
 
 

@@ -344,9 +344,10 @@ __device__ __forceinline__ void assemble_column(const AsmArgs& A, const int t, T
     hb[2] = to_lane<TV>(bs + 0.5 * b2);
   }
 
-  // Sum-factorised FP64 and FP32 lanes: the next level's velocities are loaded one wedge ahead, and
-  // the element-matrix block of the top level is carried to the next wedge (where it is the bottom
-  // block of the same J entries) instead of being scattered twice: 108 atomics per wedge, not 144.
+  // Sum-factorised FP64 and FP32 lanes (and paired lanes with the shared-memory table): the next
+  // level's velocities are loaded one wedge ahead, and the element-matrix block of the top level is
+  // carried to the next wedge (where it is the bottom block of the same J entries) instead of being
+  // scattered twice: 108 scalar atomics per wedge (54 float2 ones for FP32 values), not 144.
   constexpr bool kAhead =
       (std::is_same<TL, float>::value || std::is_same<TL, double>::value || (SBL && std::is_same<TL, f64x2>::value)) &&
       MODE == MODE_FACT;
