@@ -70,3 +70,24 @@ def test_workload_names_agree_between_arms():
     bench = load_bench()
     assert bench.workload_name(224, 10).startswith("dome-100k-tri-x10: ")
     assert "1003520 wedges" in bench.workload_name(224, 10)
+
+
+def test_traffic_record_hash_follows_code_not_comments(tmp_path):
+    """The DRAM-traffic record of the headline kernel is reported only while the kernel's code is
+    the one it was captured from: a comment edit keeps the hash, a code edit changes it."""
+    import shutil
+    bench = load_bench()
+    csrc = os.path.join("paper_2204_04321_b300", "csrc")
+    os.makedirs(tmp_path / csrc)
+    for name in ("bp_column.cuh", "bp_internal.cuh"):
+        shutil.copy(os.path.join(ROOT, csrc, name), tmp_path / csrc / name)
+    bench.ROOT = str(tmp_path)
+    h0 = bench.kernel_hash()
+    col = tmp_path / csrc / "bp_column.cuh"
+    src = col.read_text()
+    i = src.index("\n", src.index("constexpr int MODE_RES")) + 1  # inside the hashed part
+    col.write_text(src[:i] + "// an added comment line\n/* and a block\n   comment */\n\n" + src[i:] +
+                   "\n// trailing note\n")
+    assert bench.kernel_hash() == h0
+    col.write_text(src.replace("TL(0.5) * yy", "TL(0.25) * yy", 1))
+    assert bench.kernel_hash() != h0
