@@ -338,3 +338,32 @@ def slab_mesh(m: int, nlayers: int, slope: float, thickness: float, beta: float,
     b = slope * xy[:, 0]
     return Mesh(xy=xy, tri=tri, bed=b, thick=np.full(xy.shape[0], thickness),
                 beta=np.full(xy.shape[0], beta), sigma=uniform_sigma(nlayers), name="slab")
+
+
+# ---------------------------------------------------------------- warm-start network test inputs
+
+MLP_SHAPES = [(128, 16), (128,), (128, 128), (128,), (128, 128), (128,), (32, 128), (32,)]  # W1 b1 ... W4 b4
+
+
+def dyadic_mlp_case(seed: int, n: int, density: float = 0.125):
+    """A network and a batch whose values are short dyadic fractions: inputs k/4 (|k| <= 8), first-layer
+    weights in {0, +-1/4, +-1/2}, deeper weights +-1/4 on a random `density` fraction of entries,
+    biases k / 2^(2 layer + 2).  Every value is exactly a BF16 number with few significant bits, so
+    the sums a network evaluation forms stay exact in FP32 (the oracle checks that per input).
+
+    Returns (params float32 [39328] in the parameter layout W1, b1, ..., W4, b4 (weights row-major,
+    out x in), X float64 [n, 16], E float64 [n, 32] output errors k/8, |k| <= 8, from which a test
+    builds targets T = Y - E)."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for layer, (wshape, bshape) in enumerate(zip(MLP_SHAPES[0::2], MLP_SHAPES[1::2])):
+        if layer == 0:
+            W = rng.choice(np.array([-0.5, -0.25, 0.0, 0.0, 0.25, 0.5]), size=wshape)
+        else:
+            W = np.where(rng.random(wshape) < density, rng.choice(np.array([-0.25, 0.25]), size=wshape), 0.0)
+        b = rng.integers(-16, 17, size=bshape) / float(2 ** (2 * layer + 4))
+        parts += [W.ravel(), b]
+    params = np.concatenate(parts).astype(np.float32)
+    X = rng.integers(-8, 9, size=(n, 16)) / 4.0
+    E = rng.integers(-8, 9, size=(n, 32)) / 8.0
+    return params, X, E
