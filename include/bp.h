@@ -56,7 +56,8 @@ typedef enum {
   BP_ENAN = 5,      /* a non-finite value was met */
   BP_ENOCONV = 6,   /* an iteration limit was reached before the tolerance */
   BP_EUNSUP = 7,    /* a parameter combination the kernels do not implement (e.g. n != 3) */
-  BP_ESIZE = 8      /* the problem exceeds a fixed capacity of the call (see BP_NOALLOC_MAX_NDOF) */
+  BP_ESIZE = 8,     /* the problem exceeds a fixed capacity of the call (see BP_NOALLOC_MAX_NDOF) */
+  BP_EIO = 9        /* a file could not be read or written, or is not in the expected format */
 } bp_status;
 
 /* Lateral margin condition (paper Sec. 2, third boundary condition, on the vertical faces over the
@@ -274,8 +275,11 @@ typedef struct {
                          to assemble), then Newton steps; 0: Newton from the first step */
   double value32_rtol; /* BP_F32 only, > 0: while ||F|| > value32_rtol ||F(0)|| assemble with
                           BP_F32_ALL (FP32 value path: an inexact residual, rounding ~1e-7 of the
-                          element contributions), then with the FP64 value path; convergence is
-                          always tested on an FP64 residual.  0: FP64 value path throughout */
+                          element contributions), then with the FP64 value path; a residual that
+                          comes out below value32_rtol ||F(0)|| is assembled again with the FP64
+                          value path before it is tested, so convergence is always tested on an
+                          FP64 residual.  0: FP64 value path throughout; values in (0, rtol) are
+                          refused (BP_EINVAL): an FP32 residual could then pass the test */
   int device_loop;    /* 1: the CG iterations run as a device-driven loop (a conditional WHILE graph
                          node, 4 iterations per pass, programmatic launches): the device stops the
                          loop, no host check in between; 0: replays of a captured 8-iteration batch
@@ -312,7 +316,8 @@ void bp_solve_opts_default(bp_solve_opts* opts);
  * (Armijo on the energy; the last trial is taken if none passes).  After a full step that reduced
  * the residual tenfold (the quadratic regime) the next full step is taken without the test.
  * U_dev holds the last iterate on return.
- * Synchronises `stream`.  Errors: BP_EINVAL, BP_ENOMEM, BP_ECUDA, BP_ENAN (non-finite residual),
+ * Synchronises `stream`.  Errors: BP_EINVAL, BP_ENOMEM, BP_ECUDA, BP_ENAN (non-finite residual, or a
+ * non-finite Krylov residual: the solve stops at once),
  * BP_ENOCONV (max_newton reached; the report is filled either way).
  */
 int bp_newton_solve(bp_mesh* mesh, double* U_dev, const bp_solve_opts* opts, bp_solve_report* report,
@@ -390,6 +395,13 @@ int bp_mlp_gradient(bp_mlp* mlp, const uint16_t* X_dev, const float* T_dev, int6
 /* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) with the gradient of the batch; asynchronous. */
 int bp_mlp_train_step(bp_mlp* mlp, const uint16_t* X_dev, const float* T_dev, int64_t n, float lr,
                       void* stream);
+/* Write / read the FP32 master parameters as a NumPy .npy file (format 1.0: a little-endian
+ * float32 vector of bp_mlp_param_count() entries, the layout above), so numpy.save / numpy.load
+ * exchange the same files.  Loading resets Adam (as bp_mlp_set_params) and accepts .npy versions
+ * 1.0-3.0 whose header describes exactly that vector.  Synchronous (default stream).
+ * Errors: BP_EINVAL (NULL), BP_EIO (file not readable / writable, or another array), BP_ECUDA. */
+int bp_mlp_save(const bp_mlp* mlp, const char* path);
+int bp_mlp_load(bp_mlp* mlp, const char* path);
 /* Column features X[nv][16] (BF16) of an uploaded 10-layer mesh, built from the quantities
  * q = (ln(H / 1000 m), asinh(1000 s_x) / 4, asinh(1000 s_y) / 4, ln(beta / 1000)) with the nodal
  * grad s (area-weighted as for the shallow-ice guess): [0..7] hi/lo BF16 splits of the local q
@@ -428,6 +440,23 @@ enum { BP_JUDGE_RESIDUAL = 0, BP_JUDGE_ENERGY = 1, BP_JUDGE_NONE = 2 };
  * BP_ENOMEM, BP_ECUDA.
  */
 int bp_initial_guess_learned(bp_mesh* mesh, bp_mlp* mlp, double* U_dev, int judge, int* used, void* stream);
+/*
+ * The structured decoder of bp_initial_guess_learned on its own: U_dev [ndof] (dof order,
+ * 16-byte aligned) = decoder(Y_dev, shallow-ice guess) for network outputs Y_dev [nv][32] (FP32;
+ * entries 0..3 of each column are read: y_b,u, y_d,u, y_b,v, y_d,v), for any layer count.
+ * The shallow-ice guess is computed into library-owned workspace.  Asynchronous.
+ * Errors: BP_EINVAL (NULL, misaligned U), BP_ENOMEM, BP_ECUDA.
+ */
+int bp_learned_decode(bp_mesh* mesh, const float* Y_dev, double* U_dev, void* stream);
+/*
+ * The decoder's training targets for a velocity field U_dev (a Newton solution, dof order): per
+ * column and component c the scales (s_b, s_d) of the shallow-ice sliding part b_c and deformation
+ * part d_c that minimise |s_b b + s_d d - u|^2 + reg^2 (|b|^2 (s_b - 1)^2 + |d|^2 (s_d - 1)^2) over the
+ * column's levels (FP64 2 x 2 normal equations; a numerically singular column keeps s = 1),
+ * written as T_dev[a][0..3] = s - 1 clipped to [-5, 5] (FP32; T_dev[a][4..31] = 0), [nv][32].
+ * Asynchronous.  Errors: BP_EINVAL (NULL, misaligned U, reg < 0 or not finite), BP_ENOMEM, BP_ECUDA.
+ */
+int bp_learned_targets(bp_mesh* mesh, const double* U_dev, double reg, float* T_dev, void* stream);
 
 /*
  * Allocation-free variant of bp_assemble_jacobian (R not returned).  The paper has no
@@ -439,7 +468,9 @@ int bp_initial_guess_learned(bp_mesh* mesh, bp_mlp* mlp, double* U_dev, int judg
  * until the process exits; the call itself performs no allocation.
  *   - J_vals_dev, precision, scatter, method: as for bp_assemble_jacobian; J is overwritten.
  *   - The first call on each device looks up the array's device address (cudaGetSymbolAddress)
- *     with that device current; make that first call before any stream capture.
+ *     with that device current; make that first call before any stream capture.  The address is
+ *     kept for the life of the process: do not use this entry point after cudaDeviceReset on that
+ *     device (the library's module, and with it the array, may then be loaded at a new address).
  *   - All calls share the one array and leave their residual in it; each call starts it afresh.
  *     Calls whose executions overlap on the GPU (different streams, or different meshes on the
  *     same device at the same time) race on the array: serialise them.

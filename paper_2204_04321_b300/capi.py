@@ -15,7 +15,7 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libbp.so")
 
-BP_OK, BP_EINVAL, BP_EMESH, BP_ENOMEM, BP_ECUDA, BP_ENAN, BP_ENOCONV, BP_EUNSUP, BP_ESIZE = range(9)
+BP_OK, BP_EINVAL, BP_EMESH, BP_ENOMEM, BP_ECUDA, BP_ENAN, BP_ENOCONV, BP_EUNSUP, BP_ESIZE, BP_EIO = range(10)
 BP_NOALLOC_MAX_NDOF = 1048576
 BP_F64, BP_F32, BP_F64X2, BP_F32_ALL = 0, 1, 2, 3
 BP_SCATTER_AUTO, BP_SCATTER_ATOMIC, BP_SCATTER_COLOR = 0, 1, 2
@@ -118,6 +118,10 @@ SIGNATURES = {
     "bp_mlp_features": (_I, [_P, _P, _P]),
     "bp_mesh_set_beta": (_I, [_P, _P, _P]),
     "bp_initial_guess_learned": (_I, [_P, _P, _P, _I, _P, _P]),
+    "bp_learned_decode": (_I, [_P, _P, _P, _P]),
+    "bp_learned_targets": (_I, [_P, _P, ctypes.c_double, _P, _P]),
+    "bp_mlp_save": (_I, [_P, ctypes.c_char_p]),
+    "bp_mlp_load": (_I, [_P, ctypes.c_char_p]),
     "bp_mesh_set_rate_factor": (_I, [_P, _P, _P]),
 }
 
@@ -368,10 +372,12 @@ class Mlp:
                                        _stream_ptr(stream)), "bp_mlp_train_step")
 
     def save(self, path):
-        np.save(path, self.get_params())
+        """Writes the parameters as a .npy file (bp_mlp_save)."""
+        _check(lib().bp_mlp_save(self.handle, os.fsencode(path)), "bp_mlp_save")
 
     def load(self, path):
-        self.set_params(np.load(path))
+        """Reads parameters written by save() or numpy.save (bp_mlp_load)."""
+        _check(lib().bp_mlp_load(self.handle, os.fsencode(path)), "bp_mlp_load")
 
     def close(self):
         if getattr(self, "handle", None) is not None and self.handle.value:
@@ -404,6 +410,17 @@ def bp_mesh_set_beta(handle, beta, stream=None) -> None:
     b = np.ascontiguousarray(beta, dtype=np.float64)
     _check(lib().bp_mesh_set_beta(handle, b.ctypes.data_as(ctypes.c_void_p), _stream_ptr(stream)),
            "bp_mesh_set_beta")
+
+
+def bp_learned_decode(handle, Y, U, stream=None) -> None:
+    """U = structured decoder of the network outputs Y [nv, 32] (float32) on the shallow-ice guess."""
+    _check(lib().bp_learned_decode(handle, _dptr(Y), _dptr(U), _stream_ptr(stream)), "bp_learned_decode")
+
+
+def bp_learned_targets(handle, U, reg, T, stream=None) -> None:
+    """T [nv, 32] (float32) = the decoder's training targets (per-column profile scales) of U."""
+    _check(lib().bp_learned_targets(handle, _dptr(U), float(reg), _dptr(T), _stream_ptr(stream)),
+           "bp_learned_targets")
 
 
 def bp_initial_guess_learned(handle, mlp, U, judge=None, stream=None) -> bool:

@@ -167,7 +167,8 @@ extern "C" int bp_assemble_jacobian(bp_mesh* m, const double* U, double* R, void
 // loaded holds BP_NOALLOC_MAX_NDOF doubles (8 MiB) of it until the process exits.  In host code
 // the name g_noalloc_residual is only a host-side stand-in; the device address is looked up with
 // cudaGetSymbolAddress once per device, with that device current, on the entry point's first
-// call there.
+// call there, and kept for the life of the process (a cudaDeviceReset, which may reload the
+// module at another address, ends the entry point's use on that device).
 static __device__ __align__(256) double g_noalloc_residual[BP_NOALLOC_MAX_NDOF];
 
 namespace {

@@ -315,7 +315,14 @@ extern "C" int bp_ensemble_tune(bp_ensemble* e, int reps, void* stream, double* 
   if (!e || reps < 1) return BP_EINVAL;
   bp_device_guard g(e->device);
   cudaStream_t s = (cudaStream_t)stream;
-  cudaEvent_t a, b;
+  cudaEvent_t a = nullptr, b = nullptr;
+  struct EvFree {  // the events are released on every return path
+    cudaEvent_t *a, *b;
+    ~EvFree() {
+      if (*a) cudaEventDestroy(*a);
+      if (*b) cudaEventDestroy(*b);
+    }
+  } evfree{&a, &b};
   BP_CUDA_TRY(cudaEventCreate(&a));
   BP_CUDA_TRY(cudaEventCreate(&b));
   double best = 1e300;
@@ -339,8 +346,6 @@ extern "C" int bp_ensemble_tune(bp_ensemble* e, int reps, void* stream, double* 
       best_i = (int)i;
     }
   }
-  cudaEventDestroy(a);
-  cudaEventDestroy(b);
   if (chosen) {
     chosen[0] = e->cands[best_i].cpb;
     chosen[1] = e->cands[best_i].colored ? BP_SCATTER_COLOR : BP_SCATTER_ATOMIC;

@@ -29,6 +29,7 @@ extern "C" const char* bp_strerror(int status) {
     case BP_ENOCONV: return "iteration limit reached before the tolerance";
     case BP_EUNSUP: return "unsupported parameters (the kernels implement Glen exponent n = 3)";
     case BP_ESIZE: return "problem exceeds the fixed capacity of this call (BP_NOALLOC_MAX_NDOF dofs)";
+    case BP_EIO: return "file could not be read or written, or is not in the expected format";
     default: return "unknown status";
   }
 }

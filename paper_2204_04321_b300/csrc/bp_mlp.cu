@@ -18,7 +18,9 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
+#include <string>
 #include <vector>
 
 #include "bp_internal.cuh"
@@ -528,6 +530,42 @@ __global__ void k_scatter_prediction(const float* __restrict__ Y, const double* 
   }
 }
 
+// Decoder training targets: per column and component, the scales (s_b, s_d) of the shallow-ice
+// sliding part b (the bed value, at every level) and deformation part d = u_sia - b that minimise
+//   |s_b b + s_d d - u|^2 + reg^2 (|b|^2 (s_b - 1)^2 + |d|^2 (s_d - 1)^2)
+// (2 x 2 normal equations, solved in FP64 by Cramer's rule; a numerically singular system keeps
+// s = 1), written as y = s - 1 clipped to [-5, 5] in T[a][0..3]; T[a][4..31] = 0.
+__global__ void k_profile_scales(const double* __restrict__ U, const double* __restrict__ Usia, int nv, int L,
+                                 double reg2, float* __restrict__ T) {
+  const int a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= nv) return;
+  const int64_t base = 2LL * a * (L + 1);
+  float* t = T + (int64_t)a * OUT;
+  for (int c = 0; c < 2; ++c) {
+    const double b = Usia[base + c];
+    double bb = 0.0, dd = 0.0, bd = 0.0, ub = 0.0, ud = 0.0;
+    for (int l = 0; l <= L; ++l) {
+      const double d = Usia[base + 2 * l + c] - b, u = U[base + 2 * l + c];
+      bb += b * b;
+      dd += d * d;
+      bd += b * d;
+      ub += u * b;
+      ud += u * d;
+    }
+    const double a11 = (1.0 + reg2) * bb, a22 = (1.0 + reg2) * dd, a12 = bd;
+    const double r1 = ub + reg2 * bb, r2 = ud + reg2 * dd;
+    const double det = a11 * a22 - a12 * a12;
+    double sb = 1.0, sd = 1.0;
+    if (det > 1e-30 * (a11 * a22 + 1e-300)) {
+      sb = (r1 * a22 - r2 * a12) / det;
+      sd = (a11 * r2 - a12 * r1) / det;
+    }
+    t[2 * c] = (float)fmin(fmax(sb - 1.0, -5.0), 5.0);
+    t[2 * c + 1] = (float)fmin(fmax(sd - 1.0, -5.0), 5.0);
+  }
+  for (int j = 4; j < OUT; ++j) t[j] = 0.f;
+}
+
 uint64_t splitmix64(uint64_t x) {
   x += 0x9E3779B97F4A7C15ull;
   x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
@@ -659,6 +697,70 @@ extern "C" int bp_mlp_get_params(const bp_mlp* net, float* host, int64_t n, void
   return BP_OK;
 }
 
+// Parameters on disk: the NumPy .npy format (version 1.0) of a little-endian float32 vector of
+// NPARAM entries, so that numpy.save / numpy.load read and write the same files.
+namespace {
+std::string npy_header() {
+  std::string h = "{'descr': '<f4', 'fortran_order': False, 'shape': (" + std::to_string(NPARAM) + ",), }";
+  const size_t pre = 10;  // magic (6), version (2), header length (2)
+  while ((pre + h.size() + 1) % 64 != 0) h.push_back(' ');
+  h.push_back('\n');
+  return h;
+}
+}  // namespace
+
+extern "C" int bp_mlp_save(const bp_mlp* net, const char* path) {
+  if (!net || !path) return BP_EINVAL;
+  std::vector<float> p(NPARAM);
+  int rc = bp_mlp_get_params(net, p.data(), NPARAM, nullptr);
+  if (rc) return rc;
+  const std::string h = npy_header();
+  FILE* f = std::fopen(path, "wb");
+  if (!f) return BP_EIO;
+  const unsigned char magic[8] = {0x93, 'N', 'U', 'M', 'P', 'Y', 1, 0};
+  const unsigned char hl[2] = {(unsigned char)(h.size() & 0xFF), (unsigned char)(h.size() >> 8)};
+  bool ok = std::fwrite(magic, 1, 8, f) == 8 && std::fwrite(hl, 1, 2, f) == 2 &&
+            std::fwrite(h.data(), 1, h.size(), f) == h.size() &&
+            std::fwrite(p.data(), sizeof(float), NPARAM, f) == (size_t)NPARAM;  // little-endian host
+  ok = (std::fclose(f) == 0) && ok;
+  return ok ? BP_OK : BP_EIO;
+}
+
+extern "C" int bp_mlp_load(bp_mlp* net, const char* path) {
+  if (!net || !path) return BP_EINVAL;
+  FILE* f = std::fopen(path, "rb");
+  if (!f) return BP_EIO;
+  struct Closer {
+    FILE* f;
+    ~Closer() { std::fclose(f); }
+  } closer{f};
+  unsigned char pre[8];
+  if (std::fread(pre, 1, 8, f) != 8 || pre[0] != 0x93 || std::memcmp(pre + 1, "NUMPY", 5) != 0) return BP_EIO;
+  size_t hlen = 0;
+  if (pre[6] == 1) {
+    unsigned char b[2];
+    if (std::fread(b, 1, 2, f) != 2) return BP_EIO;
+    hlen = b[0] | ((size_t)b[1] << 8);
+  } else if (pre[6] == 2 || pre[6] == 3) {
+    unsigned char b[4];
+    if (std::fread(b, 1, 4, f) != 4) return BP_EIO;
+    hlen = b[0] | ((size_t)b[1] << 8) | ((size_t)b[2] << 16) | ((size_t)b[3] << 24);
+  } else {
+    return BP_EIO;
+  }
+  if (hlen > 4096) return BP_EIO;
+  std::string h(hlen, '\0');
+  if (std::fread(&h[0], 1, hlen, f) != hlen) return BP_EIO;
+  // the header must describe a C-ordered little-endian float32 vector of exactly NPARAM entries
+  const std::string shape = "(" + std::to_string(NPARAM) + ",)";
+  if (h.find("'<f4'") == std::string::npos || h.find("'fortran_order': False") == std::string::npos ||
+      h.find(shape) == std::string::npos)
+    return BP_EIO;
+  std::vector<float> p(NPARAM);
+  if (std::fread(p.data(), sizeof(float), NPARAM, f) != (size_t)NPARAM) return BP_EIO;
+  return bp_mlp_set_params(net, p.data(), NPARAM, nullptr);
+}
+
 extern "C" int bp_mlp_create(uint64_t seed, bp_mlp** out) {
   if (!out) return BP_EINVAL;
   *out = nullptr;
@@ -764,6 +866,43 @@ extern "C" int bp_mlp_features(bp_mesh* m, uint16_t* X, void* stream) {
   return BP_OK;
 }
 
+namespace {
+// U = decoder(Y, shallow-ice guess), the guess computed into Usia (workspace)
+int decode_with_sia(bp_mesh* m, const float* Y, double* Usia, double* U, cudaStream_t s) {
+  int rc = bp_initial_guess(m, BP_GUESS_SIA, Usia, s);
+  if (rc) return rc;
+  k_scatter_prediction<<<(m->nv + 127) / 128, 128, 0, s>>>(Y, Usia, m->nv, m->nl, U);
+  BP_CUDA_TRY(cudaGetLastError());
+  return BP_OK;
+}
+}  // namespace
+
+extern "C" int bp_learned_decode(bp_mesh* m, const float* Y, double* U, void* stream) {
+  if (!m || !Y || !U || !bp_aligned16(U)) return BP_EINVAL;
+  bp_device_guard g(m->device);
+  uint16_t* X = nullptr;
+  float* Yw = nullptr;
+  double *Usia = nullptr, *R = nullptr, *red = nullptr;
+  int rc = bp_learned_scratch(m, &X, &Yw, &Usia, &R, &red);
+  if (rc) return rc;
+  return decode_with_sia(m, Y, Usia, U, (cudaStream_t)stream);
+}
+
+extern "C" int bp_learned_targets(bp_mesh* m, const double* U, double reg, float* T, void* stream) {
+  if (!m || !U || !T || !bp_aligned16(U) || !(reg >= 0) || !std::isfinite(reg)) return BP_EINVAL;
+  bp_device_guard g(m->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  uint16_t* X = nullptr;
+  float* Yw = nullptr;
+  double *Usia = nullptr, *R = nullptr, *red = nullptr;
+  int rc = bp_learned_scratch(m, &X, &Yw, &Usia, &R, &red);
+  if (rc) return rc;
+  if ((rc = bp_initial_guess(m, BP_GUESS_SIA, Usia, s))) return rc;
+  k_profile_scales<<<(m->nv + 127) / 128, 128, 0, s>>>(U, Usia, m->nv, m->nl, reg * reg, T);
+  BP_CUDA_TRY(cudaGetLastError());
+  return BP_OK;
+}
+
 extern "C" int bp_initial_guess_learned(bp_mesh* m, bp_mlp* net, double* U, int judge, int* used, void* stream) {
   if (!m || !net || !U || !bp_aligned16(U)) return BP_EINVAL;
   if (judge < BP_JUDGE_RESIDUAL || judge > BP_JUDGE_NONE) return BP_EINVAL;
@@ -775,11 +914,9 @@ extern "C" int bp_initial_guess_learned(bp_mesh* m, bp_mlp* net, double* U, int 
   double *Usia = nullptr, *R = nullptr, *red = nullptr;
   int rc = bp_learned_scratch(m, &X, &Y, &Usia, &R, &red);
   if (rc) return rc;
-  if ((rc = bp_initial_guess(m, BP_GUESS_SIA, Usia, s))) return rc;
   if ((rc = bp_mlp_features(m, X, s))) return rc;
   if ((rc = launch_forward(net, X, m->nv, Y, false, s))) return rc;
-  k_scatter_prediction<<<(m->nv + 127) / 128, 128, 0, s>>>(Y, Usia, m->nv, m->nl, U);
-  BP_CUDA_TRY(cudaGetLastError());
+  if ((rc = decode_with_sia(m, Y, Usia, U, s))) return rc;
   if ((rc = check_err(net, s))) return rc;
   // the FP64 residual norm (or the FP64 energy) judges the prediction against the shallow-ice guess
   bool keep = true;

@@ -514,9 +514,9 @@ __global__ void __launch_bounds__(UPD_NT) k_cg_init_cols(const Prec<float> P, co
   block_add(rr, scal + 2);
 }
 
-// beta = r_{k+1}.z_{k+1} / r_k.z_k;  p = z + beta p;  stop once r.r <= eta^2 r_0.r_0 (flag 1) or the
-// iteration limit is reached (flag 4).  The scalars are formed once per block; the update runs on
-// (u, v) pairs.
+// beta = r_{k+1}.z_{k+1} / r_k.z_k;  p = z + beta p;  stop once r.r <= eta^2 r_0.r_0 (flag 1), the
+// iteration limit is reached (flag 4) or r.r is not finite (flag 3, a breakdown that the Newton
+// solve reports as BP_ENAN).  The scalars are formed once per block; the update runs on (u, v) pairs.
 // Inside the device-driven loop (set_loop != 0) the first thread of block 0 also sets the loop's
 // condition on every path: 1 only when no stop flag is up after this iteration, so the loop ends at
 // convergence, at the iteration limit, or after a breakdown flagged by the update.
@@ -534,11 +534,12 @@ __global__ void __launch_bounds__(NT) k_cg_direction(const int* kbase, int j, co
     if (!done) {
       const int k = *kbase + j;
       const double rr = scal[3 * (k + 1) + 2];
-      const bool conv = rr <= cgpar[0] * scal[2] || !isfinite(rr);
+      const bool bad = !isfinite(rr);
+      const bool conv = rr <= cgpar[0] * scal[2];
       const bool limit = (double)(k + 1) >= cgpar[1];
-      done = conv || limit;
+      done = bad || conv || limit;
       s_beta = (V)(scal[3 * (k + 1) + 1] / scal[3 * k + 1]);
-      if (done && blockIdx.x == 0) *stop = conv ? 1 : 4;
+      if (done && blockIdx.x == 0) *stop = bad ? 3 : conv ? 1 : 4;
     }
     s_done = done;
     if (set_loop && blockIdx.x == 0) cudaGraphSetConditional(loop, done ? 0u : 1u);
@@ -1288,7 +1289,12 @@ int cg_solve(bp_mesh* m, const M* J, double eta, int maxit, int check_every, boo
   int taken = k;
   for (int j = 1; j <= k; ++j) {
     const double rr = w->host[3 * j + 2];
-    if (rr <= tol2 * rr0 || !std::isfinite(rr)) {
+    if (!std::isfinite(rr)) {  // breakdown: Newton reports BP_ENAN at once
+      taken = j;
+      *status = 3;
+      break;
+    }
+    if (rr <= tol2 * rr0) {
       taken = j;
       break;
     }
@@ -1850,7 +1856,12 @@ int mdsc_cg_solve(bp_mesh* m, const M* J, double eta, int maxit, bool device_loo
   int taken = k;
   for (int j = 1; j <= k; ++j) {
     const double rr = w->host[3 * j + 2];
-    if (rr <= tol2 * rr0 || !std::isfinite(rr)) {
+    if (!std::isfinite(rr)) {  // breakdown: Newton reports BP_ENAN at once
+      taken = j;
+      *status = 3;
+      break;
+    }
+    if (rr <= tol2 * rr0) {
       taken = j;
       break;
     }
@@ -2047,6 +2058,7 @@ extern "C" int bp_newton_solve(bp_mesh* m, double* U, const bp_solve_opts* opts,
   const bp_solve_opts o = *opts;
   if (o.line_search < 0 || o.line_search > BP_LS_QUADRATIC) return BP_EINVAL;
   if (!(o.picard_rtol >= 0) || !(o.value32_rtol >= 0)) return BP_EINVAL;
+  if (o.value32_rtol > 0 && o.value32_rtol < o.rtol) return BP_EINVAL;  // an FP32 residual could pass the test
   if ((o.device_loop != 0 && o.device_loop != 1) ||
       (o.preconditioner != BP_PREC_COLUMN && o.preconditioner != BP_PREC_MDSC))
     return BP_EINVAL;
@@ -2085,8 +2097,10 @@ extern "C" int bp_newton_solve(bp_mesh* m, double* U, const bp_solve_opts* opts,
     const bool picard = o.picard_rtol > 0 && (k == 0 || rep->history[k - 1] > o.picard_rtol);
     // FP32 value path (inexact residual) while the previous residual was above value32_rtol; a
     // residual that comes out below it is assembled again with the FP64 value path before it is
-    // tested or used, so that convergence is always judged on the FP64 residual
+    // tested or used, so that convergence is always judged on the FP64 residual (value32_rtol is
+    // 0 or at least rtol: every residual that can pass the test is an FP64 one)
     bool v32 = f32 && o.value32_rtol > 0 && (k == 0 || rep->history[k - 1] > o.value32_rtol);
+    const double v32_exit = o.value32_rtol * fref;
     double fn;
     for (;;) {
       if ((rc = bp_assemble_jacobian_ex(m, U, w->R, w->J, v32 ? BP_F32_ALL : o.precision, BP_SCATTER_ATOMIC,
@@ -2094,7 +2108,7 @@ extern "C" int bp_newton_solve(bp_mesh* m, double* U, const bp_solve_opts* opts,
         return rc;
       if ((rc = dot_host(m, w->R, w->R, m->ndof, s, &fn))) return rc;
       fn = std::sqrt(fn);
-      if (v32 && std::isfinite(fn) && fn <= o.value32_rtol * fref) {
+      if (v32 && std::isfinite(fn) && fn <= v32_exit) {
         v32 = false;
         continue;
       }

@@ -25,6 +25,7 @@ from . import capi, synth
 TRAIN_SEED0 = 10000   # beta seeds of the training / validation solutions
 TEST_SEED0 = 90000    # unseen beta seeds of the evaluation
 FIT_REG = 0.1         # Tikhonov weight of the per-column profile fit toward the shallow-ice scales
+                      # (the fit itself is bp_learned_targets)
 HERE = os.path.dirname(os.path.abspath(__file__))
 DEFAULT_WEIGHTS = os.path.join(HERE, "weights", "warmstart_dome224_l10.npy")
 
@@ -74,36 +75,13 @@ def solve(dm, precision=capi.BP_F32, guess="sia", mlp=None, max_krylov=4000, **o
     return U, rep
 
 
-def profile_scales(Ucol, Scol, reg=FIT_REG):
-    """Targets of the structured decoder: for each column [n, 11, 2] and component, the scales
-    (1 + y_b, 1 + y_d) of the shallow-ice sliding part b and deformation part d(sigma) that best fit
-    the solution in least squares, regularised toward 1 with weight reg^2 (||b||^2, ||d||^2).
-    Returns y = scale - 1 as [n, 4] = (y_b,u, y_d,u, y_b,v, y_d,v), clipped to [-5, 5]."""
-    import torch
-    out = []
-    for c in range(2):
-        u = Ucol[:, :, c]
-        b = Scol[:, :1, c].expand_as(u)
-        d = Scol[:, :, c] - b
-        bb, dd, bd = (b * b).sum(1), (d * d).sum(1), (b * d).sum(1)
-        ub, ud = (u * b).sum(1), (u * d).sum(1)
-        r2 = reg * reg
-        a11, a22, a12 = bb * (1 + r2), dd * (1 + r2), bd
-        r1, r2v = ub + r2 * bb, ud + r2 * dd
-        det = a11 * a22 - a12 * a12
-        ok = det > 1e-30 * (a11 * a22 + 1e-300)
-        sb = torch.where(ok, (r1 * a22 - r2v * a12) / torch.where(ok, det, torch.ones_like(det)), torch.ones_like(det))
-        sd = torch.where(ok, (a11 * r2v - a12 * r1) / torch.where(ok, det, torch.ones_like(det)), torch.ones_like(det))
-        out += [(sb - 1).clamp(-5, 5), (sd - 1).clamp(-5, 5)]
-    return torch.stack(out, 1)
-
-
 def generate(mesh, seeds, cols_per_solution=4096, precision=capi.BP_F32, log=None):
     """Solutions for each beta seed; returns X [n, 16] bfloat16 and T [n, 32] float32 (CUDA)."""
     import torch
     dm = capi.DeviceMesh(mesh)
     nv = mesh.nv
     Xall = torch.empty(nv, 16, dtype=torch.bfloat16, device=dm.device)
+    Tall = torch.empty(nv, 32, dtype=torch.float32, device=dm.device)
     Xs, Ts, stats = [], [], []
     for i, seed in enumerate(seeds):
         beta = synth.lognormal_beta_field_torch(mesh.xy, seed, dm.device)
@@ -114,12 +92,9 @@ def generate(mesh, seeds, cols_per_solution=4096, precision=capi.BP_F32, log=Non
         capi.bp_mlp_features(dm.handle, Xall)
         cols = torch.as_tensor(np.random.default_rng(seed).choice(nv, min(cols_per_solution, nv), replace=False),
                                device=dm.device)
-        S = torch.empty_like(U)
-        capi.bp_initial_guess(dm.handle, capi.BP_GUESS_SIA, S)
-        T = torch.zeros(len(cols), 32, dtype=torch.float32, device=dm.device)
-        T[:, :4] = profile_scales(U.view(nv, 11, 2)[cols], S.view(nv, 11, 2)[cols]).float()
+        capi.bp_learned_targets(dm.handle, U, FIT_REG, Tall)   # per-column profile scales (kernel)
         Xs.append(Xall[cols].clone())
-        Ts.append(T)
+        Ts.append(Tall[cols].clone())
         stats.append({"seed": seed, "newton_iters": rep["newton_iters"], "krylov_iters": rep["krylov_iters"],
                       "s": rep["wall_s"]})
         if log and (i % 100 == 0 or i == len(seeds) - 1):

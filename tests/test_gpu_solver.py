@@ -253,8 +253,12 @@ def test_fp32_value_path_steps_then_fp64_reach_the_same_solution(geometry):
         steps.append(rep["value32_steps"])
     assert steps[0] == 0 and steps[1] >= 1
     assert rel_inf(sols[0], sols[1]) <= 1e-6
-    with pytest.raises(c.BPError):
-        c.bp_newton_solve(dm.handle, U, precision=c.BP_F32, value32_rtol=-1.0)
+    for bad in (-1.0, 5e-9):  # below rtol (1e-8) an FP32 residual could pass the convergence test
+        with pytest.raises(c.BPError) as e:
+            c.bp_newton_solve(dm.handle, U, precision=c.BP_F32, value32_rtol=bad)
+        assert e.value.status == c.BP_EINVAL
+    rc, rep = c.bp_newton_solve(dm.handle, U, precision=c.BP_F32, value32_rtol=1e-8)  # = rtol: allowed
+    assert rc == c.BP_OK
 
 
 @pytest.mark.parametrize("precision", [0, 1])

@@ -68,3 +68,32 @@ def test_noalloc_refuses_meshes_beyond_capacity():
     assert rc == capi.BP_ESIZE
     assert "capacity" in capi.bp_strerror(rc)
     dm.close()
+
+
+def test_noalloc_first_call_on_a_fresh_mesh_allocates_nothing():
+    """A caller that cannot allocate must be able to rely on it: the device's free memory is the
+    same before and after the entry point's first call on a freshly uploaded mesh (the library's
+    kernels are already loaded by an ordinary assembly on another mesh)."""
+    from paper_2204_04321_b300 import capi
+    L = capi.lib()
+    warm = capi.DeviceMesh(synth.dome_mesh(6, 3, 11, 12))
+    Uw = torch.as_tensor(synth.random_velocity(warm.mesh, 1), device="cuda")
+    warm.jacobian(Uw)
+    Jw = torch.empty(warm.nnz, dtype=torch.float64, device="cuda")
+    assert L.bp_assemble_jacobian_noalloc(warm.handle, ctypes.c_void_p(Uw.data_ptr()),
+                                          ctypes.c_void_p(Jw.data_ptr()), capi.BP_F64,
+                                          capi.BP_SCATTER_ATOMIC, capi.BP_JAC_FACTORED, None) == capi.BP_OK
+    mesh = synth.config_small()
+    dm = capi.DeviceMesh(mesh)
+    U = torch.as_tensor(synth.random_velocity(mesh, 103), device="cuda")
+    J = torch.empty(dm.nnz, dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    rc = L.bp_assemble_jacobian_noalloc(dm.handle, ctypes.c_void_p(U.data_ptr()), ctypes.c_void_p(J.data_ptr()),
+                                        capi.BP_F64, capi.BP_SCATTER_ATOMIC, capi.BP_JAC_FACTORED, None)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert rc == capi.BP_OK
+    assert free1 == free0, (free0, free1)
+    dm.close()
+    warm.close()
