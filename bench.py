@@ -6,8 +6,8 @@ the assembly path: gather, basis, interpolation, viscosity, residual, Jacobian, 
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-`--impl reference` times the CPU oracle (single-threaded FP64 C++) on a bounded sample of the
-same workload.  Under torchrun (N > 1) every rank assembles its own replica of the workload
+`--impl reference` times the CPU oracle (FP64 C++, its columns taken colour by colour on all host
+cores) on a bounded sample of the same workload.  Under torchrun (N > 1) every rank assembles its own replica of the workload
 (no collective on the data path: weak scaling); rank 0 prints one JSON line.
 """
 from __future__ import annotations
@@ -29,17 +29,15 @@ import numpy as np  # noqa: E402
 
 METRIC = "residual+Jacobian wedge cells/s"
 UNIT = "wedges/s"
-# FP64 peak from unit counts and clock: 148 SMs x 2 FP64 FMA per clock per SM x 2 flop x 2.032 GHz
-# (2 FMA/clk/SM is the rate behind NVIDIA's nominal 1.25 TFLOP/s; a dependent-chain-free DFMA probe
-# measured 1.87 per clock per SM).  No tensor-core FP64 path is used.
-FP64_PEAK_TFLOPS = 148 * 2 * 2 * 2.032e9 / 1e12
-FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12   # 148 SMs x 128 FP32 lanes x FMA x max clock
-# FP64 flops per wedge of the residual + Jacobian assembly (factored formulation), counted with
-# ncu on 450,000 wedges: (2 x DFMA + DADD + DMUL) / wedges, with the library inverse cube root.
-# Fixed as the algorithm's work figure (the kernel now executes 2,962: its inverse cube root is an
-# FP32 seed plus one FP64 correction).
-FLOPS_PER_WEDGE_JAC64 = 3002  # ncu: (2 DFMA + DADD + DMUL) per wedge of the factored kernel
+# Nominal FP64 rate from unit counts and the maximum clock: 148 SMs x 2 FP64 FMA per clock per SM x
+# 2 flop x 2.032 GHz (the rate behind NVIDIA's nominal 1.25 TFLOP/s).  The roofline's denominator is
+# the rate measured on the device at run time (bp_measure_fma_peak); this one is reported beside it.
+FP64_NOMINAL_TFLOPS = 148 * 2 * 2 * 2.032e9 / 1e12
 L2_FLUSH_BYTES = 512 << 20
+# The FP64 flops per wedge of the assembly kernel (2 DFMA + DADD + DMUL executed, ncu thread-level
+# instruction counters) and its DRAM bytes per wedge come from one capture, recorded in this file
+# with a hash of the kernel's code: both apply only while the hash matches.
+KERNEL_RECORD = os.path.join(ROOT, "profiles", "assemble_jacobian_f64_traffic.json")
 
 
 def read_peaks():
@@ -143,27 +141,66 @@ def dist_env():
     return ws, rank, local
 
 
-def cpu_oracle_sample(seconds_budget: float = 20.0):
-    """Time the CPU oracle (residual + dual-number Jacobian, single thread) on a sample mesh of the
-    workload's generator: a 100 x 100 grid (20,000 triangles) x 10 layers = 200,000 wedges."""
-    import oracle
+def host_cores() -> int:
+    """Host cores this process may run on."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def cpu_model() -> str:
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def oracle_sample_mesh():
+    """The CPU oracle's sample of the workload: the same generators on a 100 x 100 grid (20,000
+    triangles) x 10 layers = 200,000 wedges."""
     from paper_2204_04321_b300 import synth
-    mesh = synth.dome_mesh(100, 10, 201, 202, bed="sinusoidal", beta="field", name="dome-20k-tri-x10")
-    om = oracle.OracleMesh(mesh)
-    U = synth.random_velocity(mesh, 5, 50.0)
-    om.pattern()
+    return synth.dome_mesh(100, 10, 201, 202, bed="sinusoidal", beta="field", name="dome-20k-tri-x10")
+
+
+def time_oracle(om, U, nthreads, max_runs=5, seconds_budget=10.0):
+    """Median time of the oracle's residual + 12-lane dual Jacobian into CSR: the plain element loop
+    (nthreads = 0), or the same loop taken colour by colour on nthreads std::threads."""
     runs = []
     t_end = time.perf_counter() + seconds_budget
     while True:
         t0 = time.perf_counter()
-        om.jacobian(U)
+        if nthreads == 0:
+            om.jacobian(U)
+        else:
+            om.jacobian_colored(U, nthreads)
         runs.append(time.perf_counter() - t0)
-        if time.perf_counter() > t_end or len(runs) >= 5:
+        if time.perf_counter() > t_end or len(runs) >= max_runs:
             break
-    t = statistics.median(runs)
-    return {"value": mesh.nwedges / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+    return statistics.median(runs), len(runs)
+
+
+def cpu_oracle_sample():
+    """The CPU oracle timed on the host's cores (all of them, and one) on the sample mesh."""
+    import oracle
+    from paper_2204_04321_b300 import synth
+    mesh = oracle_sample_mesh()
+    om = oracle.OracleMesh(mesh)
+    U = synth.random_velocity(mesh, 5, 50.0)
+    om.pattern()
+    cores = host_cores()
+    t_all, n_all = time_oracle(om, U, cores, max_runs=7)
+    t_one, n_one = time_oracle(om, U, 0)
+    return {"value": mesh.nwedges / t_all, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "cpu_model": cpu_model(),
             "sample": f"{mesh.name}: {mesh.nwedges} wedges, residual + 12-lane dual Jacobian into CSR, "
-                      f"median of {len(runs)} runs, g++ -O2, 1 thread"}
+                      f"columns colour by colour on {cores} threads, median of {n_all} runs, g++ -O2",
+            "single_thread": {"value": mesh.nwedges / t_one, "unit": UNIT, "cores": 1,
+                              "sample": f"the same, plain element loop, 1 thread, median of {n_one} runs"}}
 
 
 def run_reference(args):
@@ -172,15 +209,16 @@ def run_reference(args):
         return 0
     from paper_2204_04321_b300 import synth
     import oracle
-    mesh = synth.dome_mesh(100, 10, 201, 202, bed="sinusoidal", beta="field", name="dome-20k-tri-x10")
+    mesh = oracle_sample_mesh()
     om = oracle.OracleMesh(mesh)
     U = synth.random_velocity(mesh, 5, 50.0)
     om.pattern()
+    cores = host_cores()
     for _ in range(args.warmup):
-        om.jacobian(U)
+        om.jacobian_colored(U, cores)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        om.jacobian(U)
+        om.jacobian_colored(U, cores)
     dt = time.perf_counter() - t0
     value = mesh.nwedges * args.steps / dt
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
@@ -189,9 +227,10 @@ def run_reference(args):
             "data": "synthetic",
             "config": {"workload": workload_name(args.mesh_m, args.layers),
                        "sample": "each step: dome-20k-tri-x10, 200,000 wedges, same generators",
-                       "oracle": "CPU FP64, 1 thread"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": "dome-20k-tri-x10, 200,000 wedges per step"},
+                       "oracle": f"CPU FP64, columns colour by colour on {cores} threads"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "cpu_model": cpu_model(),
+                             "sample": f"dome-20k-tri-x10, 200,000 wedges per step, {cores} threads"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -352,16 +391,15 @@ def run_ours(args):
 
     newton = newton_section(capi, synth, dm, mesh, dev, skip_large=args.no_large) if not args.no_newton else None
     mlp = mlp_section(capi, dev) if not args.no_mlp else None
-    flops = FLOPS_PER_WEDGE_JAC64 * W
-    achieved = flops / (kernel_ms * 1e-3) / 1e12
+    with open(KERNEL_RECORD) as f:
+        rec = json.load(f)
+    rec_current = rec.get("kernel_source_hash") == kernel_hash()
+    flops_per_wedge = rec["fp64_flops_per_wedge_executed"]
+    achieved = flops_per_wedge * W / (kernel_ms * 1e-3) / 1e12
+    traffic = rec["bytes_per_wedge"] * W if rec_current else None
     peaks = read_peaks()
-    traffic = None
-    prof = os.path.join(ROOT, "profiles", "assemble_jacobian_f64_traffic.json")
-    if os.path.exists(prof):
-        with open(prof) as f:
-            pj = json.load(f)
-        if pj.get("kernel_source_hash") == kernel_hash():
-            traffic = pj["bytes_per_wedge"] * W
+    fp64_peak = capi.bp_measure_fma_peak(capi.BP_F64, stream)
+    fp32_peak = capi.bp_measure_fma_peak(capi.BP_F32, stream)
 
     if not args.no_ensemble:
         ensemble = ensemble_section(capi, synth, dev)
@@ -376,13 +414,17 @@ def run_ours(args):
                        "ndof": dm.ndof, "nnz": dm.nnz, "lanes": "f64, sum-factorised",
                        "scatter": "atomic", "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU",
                        "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MB write outside the timed events)"},
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                         "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
+                         "frac": achieved / fp64_peak, "traffic": traffic,
                          "kernel": "k_assemble<factored, double, atomic>",
-                         "kernel_ms": kernel_ms, "flops_per_wedge": FLOPS_PER_WEDGE_JAC64,
-                         "peak_note": "FP64 from unit counts and clock: 148 SMs x 2 DFMA/clk x 2 x 2.032 GHz "
-                                      "(MEASURED_PEAKS.json has no FP64 entry); HBM measured "
-                                      + str(peaks.get("hbm_gbs")) + " GB/s"},
+                         "kernel_ms": kernel_ms, "flops_per_wedge": flops_per_wedge,
+                         "flops_record_matches_kernel": rec_current,
+                         "peak_note": "FP64 FMA rate measured in this run (bp_measure_fma_peak: 8 independent DFMA "
+                                      "chains per thread, 64 warps per SM); MEASURED_PEAKS.json has no FP64 entry",
+                         "nominal_peak": FP64_NOMINAL_TFLOPS, "frac_of_nominal": achieved / FP64_NOMINAL_TFLOPS,
+                         "fp32_fma_peak_measured": fp32_peak,
+                         "hbm_peak_measured_gbs": peaks.get("hbm_gbs"),
+                         "hbm_achieved_gbs": (traffic / (kernel_ms * 1e-3) / 1e9) if traffic else None},
             "secondary": {
                 "residual_only": {"value": W / (res_ms * 1e-3), "unit": UNIT, "ms": res_ms},
                 "jacobian_f32_lanes": {"value": W / (jac32_ms * 1e-3), "unit": UNIT, "ms": jac32_ms},
@@ -505,7 +547,7 @@ def ensemble_section(capi, synth, dev, reps=5):
            "nnz": int(sum(d.nnz for d in ens.dms)), "dtype": "f64",
            "chosen": {"cells_per_block": chosen[0],
                       "scatter": "color" if chosen[1] == capi.BP_SCATTER_COLOR else "atomic"},
-           "tuner_ms": times, "achieved_tflops": FLOPS_PER_WEDGE_JAC64 * W / (ms * 1e-3) / 1e12,
+           "tuner_ms": times,
            "member_vs_single_launch_rel_inf": {"R": worst_r, "J": worst_j}}
     ens.close()
     del U

@@ -459,6 +459,15 @@ int bp_learned_decode(bp_mesh* mesh, const float* Y_dev, double* U_dev, void* st
 int bp_learned_targets(bp_mesh* mesh, const double* U_dev, double reg, float* T_dev, void* stream);
 
 /*
+ * Measured FMA throughput of the current device (the roofline denominator of the assembly, which
+ * is bound by the FP64 pipe; the paper names no such figure): a kernel of 8 independent FMA chains
+ * per thread, 64 warps per SM on every SM, best of 5 timed launches after a warm-up (CUDA events
+ * on `stream`), 2 flops per FMA.  precision: BP_F64 (DFMA) or BP_F32 (FFMA).  Allocates and frees a
+ * small output buffer; synchronises `stream`.  Errors: BP_EINVAL, BP_ENOMEM, BP_ECUDA.
+ */
+int bp_measure_fma_peak(int precision, double* tflops, void* stream);
+
+/*
  * Allocation-free variant of bp_assemble_jacobian (R not returned).  The paper has no
  * counterpart: this entry point exists for callers that must not allocate device memory once
  * running (a fixed device-memory budget, or a host framework whose allocator owns all device

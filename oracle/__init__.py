@@ -31,7 +31,7 @@ def build(force: bool = False) -> str:
     """Compile the oracle with plain g++ -O2 (no fast-math)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["g++", "-O2", "-std=c++17", "-shared", "-fPIC", "-o", tmp, _SRC])
+        subprocess.check_call(["g++", "-O2", "-std=c++17", "-pthread", "-shared", "-fPIC", "-o", tmp, _SRC])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -54,6 +54,7 @@ def lib():
             P = ctypes.c_void_p
             L.oracle_residual.argtypes = [P, P, P, P]
             L.oracle_jacobian.argtypes = [P, P, P, P, P, P, P]
+            L.oracle_jacobian_colored.argtypes = [P, P, P, P, P, P, ctypes.c_int]
             L.oracle_pattern_nnz.argtypes = [P, P]
             L.oracle_pattern.argtypes = [P, P, P]
             L.oracle_energy.argtypes = [P, P]
@@ -130,6 +131,19 @@ class OracleMesh:
                                    _ptr(rowptr), _ptr(colidx), _ptr(vals), _ptr(R))
         if rc:
             raise RuntimeError(f"oracle_jacobian failed ({rc})")
+        return rowptr, colidx, vals, R
+
+    def jacobian_colored(self, U: np.ndarray, nthreads: int = 1):
+        """The same Jacobian and residual, columns taken colour by colour and each colour's columns
+        split among `nthreads` threads: bitwise the same for every thread count."""
+        rowptr, colidx = self.pattern()
+        U = np.ascontiguousarray(U, dtype=np.float64)
+        vals = np.empty(colidx.shape[0])
+        R = np.empty(self.ndof)
+        rc = lib().oracle_jacobian_colored(self.dptr, _ptr(U), _ptr(rowptr), _ptr(colidx), _ptr(vals), _ptr(R),
+                                           int(nthreads))
+        if rc:
+            raise RuntimeError(f"oracle_jacobian_colored failed ({rc})")
         return rowptr, colidx, vals, R
 
     def jacobian_scipy(self, U: np.ndarray):

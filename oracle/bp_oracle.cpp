@@ -39,10 +39,12 @@
 // Nothing here is blocked, fused or reordered for speed.
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
 #include <map>
+#include <thread>
 #include <utility>
 #include <vector>
 
@@ -547,6 +549,69 @@ int oracle_pattern(const oracle_mesh* d, int64_t* rowptr, int32_t* colidx) {
   return 0;
 }
 
+}  // extern "C"
+
+namespace {
+// The wedges of one column (base triangle t), bottom to top: 12-lane dual residual, element matrix
+// added into the CSR values, element residual into R (nullable).  Returns 2 if the pattern lacks an
+// entry the element needs.
+int jacobian_column(const Mesh& m, int t, const double* U, const int64_t* rowptr, const int32_t* colidx,
+                    double* vals, double* R) {
+  int64_t vert[3];
+  for (int a = 0; a < 3; ++a) vert[a] = m.tri[3 * (int64_t)t + a];
+  for (int l = 0; l < m.nlayers; ++l) {
+    double Ue[12], Re[12], Ke[144];
+    int64_t dofs[12];
+    gather_element(m, l, vert, U, Ue);
+    Dual Ud[12], Rd[12];
+    for (int j = 0; j < 12; ++j) {
+      Ud[j] = dconst(Ue[j]);
+      Ud[j].d[j] = 1.0;
+    }
+    element_residual<Dual>(m, t, l, Ud, Rd);
+    for (int i = 0; i < 12; ++i) {
+      Re[i] = Rd[i].v;
+      for (int j = 0; j < 12; ++j) Ke[12 * i + j] = Rd[i].d[j];
+    }
+    node_dofs(m, l, vert, dofs);
+    for (int i = 0; i < 12; ++i) {
+      if (R) R[dofs[i]] += Re[i];
+      const int32_t* b = colidx + rowptr[dofs[i]];
+      const int32_t* e = colidx + rowptr[dofs[i] + 1];
+      for (int j = 0; j < 12; ++j) {
+        const int32_t* p = std::lower_bound(b, e, (int32_t)dofs[j]);
+        if (p == e || *p != dofs[j]) return 2;  // pattern does not hold this entry
+        vals[p - colidx] += Ke[12 * i + j];
+      }
+    }
+  }
+  return 0;
+}
+
+// Greedy colouring of the base triangles: each triangle, in index order, takes the smallest colour
+// that no earlier triangle sharing one of its vertices has.  Triangles of one colour share no
+// vertex, so their columns write disjoint rows.
+std::vector<std::vector<int>> triangle_colours(const Mesh& m) {
+  std::vector<std::vector<int>> vert_cols(m.nv);
+  std::vector<std::vector<int>> classes;
+  for (int t = 0; t < m.ntri; ++t) {
+    int c = 0;
+    for (;; ++c) {
+      bool used = false;
+      for (int a = 0; a < 3 && !used; ++a)
+        for (int u : vert_cols[m.tri[3 * (int64_t)t + a]]) used |= (u == c);
+      if (!used) break;
+    }
+    if (c == (int)classes.size()) classes.emplace_back();
+    classes[c].push_back(t);
+    for (int a = 0; a < 3; ++a) vert_cols[m.tri[3 * (int64_t)t + a]].push_back(c);
+  }
+  return classes;
+}
+}  // namespace
+
+extern "C" {
+
 // Jacobian values on the given pattern (overwritten) and, if R != NULL, the residual.
 int oracle_jacobian(const oracle_mesh* d, const double* U, const uint8_t* tri_mask,
                     const int64_t* rowptr, const int32_t* colidx, double* vals, double* R) {
@@ -557,36 +622,43 @@ int oracle_jacobian(const oracle_mesh* d, const double* U, const uint8_t* tri_ma
   if (R) std::memset(R, 0, sizeof(double) * ndof);
   for (int t = 0; t < m.ntri; ++t) {
     if (tri_mask && !tri_mask[t]) continue;
-    int64_t vert[3];
-    for (int a = 0; a < 3; ++a) vert[a] = m.tri[3 * (int64_t)t + a];
-    for (int l = 0; l < m.nlayers; ++l) {
-      double Ue[12], Re[12], Ke[144];
-      int64_t dofs[12];
-      gather_element(m, l, vert, U, Ue);
-      Dual Ud[12], Rd[12];
-      for (int j = 0; j < 12; ++j) {
-        Ud[j] = dconst(Ue[j]);
-        Ud[j].d[j] = 1.0;
-      }
-      element_residual<Dual>(m, t, l, Ud, Rd);
-      for (int i = 0; i < 12; ++i) {
-        Re[i] = Rd[i].v;
-        for (int j = 0; j < 12; ++j) Ke[12 * i + j] = Rd[i].d[j];
-      }
-      node_dofs(m, l, vert, dofs);
-      for (int i = 0; i < 12; ++i) {
-        if (R) R[dofs[i]] += Re[i];
-        const int32_t* b = colidx + rowptr[dofs[i]];
-        const int32_t* e = colidx + rowptr[dofs[i] + 1];
-        for (int j = 0; j < 12; ++j) {
-          const int32_t* p = std::lower_bound(b, e, (int32_t)dofs[j]);
-          if (p == e || *p != dofs[j]) return 2;  // pattern does not hold this entry
-          vals[p - colidx] += Ke[12 * i + j];
-        }
-      }
-    }
+    const int rc = jacobian_column(m, t, U, rowptr, colidx, vals, R);
+    if (rc) return rc;
   }
   if (R) lateral_load(m, tri_mask, R);
+  return 0;
+}
+
+// The same Jacobian and residual with the columns taken colour by colour (oracle's own greedy
+// colouring), the columns of one colour split among `nthreads` std::threads.  Every matrix entry
+// and residual row receives its contributions in colour order whatever nthreads is, so the result
+// is bitwise the same for every thread count (it differs from oracle_jacobian only in the order of
+// the additions).  Used to time the oracle on all host cores.
+int oracle_jacobian_colored(const oracle_mesh* d, const double* U, const int64_t* rowptr,
+                            const int32_t* colidx, double* vals, double* R, int nthreads) {
+  const Mesh m = unpack(d);
+  if (!mesh_ok(m) || nthreads < 1) return 1;
+  const int64_t ndof = 2 * (int64_t)m.nv * (m.nlayers + 1);
+  std::memset(vals, 0, sizeof(double) * rowptr[ndof]);
+  if (R) std::memset(R, 0, sizeof(double) * ndof);
+  const std::vector<std::vector<int>> classes = triangle_colours(m);
+  std::atomic<int> status{0};
+  for (const std::vector<int>& cls : classes) {
+    const int64_t n = (int64_t)cls.size();
+    const int nt = (int)std::min<int64_t>(nthreads, n);
+    std::vector<std::thread> pool;
+    for (int k = 0; k < nt; ++k) {
+      pool.emplace_back([&, k]() {
+        for (int64_t i = n * k / nt; i < n * (k + 1) / nt; ++i) {
+          const int rc = jacobian_column(m, cls[i], U, rowptr, colidx, vals, R);
+          if (rc) status.store(rc);
+        }
+      });
+    }
+    for (std::thread& th : pool) th.join();
+    if (status.load()) return status.load();
+  }
+  if (R) lateral_load(m, nullptr, R);
   return 0;
 }
 

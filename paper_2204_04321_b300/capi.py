@@ -121,6 +121,7 @@ SIGNATURES = {
     "bp_learned_decode": (_I, [_P, _P, _P, _P]),
     "bp_learned_targets": (_I, [_P, _P, ctypes.c_double, _P, _P]),
     "bp_mlp_save": (_I, [_P, ctypes.c_char_p]),
+    "bp_measure_fma_peak": (_I, [_I, _P, _P]),
     "bp_mlp_load": (_I, [_P, ctypes.c_char_p]),
     "bp_mesh_set_rate_factor": (_I, [_P, _P, _P]),
 }
@@ -410,6 +411,13 @@ def bp_mesh_set_beta(handle, beta, stream=None) -> None:
     b = np.ascontiguousarray(beta, dtype=np.float64)
     _check(lib().bp_mesh_set_beta(handle, b.ctypes.data_as(ctypes.c_void_p), _stream_ptr(stream)),
            "bp_mesh_set_beta")
+
+
+def bp_measure_fma_peak(precision, stream=None) -> float:
+    """Measured FP64 (BP_F64) or FP32 (BP_F32) FMA throughput of the current device, TFLOP/s."""
+    out = ctypes.c_double()
+    _check(lib().bp_measure_fma_peak(precision, ctypes.byref(out), _stream_ptr(stream)), "bp_measure_fma_peak")
+    return out.value
 
 
 def bp_learned_decode(handle, Y, U, stream=None) -> None:

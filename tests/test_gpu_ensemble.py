@@ -80,3 +80,45 @@ def test_misaligned_fp32_jacobian_is_rejected():
         with pytest.raises(capi.BPError) as e:
             capi.bp_assemble_jacobian(dm.handle, U, None, Jbuf[1:], prec)   # 4-byte, not 8-byte aligned
         assert e.value.status == capi.BP_EINVAL
+
+
+@pytest.mark.slow
+def test_full_ensemble_64_members_sampled_rows_match_oracle():
+    """The 64-member ensemble of the benchmark (5k-50k triangles, 5-20 layers each, 19.5 M wedges)
+    in one autotuned persistent launch: on every member, the rows of 3 sampled base vertices (all
+    levels, both components) against the oracle's element loop over the columns touching them."""
+    from paper_2204_04321_b300 import capi
+    ms = synth.ensemble_members()
+    Us = [synth.random_velocity(m, 500 + i) for i, m in enumerate(ms)]
+    ens = capi.Ensemble(ms, [torch.as_tensor(u, device="cuda") for u in Us], precision=capi.BP_F64)
+    ens.tune(reps=1)
+    ens.assemble()
+    torch.cuda.synchronize()
+    worst_r = worst_j = 0.0
+    for i, (m, U) in enumerate(zip(ms, Us)):
+        om = oracle.OracleMesh(m)
+        rng = np.random.default_rng(7000 + i)
+        verts = np.unique(rng.choice(m.nv, 3, replace=False))
+        mask = np.isin(m.tri, verts).any(axis=1)
+        rows = np.sort(np.concatenate([m.dof(verts, l, c) for l in range(m.nlayers + 1) for c in (0, 1)]))
+        Rc = om.residual(U, tri_mask=mask)
+        R = ens.R[i].cpu().numpy()
+        worst_r = max(worst_r, rel_inf(R[rows], Rc[rows]))
+        rowptr, colidx = (t.cpu().numpy() for t in ens.dms[i].pattern())
+        J = ens.J[i].cpu().numpy()
+        want = {}
+        rowset = set(rows.tolist())
+        for t in np.nonzero(mask)[0]:
+            for l in range(m.nlayers):
+                _, Ke = om.element(U, int(t), l)
+                d = [int(m.dof(m.tri[t, a], l + k, cc)) for k in (0, 1) for a in range(3) for cc in (0, 1)]
+                for a in range(12):
+                    if d[a] in rowset:
+                        for b in range(12):
+                            want[(d[a], d[b])] = want.get((d[a], d[b]), 0.0) + Ke[a, b]
+        got = np.array([J[rowptr[r] + np.searchsorted(colidx[rowptr[r]:rowptr[r + 1]], c)] for (r, c) in want])
+        ref = np.array(list(want.values()))
+        worst_j = max(worst_j, rel_inf(got, ref))
+        assert len(want) == sum(rowptr[r + 1] - rowptr[r] for r in rows)   # no other entry is touched
+    assert worst_r <= 1e-12 and worst_j <= 1e-12, (worst_r, worst_j)
+    ens.close()

@@ -284,3 +284,26 @@ def test_device_driven_cg_loop_matches_host_checked_batches(precision, layers):
     assert rel_inf(U1, U0) <= 1e-6
     with pytest.raises(c.BPError):
         c.bp_newton_solve(dm.handle, U, device_loop=2)
+
+
+@pytest.mark.slow
+def test_mixed_newton_4m_wedges_checked_by_oracle():
+    """The 3,996,180-wedge dome solved with FP32 Jacobian lanes and Krylov from the shallow-ice
+    guess: the oracle's FP64 residual of the solution is at most 1.1e-8 ||F(0)||, and the solution
+    agrees with the plain FP64 path's to 1e-6 (max norm, relative)."""
+    c = capi()
+    mesh = synth.config_large()
+    dm = c.DeviceMesh(mesh)
+    sols = []
+    for precision in (c.BP_F32, c.BP_F64):
+        U = torch.empty(dm.ndof, dtype=torch.float64, device="cuda")
+        c.bp_initial_guess(dm.handle, c.BP_GUESS_SIA, U)
+        rc, rep = c.bp_newton_solve(dm.handle, U, max_krylov=4000, precision=precision)
+        assert rc == c.BP_OK, rep
+        sols.append(U.cpu().numpy())
+        del U
+    dm.close()
+    om = oracle.OracleMesh(mesh)
+    f = np.linalg.norm(om.residual(sols[0])) / np.linalg.norm(om.residual(np.zeros_like(sols[0])))
+    assert f <= 1.1e-8, f
+    assert rel_inf(sols[0], sols[1]) <= 1e-6

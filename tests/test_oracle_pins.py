@@ -612,3 +612,24 @@ def test_arrhenius_rate_factor_values():
     assert cold < A[0] < warm
     # Q = 115 kJ/mol above -10 C: A(-2 C) / A(-10 C) = exp(Q/R (1/263.15 - 1/271.15))
     assert warm / A[0] == pytest.approx(math.exp(1.15e5 / 8.314 * (1 / 263.15 - 1 / 271.15)), rel=1e-12)
+
+
+def test_threaded_colored_oracle_is_bitwise_independent_of_the_thread_count():
+    """The coloured, threaded oracle (used to time the oracle on all host cores) gives bitwise the
+    same Jacobian and residual for 1, 3 and 8 threads, and the plain oracle's up to summation order."""
+    mesh = synth.dome_mesh(9, 4, 51, 52, bed="sinusoidal", beta="field")
+    om = oracle.OracleMesh(mesh)
+    U = synth.random_velocity(mesh, 53)
+    _, _, v1, R1 = om.jacobian_colored(U, 1)
+    for nt in (3, 8):
+        _, _, vn, Rn = om.jacobian_colored(U, nt)
+        assert np.array_equal(vn, v1) and np.array_equal(Rn, R1)
+    _, _, v0, R0 = om.jacobian(U)
+    assert np.abs(v1 - v0).max() <= 1e-14 * np.abs(v0).max()
+    assert np.abs(R1 - R0).max() <= 1e-14 * np.abs(R0).max()
+    marine = synth.marine_mesh(6, 3, 45, 46)  # with the lateral (ocean margin) load
+    om = oracle.OracleMesh(marine)
+    U = synth.random_velocity(marine, 54)
+    _, _, v2, R2 = om.jacobian_colored(U, 4)
+    _, _, v0, R0 = om.jacobian(U)
+    assert np.abs(R2 - R0).max() <= 1e-14 * np.abs(R0).max() and np.abs(v2 - v0).max() <= 1e-14 * np.abs(v0).max()
