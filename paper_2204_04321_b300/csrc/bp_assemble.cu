@@ -36,6 +36,18 @@ __global__ void __launch_bounds__(128, min_blocks<TL, TV>()) k_assemble(const As
   }
 }
 
+// Paired-FP32 lanes with the staged rank-one part (blocks of 64: 81 lanes per thread in shared memory,
+// the in-plane table, the carried block and the 6 points' rank-one factors).
+constexpr int STAGED_TPB = 64;
+template <bool ATOMIC>
+__global__ void __launch_bounds__(STAGED_TPB) k_assemble_staged(const AsmArgs A) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= A.count) return;
+  const int t = A.tri_list ? A.tri_list[idx] : idx;
+  __shared__ __align__(16) unsigned char sraw[81 * STAGED_TPB * sizeof(f64x2)];
+  assemble_column<MODE_FACT, f64x2, ATOMIC, false, double, true, true>(A, t, reinterpret_cast<f64x2*>(sraw) + threadIdx.x);
+}
+
 AsmArgs make_args(const bp_mesh* m, const double* U, double* R, void* J) {
   AsmArgs a{};
   a.xy = m->xy;
@@ -75,6 +87,20 @@ int launch(const bp_mesh* m, AsmArgs a, int scatter, cudaStream_t s) {
   return BP_OK;
 }
 
+int launch_staged(const bp_mesh* m, AsmArgs a, int scatter, cudaStream_t s) {
+  if (scatter == BP_SCATTER_COLOR) {
+    for (int c = 0; c < m->ncolors; ++c) {
+      a.tri_list = m->color_tris + m->color_off[c];
+      a.count = m->color_off[c + 1] - m->color_off[c];
+      k_assemble_staged<false><<<(a.count + STAGED_TPB - 1) / STAGED_TPB, STAGED_TPB, 0, s>>>(a);
+    }
+  } else {
+    k_assemble_staged<true><<<(a.count + STAGED_TPB - 1) / STAGED_TPB, STAGED_TPB, 0, s>>>(a);
+  }
+  BP_CUDA_TRY(cudaGetLastError());
+  return BP_OK;
+}
+
 // Argument checks shared by the Jacobian entry points.
 int check_jacobian_args(int precision, int scatter, int method) {
   if (precision != BP_F64 && precision != BP_F32 && precision != BP_F64X2 && precision != BP_F32_ALL)
@@ -93,7 +119,7 @@ size_t jacobian_value_bytes(int precision) {
 int launch_jacobian(const bp_mesh* m, const AsmArgs& a, int precision, int scatter, int method, cudaStream_t s) {
   switch (precision) {
     case BP_F64X2:
-      return launch<MODE_FACT, f64x2>(m, a, scatter, s);
+      return launch_staged(m, a, scatter, s);
     case BP_F32_ALL:
       return launch<MODE_FACT, float, false, float>(m, a, scatter, s);
     case BP_F64:

@@ -157,7 +157,8 @@ struct LaneStore {
 template <>
 struct LaneStore<f64x2> {
   using type = double;
-  static __device__ __forceinline__ double cast(const f64x2 v) { return v.value(); }
+  // hi + lo in FP64: the two widenings repack the fields on the integer pipe, one FP64 addition
+  static __device__ __forceinline__ double cast(const f64x2 v) { return f64_of(v.hi) + f64_of(v.lo); }
 };
 
 // acc + x or acc - x with the sign known at compile time after unrolling
@@ -244,10 +245,17 @@ __device__ __forceinline__ Dual<TL, NL> operator*(double s, const Dual<TL, NL>& 
 // they are formed once per column into shared memory (sbl: this thread's first slot, consecutive
 // slots blockDim.x apart; 24 slots) and read per wedge instead of being formed again at every
 // level.  With FP64 or FP32 lanes the carried element block takes 21 more slots there.
-template <int MODE, class TL, bool ATOMIC, bool PICARD = false, class TV = double, bool SBL = false>
+// STAGE (factored method with SBL, Jacobian not Picard): the rank-one part is applied after the
+// value path, in a loop over the 6 quadrature points that is not unrolled: each point's rank-one
+// factors (Wp, the three strain combinations, tau_1, tau_2) wait in shared memory (slots 45..80),
+// and the element matrix is started only after the value path, so that it is not live there.  For
+// the paired-FP32 lanes, whose fully unrolled arithmetic outgrows the instruction cache.
+template <int MODE, class TL, bool ATOMIC, bool PICARD = false, class TV = double, bool SBL = false,
+          bool STAGE = false>
 __device__ __forceinline__ void assemble_column(const AsmArgs& A, const int t, TL* sbl = nullptr) {
   static_assert(std::is_same<TV, double>::value || (MODE == MODE_FACT && std::is_same<TL, float>::value),
                 "the FP32 value path exists for the factored method with FP32 lanes only");
+  static_assert(!STAGE || (SBL && MODE == MODE_FACT && !PICARD), "the staged rank-one part needs SBL");
   const int L = A.L;
 
   // ---- column geometry (per base triangle)
@@ -447,16 +455,19 @@ __device__ __forceinline__ void assemble_column(const AsmArgs& A, const int t, T
         invhL[tp] = to_lane<TL>(invh[tp]);
       }
     }
-    if constexpr (MODE != MODE_RES) {
+    auto start_element_matrix = [&]() {
+      if constexpr (MODE != MODE_RES) {
 #pragma unroll
-      for (int k = 0; k < 78; ++k) K[k] = TL(0);
-    }
-    if constexpr (kAhead) {  // the previous wedge's top-top block starts this wedge's bottom-bottom block
+        for (int k = 0; k < 78; ++k) K[k] = TL(0);
+      }
+      if constexpr (kAhead) {  // the previous wedge's top-top block starts this wedge's bottom-bottom block
 #pragma unroll
-      for (int i = 0; i < 6; ++i)
+        for (int i = 0; i < 6; ++i)
 #pragma unroll
-        for (int j = i; j < 6; ++j) K[uidx(i, j)] = KC(uidx6(i, j));
-    }
+          for (int j = i; j < 6; ++j) K[uidx(i, j)] = KC(uidx6(i, j));
+      }
+    };
+    if constexpr (!STAGE) start_element_matrix();
 
     if constexpr (MODE == MODE_DUAL) {
       // ---- literal forward mode: 12 lanes, lane j = d / dU_j (j = 2 * (3k + a) + c)
@@ -582,7 +593,16 @@ __device__ __forceinline__ void assemble_column(const AsmArgs& A, const int t, T
               tau1 = to_lane<TL>(2.0 * invh[tp] * t1);
               tau2 = to_lane<TL>(2.0 * invh[tp] * t2);
             }
-            if constexpr (!PICARD) {
+            if constexpr (STAGE) {  // park the point's rank-one factors (slots 45 + 6 q ..)
+              const int bs = blockDim.x;
+              TL* const sq = sbl + (45 + 6 * (3 * z + tp)) * bs;
+              sq[0] = Wp;
+              sq[bs] = lane_from<TL>(g1x);
+              sq[2 * bs] = lane_from<TL>(exy);
+              sq[3 * bs] = lane_from<TL>(g2y);
+              sq[4 * bs] = tau1;
+              sq[5 * bs] = tau2;
+            } else if constexpr (!PICARD) {
             const TL fg1x = lane_from<TL>(g1x), fexy = lane_from<TL>(exy), fg2y = lane_from<TL>(g2y);
             // p_{(a,k),c} = psi_k alpha_{a,c} -/+ t_{a,c},  alpha = g_c,xy . Lambda_a,  t = lambda_a tau_c / 2
             TL p[12];
@@ -620,6 +640,36 @@ __device__ __forceinline__ void assemble_column(const AsmArgs& A, const int t, T
         for (int a = 0; a < 3; ++a) {
           Rl[k][a][0] = lxV[a] * A1x + lyV[a] * A1y + TV(dpsi(k)) * (T1s + TV(0.5) * TW1[a]);
           Rl[k][a][1] = lxV[a] * A2x + lyV[a] * A2y + TV(dpsi(k)) * (T2s + TV(0.5) * TW2[a]);
+        }
+      }
+      if constexpr (STAGE) {
+        start_element_matrix();
+        const int bs = blockDim.x;
+#pragma unroll 1
+        for (int q = 0; q < 6; ++q) {
+          const int z = q >= 3 ? 1 : 0, tp = q - 3 * z;
+          const TL* const sq = sbl + (45 + 6 * q) * bs;
+          const TL Wp = sq[0], fg1x = sq[bs], fexy = sq[2 * bs], fg2y = sq[3 * bs], tau1 = sq[4 * bs],
+                   tau2 = sq[5 * bs];
+          const TL ps0 = z ? TL(BP_QP_Q) : TL(BP_QP_P), ps1 = z ? TL(BP_QP_P) : TL(BP_QP_Q);
+          TL p[12];
+#pragma unroll
+          for (int a = 0; a < 3; ++a) {
+            const TL al1 = fg1x * clx[a] + fexy * cly[a];
+            const TL al2 = fexy * clx[a] + fg2y * cly[a];
+            const TL h = a == tp ? TL(1.0 / 3.0) : TL(1.0 / 12.0);  // lambda_a(tp) / 2
+            const TL t1a = h * tau1, t2a = h * tau2;
+            p[2 * a] = ps0 * al1 - t1a;
+            p[2 * a + 1] = ps0 * al2 - t2a;
+            p[2 * (3 + a)] = ps1 * al1 + t1a;
+            p[2 * (3 + a) + 1] = ps1 * al2 + t2a;
+          }
+#pragma unroll
+          for (int i = 0; i < 12; ++i) {
+            const TL pw = Wp * p[i];
+#pragma unroll
+            for (int j = i; j < 12; ++j) acc_fma(K[uidx(i, j)], pw, p[j]);
+          }
         }
       }
       if constexpr (MODE == MODE_FACT) {
