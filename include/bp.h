@@ -250,7 +250,7 @@ enum { BP_GUESS_ZERO = 0, BP_GUESS_SIA = 1 };
  */
 int bp_initial_guess(bp_mesh* mesh, int kind, double* U_dev, void* stream);
 
-enum { BP_KRYLOV_CG = 0 };
+enum { BP_KRYLOV_CG = 0, BP_KRYLOV_GMRES = 1 };
 /* Preconditioner of the Newton solve's CG (bp_solve_opts.preconditioner). */
 enum { BP_PREC_COLUMN = 0, BP_PREC_MDSC = 1 };
 /* Line search of bp_newton_solve (bp_solve_opts.line_search). */
@@ -263,7 +263,10 @@ typedef struct {
   double eta_max;     /* Eisenstat-Walker forcing term cap (choice 2, gamma = 0.9) */
   int precision;      /* BP_F64: FP64 Jacobian and Krylov; BP_F32: FP32 Jacobian lanes and Krylov
                          (inexact Newton); the residual, viscosity, norms and update stay FP64 */
-  int krylov;         /* BP_KRYLOV_CG (the Jacobian is SPD) */
+  int krylov;         /* BP_KRYLOV_CG (default: the Jacobian is SPD), or BP_KRYLOV_GMRES: restarted
+                         GMRES(gmres_restart) as the paper's Krylov method, right-preconditioned by
+                         the column solve (classical Gram-Schmidt twice; the Hessenberg problem on the
+                         host, one synchronisation per iteration), a cross-check of CG */
   int line_search;    /* Armijo test on the energy change (c = 1e-4, at most 11 trials), a BP_LS_*:
                          BP_LS_OFF full steps; BP_LS_HALVING alpha = 1, 1/2, ..., 2^-10;
                          BP_LS_QUADRATIC backtracking by quadratic interpolation of the energy
@@ -286,7 +289,8 @@ typedef struct {
                          with a host check every check_every iterations */
   int preconditioner; /* BP_PREC_COLUMN: the vertical-line block solve; BP_PREC_MDSC: the two-level
                          semicoarsening cycle (bp_mdsc_setup); with device_loop 0 its iterations are
-                         launched from the host, one host check each */
+                         launched from the host, one host check each (CG only: BP_EUNSUP with GMRES) */
+  int gmres_restart;  /* GMRES restart length m, 1..64 (default 50; the basis holds m + 1 vectors) */
 } bp_solve_opts;
 
 typedef struct {
@@ -304,7 +308,7 @@ typedef struct {
 } bp_solve_report;
 
 /* Defaults: rtol 1e-8, 50 Newton, 1000 Krylov, eta_max 0.1, BP_F64, CG, line search on, check 8,
- * picard_rtol 0, value32_rtol 0, device_loop 1, BP_PREC_COLUMN. */
+ * picard_rtol 0, value32_rtol 0, device_loop 1, BP_PREC_COLUMN, gmres_restart 50. */
 void bp_solve_opts_default(bp_solve_opts* opts);
 
 /*

@@ -21,7 +21,7 @@ BP_F64, BP_F32, BP_F64X2, BP_F32_ALL = 0, 1, 2, 3
 BP_SCATTER_AUTO, BP_SCATTER_ATOMIC, BP_SCATTER_COLOR = 0, 1, 2
 BP_JAC_AUTO, BP_JAC_DUAL, BP_JAC_FACTORED = 0, 1, 2
 BP_GUESS_ZERO, BP_GUESS_SIA = 0, 1
-BP_KRYLOV_CG = 0
+BP_KRYLOV_CG, BP_KRYLOV_GMRES = 0, 1
 BP_PREC_COLUMN, BP_PREC_MDSC = 0, 1
 BP_JUDGE_RESIDUAL, BP_JUDGE_ENERGY, BP_JUDGE_NONE = 0, 1, 2
 BP_LS_OFF, BP_LS_HALVING, BP_LS_QUADRATIC = 0, 1, 2
@@ -58,7 +58,8 @@ class bp_solve_opts(ctypes.Structure):
     _fields_ = [("rtol", ctypes.c_double), ("max_newton", ctypes.c_int), ("max_krylov", ctypes.c_int),
                 ("eta_max", ctypes.c_double), ("precision", ctypes.c_int), ("krylov", ctypes.c_int),
                 ("line_search", ctypes.c_int), ("check_every", ctypes.c_int), ("picard_rtol", ctypes.c_double),
-                ("value32_rtol", ctypes.c_double), ("device_loop", ctypes.c_int), ("preconditioner", ctypes.c_int)]
+                ("value32_rtol", ctypes.c_double), ("device_loop", ctypes.c_int), ("preconditioner", ctypes.c_int),
+                ("gmres_restart", ctypes.c_int)]
 
 
 class bp_solve_report(ctypes.Structure):

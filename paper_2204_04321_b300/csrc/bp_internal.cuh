@@ -62,6 +62,10 @@ struct bp_solver_ws {
   int64_t nbr_total = 0;
   bool has_mdsc = false, mdsc_f32 = false;
   void* mdsc_loop[2] = {nullptr, nullptr};  // device-driven PCG loops with the MDSC cycle
+  // GMRES(m): Krylov basis (m + 1 vectors, double storage) and the Hessenberg column / coefficients
+  double* gm_basis = nullptr;
+  double* gm_h = nullptr;
+  int gm_cap = 0;
 };
 
 struct bp_mesh {

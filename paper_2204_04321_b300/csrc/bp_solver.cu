@@ -20,6 +20,7 @@ constexpr int GRID_CAP = 148 * 8;  // grid-stride kernels: 8 blocks of NT per SM
 constexpr int UPD_NT = 128;        // threads of the staged CG update (one warp solves the block's columns)
 constexpr int CG_BATCH = 8;        // CG iterations per replay of the captured batch graph
 constexpr int LOOP_BODY = 4;       // CG iterations per pass of the device-driven loop
+constexpr int GMRES_MAX_RESTART = 64;  // largest GMRES restart length
 
 // Programmatic dependent launch inside the CG loop: each kernel lets the next one be scheduled at
 // once (its blocks then wait on the SM instead of behind the launch latency) and waits for the
@@ -1308,6 +1309,195 @@ int cg_solve(bp_mesh* m, const M* J, double eta, int maxit, int check_every, boo
   return BP_OK;
 }
 
+// ------------------------------------------------------------------ GMRES(m)
+// Paper Sec. 3.1: the Newton step's linear system is solved by preconditioned GMRES.  The Jacobian
+// here is symmetric positive definite, so CG is the default; GMRES(m) with the same column
+// preconditioner is the cross-check.  Right preconditioning (J M^-1 u = -R, delta = M^-1 u), so
+// the least-squares residual |g_{k+1}| is the true residual norm ||-R - J delta|| that CG's test
+// also uses; Arnoldi by classical Gram-Schmidt applied twice (each pass one multi-dot and one
+// multi-axpy over the basis), the small Hessenberg problem (Givens rotations) on the host.
+
+// h[i] += basis_i . w for i = 0..k (blockIdx.y = i; one FP64 atomic per block)
+template <class V>
+__global__ void __launch_bounds__(NT) k_gm_multidot(const V* __restrict__ basis, int64_t n,
+                                                   const V* __restrict__ w, double* h) {
+  const V* v = basis + (int64_t)blockIdx.y * n;
+  V sum = V(0);
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    sum += v[e] * w[e];
+  block_add(sum, h + blockIdx.y);
+}
+
+// w -= sum_{i <= k} c_i basis_i  (c in device memory, k + 1 values); or, with out != nullptr,
+// out = sum_i c_i basis_i (w unused)
+template <class V>
+__global__ void __launch_bounds__(NT) k_gm_combine(const V* __restrict__ basis, int64_t n, int k1,
+                                                  const double* __restrict__ c, V* __restrict__ w, V* out) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    V acc = V(0);
+    for (int i = 0; i < k1; ++i) acc += (V)c[i] * basis[(int64_t)i * n + e];
+    if (out)
+      out[e] = acc;
+    else
+      w[e] -= acc;
+  }
+}
+
+// y = a x (a from device memory: 1 / norm), or y = -R (x == nullptr)
+template <class V>
+__global__ void __launch_bounds__(NT) k_gm_scale(const V* __restrict__ x, const double* __restrict__ a,
+                                                const double* __restrict__ R, int64_t n, V* __restrict__ y) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    y[e] = x ? (V)(*a) * x[e] : (V)(-R[e]);
+}
+
+// r = -R - Jx (Jx given)
+template <class V>
+__global__ void __launch_bounds__(NT) k_gm_residual(const double* __restrict__ R, const V* __restrict__ Jx,
+                                                   int64_t n, V* __restrict__ r) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    r[e] = (V)(-R[e]) - Jx[e];
+}
+
+template <class V>
+__global__ void __launch_bounds__(NT) k_gm_add(const V* __restrict__ d, int64_t n, V* __restrict__ x) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    x[e] += d[e];
+}
+
+int gmres_alloc(bp_mesh* m, int restart) {
+  bp_solver_ws* w = m->ws;
+  if (w->gm_basis && w->gm_cap >= restart) return BP_OK;
+  int rc;
+  // basis vectors (restart + 1) x ndof (double storage; FP32 vectors use the first half)
+  if ((rc = bp_alloc(m, &w->gm_basis, (size_t)(restart + 1) * m->ndof))) return rc;
+  if (!w->gm_h && (rc = bp_alloc(m, &w->gm_h, 2 * (size_t)(GMRES_MAX_RESTART + 2)))) return rc;
+  w->gm_cap = restart;
+  return BP_OK;
+}
+
+// GMRES(restart) on J delta = -R (w->R) to ||-R - J delta|| <= eta ||R||; delta in ws->x (type V).
+template <class M, class V>
+int gmres_solve(bp_mesh* m, const M* J, double eta, int maxit, int restart, cudaStream_t s, int* iters,
+                int* status) {
+  bp_solver_ws* w = m->ws;
+  int rc = gmres_alloc(m, restart);
+  if (rc) return rc;
+  const Prec<V> P = prec_of<V>(m);
+  const int64_t n = m->ndof;
+  V* basis = reinterpret_cast<V*>(w->gm_basis);
+  V* x = reinterpret_cast<V*>(w->x);
+  V* wv = reinterpret_cast<V*>(w->r);   // Arnoldi vector
+  V* z = reinterpret_cast<V*>(w->z);    // M^-1 v, and the update
+  V* u = reinterpret_cast<V*>(w->p);
+  double* hd = w->gm_h;                 // device: h column (first half), combination coefficients (second)
+  double* hh = w->host;                 // pinned host mirror
+  const int gvec = grid_for(n, NT), gcol = (m->nv + 127) / 128, gspmv = grid_for(n / 2 * TPR, NT);
+  *status = 0;
+  BP_CUDA_TRY(cudaMemsetAsync(x, 0, n * sizeof(V), s));
+  double bnorm;
+  if ((rc = dot_host(m, w->R, w->R, n, s, &bnorm))) return rc;
+  bnorm = std::sqrt(bnorm);
+  if (!std::isfinite(bnorm)) {
+    *status = 3;
+    *iters = 0;
+    return BP_OK;
+  }
+  const double target = eta * bnorm;
+  std::vector<double> H((size_t)(restart + 1) * restart), cs(restart), sn(restart), g(restart + 1);
+  auto Hat = [&](int i, int j) -> double& { return H[(size_t)j * (restart + 1) + i]; };
+  int total = 0;
+  double res = bnorm;
+  // the residual of the current iterate: r = -R - J x (x = 0 at the first cycle)
+  k_gm_scale<V><<<gvec, NT, 0, s>>>(nullptr, nullptr, w->R, n, wv);
+  BP_CUDA_TRY(cudaGetLastError());
+  while (total < maxit && res > target) {
+    // v_0 = r / ||r||
+    if (total > 0) {
+      k_spmv_pairs<M, V, false><<<gspmv, NT, 0, s>>>(m->rowptr, m->nbr_ptr, m->nbr_idx, m->nl, J, (int)(n / 2), x,
+                                                     z, nullptr, nullptr, nullptr, 0);
+      k_gm_residual<V><<<gvec, NT, 0, s>>>(w->R, z, n, wv);
+    }
+    double beta;
+    if ((rc = dot_host(m, wv, wv, n, s, &beta))) return rc;
+    beta = std::sqrt(beta);
+    if (!std::isfinite(beta)) {
+      *status = 3;
+      break;
+    }
+    hh[0] = 1.0 / beta;
+    BP_CUDA_TRY(cudaMemcpyAsync(hd, hh, sizeof(double), cudaMemcpyHostToDevice, s));
+    k_gm_scale<V><<<gvec, NT, 0, s>>>(wv, hd, nullptr, n, basis);
+    std::fill(g.begin(), g.end(), 0.0);
+    g[0] = beta;
+    int k = 0;
+    for (; k < restart && total < maxit; ++k, ++total) {
+      // w = J M^-1 v_k
+      k_colprec_apply<V, V><<<gcol, 128, 0, s>>>(P, basis + (int64_t)k * n, z);
+      k_spmv_pairs<M, V, false><<<gspmv, NT, 0, s>>>(m->rowptr, m->nbr_ptr, m->nbr_idx, m->nl, J, (int)(n / 2), z,
+                                                     wv, nullptr, nullptr, nullptr, 0);
+      // classical Gram-Schmidt, twice
+      for (int i = 0; i <= k; ++i) Hat(i, k) = 0.0;
+      for (int pass = 0; pass < 2; ++pass) {
+        BP_CUDA_TRY(cudaMemsetAsync(hd, 0, (k + 1) * sizeof(double), s));
+        k_gm_multidot<V><<<dim3(std::min(gvec, 64), k + 1), NT, 0, s>>>(basis, n, wv, hd);
+        k_gm_combine<V><<<gvec, NT, 0, s>>>(basis, n, k + 1, hd, wv, nullptr);
+        BP_CUDA_TRY(cudaMemcpyAsync(hh, hd, (k + 1) * sizeof(double), cudaMemcpyDeviceToHost, s));
+        BP_CUDA_TRY(cudaStreamSynchronize(s));
+        for (int i = 0; i <= k; ++i) Hat(i, k) += hh[i];
+      }
+      double hn;
+      if ((rc = dot_host(m, wv, wv, n, s, &hn))) return rc;
+      hn = std::sqrt(hn);
+      Hat(k + 1, k) = hn;
+      if (!std::isfinite(hn)) {
+        *status = 3;
+        break;
+      }
+      // Givens rotations of the new column, then a new rotation zeroing H(k+1, k)
+      for (int i = 0; i < k; ++i) {
+        const double a = Hat(i, k), b = Hat(i + 1, k);
+        Hat(i, k) = cs[i] * a + sn[i] * b;
+        Hat(i + 1, k) = -sn[i] * a + cs[i] * b;
+      }
+      const double a = Hat(k, k), b = Hat(k + 1, k), rr = std::hypot(a, b);
+      cs[k] = rr > 0 ? a / rr : 1.0;
+      sn[k] = rr > 0 ? b / rr : 0.0;
+      Hat(k, k) = rr;
+      Hat(k + 1, k) = 0.0;
+      g[k + 1] = -sn[k] * g[k];
+      g[k] = cs[k] * g[k];
+      res = std::fabs(g[k + 1]);
+      if (res <= target || hn == 0.0) {
+        ++k;
+        ++total;
+        break;
+      }
+      // v_{k+1} = w / ||w||
+      hh[0] = 1.0 / hn;
+      BP_CUDA_TRY(cudaMemcpyAsync(hd, hh, sizeof(double), cudaMemcpyHostToDevice, s));
+      k_gm_scale<V><<<gvec, NT, 0, s>>>(wv, hd, nullptr, n, basis + (int64_t)(k + 1) * n);
+    }
+    if (*status == 3) break;
+    // y = H^-1 g (upper triangular k x k);  x += M^-1 V y
+    std::vector<double> y(k);
+    for (int i = k - 1; i >= 0; --i) {
+      double t = g[i];
+      for (int j = i + 1; j < k; ++j) t -= Hat(i, j) * y[j];
+      y[i] = t / Hat(i, i);
+    }
+    for (int i = 0; i < k; ++i) hh[i] = y[i];
+    BP_CUDA_TRY(cudaMemcpyAsync(hd + GMRES_MAX_RESTART + 2, hh, k * sizeof(double), cudaMemcpyHostToDevice, s));
+    k_gm_combine<V><<<gvec, NT, 0, s>>>(basis, n, k, hd + GMRES_MAX_RESTART + 2, nullptr, u);
+    k_colprec_apply<V, V><<<gcol, 128, 0, s>>>(P, u, z);
+    k_gm_add<V><<<gvec, NT, 0, s>>>(z, n, x);
+    BP_CUDA_TRY(cudaGetLastError());
+    BP_CUDA_TRY(cudaStreamSynchronize(s));  // the host mirror is rewritten by the next cycle
+  }
+  *iters = total;
+  return BP_OK;
+}
+
 // ------------------------------------------------------------------ MDSC two-level preconditioner
 // Paper Sec. 4.4: the multigrid preconditioner coarsens the extruded mesh vertically first, with a
 // prolongation built from per-vertical-line solves, and solves the resulting plane problem by a 2D
@@ -2050,6 +2240,7 @@ extern "C" void bp_solve_opts_default(bp_solve_opts* o) {
   o->value32_rtol = 0.0;
   o->device_loop = 1;
   o->preconditioner = BP_PREC_COLUMN;
+  o->gmres_restart = 50;
 }
 
 extern "C" int bp_newton_solve(bp_mesh* m, double* U, const bp_solve_opts* opts, bp_solve_report* rep,
@@ -2063,8 +2254,12 @@ extern "C" int bp_newton_solve(bp_mesh* m, double* U, const bp_solve_opts* opts,
       (o.preconditioner != BP_PREC_COLUMN && o.preconditioner != BP_PREC_MDSC))
     return BP_EINVAL;
   if (!(o.rtol > 0) || o.max_newton < 0 || o.max_newton > 64 || o.max_krylov < 1 || o.check_every < 1 ||
-      (o.precision != BP_F64 && o.precision != BP_F32) || o.krylov != BP_KRYLOV_CG || !(o.eta_max > 0))
+      (o.precision != BP_F64 && o.precision != BP_F32) ||
+      (o.krylov != BP_KRYLOV_CG && o.krylov != BP_KRYLOV_GMRES) || !(o.eta_max > 0))
     return BP_EINVAL;
+  if (o.krylov == BP_KRYLOV_GMRES &&
+      (o.gmres_restart < 1 || o.gmres_restart > GMRES_MAX_RESTART || o.preconditioner != BP_PREC_COLUMN))
+    return o.preconditioner != BP_PREC_COLUMN ? BP_EUNSUP : BP_EINVAL;
   bp_device_guard g(m->device);
   cudaStream_t s = (cudaStream_t)stream;
   int rc = ensure_ws(m, s);
@@ -2152,7 +2347,13 @@ extern "C" int bp_newton_solve(bp_mesh* m, double* U, const bp_solve_opts* opts,
     if (rc) return rc;
     BP_CUDA_TRY(cudaEventRecord(ev[4], s));
     int its = 0, kst = 0;
-    if (mdsc && f32)
+    const bool gmres = o.krylov == BP_KRYLOV_GMRES;
+    if (gmres && f32)
+      rc = gmres_solve<float, float>(m, reinterpret_cast<const float*>(w->J), eta, o.max_krylov, o.gmres_restart, s,
+                                     &its, &kst);
+    else if (gmres)
+      rc = gmres_solve<double, double>(m, w->J, eta, o.max_krylov, o.gmres_restart, s, &its, &kst);
+    else if (mdsc && f32)
       rc = mdsc_cg_solve<float, float>(m, reinterpret_cast<const float*>(w->J), eta, o.max_krylov,
                                        o.device_loop != 0, s, &its, &kst);
     else if (mdsc)

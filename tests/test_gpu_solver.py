@@ -307,3 +307,36 @@ def test_mixed_newton_4m_wedges_checked_by_oracle():
     f = np.linalg.norm(om.residual(sols[0])) / np.linalg.norm(om.residual(np.zeros_like(sols[0])))
     assert f <= 1.1e-8, f
     assert rel_inf(sols[0], sols[1]) <= 1e-6
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_gmres_newton_reaches_the_cg_solution(precision):
+    """GMRES(m) with the column preconditioner (the paper's Krylov method) as the cross-check of CG:
+    the same Newton solution to 1e-7, the oracle's FP64 residual at 1e-8, with restart lengths that
+    do and do not restart within a Newton step."""
+    c = capi()
+    mesh = synth.dome_mesh(16, 5, 81, 82, bed="sinusoidal", beta="field")
+    om = oracle.OracleMesh(mesh)
+    dm = c.DeviceMesh(mesh)
+    f0 = np.linalg.norm(om.residual(np.zeros(mesh.ndof)))
+    sols = {}
+    for name, kw in (("cg", {}), ("gmres50", {"krylov": c.BP_KRYLOV_GMRES}),
+                     ("gmres5", {"krylov": c.BP_KRYLOV_GMRES, "gmres_restart": 5})):
+        U = torch.empty(dm.ndof, dtype=torch.float64, device="cuda")
+        c.bp_initial_guess(dm.handle, c.BP_GUESS_SIA, U)
+        rc, rep = c.bp_newton_solve(dm.handle, U, precision=precision, max_krylov=4000, **kw)
+        assert rc == c.BP_OK, (name, rep)
+        Uh = U.cpu().numpy()
+        assert np.linalg.norm(om.residual(Uh)) <= 1.1e-8 * f0, name
+        sols[name] = (Uh, rep)
+    for name in ("gmres50", "gmres5"):
+        assert rel_inf(sols[name][0], sols["cg"][0]) <= 1e-7, name
+    assert sols["gmres5"][1]["krylov_iters"] >= sols["gmres50"][1]["krylov_iters"]
+    for bad in ({"gmres_restart": 0}, {"gmres_restart": 65}, {"krylov": 7}):
+        with pytest.raises(c.BPError) as e:
+            c.bp_newton_solve(dm.handle, U, krylov=c.BP_KRYLOV_GMRES if "gmres_restart" in bad else bad["krylov"],
+                              **{k: v for k, v in bad.items() if k != "krylov"})
+        assert e.value.status == c.BP_EINVAL
+    with pytest.raises(c.BPError) as e:
+        c.bp_newton_solve(dm.handle, U, krylov=c.BP_KRYLOV_GMRES, preconditioner=c.BP_PREC_MDSC)
+    assert e.value.status == c.BP_EUNSUP
