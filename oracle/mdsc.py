@@ -16,6 +16,10 @@ Definitions (dof = 2 (a (L + 1) + l) + c, vertex a, level l, component c):
   diagonal blocks of A_c) over [lam_hi / ratio, lam_hi], lam_hi the Gershgorin bound of D^-1 A_c;
 * smoother S = omega T^-1;
 * one symmetric cycle: z1 = S r; z2 = z1 + P B_c P^T (r - J z1); z = z2 + S (r - J z2).
+With `TwoLevelAMG` the plane solve B_c is one V-cycle of smoothed-aggregation multigrid on A_c
+(`PlaneAMG`, stated below).  Parity status: pinned by tests/test_oracle_mdsc.py (harmonic extension,
+Galerkin projection, Chebyshev extremal errors, aggregation by hand, null-space preservation of the
+smoothed prolongation, V-cycle symmetry and grid-independent contraction).
 """
 from __future__ import annotations
 
@@ -146,3 +150,150 @@ def pcg(J: sp.csr_matrix, b: np.ndarray, apply, tol: float, maxit: int = 10000):
         p = z + (rz_new / rz) * p
         rz = rz_new
     return x, maxit
+
+
+# ---------------------------------------------------------------- smoothed-aggregation plane hierarchy
+# Paper Sec. 4.4 / Sec. 3.1: after the vertical semicoarsening to one layer, the plane problem is
+# solved by smoothed-aggregation algebraic multigrid with a Chebyshev smoother.  Statement used here
+# (Vanek, Mandel and Brezina 1996, "Algebraic multigrid by smoothed aggregation"), on 2 x 2 blocks
+# (u, v per vertex):
+# * aggregation of the block graph G (the sparsity pattern of A, a vertex adjacent to itself):
+#   pass 1, vertices in index order: a vertex whose whole neighbourhood is still free starts a new
+#   aggregate made of that neighbourhood; pass 2: every vertex still free joins the aggregate (from
+#   pass 1) of its lowest-numbered neighbour that pass 1 aggregated;
+# * tentative prolongation Pt: block (i, agg(i)) = I (the two translations, the near-null space of
+#   the plane operator);
+# * smoothed prolongation P = (I - omega D^-1 A) Pt with omega = 4 / (3 lam), lam the Gershgorin bound
+#   of D^-1 A (D the 2 x 2 diagonal blocks);
+# * coarse operator P^T A P (Galerkin); its pattern is the next graph;
+# * coarsening stops when a level has at most AMG_COARSE vertices, when it shrinks by less than
+#   AMG_MIN_RATIO, or after AMG_MAX_LEVELS levels; the coarsest level is solved exactly;
+# * V-cycle: AMG_SMOOTH Chebyshev steps (block Jacobi over [lam / CHEB_RATIO, lam], from zero) as
+#   pre-smoother, coarse correction, the same polynomial applied to the new residual as post-smoother
+#   (symmetric positive definite for CG).
+
+AMG_COARSE = 64
+AMG_MIN_RATIO = 0.8
+AMG_MAX_LEVELS = 8
+AMG_SMOOTH = 3
+
+
+def block_pattern(A: sp.csr_matrix) -> list:
+    """Neighbour lists (sorted, a vertex included) of the 2 x 2 block graph of A (structural)."""
+    A = A.tocsr()
+    n = A.shape[0] // 2
+    out = []
+    for a in range(n):
+        cols = set()
+        for row in (2 * a, 2 * a + 1):
+            cols.update(int(c) // 2 for c in A.indices[A.indptr[row]:A.indptr[row + 1]])
+        cols.add(a)
+        out.append(np.array(sorted(cols), dtype=np.int64))
+    return out
+
+
+def aggregate(nbrs: list) -> np.ndarray:
+    """Aggregate index of every vertex (the two passes above)."""
+    n = len(nbrs)
+    agg = np.full(n, -1, dtype=np.int64)
+    count = 0
+    for a in range(n):
+        if all(agg[b] < 0 for b in nbrs[a]):
+            agg[nbrs[a]] = count
+            count += 1
+    first = agg.copy()  # pass-1 assignments
+    for a in range(n):
+        if agg[a] < 0:
+            joined = [b for b in nbrs[a] if first[b] >= 0]
+            agg[a] = first[min(joined)]
+    return agg
+
+
+def tentative(agg: np.ndarray) -> sp.csr_matrix:
+    n = agg.shape[0]
+    nc = int(agg.max()) + 1
+    rows = np.arange(2 * n)
+    cols = 2 * np.repeat(agg, 2) + np.tile([0, 1], n)
+    return sp.csr_matrix((np.ones(2 * n), (rows, cols)), shape=(2 * n, 2 * nc))
+
+
+def structural(M: sp.csr_matrix) -> sp.csr_matrix:
+    """The same pattern with every stored entry 1 (explicit zeros kept)."""
+    M = M.tocsr().copy()
+    M.data[:] = 1.0
+    return M
+
+
+class AmgLevel:
+    def __init__(self, A: sp.csr_matrix, nbrs: list):
+        self.A = A.tocsr()
+        self.nbrs = nbrs
+        self.Dinv = block_diag_inverse(self.A)
+        self.lam = gershgorin_bound(self.A, self.Dinv)
+
+
+class PlaneAMG:
+    """The smoothed-aggregation hierarchy of the plane operator and its V-cycle."""
+
+    def __init__(self, Ac: sp.csr_matrix, nbrs0: list, smooth: int = AMG_SMOOTH):
+        self.smooth = smooth
+        self.levels = [AmgLevel(Ac, nbrs0)]
+        self.P, self.agg = [], []
+        while True:
+            lv = self.levels[-1]
+            n = len(lv.nbrs)
+            if n <= AMG_COARSE or len(self.levels) >= AMG_MAX_LEVELS:
+                break
+            agg = aggregate(lv.nbrs)
+            nc = int(agg.max()) + 1
+            if nc > AMG_MIN_RATIO * n:
+                break
+            Pt = tentative(agg)
+            omega = 4.0 / (3.0 * lv.lam)
+            P = (Pt - omega * (lv.Dinv @ (lv.A @ Pt))).tocsr()
+            # pattern: structural product (no entry dropped where values cancel)
+            Ppat = structural(Pt + structural(lv.Dinv) @ structural(lv.A) @ Pt)
+            P = (P + 0.0 * Ppat).tocsr()
+            P.sort_indices()
+            Anext = (P.T @ lv.A @ P).tocsr()
+            Apat = structural(structural(P).T @ structural(lv.A) @ structural(P))
+            Anext = (Anext + 0.0 * Apat).tocsr()
+            Anext.sort_indices()
+            self.P.append(P)
+            self.agg.append(agg)
+            self.levels.append(AmgLevel(Anext, block_pattern(Anext)))
+        self.coarse = self.levels[-1].A.toarray()
+
+    def sizes(self):
+        return [len(lv.nbrs) for lv in self.levels]
+
+    def vcycle(self, b: np.ndarray, k: int = 0) -> np.ndarray:
+        lv = self.levels[k]
+        if k == len(self.levels) - 1:
+            return np.linalg.solve(self.coarse, b)
+        lo = lv.lam / CHEB_RATIO
+        x = chebyshev(lv.A, lv.Dinv, b, lo, lv.lam, self.smooth)
+        P = self.P[k]
+        x = x + P @ self.vcycle(P.T @ (b - lv.A @ x), k + 1)
+        return x + chebyshev(lv.A, lv.Dinv, b - lv.A @ x, lo, lv.lam, self.smooth)
+
+
+def plane_neighbours(nv: int, tri: np.ndarray) -> list:
+    """Closed neighbourhoods of the base vertices (the pattern of the plane operator)."""
+    nb = [set([a]) for a in range(nv)]
+    for t in tri:
+        for a in t:
+            nb[int(a)].update(int(x) for x in t)
+    return [np.array(sorted(s), dtype=np.int64) for s in nb]
+
+
+class TwoLevelAMG(TwoLevel):
+    """The semicoarsening cycle of TwoLevel with the plane problem solved by one SA-AMG V-cycle."""
+
+    def __init__(self, J: sp.csr_matrix, nv: int, L: int, tri: np.ndarray, omega: float = OMEGA,
+                 smooth: int = AMG_SMOOTH):
+        super().__init__(J, nv, L, omega=omega)
+        self.amg = PlaneAMG(self.Ac, plane_neighbours(nv, tri), smooth)
+
+    def plane_solve(self, rc: np.ndarray) -> np.ndarray:
+        return self.amg.vcycle(rc)
