@@ -224,6 +224,32 @@ int bp_mdsc_setup(bp_mesh* mesh, const void* J_vals_dev, int precision, void* st
 int bp_mdsc_apply(bp_mesh* mesh, const void* J_vals_dev, const double* r_dev, double* z_dev, void* stream);
 
 /*
+ * The MDSC cycle with the plane problem solved by smoothed-aggregation algebraic multigrid (paper
+ * Sec. 4.4 and Sec. 3.1: semicoarsening to one layer, then AMG in 2D with a Chebyshev smoother):
+ * the cycle of bp_mdsc_setup with B_c = one V-cycle on A_c:
+ *   aggregation of each level's block graph (pattern of A_k, 2 x 2 blocks): vertices in order, a
+ *     vertex whose whole neighbourhood is free starts an aggregate of that neighbourhood; then each
+ *     vertex still free joins the first-pass aggregate of its lowest-numbered such neighbour;
+ *   P_k = (I - 4 / (3 lam_k) D_k^-1 A_k) Pt_k, Pt_k(i, agg(i)) = I (the two translations);
+ *   A_{k+1} = P_k^T A_k P_k; levels until <= 64 vertices (at most 8 levels; coarsening stops when a
+ *     level shrinks by less than 0.8); the coarsest solved with its dense inverse (<= 512 vertices);
+ *   V-cycle: 3 Chebyshev block-Jacobi steps over [lam_k / 30, lam_k] from zero, coarse correction,
+ *     the same polynomial on the new residual (symmetric positive definite).
+ * The aggregates and patterns depend on the mesh only and are built on the host at the first setup
+ * of the mesh; each setup then forms the levels on the device.  bp_mdsc_amg_setup synchronises
+ * `stream` (it reads the level-0 Gershgorin bound back); bp_mdsc_amg_apply is asynchronous.
+ * bp_mdsc_amg_levels writes the vertex count of each level (at most max_levels) and the number of
+ * levels; bp_mdsc_amg_aggregates copies the aggregate index of every vertex of level `level`
+ * (0 .. levels - 2) to host memory.
+ * Errors: BP_EINVAL (NULL, misaligned, unknown precision, no setup, level out of range),
+ * BP_EUNSUP (coarsest level above 512 vertices), BP_ENOMEM, BP_ENAN, BP_ECUDA.
+ */
+int bp_mdsc_amg_setup(bp_mesh* mesh, const void* J_vals_dev, int precision, void* stream);
+int bp_mdsc_amg_apply(bp_mesh* mesh, const void* J_vals_dev, const double* r_dev, double* z_dev, void* stream);
+int bp_mdsc_amg_levels(const bp_mesh* mesh, int32_t* sizes_host, int max_levels, int* nlevels);
+int bp_mdsc_amg_aggregates(const bp_mesh* mesh, int level, int32_t* agg_host);
+
+/*
  * Discrete energy Pi_h(U) = sum_q w det J A^(-1/n) 2n/(n+1) (eps_e^2 + delta)^((n+1)/(2n))
  * + sum_i load_i U_i + 1/2 sum_bed U_b^T M_beta U_b, whose gradient is the residual (same
  * quadrature).  Not written in the paper: it follows from Eq. effvisc / effeps and is the merit
@@ -252,7 +278,7 @@ int bp_initial_guess(bp_mesh* mesh, int kind, double* U_dev, void* stream);
 
 enum { BP_KRYLOV_CG = 0, BP_KRYLOV_GMRES = 1 };
 /* Preconditioner of the Newton solve's CG (bp_solve_opts.preconditioner). */
-enum { BP_PREC_COLUMN = 0, BP_PREC_MDSC = 1 };
+enum { BP_PREC_COLUMN = 0, BP_PREC_MDSC = 1, BP_PREC_MDSC_AMG = 2 };
 /* Line search of bp_newton_solve (bp_solve_opts.line_search). */
 enum { BP_LS_OFF = 0, BP_LS_HALVING = 1, BP_LS_QUADRATIC = 2 };
 
@@ -288,8 +314,10 @@ typedef struct {
                          loop, no host check in between; 0: replays of a captured 8-iteration batch
                          with a host check every check_every iterations */
   int preconditioner; /* BP_PREC_COLUMN: the vertical-line block solve; BP_PREC_MDSC: the two-level
-                         semicoarsening cycle (bp_mdsc_setup); with device_loop 0 its iterations are
-                         launched from the host, one host check each (CG only: BP_EUNSUP with GMRES) */
+                         semicoarsening cycle (bp_mdsc_setup); BP_PREC_MDSC_AMG: the same cycle with
+                         the SA-AMG plane solve (bp_mdsc_amg_setup); with device_loop 0 their iterations
+                         are launched from the host, one host check each (CG only: BP_EUNSUP with
+                         GMRES) */
   int gmres_restart;  /* GMRES restart length m, 1..64 (default 50; the basis holds m + 1 vectors) */
 } bp_solve_opts;
 

@@ -22,7 +22,7 @@ BP_SCATTER_AUTO, BP_SCATTER_ATOMIC, BP_SCATTER_COLOR = 0, 1, 2
 BP_JAC_AUTO, BP_JAC_DUAL, BP_JAC_FACTORED = 0, 1, 2
 BP_GUESS_ZERO, BP_GUESS_SIA = 0, 1
 BP_KRYLOV_CG, BP_KRYLOV_GMRES = 0, 1
-BP_PREC_COLUMN, BP_PREC_MDSC = 0, 1
+BP_PREC_COLUMN, BP_PREC_MDSC, BP_PREC_MDSC_AMG = 0, 1, 2
 BP_JUDGE_RESIDUAL, BP_JUDGE_ENERGY, BP_JUDGE_NONE = 0, 1, 2
 BP_LS_OFF, BP_LS_HALVING, BP_LS_QUADRATIC = 0, 1, 2
 BP_MARGIN_FREE, BP_MARGIN_OCEAN = 0, 1
@@ -123,6 +123,10 @@ SIGNATURES = {
     "bp_learned_targets": (_I, [_P, _P, ctypes.c_double, _P, _P]),
     "bp_mlp_save": (_I, [_P, ctypes.c_char_p]),
     "bp_measure_fma_peak": (_I, [_I, _P, _P]),
+    "bp_mdsc_amg_setup": (_I, [_P, _P, _I, _P]),
+    "bp_mdsc_amg_apply": (_I, [_P, _P, _P, _P, _P]),
+    "bp_mdsc_amg_levels": (_I, [_P, _P, _I, _P]),
+    "bp_mdsc_amg_aggregates": (_I, [_P, _I, _P]),
     "bp_mlp_load": (_I, [_P, ctypes.c_char_p]),
     "bp_mesh_set_rate_factor": (_I, [_P, _P, _P]),
 }
@@ -249,6 +253,31 @@ def bp_mdsc_setup(handle, J, precision=BP_F64, stream=None) -> None:
 
 def bp_mdsc_apply(handle, J, r, z, stream=None) -> None:
     _check(lib().bp_mdsc_apply(handle, _dptr(J), _dptr(r), _dptr(z), _stream_ptr(stream)), "bp_mdsc_apply")
+
+
+def bp_mdsc_amg_setup(handle, J, precision=BP_F64, stream=None) -> None:
+    _check(lib().bp_mdsc_amg_setup(handle, _dptr(J), precision, _stream_ptr(stream)), "bp_mdsc_amg_setup")
+
+
+def bp_mdsc_amg_apply(handle, J, r, z, stream=None) -> None:
+    _check(lib().bp_mdsc_amg_apply(handle, _dptr(J), _dptr(r), _dptr(z), _stream_ptr(stream)), "bp_mdsc_amg_apply")
+
+
+def bp_mdsc_amg_levels(handle):
+    """Vertex counts of the SA-AMG plane levels (after bp_mdsc_amg_setup)."""
+    n = ctypes.c_int()
+    sizes = np.zeros(16, dtype=np.int32)
+    _check(lib().bp_mdsc_amg_levels(handle, sizes.ctypes.data_as(ctypes.c_void_p), 16, ctypes.byref(n)),
+           "bp_mdsc_amg_levels")
+    return [int(x) for x in sizes[:n.value]]
+
+
+def bp_mdsc_amg_aggregates(handle, level, n):
+    """Aggregate index of each of the n vertices of plane level `level`."""
+    out = np.empty(n, dtype=np.int32)
+    _check(lib().bp_mdsc_amg_aggregates(handle, level, out.ctypes.data_as(ctypes.c_void_p)),
+           "bp_mdsc_amg_aggregates")
+    return out
 
 
 def bp_energy(handle, U, stream=None) -> float:

@@ -60,9 +60,11 @@ struct bp_solver_ws {
   double *mz1 = nullptr, *mt = nullptr, *ms = nullptr;  // [ndof] fine scratch
   double *mrc = nullptr, *mec = nullptr, *mrr = nullptr, *md0 = nullptr, *md1 = nullptr;  // [2 nv]
   int64_t nbr_total = 0;
-  bool has_mdsc = false, mdsc_f32 = false;
+  bool has_mdsc = false, mdsc_f32 = false, has_amg = false;
   void* mdsc_loop[2] = {nullptr, nullptr};  // device-driven PCG loops with the MDSC cycle
   // GMRES(m): Krylov basis (m + 1 vectors, double storage) and the Hessenberg column / coefficients
+  void* amg = nullptr;        // smoothed-aggregation hierarchy of the MDSC plane solve (built once per mesh)
+  void* amg_loop[2] = {nullptr, nullptr};  // device-driven PCG loops with the MDSC-AMG cycle
   double* gm_basis = nullptr;
   double* gm_h = nullptr;
   int gm_cap = 0;

@@ -4,6 +4,7 @@
 // scalars (the Jacobian is symmetric positive definite: it is the Hessian of a convex energy),
 // the discrete energy for the damped-Newton line search, and a shallow-ice initial guess.
 #include <algorithm>
+#include <memory>
 #include <cmath>
 #include <cstring>
 #include <type_traits>
@@ -1832,8 +1833,507 @@ int mdsc_setup_t(bp_mesh* m, const M* J, cudaStream_t s) {
   return BP_OK;
 }
 
+// ------------------------------------------------------------------ SA-AMG plane solve of the MDSC cycle
+// Paper Sec. 4.4 / Sec. 3.1: after the vertical semicoarsening to one layer, the plane problem A_c is
+// solved by smoothed-aggregation algebraic multigrid with a Chebyshev smoother.  Statement (on 2 x 2
+// blocks, u and v per vertex):
+//   aggregation of the level's block graph (pattern of A_k, a vertex adjacent to itself): pass 1 in
+//     vertex order, a vertex whose whole neighbourhood is free starts an aggregate of that
+//     neighbourhood; pass 2, a vertex still free joins the pass-1 aggregate of its lowest-numbered
+//     neighbour that pass 1 aggregated;
+//   P_k = (I - omega D^-1 A_k) Pt, Pt(i, agg(i)) = I, omega = 4 / (3 lam_k), lam_k the Gershgorin
+//     bound of D^-1 A_k;  A_{k+1} = P_k^T A_k P_k;
+//   coarsening stops at <= AMG_COARSE vertices, when a level shrinks by less than AMG_MIN_RATIO, or
+//     after AMG_MAX_LEVELS levels; the coarsest level is solved with its dense inverse;
+//   V-cycle: AMG_SMOOTH Chebyshev steps (block Jacobi over [lam / MDSC_RATIO, lam], from zero),
+//     coarse correction, the same polynomial on the new residual (symmetric positive definite).
+// The aggregates and every sparsity pattern depend on the mesh only: they are built once per mesh on
+// the host, with the index lists that the numeric products need (P values: the A entries summed per
+// entry; T = A P: (A, P) entry pairs; A_{k+1} = P^T T: (P, T) entry pairs); each Newton step then
+// forms P, T, A_{k+1}, D^-1, lam and the dense coarse inverse on the device.
+constexpr int AMG_COARSE = 64;
+constexpr double AMG_MIN_RATIO = 0.8;
+constexpr int AMG_MAX_LEVELS = 8;
+constexpr int AMG_SMOOTH = 3;
+constexpr int AMG_DENSE_MAX = 512;  // largest coarsest level (vertices) the dense inverse takes
+
+struct AmgLevel {
+  int n = 0, nnz = 0;
+  const int32_t* ptr = nullptr;  // CSR of A_k over the level's vertices (level 0: the mesh's neighbourhoods)
+  const int32_t* col = nullptr;
+  int32_t* diag = nullptr;       // [n] entry of the diagonal block
+  double *A = nullptr, *Dinv = nullptr, *lam = nullptr, *cheb = nullptr;  // (F storage)
+  double *b = nullptr, *x = nullptr, *r = nullptr, *y = nullptr, *rr = nullptr, *d0 = nullptr, *d1 = nullptr;
+  // to the next level
+  int pnnz = 0, tnnz = 0;
+  int32_t *pptr = nullptr, *pcol = nullptr, *prow = nullptr, *ptptr = nullptr, *ptsrc = nullptr;
+  int32_t *pvptr = nullptr, *pvsrc = nullptr, *pdiag = nullptr, *tvptr = nullptr, *tvsrc = nullptr;
+  int32_t *cvptr = nullptr, *cvsrc = nullptr;
+  double *P = nullptr, *T = nullptr;
+};
+
+struct AmgHier {
+  std::vector<AmgLevel> lv;
+  std::vector<std::vector<int32_t>> agg;  // host copies of the aggregates of levels 0 .. L-2
+  double* W = nullptr;                    // dense Gauss-Jordan scratch [N][2N], N = 2 n_coarsest
+  double* Cinv = nullptr;                 // dense inverse of the coarsest operator [N][N]
+};
+
+// ---- host construction (once per mesh)
+std::vector<int32_t> amg_aggregate(const std::vector<int32_t>& ptr, const std::vector<int32_t>& col) {
+  const int n = (int)ptr.size() - 1;
+  std::vector<int32_t> agg(n, -1);
+  int count = 0;
+  for (int a = 0; a < n; ++a) {
+    bool free_nbhd = true;
+    for (int e = ptr[a]; e < ptr[a + 1] && free_nbhd; ++e) free_nbhd = agg[col[e]] < 0;
+    if (!free_nbhd) continue;
+    for (int e = ptr[a]; e < ptr[a + 1]; ++e) agg[col[e]] = count;
+    ++count;
+  }
+  const std::vector<int32_t> first = agg;
+  for (int a = 0; a < n; ++a) {
+    if (agg[a] >= 0) continue;
+    for (int e = ptr[a]; e < ptr[a + 1]; ++e)  // columns sorted: the lowest-numbered such neighbour
+      if (first[col[e]] >= 0) {
+        agg[a] = first[col[e]];
+        break;
+      }
+  }
+  return agg;
+}
+
+template <class T>
+int amg_upload(bp_mesh* m, const std::vector<T>& v, T** out) {
+  int rc = bp_alloc(m, out, v.size());
+  if (rc) return rc;
+  if (!v.empty()) BP_CUDA_TRY(cudaMemcpy(*out, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+  return BP_OK;
+}
+
+int amg_level_vectors(bp_mesh* m, AmgLevel& L, bool level0) {
+  int rc;
+  const size_t n2 = 2 * (size_t)L.n;
+  bp_solver_ws* w = m->ws;
+  if (level0) {  // borrow the MDSC plane vectors (the one-level Chebyshev plane solve's scratch)
+    L.b = w->mrc, L.x = w->mec, L.rr = w->mrr, L.d0 = w->md0, L.d1 = w->md1;
+  } else {
+    if ((rc = bp_alloc(m, &L.b, n2)) || (rc = bp_alloc(m, &L.x, n2)) || (rc = bp_alloc(m, &L.rr, n2)) ||
+        (rc = bp_alloc(m, &L.d0, n2)) || (rc = bp_alloc(m, &L.d1, n2)))
+      return rc;
+  }
+  if ((rc = bp_alloc(m, &L.r, n2)) || (rc = bp_alloc(m, &L.y, n2)) || (rc = bp_alloc(m, &L.cheb, 2 * AMG_SMOOTH + 2)))
+    return rc;
+  return BP_OK;
+}
+
+int amg_build(bp_mesh* m) {
+  bp_solver_ws* w = m->ws;
+  if (w->amg) return BP_OK;
+  std::unique_ptr<AmgHier> owner(new AmgHier());
+  AmgHier* H = owner.get();
+  int rc = BP_OK;
+  // level 0: the plane operator on the base vertices' closed neighbourhoods
+  std::vector<int32_t> gptr(m->nv + 1), gcol;
+  BP_CUDA_TRY(cudaMemcpy(gptr.data(), m->nbr_ptr, (m->nv + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost));
+  gcol.resize(gptr[m->nv]);
+  BP_CUDA_TRY(cudaMemcpy(gcol.data(), m->nbr_idx, gcol.size() * sizeof(int32_t), cudaMemcpyDeviceToHost));
+  {
+    AmgLevel L0;
+    L0.n = m->nv;
+    L0.nnz = gptr[m->nv];
+    L0.ptr = m->nbr_ptr;
+    L0.col = m->nbr_idx;
+    L0.diag = w->dslot;  // absolute entry = ptr[a] + dslot[a]: see k_amg_diag (level 0 keeps dslot)
+    L0.A = w->mAc, L0.Dinv = w->mDinv, L0.lam = w->mlam;
+    if ((rc = amg_level_vectors(m, L0, true))) return rc;
+    H->lv.push_back(L0);
+  }
+  for (;;) {
+    AmgLevel& L = H->lv.back();
+    const int n = L.n;
+    if (n <= AMG_COARSE || (int)H->lv.size() >= AMG_MAX_LEVELS) break;
+    std::vector<int32_t> agg = amg_aggregate(gptr, gcol);
+    int nc = 0;
+    for (int32_t a : agg) nc = std::max(nc, a + 1);
+    if (nc > AMG_MIN_RATIO * n) break;
+    // P: row i holds the aggregates of i's neighbourhood
+    std::vector<int32_t> pptr(n + 1, 0), pcol, prow, pvptr(1, 0), pvsrc, pdiag;
+    for (int i = 0; i < n; ++i) {
+      std::vector<int32_t> js;
+      for (int e = gptr[i]; e < gptr[i + 1]; ++e) js.push_back(agg[gcol[e]]);
+      std::sort(js.begin(), js.end());
+      js.erase(std::unique(js.begin(), js.end()), js.end());
+      for (int32_t J : js) {
+        pcol.push_back(J);
+        prow.push_back(i);
+        pdiag.push_back(J == agg[i] ? 1 : 0);
+        for (int e = gptr[i]; e < gptr[i + 1]; ++e)
+          if (agg[gcol[e]] == J) pvsrc.push_back(e);
+        pvptr.push_back((int32_t)pvsrc.size());
+      }
+      pptr[i + 1] = (int32_t)pcol.size();
+    }
+    const int pnnz = (int)pcol.size();
+    // P^T: per coarse row, its P entries in fine-row order
+    std::vector<int32_t> ptptr(nc + 1, 0), ptsrc(pnnz);
+    for (int f = 0; f < pnnz; ++f) ++ptptr[pcol[f] + 1];
+    for (int I = 0; I < nc; ++I) ptptr[I + 1] += ptptr[I];
+    {
+      std::vector<int32_t> fill(ptptr.begin(), ptptr.end() - 1);
+      for (int f = 0; f < pnnz; ++f) ptsrc[fill[pcol[f]]++] = f;
+    }
+    // T = A P: row i, columns the P columns of i's neighbours; terms (A entry, P entry)
+    std::vector<int32_t> tptr(n + 1, 0), tcol, tvptr(1, 0), tvsrc;
+    for (int i = 0; i < n; ++i) {
+      std::vector<std::pair<int32_t, std::pair<int32_t, int32_t>>> terms;  // (J, (A entry, P entry))
+      for (int e = gptr[i]; e < gptr[i + 1]; ++e) {
+        const int j = gcol[e];
+        for (int f = pptr[j]; f < pptr[j + 1]; ++f) terms.push_back({pcol[f], {e, f}});
+      }
+      std::sort(terms.begin(), terms.end());
+      for (size_t q = 0; q < terms.size();) {
+        const int32_t J = terms[q].first;
+        tcol.push_back(J);
+        for (; q < terms.size() && terms[q].first == J; ++q) {
+          tvsrc.push_back(terms[q].second.first);
+          tvsrc.push_back(terms[q].second.second);
+        }
+        tvptr.push_back((int32_t)(tvsrc.size() / 2));
+      }
+      tptr[i + 1] = (int32_t)tcol.size();
+    }
+    // A_{k+1} = P^T T: row I, columns the T columns of the fine rows in aggregate support; terms (P, T)
+    std::vector<int32_t> cptr(nc + 1, 0), ccol, cvptr(1, 0), cvsrc, cdiag(nc, -1);
+    for (int I = 0; I < nc; ++I) {
+      std::vector<std::pair<int32_t, std::pair<int32_t, int32_t>>> terms;
+      for (int q = ptptr[I]; q < ptptr[I + 1]; ++q) {
+        const int f = ptsrc[q], i = prow[f];
+        for (int t = tptr[i]; t < tptr[i + 1]; ++t) terms.push_back({tcol[t], {f, t}});
+      }
+      std::sort(terms.begin(), terms.end());
+      for (size_t q = 0; q < terms.size();) {
+        const int32_t J = terms[q].first;
+        if (J == I) cdiag[I] = (int32_t)ccol.size() - cptr[I];
+        ccol.push_back(J);
+        for (; q < terms.size() && terms[q].first == J; ++q) {
+          cvsrc.push_back(terms[q].second.first);
+          cvsrc.push_back(terms[q].second.second);
+        }
+        cvptr.push_back((int32_t)(cvsrc.size() / 2));
+      }
+      cptr[I + 1] = (int32_t)ccol.size();
+    }
+    // device copies of this level's prolongation data and of the next level
+    AmgLevel N;
+    N.n = nc;
+    N.nnz = (int)ccol.size();
+    int32_t *dptr = nullptr, *dcol = nullptr;
+    if ((rc = amg_upload(m, pptr, &L.pptr)) || (rc = amg_upload(m, pcol, &L.pcol)) ||
+        (rc = amg_upload(m, prow, &L.prow)) || (rc = amg_upload(m, ptptr, &L.ptptr)) ||
+        (rc = amg_upload(m, ptsrc, &L.ptsrc)) || (rc = amg_upload(m, pvptr, &L.pvptr)) ||
+        (rc = amg_upload(m, pvsrc, &L.pvsrc)) || (rc = amg_upload(m, pdiag, &L.pdiag)) ||
+        (rc = amg_upload(m, tvptr, &L.tvptr)) || (rc = amg_upload(m, tvsrc, &L.tvsrc)) ||
+        (rc = amg_upload(m, cvptr, &L.cvptr)) || (rc = amg_upload(m, cvsrc, &L.cvsrc)) ||
+        (rc = amg_upload(m, cptr, &dptr)) || (rc = amg_upload(m, ccol, &dcol)) ||
+        (rc = amg_upload(m, cdiag, &N.diag)) || (rc = bp_alloc(m, &L.P, 4 * (size_t)pnnz)) ||
+        (rc = bp_alloc(m, &L.T, 4 * tcol.size())) || (rc = bp_alloc(m, &N.A, 4 * ccol.size())) ||
+        (rc = bp_alloc(m, &N.Dinv, 4 * (size_t)nc)) || (rc = bp_alloc(m, &N.lam, 1)))
+      return rc;
+    L.pnnz = pnnz;
+    L.tnnz = (int)tcol.size();
+    N.ptr = dptr;
+    N.col = dcol;
+    if ((rc = amg_level_vectors(m, N, false))) return rc;
+    H->agg.push_back(std::move(agg));
+    H->lv.push_back(N);
+    gptr = std::move(cptr);
+    gcol = std::move(ccol);
+  }
+  const int nco = H->lv.back().n;
+  if (nco > AMG_DENSE_MAX) return BP_EUNSUP;
+  const size_t N2 = 2 * (size_t)nco;
+  if ((rc = bp_alloc(m, &H->W, 2 * N2 * N2)) || (rc = bp_alloc(m, &H->Cinv, N2 * N2))) return rc;
+  w->amg = owner.release();
+  return BP_OK;
+}
+
+// ---- device kernels (F: double or float; blocks row-major uu, uv, vu, vv)
+template <class F>
+__global__ void __launch_bounds__(128) k_amg_pvals(int pnnz, const int32_t* __restrict__ prow,
+                                                   const int32_t* __restrict__ pvptr, const int32_t* __restrict__ pvsrc,
+                                                   const int32_t* __restrict__ pdiag, const F* __restrict__ A,
+                                                   const F* __restrict__ Dinv, const double* __restrict__ lam,
+                                                   F* __restrict__ P) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= pnnz) return;
+  const int i = prow[e];
+  F S[4] = {F(0), F(0), F(0), F(0)};
+  for (int t = pvptr[e]; t < pvptr[e + 1]; ++t)
+#pragma unroll
+    for (int k = 0; k < 4; ++k) S[k] += A[4 * (int64_t)pvsrc[t] + k];
+  F Di[4];
+  load2x2(Dinv + 4 * (int64_t)i, 1, Di);
+  const F om = (F)(4.0 / (3.0 * *lam));
+  const F one = pdiag[e] ? F(1) : F(0);
+  P[4 * (int64_t)e + 0] = one - om * (Di[0] * S[0] + Di[1] * S[2]);
+  P[4 * (int64_t)e + 1] = -om * (Di[0] * S[1] + Di[1] * S[3]);
+  P[4 * (int64_t)e + 2] = -om * (Di[2] * S[0] + Di[3] * S[2]);
+  P[4 * (int64_t)e + 3] = one - om * (Di[2] * S[1] + Di[3] * S[3]);
+}
+
+// out[e] = sum over the entry's pairs (a, b) of X[a]^(T if TX) Y[b]
+template <class F, bool TX>
+__global__ void __launch_bounds__(128) k_amg_pairs(int nnz, const int32_t* __restrict__ vptr,
+                                                   const int32_t* __restrict__ vsrc, const F* __restrict__ X,
+                                                   const F* __restrict__ Y, F* __restrict__ out) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nnz) return;
+  F o[4] = {F(0), F(0), F(0), F(0)};
+  for (int t = vptr[e]; t < vptr[e + 1]; ++t) {
+    F a[4], b[4];
+    load2x2(X + 4 * (int64_t)vsrc[2 * t], 1, a);
+    load2x2(Y + 4 * (int64_t)vsrc[2 * t + 1], 1, b);
+    if (TX) {
+      const F t1 = a[1];
+      a[1] = a[2];
+      a[2] = t1;
+    }
+    o[0] += a[0] * b[0] + a[1] * b[2];
+    o[1] += a[0] * b[1] + a[1] * b[3];
+    o[2] += a[2] * b[0] + a[3] * b[2];
+    o[3] += a[2] * b[1] + a[3] * b[3];
+  }
+#pragma unroll
+  for (int k = 0; k < 4; ++k) out[4 * (int64_t)e + k] = o[k];
+}
+
+// D^-1 of the diagonal blocks and the Gershgorin bound of D^-1 A (atomic maximum; lam zeroed before)
+template <class F>
+__global__ void __launch_bounds__(128) k_amg_diag(int n, const int32_t* __restrict__ ptr,
+                                                  const int32_t* __restrict__ diag, const F* __restrict__ A,
+                                                  F* __restrict__ Dinv, double* lam) {
+  const int a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= n) return;
+  F D[4], Di[4];
+  load2x2(A + 4 * (int64_t)(ptr[a] + diag[a]), 1, D);
+  const F idet = F(1) / (D[0] * D[3] - D[1] * D[2]);
+  Di[0] = D[3] * idet, Di[1] = -D[1] * idet, Di[2] = -D[2] * idet, Di[3] = D[0] * idet;
+#pragma unroll
+  for (int e = 0; e < 4; ++e) Dinv[(int64_t)a * 4 + e] = Di[e];
+  F s0 = F(0), s1 = F(0);
+  for (int e = ptr[a]; e < ptr[a + 1]; ++e) {
+    F B[4];
+    load2x2(A + 4 * (int64_t)e, 1, B);
+    s0 += fabs(Di[0] * B[0] + Di[1] * B[2]) + fabs(Di[0] * B[1] + Di[1] * B[3]);
+    s1 += fabs(Di[2] * B[0] + Di[3] * B[2]) + fabs(Di[2] * B[1] + Di[3] * B[3]);
+  }
+  const double g = (double)(s0 > s1 ? s0 : s1);
+  atomicMax(reinterpret_cast<unsigned long long*>(lam), (unsigned long long)__double_as_longlong(g));
+}
+
+// Chebyshev coefficients over [lam / ratio, lam] (the recurrence of the MDSC plane iteration)
+__global__ void k_amg_cheb(const double* lam, double ratio, int steps, double* c) {
+  const double hi = *lam, lo = hi / ratio;
+  const double theta = 0.5 * (hi + lo), delta = 0.5 * (hi - lo), sigma = theta / delta;
+  c[0] = 1.0 / theta;
+  double rho = 1.0 / sigma;
+  for (int k = 0; k < steps; ++k) {
+    const double rn = 1.0 / (2.0 * sigma - rho);
+    c[1 + 2 * k] = rn * rho;
+    c[2 + 2 * k] = 2.0 * rn / delta;
+    rho = rn;
+  }
+}
+
+// Dense inverse of the coarsest operator by Gauss-Jordan elimination without pivoting (SPD), one block.
+template <class F>
+__global__ void __launch_bounds__(256) k_amg_dense_inverse(int n, const int32_t* __restrict__ ptr,
+                                                           const int32_t* __restrict__ col, const F* __restrict__ A,
+                                                           F* __restrict__ W, F* __restrict__ Cinv) {
+  const int N = 2 * n, N2 = 2 * N;
+  __shared__ F fcol[2 * AMG_DENSE_MAX];
+  for (int idx = threadIdx.x; idx < N * N2; idx += blockDim.x) {
+    const int i = idx / N2, j = idx % N2;
+    W[idx] = (j == N + i) ? F(1) : F(0);
+  }
+  __syncthreads();
+  for (int a = threadIdx.x; a < n; a += blockDim.x)
+    for (int e = ptr[a]; e < ptr[a + 1]; ++e)
+#pragma unroll
+      for (int r = 0; r < 2; ++r)
+#pragma unroll
+        for (int c = 0; c < 2; ++c) W[(2 * a + r) * N2 + 2 * col[e] + c] = A[4 * (int64_t)e + 2 * r + c];
+  __syncthreads();
+  for (int p = 0; p < N; ++p) {
+    const F ip = F(1) / W[p * N2 + p];
+    __syncthreads();
+    for (int j = threadIdx.x; j < N2; j += blockDim.x) W[p * N2 + j] *= ip;
+    __syncthreads();
+    for (int i = threadIdx.x; i < N; i += blockDim.x) fcol[i] = (i == p) ? F(0) : W[i * N2 + p];
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < N * N2; idx += blockDim.x) {
+      const int i = idx / N2, j = idx % N2;
+      if (i != p) W[idx] -= fcol[i] * W[p * N2 + j];
+    }
+    __syncthreads();
+  }
+  for (int idx = threadIdx.x; idx < N * N; idx += blockDim.x) {
+    const int i = idx / N, j = idx % N;
+    Cinv[idx] = W[i * N2 + N + j];
+  }
+}
+
+template <class F>
+__global__ void __launch_bounds__(256) k_amg_dense_apply(int N, const F* __restrict__ Cinv, const F* __restrict__ b,
+                                                         F* __restrict__ x) {
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    F s = F(0);
+    for (int j = 0; j < N; ++j) s += Cinv[(int64_t)i * N + j] * b[j];
+    x[i] = s;
+  }
+}
+
+// r = b - A x
+template <class F>
+__global__ void __launch_bounds__(128) k_amg_residual(int n, const int32_t* __restrict__ ptr,
+                                                      const int32_t* __restrict__ col, const F* __restrict__ A,
+                                                      const F* __restrict__ x, const F* __restrict__ b,
+                                                      F* __restrict__ r) {
+  const int a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= n) return;
+  F q0 = F(0), q1 = F(0);
+  for (int e = ptr[a]; e < ptr[a + 1]; ++e) {
+    F B[4];
+    load2x2(A + 4 * (int64_t)e, 1, B);
+    const int c = col[e];
+    q0 += B[0] * x[2 * c] + B[1] * x[2 * c + 1];
+    q1 += B[2] * x[2 * c] + B[3] * x[2 * c + 1];
+  }
+  r[2 * a] = b[2 * a] - q0;
+  r[2 * a + 1] = b[2 * a + 1] - q1;
+}
+
+// bc = P^T r (one thread per coarse vertex)
+template <class F>
+__global__ void __launch_bounds__(128) k_amg_restrict(int nc, const int32_t* __restrict__ ptptr,
+                                                      const int32_t* __restrict__ ptsrc,
+                                                      const int32_t* __restrict__ prow, const F* __restrict__ P,
+                                                      const F* __restrict__ r, F* __restrict__ bc) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  if (I >= nc) return;
+  F s0 = F(0), s1 = F(0);
+  for (int q = ptptr[I]; q < ptptr[I + 1]; ++q) {
+    const int f = ptsrc[q], i = prow[f];
+    F B[4];
+    load2x2(P + 4 * (int64_t)f, 1, B);
+    s0 += B[0] * r[2 * i] + B[2] * r[2 * i + 1];
+    s1 += B[1] * r[2 * i] + B[3] * r[2 * i + 1];
+  }
+  bc[2 * I] = s0;
+  bc[2 * I + 1] = s1;
+}
+
+// x += P xc (one thread per fine vertex)
+template <class F>
+__global__ void __launch_bounds__(128) k_amg_prolong_add(int n, const int32_t* __restrict__ pptr,
+                                                         const int32_t* __restrict__ pcol, const F* __restrict__ P,
+                                                         const F* __restrict__ xc, F* __restrict__ x) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  F s0 = F(0), s1 = F(0);
+  for (int f = pptr[i]; f < pptr[i + 1]; ++f) {
+    F B[4];
+    load2x2(P + 4 * (int64_t)f, 1, B);
+    const int J = pcol[f];
+    s0 += B[0] * xc[2 * J] + B[1] * xc[2 * J + 1];
+    s1 += B[2] * xc[2 * J] + B[3] * xc[2 * J + 1];
+  }
+  x[2 * i] += s0;
+  x[2 * i + 1] += s1;
+}
+
+template <class F>
+__global__ void __launch_bounds__(NT) k_amg_add(int n2, const F* __restrict__ y, F* __restrict__ x) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n2) x[i] += y[i];
+}
+
+template <class F>
+F* fp(double* p) {
+  return reinterpret_cast<F*>(p);
+}
+
+// Numeric setup of the hierarchy from level 0 (A_c, D^-1, lam already formed by mdsc_setup_t).
+template <class F>
+int amg_numeric(bp_mesh* m, cudaStream_t s) {
+  AmgHier* H = static_cast<AmgHier*>(m->ws->amg);
+  const int nl = (int)H->lv.size();
+  for (int k = 0; k < nl; ++k) {
+    AmgLevel& L = H->lv[k];
+    if (k > 0) {
+      BP_CUDA_TRY(cudaMemsetAsync(L.lam, 0, sizeof(double), s));
+      k_amg_diag<F><<<(L.n + 127) / 128, 128, 0, s>>>(L.n, L.ptr, L.diag, fp<F>(L.A), fp<F>(L.Dinv), L.lam);
+    }
+    if (k == nl - 1) break;
+    k_amg_cheb<<<1, 1, 0, s>>>(L.lam, MDSC_RATIO, AMG_SMOOTH, L.cheb);
+    AmgLevel& N = H->lv[k + 1];
+    k_amg_pvals<F><<<(L.pnnz + 127) / 128, 128, 0, s>>>(L.pnnz, L.prow, L.pvptr, L.pvsrc, L.pdiag, fp<F>(L.A),
+                                                        fp<F>(L.Dinv), L.lam, fp<F>(L.P));
+    k_amg_pairs<F, false><<<(L.tnnz + 127) / 128, 128, 0, s>>>(L.tnnz, L.tvptr, L.tvsrc, fp<F>(L.A), fp<F>(L.P),
+                                                               fp<F>(L.T));
+    k_amg_pairs<F, true><<<(N.nnz + 127) / 128, 128, 0, s>>>(N.nnz, L.cvptr, L.cvsrc, fp<F>(L.P), fp<F>(L.T),
+                                                             fp<F>(N.A));
+  }
+  const AmgLevel& C = H->lv.back();
+  k_amg_dense_inverse<F><<<1, 256, 0, s>>>(C.n, C.ptr, C.col, fp<F>(C.A), fp<F>(H->W), fp<F>(H->Cinv));
+  BP_CUDA_TRY(cudaGetLastError());
+  return BP_OK;
+}
+
+// x_k = V-cycle(b_k) on level k
+template <class F>
+void amg_vcycle(const AmgHier* H, int k, cudaStream_t s) {
+  const AmgLevel& L = H->lv[k];
+  const int g = (L.n + 127) / 128, gv = (L.n + NT - 1) / NT;
+  if (k == (int)H->lv.size() - 1) {
+    k_amg_dense_apply<F><<<1, 256, 0, s>>>(2 * L.n, fp<F>(H->Cinv), fp<F>(L.b), fp<F>(L.x));
+    return;
+  }
+  F* d[2] = {fp<F>(L.d0), fp<F>(L.d1)};
+  // pre-smoothing: x = Cheb(b) from zero
+  k_mdsc_cheb_init<F><<<gv, NT, 0, s>>>(fp<F>(L.Dinv), L.cheb, fp<F>(L.b), fp<F>(L.x), fp<F>(L.rr), d[0], L.n);
+  for (int q = 0; q < AMG_SMOOTH; ++q)
+    k_mdsc_cheb_step<F><<<gv, NT, 0, s>>>(fp<F>(L.A), fp<F>(L.Dinv), L.ptr, L.col, L.cheb, q, d[q & 1],
+                                          d[(q + 1) & 1], fp<F>(L.x), fp<F>(L.rr), L.n);
+  // coarse correction
+  const AmgLevel& N = H->lv[k + 1];
+  k_amg_residual<F><<<g, 128, 0, s>>>(L.n, L.ptr, L.col, fp<F>(L.A), fp<F>(L.x), fp<F>(L.b), fp<F>(L.r));
+  k_amg_restrict<F><<<(N.n + 127) / 128, 128, 0, s>>>(N.n, L.ptptr, L.ptsrc, L.prow, fp<F>(L.P), fp<F>(L.r),
+                                                      fp<F>(N.b));
+  amg_vcycle<F>(H, k + 1, s);
+  k_amg_prolong_add<F><<<g, 128, 0, s>>>(L.n, L.pptr, L.pcol, fp<F>(L.P), fp<F>(N.x), fp<F>(L.x));
+  // post-smoothing: x += Cheb(b - A x)
+  k_amg_residual<F><<<g, 128, 0, s>>>(L.n, L.ptr, L.col, fp<F>(L.A), fp<F>(L.x), fp<F>(L.b), fp<F>(L.r));
+  k_mdsc_cheb_init<F><<<gv, NT, 0, s>>>(fp<F>(L.Dinv), L.cheb, fp<F>(L.r), fp<F>(L.y), fp<F>(L.rr), d[0], L.n);
+  for (int q = 0; q < AMG_SMOOTH; ++q)
+    k_mdsc_cheb_step<F><<<gv, NT, 0, s>>>(fp<F>(L.A), fp<F>(L.Dinv), L.ptr, L.col, L.cheb, q, d[q & 1],
+                                          d[(q + 1) & 1], fp<F>(L.y), fp<F>(L.rr), L.n);
+  k_amg_add<F><<<(2 * L.n + NT - 1) / NT, NT, 0, s>>>(2 * L.n, fp<F>(L.y), fp<F>(L.x));
+}
+
+// MDSC setup with the SA-AMG plane solve: the two-level setup (column factors, P, A_c, D^-1, lam),
+// the hierarchy's patterns (first call on the mesh) and its numeric setup.
+template <class M>
+int mdsc_amg_setup_t(bp_mesh* m, const M* J, cudaStream_t s) {
+  int rc = mdsc_setup_t(m, J, s);
+  if (rc) return rc;
+  if ((rc = amg_build(m))) return rc;
+  return amg_numeric<M>(m, s);
+}
+
 // z = M^-1 r (the cycle above) for vectors V, Jacobian values M, factors and plane data F.
-template <class M, class V, class F>
+template <class M, class V, class F, bool AMG = false>
 void mdsc_apply_launch(bp_mesh* m, const M* J, const V* r, V* z, cudaStream_t s) {
   bp_solver_ws* w = m->ws;
   const Prec<F> Pr = prec_of<F>(m);
@@ -1858,11 +2358,15 @@ void mdsc_apply_launch(bp_mesh* m, const M* J, const V* r, V* z, cudaStream_t s)
                                                  nullptr, nullptr, nullptr, 0);
   k_mdsc_sub<V><<<gvec, NT, 0, s>>>(r, t, n);
   k_mdsc_restrict<V, F><<<gcol, 128, 0, s>>>(P, t, rc, m->nv, m->nl);
-  // ec = B_c rc
-  k_mdsc_cheb_init<F><<<gv, NT, 0, s>>>(Dinv, w->mcheb, rc, ec, rr, d[0], m->nv);
-  for (int k = 0; k < MDSC_STEPS; ++k)
-    k_mdsc_cheb_step<F><<<gv, NT, 0, s>>>(Ac, Dinv, m->nbr_ptr, m->nbr_idx, w->mcheb, k, d[k & 1], d[(k + 1) & 1],
-                                          ec, rr, m->nv);
+  // ec = B_c rc: the Chebyshev plane iteration, or one SA-AMG V-cycle (level 0 reads rc, writes ec)
+  if constexpr (AMG) {
+    amg_vcycle<F>(static_cast<const AmgHier*>(w->amg), 0, s);
+  } else {
+    k_mdsc_cheb_init<F><<<gv, NT, 0, s>>>(Dinv, w->mcheb, rc, ec, rr, d[0], m->nv);
+    for (int k = 0; k < MDSC_STEPS; ++k)
+      k_mdsc_cheb_step<F><<<gv, NT, 0, s>>>(Ac, Dinv, m->nbr_ptr, m->nbr_idx, w->mcheb, k, d[k & 1],
+                                            d[(k + 1) & 1], ec, rr, m->nv);
+  }
   // z2 = z1 + P ec (in z1);  z = z2 + S (r - J z2)
   k_mdsc_prolong_add<V, F><<<gcol, 128, 0, s>>>(P, ec, z1, m->nv, m->nl);
   k_spmv_pairs<M, V, false><<<gspmv, NT, 0, s>>>(m->rowptr, m->nbr_ptr, m->nbr_idx, m->nl, J, (int)(n / 2), z1, t,
@@ -1926,7 +2430,7 @@ __global__ void __launch_bounds__(NT) k_pcg_rz(const int* kbase, int j, int shif
 }
 
 // One MDSC-preconditioned CG iteration (the loop body when `loop` is set).
-template <class M, class V>
+template <class M, class V, bool AMG = false>
 void launch_mdsc_iteration(bp_mesh* m, const M* J, cudaStream_t s, cudaGraphConditionalHandle loop, int set_loop) {
   bp_solver_ws* w = m->ws;
   const int64_t n = m->ndof;
@@ -1939,20 +2443,21 @@ void launch_mdsc_iteration(bp_mesh* m, const M* J, cudaStream_t s, cudaGraphCond
   k_spmv_pairs<M, V, true><<<gspmv, NT, 0, s>>>(m->rowptr, m->nbr_ptr, m->nbr_idx, m->nl, J, (int)(n / 2), p, q,
                                                 w->scal, w->stop, w->kbase, 0);
   k_pcg_update<V><<<gvec, NT, 0, s>>>(w->kbase, 0, x, r, p, q, n, w->scal, w->stop);
-  mdsc_apply_launch<M, V, V>(m, J, r, z, s);
+  mdsc_apply_launch<M, V, V, AMG>(m, J, r, z, s);
   k_pcg_rz<V><<<gvec, NT, 0, s>>>(w->kbase, 0, 1, r, z, n, w->scal, w->stop);
   k_cg_direction<V><<<grid_for(n / 2, NT), NT, 0, s>>>(w->kbase, 0, w->cgpar, n / 2, z, p, w->scal, w->stop, loop,
                                                        set_loop);
   k_cg_advance<<<1, 1, 0, s>>>(w->kbase, 1);
 }
 
-template <class M, class V>
+template <class M, class V, bool AMG = false>
 int mdsc_loop_graph(bp_mesh* m, const M* J, cudaGraphExec_t* out) {
   bp_solver_ws* w = m->ws;
   const int slot = sizeof(V) == sizeof(float) ? 1 : 0;
+  void** loops = AMG ? w->amg_loop : w->mdsc_loop;
   *out = nullptr;
   if (w->cg_loop_failed[slot]) return BP_OK;
-  if (!w->mdsc_loop[slot]) {
+  if (!loops[slot]) {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     cudaStream_t cs = nullptr;
@@ -1973,7 +2478,7 @@ int mdsc_loop_graph(bp_mesh* m, const M* J, cudaGraphExec_t* out) {
       e = cudaStreamBeginCaptureToGraph(cs, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
                                         cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-      launch_mdsc_iteration<M, V>(m, J, cs, h, 1);
+      launch_mdsc_iteration<M, V, AMG>(m, J, cs, h, 1);
       const cudaError_t le = cudaGetLastError();  // a launch the capture refused
       cudaGraph_t body = nullptr;
       e = cudaStreamEndCapture(cs, &body);
@@ -1986,15 +2491,15 @@ int mdsc_loop_graph(bp_mesh* m, const M* J, cudaGraphExec_t* out) {
       cudaGetLastError();
       return BP_OK;  // the caller iterates from the host
     }
-    w->mdsc_loop[slot] = exec;
+    loops[slot] = exec;
   }
-  *out = (cudaGraphExec_t)w->mdsc_loop[slot];
+  *out = (cudaGraphExec_t)loops[slot];
   return BP_OK;
 }
 
 // MDSC-preconditioned CG on J delta = -R to ||r|| <= eta ||R||; delta in ws->x (type V).  The
 // Jacobian J must be the one mdsc_setup_t saw (captured in the loop graph by address).
-template <class M, class V>
+template <class M, class V, bool AMG = false>
 int mdsc_cg_solve(bp_mesh* m, const M* J, double eta, int maxit, bool device_loop, cudaStream_t s, int* iters,
                   int* status) {
   bp_solver_ws* w = m->ws;
@@ -2004,7 +2509,7 @@ int mdsc_cg_solve(bp_mesh* m, const M* J, double eta, int maxit, bool device_loo
   V* z = reinterpret_cast<V*>(w->z);
   V* p = reinterpret_cast<V*>(w->p);
   cudaGraphExec_t loop = nullptr;
-  int rc = device_loop ? mdsc_loop_graph<M, V>(m, J, &loop) : BP_OK;
+  int rc = device_loop ? mdsc_loop_graph<M, V, AMG>(m, J, &loop) : BP_OK;
   if (rc) return rc;
   BP_CUDA_TRY(cudaMemsetAsync(w->scal, 0, 3 * (size_t)(maxit + 2 + CG_BATCH) * sizeof(double), s));
   BP_CUDA_TRY(cudaMemsetAsync(w->stop, 0, sizeof(int), s));
@@ -2014,7 +2519,7 @@ int mdsc_cg_solve(bp_mesh* m, const M* J, double eta, int maxit, bool device_loo
   BP_CUDA_TRY(cudaMemcpyAsync(w->cgpar, w->hpar, 2 * sizeof(double), cudaMemcpyHostToDevice, s));
   const int gvec = grid_for(n, NT);
   k_pcg_init<V><<<gvec, NT, 0, s>>>(w->R, reinterpret_cast<V*>(w->x), r, n, w->scal);
-  mdsc_apply_launch<M, V, V>(m, J, r, z, s);
+  mdsc_apply_launch<M, V, V, AMG>(m, J, r, z, s);
   k_pcg_rz<V><<<gvec, NT, 0, s>>>(w->kbase, 0, 0, r, z, n, w->scal, w->stop);
   BP_CUDA_TRY(cudaMemcpyAsync(p, z, n * sizeof(V), cudaMemcpyDeviceToDevice, s));
   BP_CUDA_TRY(cudaGetLastError());
@@ -2031,7 +2536,7 @@ int mdsc_cg_solve(bp_mesh* m, const M* J, double eta, int maxit, bool device_loo
     std::memcpy(&stopflag, w->host + w->host_cap - 1, sizeof(int));
   } else {  // no conditional nodes: one iteration per host check
     while (!stopflag && k < maxit) {
-      launch_mdsc_iteration<M, V>(m, J, s, cudaGraphConditionalHandle{}, 0);
+      launch_mdsc_iteration<M, V, AMG>(m, J, s, cudaGraphConditionalHandle{}, 0);
       BP_CUDA_TRY(cudaGetLastError());
       BP_CUDA_TRY(cudaMemcpyAsync(w->host + w->host_cap - 1, w->stop, sizeof(int), cudaMemcpyDeviceToHost, s));
       BP_CUDA_TRY(cudaStreamSynchronize(s));
@@ -2083,6 +2588,9 @@ void bp_solver_ws_free(bp_mesh* m) {
     if (g) cudaGraphExecDestroy((cudaGraphExec_t)g);
   for (void* g : m->ws->mdsc_loop)
     if (g) cudaGraphExecDestroy((cudaGraphExec_t)g);
+  for (void* g : m->ws->amg_loop)
+    if (g) cudaGraphExecDestroy((cudaGraphExec_t)g);
+  delete static_cast<AmgHier*>(m->ws->amg);
   delete m->ws;  // device arrays are in m->allocations
   m->ws = nullptr;
 }
@@ -2187,6 +2695,49 @@ extern "C" int bp_mdsc_apply(bp_mesh* m, const void* J, const double* r, double*
   return BP_OK;
 }
 
+extern "C" int bp_mdsc_amg_setup(bp_mesh* m, const void* J, int precision, void* stream) {
+  if (!m || !J) return BP_EINVAL;
+  if (precision != BP_F64 && precision != BP_F32 && precision != BP_F32_ALL) return BP_EINVAL;
+  bp_device_guard g(m->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc = ensure_ws(m, s);
+  if (rc) return rc;
+  rc = precision == BP_F64 ? mdsc_amg_setup_t(m, (const double*)J, s) : mdsc_amg_setup_t(m, (const float*)J, s);
+  if (rc) return rc;
+  m->ws->has_amg = true;
+  return BP_OK;
+}
+
+extern "C" int bp_mdsc_amg_apply(bp_mesh* m, const void* J, const double* r, double* z, void* stream) {
+  if (!m || !J || !r || !z || !bp_aligned16(r) || !bp_aligned16(z) || !bp_aligned16(J)) return BP_EINVAL;
+  if (!m->ws || !m->ws->has_mdsc || !m->ws->amg) return BP_EINVAL;
+  bp_device_guard g(m->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (m->ws->mdsc_f32)
+    mdsc_apply_launch<float, double, float, true>(m, (const float*)J, r, z, s);
+  else
+    mdsc_apply_launch<double, double, double, true>(m, (const double*)J, r, z, s);
+  BP_CUDA_TRY(cudaGetLastError());
+  return BP_OK;
+}
+
+extern "C" int bp_mdsc_amg_levels(const bp_mesh* m, int32_t* sizes, int max_levels, int* nlevels) {
+  if (!m || !nlevels || !m->ws || !m->ws->amg) return BP_EINVAL;
+  const AmgHier* H = static_cast<const AmgHier*>(m->ws->amg);
+  *nlevels = (int)H->lv.size();
+  if (sizes)
+    for (int k = 0; k < std::min(max_levels, (int)H->lv.size()); ++k) sizes[k] = H->lv[k].n;
+  return BP_OK;
+}
+
+extern "C" int bp_mdsc_amg_aggregates(const bp_mesh* m, int level, int32_t* agg) {
+  if (!m || !agg || !m->ws || !m->ws->amg) return BP_EINVAL;
+  const AmgHier* H = static_cast<const AmgHier*>(m->ws->amg);
+  if (level < 0 || level >= (int)H->agg.size()) return BP_EINVAL;
+  std::copy(H->agg[level].begin(), H->agg[level].end(), agg);
+  return BP_OK;
+}
+
 extern "C" int bp_energy(bp_mesh* m, const double* U, double* out, void* stream) {
   if (!m || !U || !out) return BP_EINVAL;
   bp_device_guard g(m->device);
@@ -2251,7 +2802,8 @@ extern "C" int bp_newton_solve(bp_mesh* m, double* U, const bp_solve_opts* opts,
   if (!(o.picard_rtol >= 0) || !(o.value32_rtol >= 0)) return BP_EINVAL;
   if (o.value32_rtol > 0 && o.value32_rtol < o.rtol) return BP_EINVAL;  // an FP32 residual could pass the test
   if ((o.device_loop != 0 && o.device_loop != 1) ||
-      (o.preconditioner != BP_PREC_COLUMN && o.preconditioner != BP_PREC_MDSC))
+      (o.preconditioner != BP_PREC_COLUMN && o.preconditioner != BP_PREC_MDSC &&
+       o.preconditioner != BP_PREC_MDSC_AMG))
     return BP_EINVAL;
   if (!(o.rtol > 0) || o.max_newton < 0 || o.max_newton > 64 || o.max_krylov < 1 || o.check_every < 1 ||
       (o.precision != BP_F64 && o.precision != BP_F32) ||
@@ -2338,9 +2890,12 @@ extern "C" int bp_newton_solve(bp_mesh* m, double* U, const bp_solve_opts* opts,
     eta = std::max(eta, eta_floor);
     fprev = fn;
     // preconditioner + Krylov
+    const bool amg = o.preconditioner == BP_PREC_MDSC_AMG;
     const bool mdsc = o.preconditioner == BP_PREC_MDSC;
     BP_CUDA_TRY(cudaEventRecord(ev[3], s));
-    if (mdsc)
+    if (amg)
+      rc = f32 ? mdsc_amg_setup_t(m, reinterpret_cast<const float*>(w->J), s) : mdsc_amg_setup_t(m, w->J, s);
+    else if (mdsc)
       rc = f32 ? mdsc_setup_t(m, reinterpret_cast<const float*>(w->J), s) : mdsc_setup_t(m, w->J, s);
     else
       rc = f32 ? colprec_setup_t(m, reinterpret_cast<const float*>(w->J), s) : colprec_setup_t(m, w->J, s);
@@ -2353,6 +2908,11 @@ extern "C" int bp_newton_solve(bp_mesh* m, double* U, const bp_solve_opts* opts,
                                      &its, &kst);
     else if (gmres)
       rc = gmres_solve<double, double>(m, w->J, eta, o.max_krylov, o.gmres_restart, s, &its, &kst);
+    else if (amg && f32)
+      rc = mdsc_cg_solve<float, float, true>(m, reinterpret_cast<const float*>(w->J), eta, o.max_krylov,
+                                             o.device_loop != 0, s, &its, &kst);
+    else if (amg)
+      rc = mdsc_cg_solve<double, double, true>(m, w->J, eta, o.max_krylov, o.device_loop != 0, s, &its, &kst);
     else if (mdsc && f32)
       rc = mdsc_cg_solve<float, float>(m, reinterpret_cast<const float*>(w->J), eta, o.max_krylov,
                                        o.device_loop != 0, s, &its, &kst);
