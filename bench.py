@@ -343,12 +343,16 @@ def run_ours(args):
                                                         capi.BP_SCATTER_COLOR, capi.BP_JAC_FACTORED, stream))
     all32_ms = timed(lambda: capi.bp_assemble_jacobian(dm.handle, U, R, J32, capi.BP_F32_ALL,
                                                        capi.BP_SCATTER_ATOMIC, capi.BP_JAC_FACTORED, stream))
+    ds32_ms = timed(lambda: capi.bp_assemble_jacobian(dm.handle, U, R, J32, capi.BP_F32_DS,
+                                                      capi.BP_SCATTER_ATOMIC, capi.BP_JAC_FACTORED, stream))
     all32c_ms = timed(lambda: capi.bp_assemble_jacobian(dm.handle, U, R, J32, capi.BP_F32_ALL,
                                                         capi.BP_SCATTER_COLOR, capi.BP_JAC_FACTORED, stream))
     dual_ms = timed(lambda: capi.bp_assemble_jacobian(dm.handle, U, R, J, capi.BP_F64,
                                                       capi.BP_SCATTER_ATOMIC, capi.BP_JAC_DUAL, stream), reps=5)
     pair_ms = timed(lambda: capi.bp_assemble_jacobian(dm.handle, U, R, J, capi.BP_F64X2,
                                                       capi.BP_SCATTER_ATOMIC, capi.BP_JAC_FACTORED, stream))
+    pair_ds_ms = timed(lambda: capi.bp_assemble_jacobian(dm.handle, U, R, J, capi.BP_F64X2_DS,
+                                                         capi.BP_SCATTER_ATOMIC, capi.BP_JAC_FACTORED, stream))
     # temperature-dependent rate factor (nodal Arrhenius field interpolated at the quadrature points)
     capi.bp_mesh_set_rate_factor(dm.handle, synth.arrhenius_rate_factor(mesh))
     arr_ms = timed(lambda: capi.bp_assemble_jacobian(dm.handle, U, R, J, capi.BP_F64,
@@ -435,6 +439,13 @@ def run_ours(args):
                 "jacobian_f64_dual12": {"value": W / (dual_ms * 1e-3), "unit": UNIT, "ms": dual_ms},
                 "jacobian_paired_f32_lanes": {"value": W / (pair_ms * 1e-3), "unit": UNIT, "ms": pair_ms,
                                               "note": "FP64-accurate (1e-12 parity) lanes of hi+lo FP32 pairs"},
+                "jacobian_paired_lanes_double_single_values": {
+                    "value": W / (pair_ds_ms * 1e-3), "unit": UNIT, "ms": pair_ds_ms,
+                    "note": "BP_F64X2_DS: paired lanes and a double-single value path; R and J FP64-accurate "
+                            "(1e-12 parity) with the quadrature-point arithmetic on the FP32 pipe"},
+                "jacobian_f32_lanes_double_single_values": {
+                    "value": W / (ds32_ms * 1e-3), "unit": UNIT, "ms": ds32_ms,
+                    "note": "BP_F32_DS: FP32 lanes, double-single value path (R FP64-accurate)"},
                 "jacobian_f64_arrhenius_field": {"value": W / (arr_ms * 1e-3), "unit": UNIT, "ms": arr_ms,
                                                  "note": "nodal rate-factor field (Arrhenius) instead of a constant A"},
                 "zero_init_ms": zero_ms, "wall_s_timed_region": t_wall},
@@ -623,6 +634,12 @@ def newton_section(capi, synth, dm, mesh, dev, skip_large=False, reps=3):
     f32, U32 = solve(dm, capi.BP_F32)
     out[mesh.name] = {"f64": f64, "mixed_f32": f32, "speedup_mixed": f64["s"] / f32["s"],
                       "mixed_vs_f64_solution_rel_inf": float((U32 - U64).abs().max() / U64.abs().max())}
+    # the same two paths with the double-single value path (residual FP64-accurate on the FP32 pipe):
+    # FP64-accurate Jacobian from paired lanes with FP64 Krylov, and FP32 lanes with FP32 Krylov
+    for name, prec in (("f64_accurate_double_single", capi.BP_F64X2_DS), ("mixed_f32_double_single", capi.BP_F32_DS)):
+        v, Uv = solve(dm, prec)
+        v["vs_f64_solution_rel_inf"] = float((Uv - U64).abs().max() / U64.abs().max())
+        out[mesh.name][name] = v
     # early steps with the FP32 value path (inexact residual) until ||F|| <= tau ||F(0)||
     for tau in (1e-2, 1e-3, 1e-4):
         v, Uv = solve(dm, capi.BP_F32, value32_rtol=tau)
@@ -630,10 +647,16 @@ def newton_section(capi, synth, dm, mesh, dev, skip_large=False, reps=3):
         out[mesh.name][f"mixed_f32_value32_until_{tau:g}"] = v
     # the MDSC two-level preconditioner (semicoarsening + Chebyshev plane iteration) instead of the
     # vertical-line solve
-    for name, prec in (("f64_mdsc", capi.BP_F64), ("mixed_f32_mdsc", capi.BP_F32)):
-        v, Uv = solve(dm, prec, preconditioner=capi.BP_PREC_MDSC)
+    for name, prec, pk in (("f64_mdsc", capi.BP_F64, capi.BP_PREC_MDSC),
+                           ("mixed_f32_mdsc", capi.BP_F32, capi.BP_PREC_MDSC),
+                           ("mixed_f32_mdsc_amg", capi.BP_F32, capi.BP_PREC_MDSC_AMG)):
+        v, Uv = solve(dm, prec, preconditioner=pk)
         v["vs_f64_solution_rel_inf"] = float((Uv - U64).abs().max() / U64.abs().max())
         out[mesh.name][name] = v
+    # GMRES(50) with the column preconditioner (the paper's Krylov method), the cross-check of CG
+    v, Uv = solve(dm, capi.BP_F32, krylov=capi.BP_KRYLOV_GMRES)
+    v["vs_f64_solution_rel_inf"] = float((Uv - U64).abs().max() / U64.abs().max())
+    out[mesh.name]["mixed_f32_gmres50"] = v
     out[mesh.name]["learned_start_mixed"] = learned_start(capi, dm, dev, reps)
     # the ocean margin condition (lateral faces of a grounded calving front, partly below sea level)
     marine = synth.config_marine()
@@ -657,12 +680,44 @@ def newton_section(capi, synth, dm, mesh, dev, skip_large=False, reps=3):
         b32, V32 = solve(dmb, capi.BP_F32, reps=1)
         bv, _ = solve(dmb, capi.BP_F32, reps=1, value32_rtol=1e-3)
         bm, _ = solve(dmb, capi.BP_F32, reps=1, preconditioner=capi.BP_PREC_MDSC)
+        ba, _ = solve(dmb, capi.BP_F32, reps=1, preconditioner=capi.BP_PREC_MDSC_AMG)
         out[big.name] = {"wedges": big.nwedges, "f64": b64, "mixed_f32": b32, "speedup_mixed": b64["s"] / b32["s"],
-                         "mixed_f32_value32_until_1e-3": bv, "mixed_f32_mdsc": bm,
+                         "mixed_f32_value32_until_1e-3": bv, "mixed_f32_mdsc": bm, "mixed_f32_mdsc_amg": ba,
                          "mixed_vs_f64_solution_rel_inf": float((V32 - V64).abs().max() / V64.abs().max())}
         del V64, V32
         dmb.close()
     return out
+
+
+def mdsc_scaling(ms):
+    """Mixed-precision Newton solves (shallow-ice start, 1e-8) of growing domes (m x m grid, 10 layers)
+    with the column preconditioner, the MDSC cycle (Chebyshev plane solve) and the MDSC cycle with the
+    SA-AMG plane solve: time (best of 2), Newton steps, CG iterations; one JSON line per mesh."""
+    import torch
+    from paper_2204_04321_b300 import capi, synth
+    for m in ms:
+        mesh = synth.dome_mesh(m, 10, 201, 202, bed="sinusoidal", beta="field")
+        dm = capi.DeviceMesh(mesh)
+        row = {"m": m, "wedges": mesh.nwedges}
+        for name, pk in (("column", capi.BP_PREC_COLUMN), ("mdsc", capi.BP_PREC_MDSC),
+                         ("mdsc_amg", capi.BP_PREC_MDSC_AMG)):
+            ts, rep = [], None
+            for _ in range(2):
+                U = torch.empty(dm.ndof, dtype=torch.float64, device="cuda")
+                capi.bp_initial_guess(dm.handle, capi.BP_GUESS_SIA, U)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                _, rep = capi.bp_newton_solve(dm.handle, U, precision=capi.BP_F32, max_krylov=8000,
+                                              preconditioner=pk)
+                torch.cuda.synchronize()
+                ts.append(time.perf_counter() - t0)
+                del U
+            row[name] = {"s": min(ts), "newton": rep["newton_iters"], "cg": rep["krylov_iters"],
+                         "converged": rep["converged"], "t_krylov": rep["t_krylov"], "t_precond": rep["t_precond"]}
+        row["amg_levels"] = capi.bp_mdsc_amg_levels(dm.handle)
+        dm.close()
+        torch.cuda.empty_cache()
+        print(json.dumps(row), flush=True)
 
 
 def kernel_hash():
@@ -702,6 +757,8 @@ def main():
     ap.add_argument("--cg-host-loop", action="store_true",
                     help="iterate CG from the host (device_loop 0) so that a kernel profiler lists every "
                          "CG launch (the device-driven loop launches its kernels from the device)")
+    ap.add_argument("--mdsc-scaling", type=int, nargs="+", metavar="M",
+                    help="only the preconditioner comparison on m x m x 10 domes (one JSON line each)")
     ap.add_argument("--mesh-m", type=int, default=224, help="base grid size (224: the 1M-wedge workload)")
     ap.add_argument("--layers", type=int, default=10)
     args = ap.parse_args()
@@ -709,6 +766,8 @@ def main():
         SOLVE_KW["device_loop"] = 0
     if args.impl == "reference":
         return run_reference(args)
+    if args.mdsc_scaling:
+        return mdsc_scaling(args.mdsc_scaling) or 0
     return run_ours(args)
 
 

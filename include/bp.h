@@ -106,14 +106,23 @@ typedef struct {
   int64_t device_bytes; /* device memory held by the mesh object */
 } bp_mesh_info_t;
 
-/* Jacobian precision of the derivative lanes (the residual is FP64 except with BP_F32_ALL):
+/* Jacobian precision of the derivative lanes (the residual is FP64 except with BP_F32_ALL, and
+ * FP64-accurate double-single with the _DS kinds):
  *   BP_F64   native FP64 lanes;
  *   BP_F32   FP32 lanes (J values are float);
  *   BP_F64X2 FP64-accurate lanes built from pairs of FP32 numbers (hi + lo, error-free sum and
  *            product transformations, relative error ~2^-46 per operation); J values are double;
  *            Jacobian assembly only, sum-factorised method only.  It moves the lane arithmetic to
- *            the FP32 pipe (~60x the FP64 rate on B300), but the doubled register footprint of the
- *            element matrix spills, and on B300 it measures slower than BP_F64 lanes.
+ *            the FP32 pipe (~60x the FP64 rate on B300); the rank-one part of the element matrix
+ *            is applied in a loop over the quadrature points whose factors wait in shared memory.
+ *   BP_F32_DS   FP32 lanes with a double-single value path: the quadrature-point arithmetic of the
+ *            residual and of the viscosity in pairs of FP32 numbers (~2^-47 per operation; the
+ *            inverse cube root from an FP32 seed and one pair correction), the per-column and
+ *            per-level geometry in FP64.  R is FP64-accurate (same parity bar as BP_F64); J values
+ *            are float.  Sum-factorised method only.
+ *   BP_F64X2_DS paired lanes and the double-single value path: residual and Jacobian FP64-accurate
+ *            with the quadrature-point arithmetic on the FP32 pipe; J values are double.
+ *            Sum-factorised method only; no Picard matrix.
  *   BP_F32_ALL  FP32 lanes and an FP32 value path: the geometry, the 2D velocity gradients and the
  *            vertical velocity differences are formed in FP64 and rounded once, everything at the
  *            quadrature points (strain rates, viscosity, stresses, element residual) runs in FP32.
@@ -121,7 +130,7 @@ typedef struct {
  *            ~1e-7 of the element contributions).  Sum-factorised method only.  Meant for the
  *            early steps of an inexact Newton solve (bp_solve_opts.value32_rtol), where the
  *            residual is far above that rounding. */
-enum { BP_F64 = 0, BP_F32 = 1, BP_F64X2 = 2, BP_F32_ALL = 3 };
+enum { BP_F64 = 0, BP_F32 = 1, BP_F64X2 = 2, BP_F32_ALL = 3, BP_F32_DS = 4, BP_F64X2_DS = 5 };
 /* Scatter of element contributions: atomics, or colour by colour with plain read-modify-write. */
 enum { BP_SCATTER_AUTO = 0, BP_SCATTER_ATOMIC = 1, BP_SCATTER_COLOR = 2 };
 /* How the element Jacobian is formed: forward-mode dual numbers with 12 lanes (one per
@@ -288,7 +297,11 @@ typedef struct {
   int max_krylov;     /* Krylov iterations per Newton step */
   double eta_max;     /* Eisenstat-Walker forcing term cap (choice 2, gamma = 0.9) */
   int precision;      /* BP_F64: FP64 Jacobian and Krylov; BP_F32: FP32 Jacobian lanes and Krylov
-                         (inexact Newton); the residual, viscosity, norms and update stay FP64 */
+                         (inexact Newton); the residual, viscosity, norms and update stay FP64.
+                         BP_F64X2_DS: FP64-accurate residual and Jacobian from the double-single value
+                         path and paired lanes, FP64 Krylov, the line search's energy change in pairs
+                         (no Picard steps); BP_F32_DS: as BP_F32 with the double-single value path
+                         (residual FP64-accurate) */
   int krylov;         /* BP_KRYLOV_CG (default: the Jacobian is SPD), or BP_KRYLOV_GMRES: restarted
                          GMRES(gmres_restart) as the paper's Krylov method, right-preconditioned by
                          the column solve (classical Gram-Schmidt twice; the Hessenberg problem on the

@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(HERE, "libbp.so")
 
 BP_OK, BP_EINVAL, BP_EMESH, BP_ENOMEM, BP_ECUDA, BP_ENAN, BP_ENOCONV, BP_EUNSUP, BP_ESIZE, BP_EIO = range(10)
 BP_NOALLOC_MAX_NDOF = 1048576
-BP_F64, BP_F32, BP_F64X2, BP_F32_ALL = 0, 1, 2, 3
+BP_F64, BP_F32, BP_F64X2, BP_F32_ALL, BP_F32_DS, BP_F64X2_DS = 0, 1, 2, 3, 4, 5
 BP_SCATTER_AUTO, BP_SCATTER_ATOMIC, BP_SCATTER_COLOR = 0, 1, 2
 BP_JAC_AUTO, BP_JAC_DUAL, BP_JAC_FACTORED = 0, 1, 2
 BP_GUESS_ZERO, BP_GUESS_SIA = 0, 1
@@ -499,7 +499,7 @@ class DeviceMesh:
                  R=None, J=None, want_residual=True, stream=None):
         import torch
         if J is None:
-            J = torch.empty(self.nnz, dtype=torch.float32 if precision in (BP_F32, BP_F32_ALL) else torch.float64,
+            J = torch.empty(self.nnz, dtype=torch.float32 if precision in (BP_F32, BP_F32_ALL, BP_F32_DS) else torch.float64,
                             device=self.device)
         if R is None and want_residual:
             R = torch.empty(self.ndof, dtype=torch.float64, device=self.device)

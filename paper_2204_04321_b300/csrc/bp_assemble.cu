@@ -39,13 +39,13 @@ __global__ void __launch_bounds__(128, min_blocks<TL, TV>()) k_assemble(const As
 // Paired-FP32 lanes with the staged rank-one part (blocks of 64: 81 lanes per thread in shared memory,
 // the in-plane table, the carried block and the 6 points' rank-one factors).
 constexpr int STAGED_TPB = 64;
-template <bool ATOMIC>
+template <bool ATOMIC, class TV = double>
 __global__ void __launch_bounds__(STAGED_TPB) k_assemble_staged(const AsmArgs A) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= A.count) return;
   const int t = A.tri_list ? A.tri_list[idx] : idx;
   __shared__ __align__(16) unsigned char sraw[81 * STAGED_TPB * sizeof(f64x2)];
-  assemble_column<MODE_FACT, f64x2, ATOMIC, false, double, true, true>(A, t, reinterpret_cast<f64x2*>(sraw) + threadIdx.x);
+  assemble_column<MODE_FACT, f64x2, ATOMIC, false, TV, true, true>(A, t, reinterpret_cast<f64x2*>(sraw) + threadIdx.x);
 }
 
 AsmArgs make_args(const bp_mesh* m, const double* U, double* R, void* J) {
@@ -87,15 +87,16 @@ int launch(const bp_mesh* m, AsmArgs a, int scatter, cudaStream_t s) {
   return BP_OK;
 }
 
+template <class TV = double>
 int launch_staged(const bp_mesh* m, AsmArgs a, int scatter, cudaStream_t s) {
   if (scatter == BP_SCATTER_COLOR) {
     for (int c = 0; c < m->ncolors; ++c) {
       a.tri_list = m->color_tris + m->color_off[c];
       a.count = m->color_off[c + 1] - m->color_off[c];
-      k_assemble_staged<false><<<(a.count + STAGED_TPB - 1) / STAGED_TPB, STAGED_TPB, 0, s>>>(a);
+      k_assemble_staged<false, TV><<<(a.count + STAGED_TPB - 1) / STAGED_TPB, STAGED_TPB, 0, s>>>(a);
     }
   } else {
-    k_assemble_staged<true><<<(a.count + STAGED_TPB - 1) / STAGED_TPB, STAGED_TPB, 0, s>>>(a);
+    k_assemble_staged<true, TV><<<(a.count + STAGED_TPB - 1) / STAGED_TPB, STAGED_TPB, 0, s>>>(a);
   }
   BP_CUDA_TRY(cudaGetLastError());
   return BP_OK;
@@ -103,16 +104,15 @@ int launch_staged(const bp_mesh* m, AsmArgs a, int scatter, cudaStream_t s) {
 
 // Argument checks shared by the Jacobian entry points.
 int check_jacobian_args(int precision, int scatter, int method) {
-  if (precision != BP_F64 && precision != BP_F32 && precision != BP_F64X2 && precision != BP_F32_ALL)
-    return BP_EINVAL;
+  if (precision < BP_F64 || precision > BP_F64X2_DS) return BP_EINVAL;
   if (scatter < BP_SCATTER_AUTO || scatter > BP_SCATTER_COLOR) return BP_EINVAL;
   if (method < BP_JAC_AUTO || method > BP_JAC_FACTORED) return BP_EINVAL;
-  if ((precision == BP_F64X2 || precision == BP_F32_ALL) && method == BP_JAC_DUAL) return BP_EUNSUP;
+  if (precision != BP_F64 && precision != BP_F32 && method == BP_JAC_DUAL) return BP_EUNSUP;
   return BP_OK;
 }
 
 size_t jacobian_value_bytes(int precision) {
-  return (precision == BP_F32 || precision == BP_F32_ALL) ? sizeof(float) : sizeof(double);
+  return (precision == BP_F32 || precision == BP_F32_ALL || precision == BP_F32_DS) ? sizeof(float) : sizeof(double);
 }
 
 // Launch of the Jacobian kernel for checked arguments (scatter and method resolved).
@@ -120,6 +120,10 @@ int launch_jacobian(const bp_mesh* m, const AsmArgs& a, int precision, int scatt
   switch (precision) {
     case BP_F64X2:
       return launch_staged(m, a, scatter, s);
+    case BP_F64X2_DS:
+      return launch_staged<f64x2>(m, a, scatter, s);
+    case BP_F32_DS:
+      return launch<MODE_FACT, float, false, f64x2>(m, a, scatter, s);
     case BP_F32_ALL:
       return launch<MODE_FACT, float, false, float>(m, a, scatter, s);
     case BP_F64:
@@ -162,12 +166,14 @@ int bp_assemble_jacobian_ex(bp_mesh* m, const double* U, double* R, void* J, int
   BP_CUDA_TRY(cudaMemsetAsync(J, 0, m->nnz * jacobian_value_bytes(precision), s));
   const AsmArgs a = make_args(m, U, Rw, J);
   if (picard) {  // fixed-viscosity matrix (Newton solver's Picard steps): factored method, FP64 or FP32
-    if (method != BP_JAC_FACTORED || precision == BP_F64X2) return BP_EUNSUP;
+    if (method != BP_JAC_FACTORED || precision == BP_F64X2 || precision == BP_F64X2_DS) return BP_EUNSUP;
     switch (precision) {
       case BP_F64:
         return launch<MODE_FACT, double, true>(m, a, scatter, s);
       case BP_F32_ALL:
         return launch<MODE_FACT, float, true, float>(m, a, scatter, s);
+      case BP_F32_DS:
+        return launch<MODE_FACT, float, true, f64x2>(m, a, scatter, s);
       default:
         return launch<MODE_FACT, float, true>(m, a, scatter, s);
     }

@@ -27,6 +27,7 @@
 #include <cmath>
 #include <type_traits>
 
+#include "bp_ds.cuh"
 #include "bp_internal.cuh"
 
 namespace {
@@ -78,43 +79,6 @@ __device__ __forceinline__ void scatter_add(T* p, T v) {
   }
 }
 
-// ------------------------------------------------------------------ paired-FP32 lanes
-// FP64-accurate lane arithmetic from two FP32 numbers, value = hi + lo with |lo| <= ulp(hi)/2
-// (double-single arithmetic: error-free TwoSum for additions, TwoProd through fmaf for products;
-// about 2^-47 relative error per operation, 8 fewer bits than FP64 but far inside the 1e-12 parity
-// bar).  On B300 the FP32 pipe is ~63x the FP64 pipe, so lanes in this type cost a fraction of
-// native FP64 lanes; the residual (value path) stays native FP64.
-struct f64x2 {
-  float hi, lo;
-  __host__ __device__ constexpr f64x2() : hi(0.f), lo(0.f) {}
-  __host__ __device__ constexpr f64x2(float h, float l) : hi(h), lo(l) {}
-  __host__ __device__ constexpr explicit f64x2(double x) : hi((float)x), lo((float)(x - (double)(float)x)) {}
-  __host__ __device__ constexpr explicit f64x2(int x) : f64x2((double)x) {}
-  __host__ __device__ double value() const { return (double)hi + (double)lo; }
-};
-__device__ __forceinline__ f64x2 operator+(const f64x2 a, const f64x2 b) {
-  const float s = a.hi + b.hi;
-  const float bb = s - a.hi;
-  float e = (a.hi - (s - bb)) + (b.hi - bb);
-  e += a.lo + b.lo;
-  const float h = s + e;
-  return f64x2(h, e - (h - s));
-}
-__device__ __forceinline__ f64x2 operator-(const f64x2 a) { return f64x2(-a.hi, -a.lo); }
-__device__ __forceinline__ f64x2 operator-(const f64x2 a, const f64x2 b) { return a + (-b); }
-__device__ __forceinline__ f64x2 operator*(const f64x2 a, const f64x2 b) {
-  const float p = a.hi * b.hi;
-  float e = fmaf(a.hi, b.hi, -p);
-  e = fmaf(a.hi, b.lo, e);
-  e = fmaf(a.lo, b.hi, e);
-  const float h = p + e;
-  return f64x2(h, e - (h - p));
-}
-__device__ __forceinline__ f64x2& operator+=(f64x2& a, const f64x2 b) {
-  a = a + b;
-  return a;
-}
-
 // FP64 value -> lane type.  FP32 lanes convert on the integer pipe (f32_of): the FP64 pipe, which
 // would otherwise run the conversions, is the one the value path fills.
 template <class TL>
@@ -127,15 +91,18 @@ __device__ __forceinline__ float to_lane<float>(const double x) {
 }
 template <>
 __device__ __forceinline__ f64x2 to_lane<f64x2>(const double x) {  // hi + lo, both split on the integer pipe
-  const float h = f32_of(x);
-  return f64x2(h, f32_of(x - f64_of(h)));
+  return ds_of(x);
 }
 
-// A value-path quantity (type TV) as a lane (type TL): no conversion when the types agree.
+// A value-path quantity (type TV) as a lane (type TL): no conversion when the types agree; a pair
+// gives an FP32 lane its rounded sum.
 template <class TL, class TV>
 __device__ __forceinline__ TL lane_from(const TV x) {
   if constexpr (std::is_same<TL, TV>::value) {
     return x;
+  } else if constexpr (std::is_same<TV, f64x2>::value) {
+    static_assert(std::is_same<TL, float>::value, "pairs feed FP32 or paired lanes");
+    return x.hi + x.lo;
   } else {
     return to_lane<TL>(x);
   }
@@ -147,6 +114,11 @@ __device__ __forceinline__ double fma_t(const double a, const double b, const do
 __device__ __forceinline__ float fma_t(const float a, const float b, const float c) { return fmaf(a, b, c); }
 __device__ __forceinline__ double to_r(const double x) { return x; }
 __device__ __forceinline__ double to_r(const float x) { return f64_of(x); }
+// Double-single value path (TV = f64x2): the quadrature-point arithmetic of the residual in pairs
+// of FP32 numbers (~2^-47 relative per operation), FP64-accurate on the FP32 pipe.
+__device__ __forceinline__ f64x2 fma_t(const f64x2 a, const f64x2 b, const f64x2 c) { return a * b + c; }
+__device__ __forceinline__ double to_r(const f64x2 x) { return ds_value(x); }
+__device__ __forceinline__ f64x2 inv_cbrt_t(const f64x2 x) { return ds_inv_cbrt(x); }
 
 // storage type of a lane type in the Jacobian array, and the conversion
 template <class TL>
@@ -253,8 +225,10 @@ __device__ __forceinline__ Dual<TL, NL> operator*(double s, const Dual<TL, NL>& 
 template <int MODE, class TL, bool ATOMIC, bool PICARD = false, class TV = double, bool SBL = false,
           bool STAGE = false>
 __device__ __forceinline__ void assemble_column(const AsmArgs& A, const int t, TL* sbl = nullptr) {
-  static_assert(std::is_same<TV, double>::value || (MODE == MODE_FACT && std::is_same<TL, float>::value),
-                "the FP32 value path exists for the factored method with FP32 lanes only");
+  static_assert(std::is_same<TV, double>::value || (MODE == MODE_FACT && std::is_same<TL, float>::value) ||
+                    (std::is_same<TV, f64x2>::value && MODE != MODE_DUAL),
+                "the FP32 value path exists for the factored method with FP32 lanes only, the double-single "
+                "one for the residual and the factored method");
   static_assert(!STAGE || (SBL && MODE == MODE_FACT && !PICARD), "the staged rank-one part needs SBL");
   const int L = A.L;
 
@@ -340,7 +314,7 @@ __device__ __forceinline__ void assemble_column(const AsmArgs& A, const int t, T
   double guby = ub[0] * ly[0] + ub[1] * ly[1] + ub[2] * ly[2];
   double gvbx = vb[0] * lx[0] + vb[1] * lx[1] + vb[2] * lx[2];
   double gvby = vb[0] * ly[0] + vb[1] * ly[1] + vb[2] * ly[2];
-  TV carry[3][2] = {{0, 0}, {0, 0}, {0, 0}};  // residual of the current bottom level from the wedge below
+  TV carry[3][2] = {{TV(0), TV(0)}, {TV(0), TV(0)}, {TV(0), TV(0)}};  // residual of the bottom level from below
   // rate-factor field: hardness B = A^(-1/3) interpolated at the triangle points of the bottom level
   TV hb[3] = {cAV, cAV, cAV};
   if (A.Bn) {
@@ -551,8 +525,8 @@ __device__ __forceinline__ void assemble_column(const AsmArgs& A, const int t, T
       }
     } else {
       // ---- structured value path (+ sum-factorised Jacobian lanes)
-      TV P1x[2] = {0, 0}, P1y[2] = {0, 0}, P2x[2] = {0, 0}, P2y[2] = {0, 0};
-      TV TW1[3] = {0, 0, 0}, TW2[3] = {0, 0, 0};
+      TV P1x[2] = {TV(0), TV(0)}, P1y[2] = {TV(0), TV(0)}, P2x[2] = {TV(0), TV(0)}, P2y[2] = {TV(0), TV(0)};
+      TV TW1[3] = {TV(0), TV(0), TV(0)}, TW2[3] = {TV(0), TV(0), TV(0)};
 #pragma unroll
       for (int z = 0; z < 2; ++z) {
 #pragma unroll
@@ -587,6 +561,12 @@ __device__ __forceinline__ void assemble_column(const AsmArgs& A, const int t, T
               Wp = (-1.0f / 3.0f) * cqL[tp] * ef * (rf * rf * rf);
               tau1 = 2.0f * invhL[tp] * lane_from<float>(t1);
               tau2 = 2.0f * invhL[tp] * lane_from<float>(t2);
+            } else if constexpr (std::is_same<TV, f64x2>::value) {  // double-single value path, paired lanes
+              eta_q[z][tp] = eta;
+              Wp = TV(-1.0 / 3.0) * W * (r * r * r);
+              const TV ih2 = to_lane<TV>(2.0 * invh[tp]);
+              tau1 = ih2 * t1;
+              tau2 = ih2 * t2;
             } else {
               eta_q[z][tp] = to_lane<TL>(eta);
               Wp = to_lane<TL>(-(1.0 / 3.0) * W * (r * r * r));

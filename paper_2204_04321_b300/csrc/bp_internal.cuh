@@ -160,6 +160,11 @@ struct bp_device_guard {
 __host__ __device__ inline bool bp_aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 __host__ __device__ inline bool bp_aligned8(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 7u) == 0; }
 
+// Jacobian precision kinds whose values are stored as float (the others store double).
+__host__ __device__ inline bool bp_values_f32(int precision) {
+  return precision == BP_F32 || precision == BP_F32_ALL || precision == BP_F32_DS;
+}
+
 // Node level helpers of the extruded CSR pattern.
 __host__ __device__ inline int bp_nlev(int level, int L) { return (level == 0 || level == L) ? 2 : 3; }
 __host__ __device__ inline int bp_levels_before(int level) { return level == 0 ? 0 : 3 * level - 1; }

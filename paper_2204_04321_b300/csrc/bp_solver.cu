@@ -9,6 +9,7 @@
 #include <cstring>
 #include <type_traits>
 
+#include "bp_ds.cuh"
 #include "bp_internal.cuh"
 
 namespace {
@@ -577,8 +578,22 @@ template <>
 __device__ __forceinline__ float to_T<float>(const double x) {
   return f32_of(x);
 }
+template <>
+__device__ __forceinline__ f64x2 to_T<f64x2>(const double x) {
+  return ds_of(x);
+}
 __device__ __forceinline__ double from_T(const double x) { return x; }
 __device__ __forceinline__ double from_T(const float x) { return f64_of(x); }
+__device__ __forceinline__ double from_T(const f64x2 x) { return ds_value(x); }
+// a direction entry (type DT) in the arithmetic type T
+template <class T, class DT>
+__device__ __forceinline__ T dir_T(const DT x) {
+  if constexpr (std::is_same<T, f64x2>::value) {
+    return ds_of((double)x);
+  } else {
+    return (T)x;
+  }
+}
 
 // Hardness B = A^(-1/3) at the quadrature point (zeta level weights p0, p1 of layer l, triangle point
 // tp): the nodal field interpolated like the velocity, or the uniform value cA.
@@ -715,6 +730,10 @@ __device__ __forceinline__ double cube_root(double x) {  // x^(1/3) = x (x^(-1/3
   return x * r * r;
 }
 __device__ __forceinline__ float cube_root(float x) { return cbrtf(x); }
+__device__ __forceinline__ f64x2 cube_root(f64x2 x) {
+  const f64x2 r = ds_inv_cbrt(x);
+  return x * r * r;
+}
 
 // Energy change Pi_h(U + alpha D) - Pi_h(U), formed term by term as differences so that it keeps
 // its relative accuracy when it is many orders smaller than Pi_h itself (near convergence):
@@ -791,8 +810,8 @@ __global__ void __launch_bounds__(128) k_energy_change(const double2* __restrict
     for (int a = 0; a < 3; ++a) {
       u0[a] = to_T<T>(U[ub[a]]);
       v0[a] = to_T<T>(U[ub[a] + 1]);
-      a0[a] = (T)D[ub[a]];
-      b0[a] = (T)D[ub[a] + 1];
+      a0[a] = dir_T<T>(D[ub[a]]);
+      b0[a] = dir_T<T>(D[ub[a] + 1]);
     }
     auto grad2 = [&](const T* w, T& gx, T& gy) {
       gx = w[0] * tlx[0] + w[1] * tlx[1] + w[2] * tlx[2];
@@ -809,8 +828,8 @@ __global__ void __launch_bounds__(128) k_energy_change(const double2* __restrict
       for (int a = 0; a < 3; ++a) {
         u1[a] = to_T<T>(U[ub[a] + 2 * l + 2]);
         v1[a] = to_T<T>(U[ub[a] + 2 * l + 3]);
-        a1[a] = (T)D[ub[a] + 2 * l + 2];
-        b1[a] = (T)D[ub[a] + 2 * l + 3];
+        a1[a] = dir_T<T>(D[ub[a] + 2 * l + 2]);
+        b1[a] = dir_T<T>(D[ub[a] + 2 * l + 3]);
       }
       T gU1[2], gV1[2], gA1[2], gB1[2];
       grad2(u1, gU1[0], gU1[1]);
@@ -2632,12 +2651,12 @@ int bp_learned_scratch(bp_mesh* m, uint16_t** X, float** Y, double** Usia, doubl
 
 extern "C" int bp_spmv(bp_mesh* m, const void* J, int precision, const double* x, double* y, void* stream) {
   if (!m || !J || !x || !y || !bp_aligned16(x) || !bp_aligned16(y) || !bp_aligned16(J)) return BP_EINVAL;
-  if (precision != BP_F64 && precision != BP_F32 && precision != BP_F32_ALL) return BP_EINVAL;
+  if (precision < BP_F64 || precision > BP_F64X2_DS) return BP_EINVAL;
   bp_device_guard g(m->device);
   cudaStream_t s = (cudaStream_t)stream;
   const int grid = grid_for(m->ndof / 2 * TPR, NT);
   const int npairs = (int)(m->ndof / 2);
-  if (precision == BP_F64)
+  if (!bp_values_f32(precision))
     k_spmv_pairs<double, double, false><<<grid, NT, 0, s>>>(m->rowptr, m->nbr_ptr, m->nbr_idx, m->nl,
                                                             (const double*)J, npairs, x, y, nullptr, nullptr,
                                                             nullptr, 0);
@@ -2651,12 +2670,13 @@ extern "C" int bp_spmv(bp_mesh* m, const void* J, int precision, const double* x
 
 extern "C" int bp_colprec_setup(bp_mesh* m, const void* J, int precision, void* stream) {
   if (!m || !J) return BP_EINVAL;
-  if (precision != BP_F64 && precision != BP_F32 && precision != BP_F32_ALL) return BP_EINVAL;
+  if (precision < BP_F64 || precision > BP_F64X2_DS) return BP_EINVAL;
   bp_device_guard g(m->device);
   cudaStream_t s = (cudaStream_t)stream;
   int rc = ensure_ws(m, s);
   if (rc) return rc;
-  return precision == BP_F64 ? colprec_setup_t(m, (const double*)J, s) : colprec_setup_t(m, (const float*)J, s);
+  return !bp_values_f32(precision) ? colprec_setup_t(m, (const double*)J, s)
+                                    : colprec_setup_t(m, (const float*)J, s);
 }
 
 extern "C" int bp_colprec_apply(bp_mesh* m, const double* r, double* z, void* stream) {
@@ -2674,12 +2694,12 @@ extern "C" int bp_colprec_apply(bp_mesh* m, const double* r, double* z, void* st
 
 extern "C" int bp_mdsc_setup(bp_mesh* m, const void* J, int precision, void* stream) {
   if (!m || !J) return BP_EINVAL;
-  if (precision != BP_F64 && precision != BP_F32 && precision != BP_F32_ALL) return BP_EINVAL;
+  if (precision < BP_F64 || precision > BP_F64X2_DS) return BP_EINVAL;
   bp_device_guard g(m->device);
   cudaStream_t s = (cudaStream_t)stream;
   int rc = ensure_ws(m, s);
   if (rc) return rc;
-  return precision == BP_F64 ? mdsc_setup_t(m, (const double*)J, s) : mdsc_setup_t(m, (const float*)J, s);
+  return !bp_values_f32(precision) ? mdsc_setup_t(m, (const double*)J, s) : mdsc_setup_t(m, (const float*)J, s);
 }
 
 extern "C" int bp_mdsc_apply(bp_mesh* m, const void* J, const double* r, double* z, void* stream) {
@@ -2697,12 +2717,13 @@ extern "C" int bp_mdsc_apply(bp_mesh* m, const void* J, const double* r, double*
 
 extern "C" int bp_mdsc_amg_setup(bp_mesh* m, const void* J, int precision, void* stream) {
   if (!m || !J) return BP_EINVAL;
-  if (precision != BP_F64 && precision != BP_F32 && precision != BP_F32_ALL) return BP_EINVAL;
+  if (precision < BP_F64 || precision > BP_F64X2_DS) return BP_EINVAL;
   bp_device_guard g(m->device);
   cudaStream_t s = (cudaStream_t)stream;
   int rc = ensure_ws(m, s);
   if (rc) return rc;
-  rc = precision == BP_F64 ? mdsc_amg_setup_t(m, (const double*)J, s) : mdsc_amg_setup_t(m, (const float*)J, s);
+  rc = !bp_values_f32(precision) ? mdsc_amg_setup_t(m, (const double*)J, s)
+                                  : mdsc_amg_setup_t(m, (const float*)J, s);
   if (rc) return rc;
   m->ws->has_amg = true;
   return BP_OK;
@@ -2801,12 +2822,13 @@ extern "C" int bp_newton_solve(bp_mesh* m, double* U, const bp_solve_opts* opts,
   if (o.line_search < 0 || o.line_search > BP_LS_QUADRATIC) return BP_EINVAL;
   if (!(o.picard_rtol >= 0) || !(o.value32_rtol >= 0)) return BP_EINVAL;
   if (o.value32_rtol > 0 && o.value32_rtol < o.rtol) return BP_EINVAL;  // an FP32 residual could pass the test
+  if (o.picard_rtol > 0 && o.precision == BP_F64X2_DS) return BP_EUNSUP;   // no paired-lane Picard matrix
   if ((o.device_loop != 0 && o.device_loop != 1) ||
       (o.preconditioner != BP_PREC_COLUMN && o.preconditioner != BP_PREC_MDSC &&
        o.preconditioner != BP_PREC_MDSC_AMG))
     return BP_EINVAL;
   if (!(o.rtol > 0) || o.max_newton < 0 || o.max_newton > 64 || o.max_krylov < 1 || o.check_every < 1 ||
-      (o.precision != BP_F64 && o.precision != BP_F32) ||
+      (o.precision != BP_F64 && o.precision != BP_F32 && o.precision != BP_F32_DS && o.precision != BP_F64X2_DS) ||
       (o.krylov != BP_KRYLOV_CG && o.krylov != BP_KRYLOV_GMRES) || !(o.eta_max > 0))
     return BP_EINVAL;
   if (o.krylov == BP_KRYLOV_GMRES &&
@@ -2832,7 +2854,7 @@ extern "C" int bp_newton_solve(bp_mesh* m, double* U, const bp_solve_opts* opts,
   if ((rc = dot_host(m, m->load, m->load, m->ndof, s, &fref))) return rc;
   fref = std::sqrt(fref);  // ||F(0)||: at U = 0 the residual is the driving-stress load
   rep->fnorm_ref = fref;
-  const bool f32 = o.precision == BP_F32;
+  const bool f32 = bp_values_f32(o.precision);  // FP32 Jacobian values and Krylov vectors
   const double eta_floor = f32 ? 1e-5 : 1e-10;
   double eta = o.eta_max, fprev = 0.0;
   int status = BP_ENOCONV;
@@ -2954,8 +2976,12 @@ extern "C" int bp_newton_solve(bp_mesh* m, double* U, const bp_solve_opts* opts,
       const double c = 1e-4;
       for (int h = 0; h <= 10; ++h) {
         double dE;
-        rc = f32 ? energy_change_host<float, float>(m, U, reinterpret_cast<const float*>(w->x), alpha, s, &dE)
-                 : energy_change_host<double, double>(m, U, w->x, alpha, s, &dE);
+        if (f32)
+          rc = energy_change_host<float, float>(m, U, reinterpret_cast<const float*>(w->x), alpha, s, &dE);
+        else if (o.precision == BP_F64X2_DS)  // the per-point work in pairs (FP64-accurate, FP32 pipe)
+          rc = energy_change_host<f64x2, double>(m, U, w->x, alpha, s, &dE);
+        else
+          rc = energy_change_host<double, double>(m, U, w->x, alpha, s, &dE);
         if (rc) return rc;
         if (dE <= c * alpha * slope || h == 10) break;
         if (o.line_search == BP_LS_QUADRATIC) {

@@ -101,28 +101,30 @@ def test_residual_parity(name, kind):
 @pytest.mark.parametrize("name", list(MESHES))
 @pytest.mark.parametrize("method", ["factored", "dual"])
 @pytest.mark.parametrize("scatter", ["atomic", "color"])
-@pytest.mark.parametrize("precision", ["f64", "f32", "f64x2"])
+@pytest.mark.parametrize("precision", ["f64", "f32", "f64x2", "f32_ds", "f64x2_ds"])
 def test_jacobian_parity(name, method, scatter, precision):
     c = capi()
-    if precision == "f64x2" and method == "dual":
-        pytest.skip("paired-FP32 lanes are implemented for the sum-factorised method only")
+    if precision not in ("f64", "f32") and method == "dual":
+        pytest.skip("paired-FP32 lanes and the double-single value path are implemented for the "
+                    "sum-factorised method only")
     mesh = MESHES[name]()
     om = oracle.OracleMesh(mesh)
     U = synth.random_velocity(mesh, 103)
     dm = c.DeviceMesh(mesh)
-    prec = {"f64": c.BP_F64, "f32": c.BP_F32, "f64x2": c.BP_F64X2}[precision]
+    prec = {"f64": c.BP_F64, "f32": c.BP_F32, "f64x2": c.BP_F64X2, "f32_ds": c.BP_F32_DS,
+            "f64x2_ds": c.BP_F64X2_DS}[precision]
     J, R = dm.jacobian(dev(U), precision=prec,
                        scatter=c.BP_SCATTER_ATOMIC if scatter == "atomic" else c.BP_SCATTER_COLOR,
                        method=c.BP_JAC_FACTORED if method == "factored" else c.BP_JAC_DUAL)
     _, _, Jc, Rc = om.jacobian(U)
     assert rel_inf(R.cpu().numpy(), Rc) <= TOL64
     err = rel_inf(J.cpu().numpy().astype(np.float64), Jc)
-    assert err <= (TOL32 if precision == "f32" else TOL64), err
+    assert err <= (TOL32 if precision in ("f32", "f32_ds") else TOL64), err
 
 
 @pytest.mark.parametrize("name", ["small", "marine", "arrhenius"])
 @pytest.mark.parametrize("kind", ["zero", "sia"])
-@pytest.mark.parametrize("precision", ["f64", "f32"])
+@pytest.mark.parametrize("precision", ["f64", "f32", "f32_ds", "f64x2_ds"])
 def test_jacobian_parity_at_zero_and_shallow_ice_velocities(name, kind, precision):
     """U = 0 makes every strain-rate lane exactly zero (the FP32 lane conversion's zero case);
     the shallow-ice guess is the usual starting point of the Newton solve."""
@@ -131,12 +133,12 @@ def test_jacobian_parity_at_zero_and_shallow_ice_velocities(name, kind, precisio
     om = oracle.OracleMesh(mesh)
     U = velocities(mesh, kind, om)
     dm = c.DeviceMesh(mesh)
-    prec = c.BP_F64 if precision == "f64" else c.BP_F32
+    prec = {"f64": c.BP_F64, "f32": c.BP_F32, "f32_ds": c.BP_F32_DS, "f64x2_ds": c.BP_F64X2_DS}[precision]
     J, R = dm.jacobian(dev(U), precision=prec)
     _, _, Jc, Rc = om.jacobian(U)
     assert rel_inf(R.cpu().numpy(), Rc) <= TOL64
     err = rel_inf(J.cpu().numpy().astype(np.float64), Jc)
-    assert err <= (TOL32 if precision == "f32" else TOL64), err
+    assert err <= (TOL32 if precision in ("f32", "f32_ds") else TOL64), err
 
 
 # FP32 value path: the element work at the quadrature points runs in FP32, so R carries FP32
@@ -228,7 +230,8 @@ def test_full_size_dome_1m_wedges_sampled_parity():
     Rc = om.residual(U, tri_mask=mask)
     assert rel_inf(R[rows], Rc[rows]) <= TOL64
     rowptr, colidx = (t.cpu().numpy() for t in dm.pattern())
-    for prec, tol in ((c.BP_F64, TOL64), (c.BP_F32, TOL32), (c.BP_F64X2, TOL64)):
+    for prec, tol in ((c.BP_F64, TOL64), (c.BP_F32, TOL32), (c.BP_F64X2, TOL64), (c.BP_F32_DS, TOL32),
+                      (c.BP_F64X2_DS, TOL64)):
         J, Rj = dm.jacobian(Ud, precision=prec)
         J = J.cpu().numpy().astype(np.float64)
         assert rel_inf(Rj.cpu().numpy()[rows], Rc[rows]) <= TOL64

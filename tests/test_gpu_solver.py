@@ -340,3 +340,28 @@ def test_gmres_newton_reaches_the_cg_solution(precision):
     with pytest.raises(c.BPError) as e:
         c.bp_newton_solve(dm.handle, U, krylov=c.BP_KRYLOV_GMRES, preconditioner=c.BP_PREC_MDSC)
     assert e.value.status == c.BP_EUNSUP
+
+
+@pytest.mark.parametrize("precision", ["f32_ds", "f64x2_ds"])
+def test_double_single_value_path_newton_reaches_the_fp64_solution(precision):
+    """Newton with the double-single value path (residual FP64-accurate on the FP32 pipe): the
+    oracle's FP64 residual of the solution at 1e-8 and the plain FP64 path's solution to 1e-7."""
+    c = capi()
+    mesh = synth.dome_mesh(16, 5, 81, 82, bed="sinusoidal", beta="field")
+    om = oracle.OracleMesh(mesh)
+    dm = c.DeviceMesh(mesh)
+    f0 = np.linalg.norm(om.residual(np.zeros(mesh.ndof)))
+    sols = []
+    for prec in (c.BP_F64, {"f32_ds": c.BP_F32_DS, "f64x2_ds": c.BP_F64X2_DS}[precision]):
+        U = torch.empty(dm.ndof, dtype=torch.float64, device="cuda")
+        c.bp_initial_guess(dm.handle, c.BP_GUESS_SIA, U)
+        rc, rep = c.bp_newton_solve(dm.handle, U, precision=prec, max_krylov=4000)
+        assert rc == c.BP_OK, rep
+        Uh = U.cpu().numpy()
+        assert np.linalg.norm(om.residual(Uh)) <= 1.1e-8 * f0
+        sols.append(Uh)
+    assert rel_inf(sols[0], sols[1]) <= 1e-7
+    if precision == "f64x2_ds":
+        with pytest.raises(c.BPError) as e:
+            c.bp_newton_solve(dm.handle, U, precision=c.BP_F64X2_DS, picard_rtol=0.1)
+        assert e.value.status == c.BP_EUNSUP
