@@ -469,7 +469,7 @@ def run_ours(args):
     return 0
 
 
-def learned_start(capi, dm, dev, reps=3, seeds=10):
+def learned_start(capi, dm, dev, reps=3, seeds=40):
     """Mixed-precision solve from the committed learned warm start: the network's guess with the
     fallback to the shallow-ice guess judged by the FP64 residual norm, by the FP64 energy, and the
     energy-judged guess followed by Picard steps (learned.PICARD_RTOL), on this mesh's beta; then
