@@ -641,7 +641,7 @@ def newton_section(capi, synth, dm, mesh, dev, skip_large=False, reps=3):
         v["vs_f64_solution_rel_inf"] = float((Uv - U64).abs().max() / U64.abs().max())
         out[mesh.name][name] = v
     # early steps with the FP32 value path (inexact residual) until ||F|| <= tau ||F(0)||
-    for tau in (1e-2, 1e-3, 1e-4):
+    for tau in (1e-2, 1e-3, 1e-4, 1e-5):
         v, Uv = solve(dm, capi.BP_F32, value32_rtol=tau)
         v["vs_f64_solution_rel_inf"] = float((Uv - U64).abs().max() / U64.abs().max())
         out[mesh.name][f"mixed_f32_value32_until_{tau:g}"] = v
