@@ -636,8 +636,10 @@ def newton_section(capi, synth, dm, mesh, dev, skip_large=False, reps=3):
                       "mixed_vs_f64_solution_rel_inf": float((U32 - U64).abs().max() / U64.abs().max())}
     # the same two paths with the double-single value path (residual FP64-accurate on the FP32 pipe):
     # FP64-accurate Jacobian from paired lanes with FP64 Krylov, and FP32 lanes with FP32 Krylov
-    for name, prec in (("f64_accurate_double_single", capi.BP_F64X2_DS), ("mixed_f32_double_single", capi.BP_F32_DS)):
-        v, Uv = solve(dm, prec)
+    for name, prec, kw in (("f64_accurate_double_single", capi.BP_F64X2_DS, {}),
+                           ("mixed_f32_double_single", capi.BP_F32_DS, {}),
+                           ("mixed_f32_double_single_value32_until_1e-4", capi.BP_F32_DS, {"value32_rtol": 1e-4})):
+        v, Uv = solve(dm, prec, **kw)
         v["vs_f64_solution_rel_inf"] = float((Uv - U64).abs().max() / U64.abs().max())
         out[mesh.name][name] = v
     # early steps with the FP32 value path (inexact residual) until ||F|| <= tau ||F(0)||

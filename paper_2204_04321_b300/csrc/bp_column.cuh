@@ -120,6 +120,33 @@ __device__ __forceinline__ f64x2 fma_t(const f64x2 a, const f64x2 b, const f64x2
 __device__ __forceinline__ double to_r(const f64x2 x) { return ds_value(x); }
 __device__ __forceinline__ f64x2 inv_cbrt_t(const f64x2 x) { return ds_inv_cbrt(x); }
 
+// Element of a 2- or 3-array by an index that may be a compile-time constant (a register access)
+// or a warp-uniform runtime value (a select), and the matching writes.
+template <class T>
+__device__ __forceinline__ T sel2(const T (&a)[2], const int i) {
+  return i ? a[1] : a[0];
+}
+template <class T>
+__device__ __forceinline__ T sel3(const T (&a)[3], const int i) {
+  return i == 0 ? a[0] : (i == 1 ? a[1] : a[2]);
+}
+template <class T>
+__device__ __forceinline__ void put2(T (&a)[2], const int i, const T v) {
+  if (i)
+    a[1] = v;
+  else
+    a[0] = v;
+}
+template <class T>
+__device__ __forceinline__ void put3(T (&a)[3], const int i, const T v) {
+  if (i == 0)
+    a[0] = v;
+  else if (i == 1)
+    a[1] = v;
+  else
+    a[2] = v;
+}
+
 // storage type of a lane type in the Jacobian array, and the conversion
 template <class TL>
 struct LaneStore {
@@ -527,75 +554,87 @@ __device__ __forceinline__ void assemble_column(const AsmArgs& A, const int t, T
       // ---- structured value path (+ sum-factorised Jacobian lanes)
       TV P1x[2] = {TV(0), TV(0)}, P1y[2] = {TV(0), TV(0)}, P2x[2] = {TV(0), TV(0)}, P2y[2] = {TV(0), TV(0)};
       TV TW1[3] = {TV(0), TV(0), TV(0)}, TW2[3] = {TV(0), TV(0), TV(0)};
-#pragma unroll
-      for (int z = 0; z < 2; ++z) {
-#pragma unroll
-        for (int tp = 0; tp < 3; ++tp) {
-          const TV ux = GUx[z] - uz[tp] * GzxV[z];
-          const TV uy = GUy[z] - uz[tp] * GzyV[z];
-          const TV vx = GVx[z] - vz[tp] * GzxV[z];
-          const TV vy = GVy[z] - vz[tp] * GzyV[z];
-          const TV exy = TV(0.5) * (uy + vx);
-          const TV e2 = fma_t(ux, ux, fma_t(vy, vy + ux, fma_t(exy, exy, ez[tp])));
-          const TV xx = e2 + deltaV;
-          const TV r = inv_cbrt_t(xx);
-          const TV eta = (TV(psi(0, z)) * hb[tp] + TV(psi(1, z)) * ht[tp]) * r;
-          const TV W = cqV[tp] * eta;
-          const TV g1x = TV(2.0) * ux + vy, g2y = ux + TV(2.0) * vy;
-          P1x[z] = fma_t(W, g1x, P1x[z]);
-          P1y[z] = fma_t(W, exy, P1y[z]);
-          P2x[z] = fma_t(W, exy, P2x[z]);
-          P2y[z] = fma_t(W, g2y, P2y[z]);
-          const TV t1 = TV(0.5) * uz[tp] - g1x * GzxV[z] - exy * GzyV[z];
-          const TV t2 = TV(0.5) * vz[tp] - exy * GzxV[z] - g2y * GzyV[z];
-          const TV W6 = d6V * eta;
-          TW1[tp] = fma_t(W6, t1, TW1[tp]);
-          TW2[tp] = fma_t(W6, t2, TW2[tp]);
-          if constexpr (MODE == MODE_FACT) {
-            // rank-one part eta' p_i p_j with p_{(a,k),c} = psi_k g_c,xy . Lambda_a + lambda_a psi_k' g_c . Z
-            TL Wp, tau1, tau2;
-            if constexpr (kF32) {  // from r, t1, t2 converted once: FP32 arithmetic only
-              const float rf = lane_from<float>(r);
-              const float ef = lane_from<float>(eta);
-              eta_q[z][tp] = ef;
-              Wp = (-1.0f / 3.0f) * cqL[tp] * ef * (rf * rf * rf);
-              tau1 = 2.0f * invhL[tp] * lane_from<float>(t1);
-              tau2 = 2.0f * invhL[tp] * lane_from<float>(t2);
-            } else if constexpr (std::is_same<TV, f64x2>::value) {  // double-single value path, paired lanes
-              eta_q[z][tp] = eta;
-              Wp = TV(-1.0 / 3.0) * W * (r * r * r);
-              const TV ih2 = to_lane<TV>(2.0 * invh[tp]);
-              tau1 = ih2 * t1;
-              tau2 = ih2 * t2;
-            } else {
-              eta_q[z][tp] = to_lane<TL>(eta);
-              Wp = to_lane<TL>(-(1.0 / 3.0) * W * (r * r * r));
-              tau1 = to_lane<TL>(2.0 * invh[tp] * t1);
-              tau2 = to_lane<TL>(2.0 * invh[tp] * t2);
-            }
-            if constexpr (STAGE) {  // park the point's rank-one factors (slots 45 + 6 q ..)
-              const int bs = blockDim.x;
-              TL* const sq = sbl + (45 + 6 * (3 * z + tp)) * bs;
-              sq[0] = Wp;
-              sq[bs] = lane_from<TL>(g1x);
-              sq[2 * bs] = lane_from<TL>(exy);
-              sq[3 * bs] = lane_from<TL>(g2y);
-              sq[4 * bs] = tau1;
-              sq[5 * bs] = tau2;
-            } else if constexpr (!PICARD) {
+      // One quadrature point (zeta level z, triangle point tp).  The arrays indexed by z and tp are
+      // read and written through sel2 / sel3 / put2 / put3: plain register accesses when the
+      // indices are compile-time constants (the unrolled loop below), warp-uniform selects when they
+      // are not (the double-single value path runs the 6 points in a loop that is not unrolled: its
+      // pair arithmetic, ~10 instructions per FP64 one, would not fit the instruction cache 6 times).
+      auto point = [&](const int z, const int tp) {
+        const TV gzx = sel2(GzxV, z), gzy = sel2(GzyV, z);
+        const TV uzp = sel3(uz, tp), vzp = sel3(vz, tp);
+        const TV ux = sel2(GUx, z) - uzp * gzx;
+        const TV uy = sel2(GUy, z) - uzp * gzy;
+        const TV vx = sel2(GVx, z) - vzp * gzx;
+        const TV vy = sel2(GVy, z) - vzp * gzy;
+        const TV exy = TV(0.5) * (uy + vx);
+        const TV e2 = fma_t(ux, ux, fma_t(vy, vy + ux, fma_t(exy, exy, sel3(ez, tp))));
+        const TV xx = e2 + deltaV;
+        const TV r = inv_cbrt_t(xx);
+        const TV ps0 = z ? TV(BP_QP_Q) : TV(BP_QP_P), ps1 = z ? TV(BP_QP_P) : TV(BP_QP_Q);  // psi_0, psi_1 at z
+        const TV eta = (ps0 * sel3(hb, tp) + ps1 * sel3(ht, tp)) * r;
+        const TV W = sel3(cqV, tp) * eta;
+        const TV g1x = TV(2.0) * ux + vy, g2y = ux + TV(2.0) * vy;
+        put2(P1x, z, fma_t(W, g1x, sel2(P1x, z)));
+        put2(P1y, z, fma_t(W, exy, sel2(P1y, z)));
+        put2(P2x, z, fma_t(W, exy, sel2(P2x, z)));
+        put2(P2y, z, fma_t(W, g2y, sel2(P2y, z)));
+        const TV t1 = TV(0.5) * uzp - g1x * gzx - exy * gzy;
+        const TV t2 = TV(0.5) * vzp - exy * gzx - g2y * gzy;
+        const TV W6 = d6V * eta;
+        put3(TW1, tp, fma_t(W6, t1, sel3(TW1, tp)));
+        put3(TW2, tp, fma_t(W6, t2, sel3(TW2, tp)));
+        if constexpr (MODE == MODE_FACT) {
+          // rank-one part eta' p_i p_j with p_{(a,k),c} = psi_k g_c,xy . Lambda_a + lambda_a psi_k' g_c . Z
+          TL Wp, tau1, tau2, eq;
+          if constexpr (kF32) {  // from r, t1, t2 converted once: FP32 arithmetic only
+            const float rf = lane_from<float>(r);
+            const float ef = lane_from<float>(eta);
+            eq = ef;
+            Wp = (-1.0f / 3.0f) * sel3(cqL, tp) * ef * (rf * rf * rf);
+            const float ih = sel3(invhL, tp);
+            tau1 = 2.0f * ih * lane_from<float>(t1);
+            tau2 = 2.0f * ih * lane_from<float>(t2);
+          } else if constexpr (std::is_same<TV, f64x2>::value) {  // double-single value path, paired lanes
+            eq = eta;
+            Wp = TV(-1.0 / 3.0) * W * (r * r * r);
+            const TV ih2 = to_lane<TV>(2.0 * sel3(invh, tp));
+            tau1 = ih2 * t1;
+            tau2 = ih2 * t2;
+          } else {
+            eq = to_lane<TL>(eta);
+            Wp = to_lane<TL>(-(1.0 / 3.0) * W * (r * r * r));
+            const double ih = sel3(invh, tp);
+            tau1 = to_lane<TL>(2.0 * ih * t1);
+            tau2 = to_lane<TL>(2.0 * ih * t2);
+          }
+          if (z)
+            put3(eta_q[1], tp, eq);
+          else
+            put3(eta_q[0], tp, eq);
+          if constexpr (STAGE) {  // park the point's rank-one factors (slots 45 + 6 q ..)
+            const int bs = blockDim.x;
+            TL* const sq = sbl + (45 + 6 * (3 * z + tp)) * bs;
+            sq[0] = Wp;
+            sq[bs] = lane_from<TL>(g1x);
+            sq[2 * bs] = lane_from<TL>(exy);
+            sq[3 * bs] = lane_from<TL>(g2y);
+            sq[4 * bs] = tau1;
+            sq[5 * bs] = tau2;
+          } else if constexpr (!PICARD) {
             const TL fg1x = lane_from<TL>(g1x), fexy = lane_from<TL>(exy), fg2y = lane_from<TL>(g2y);
+            const TL pl0 = z ? TL(BP_QP_Q) : TL(BP_QP_P), pl1 = z ? TL(BP_QP_P) : TL(BP_QP_Q);
             // p_{(a,k),c} = psi_k alpha_{a,c} -/+ t_{a,c},  alpha = g_c,xy . Lambda_a,  t = lambda_a tau_c / 2
             TL p[12];
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
               const TL al1 = fg1x * clx[a] + fexy * cly[a];
               const TL al2 = fexy * clx[a] + fg2y * cly[a];
-              const TL h = (TL)(0.5 * lam(a, tp));
+              const TL h = a == tp ? TL(1.0 / 3.0) : TL(1.0 / 12.0);  // lambda_a(tp) / 2
               const TL t1a = h * tau1, t2a = h * tau2;
-              p[2 * a] = (TL)psi(0, z) * al1 - t1a;
-              p[2 * a + 1] = (TL)psi(0, z) * al2 - t2a;
-              p[2 * (3 + a)] = (TL)psi(1, z) * al1 + t1a;
-              p[2 * (3 + a) + 1] = (TL)psi(1, z) * al2 + t2a;
+              p[2 * a] = pl0 * al1 - t1a;
+              p[2 * a + 1] = pl0 * al2 - t2a;
+              p[2 * (3 + a)] = pl1 * al1 + t1a;
+              p[2 * (3 + a) + 1] = pl1 * al2 + t2a;
             }
 #pragma unroll
             for (int i = 0; i < 12; ++i) {
@@ -603,9 +642,17 @@ __device__ __forceinline__ void assemble_column(const AsmArgs& A, const int t, T
 #pragma unroll
               for (int j = i; j < 12; ++j) acc_fma(K[uidx(i, j)], pw, p[j]);
             }
-            }  // !PICARD
           }
         }
+      };
+      if constexpr (std::is_same<TV, f64x2>::value) {
+#pragma unroll 1
+        for (int q = 0; q < 6; ++q) point(q >= 3 ? 1 : 0, q >= 3 ? q - 3 : q);
+      } else {
+#pragma unroll
+        for (int z = 0; z < 2; ++z)
+#pragma unroll
+          for (int tp = 0; tp < 3; ++tp) point(z, tp);
       }
       // residual: R_{a,k,c} = Lambda_a . sum_z psi_k(z) P_c(z) + psi_k' sum_tp lambda_a(tp) TW_c(tp)
       const TV T1s = (TW1[0] + TW1[1] + TW1[2]) * TV(1.0 / 6.0);
