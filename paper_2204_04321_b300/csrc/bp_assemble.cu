@@ -25,14 +25,14 @@ constexpr int min_blocks() {
 
 template <int MODE, class TL, bool ATOMIC, bool PICARD = false, class TV = double>
 __global__ void __launch_bounds__(128, min_blocks<TL, TV>()) k_assemble(const AsmArgs A) {
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= A.count) return;
-  const int t = A.tri_list ? A.tri_list[idx] : idx;
+  int c, l0, l1;
+  if (!column_segment(A, blockIdx.x * blockDim.x + threadIdx.x, c, l0, l1)) return;
+  const int t = A.tri_list ? A.tri_list[c] : c;
   if constexpr (MODE == MODE_FACT) {  // in-plane coefficients (24 lanes) and carried block (21)
     __shared__ __align__(16) unsigned char sraw[45 * 128 * sizeof(TL)];
-    assemble_column<MODE, TL, ATOMIC, PICARD, TV, true>(A, t, reinterpret_cast<TL*>(sraw) + threadIdx.x);
+    assemble_column<MODE, TL, ATOMIC, PICARD, TV, true>(A, t, reinterpret_cast<TL*>(sraw) + threadIdx.x, l0, l1);
   } else {
-    assemble_column<MODE, TL, ATOMIC, PICARD, TV>(A, t);
+    assemble_column<MODE, TL, ATOMIC, PICARD, TV>(A, t, nullptr, l0, l1);
   }
 }
 
@@ -41,11 +41,40 @@ __global__ void __launch_bounds__(128, min_blocks<TL, TV>()) k_assemble(const As
 constexpr int STAGED_TPB = 64;
 template <bool ATOMIC, class TV = double>
 __global__ void __launch_bounds__(STAGED_TPB) k_assemble_staged(const AsmArgs A) {
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= A.count) return;
-  const int t = A.tri_list ? A.tri_list[idx] : idx;
+  int c, l0, l1;
+  if (!column_segment(A, blockIdx.x * blockDim.x + threadIdx.x, c, l0, l1)) return;
+  const int t = A.tri_list ? A.tri_list[c] : c;
   __shared__ __align__(16) unsigned char sraw[81 * STAGED_TPB * sizeof(f64x2)];
-  assemble_column<MODE_FACT, f64x2, ATOMIC, false, TV, true, true>(A, t, reinterpret_cast<f64x2*>(sraw) + threadIdx.x);
+  assemble_column<MODE_FACT, f64x2, ATOMIC, false, TV, true, true>(A, t, reinterpret_cast<f64x2*>(sraw) + threadIdx.x,
+                                                                  l0, l1);
+}
+
+// Tail split of an atomic launch of `count` columns: when the columns fill more than one wave of
+// resident threads but not a whole number of waves, the columns of the last partial wave are taken
+// in layer segments (at least 2 layers each, at most 4 per column), so that the last wave is made
+// of short units and the SMs finish together.  Threads to launch are returned.
+int tail_split(AsmArgs& a, int resident_threads) {
+  a.nwhole = a.count;
+  a.nseg = 0;
+  const int nseg = std::min(4, a.L / 2);
+  if (nseg < 2 || resident_threads <= 0 || a.count <= resident_threads) return a.count;
+  const int rem = a.count % resident_threads;
+  if (rem == 0) return a.count;
+  a.nwhole = a.count - rem;
+  a.nseg = nseg;
+  return a.nwhole + rem * nseg;
+}
+
+// resident threads per device of a kernel launched with `tpb` threads per block
+template <class K>
+int resident_threads(K kernel, int tpb) {
+  int dev = 0, nsm = 0, per_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, tpb, 0) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return nsm * per_sm * tpb;
 }
 
 AsmArgs make_args(const bp_mesh* m, const double* U, double* R, void* J) {
@@ -81,7 +110,9 @@ int launch(const bp_mesh* m, AsmArgs a, int scatter, cudaStream_t s) {
       k_assemble<MODE, TL, false, PICARD, TV><<<(a.count + TPB - 1) / TPB, TPB, 0, s>>>(a);
     }
   } else {
-    k_assemble<MODE, TL, true, PICARD, TV><<<(a.count + TPB - 1) / TPB, TPB, 0, s>>>(a);
+    static const int resident = resident_threads(k_assemble<MODE, TL, true, PICARD, TV>, TPB);
+    const int threads = tail_split(a, resident);
+    k_assemble<MODE, TL, true, PICARD, TV><<<(threads + TPB - 1) / TPB, TPB, 0, s>>>(a);
   }
   BP_CUDA_TRY(cudaGetLastError());
   return BP_OK;
@@ -96,7 +127,9 @@ int launch_staged(const bp_mesh* m, AsmArgs a, int scatter, cudaStream_t s) {
       k_assemble_staged<false, TV><<<(a.count + STAGED_TPB - 1) / STAGED_TPB, STAGED_TPB, 0, s>>>(a);
     }
   } else {
-    k_assemble_staged<true, TV><<<(a.count + STAGED_TPB - 1) / STAGED_TPB, STAGED_TPB, 0, s>>>(a);
+    static const int resident = resident_threads(k_assemble_staged<true, TV>, STAGED_TPB);
+    const int threads = tail_split(a, resident);
+    k_assemble_staged<true, TV><<<(threads + STAGED_TPB - 1) / STAGED_TPB, STAGED_TPB, 0, s>>>(a);
   }
   BP_CUDA_TRY(cudaGetLastError());
   return BP_OK;

@@ -49,12 +49,36 @@ struct AsmArgs {
   const int32_t* tri_list;  // nullable: the triangles of one colour
   int32_t count;            // columns handled by this launch
   int32_t L;
+  // tail split (atomic scatter): threads [0, nwhole) take whole columns; the last count - nwhole
+  // columns are taken in nseg layer segments each, by the threads that follow (nseg 0: no split)
+  int32_t nwhole, nseg;
   double cA, delta;
   const double* Bn;  // nullable: [nv][L + 1] nodal hardness A^(-1/3) (rate-factor field); else cA
   const double* U;
   double* R;
   void* J;
 };
+
+// The column and layer segment [l0, l1) of thread idx of a launch (see AsmArgs::nwhole); false for
+// threads past the end.
+__device__ __forceinline__ bool column_segment(const AsmArgs& A, int idx, int& t, int& l0, int& l1) {
+  if (A.nseg <= 1) {
+    if (idx >= A.count) return false;
+    t = idx, l0 = 0, l1 = A.L;
+    return true;
+  }
+  if (idx < A.nwhole) {
+    t = idx, l0 = 0, l1 = A.L;
+    return true;
+  }
+  const int nrest = A.count - A.nwhole, j = idx - A.nwhole;
+  if (j >= nrest * A.nseg) return false;
+  const int sgm = j / nrest;
+  t = A.nwhole + (j - sgm * nrest);
+  l0 = sgm * A.L / A.nseg;
+  l1 = (sgm + 1) * A.L / A.nseg;
+  return true;
+}
 
 __device__ __forceinline__ constexpr double psi(int k, int z) {  // psi_k at zeta level z
   return (k == z) ? BP_QP_P : BP_QP_Q;
@@ -249,15 +273,22 @@ __device__ __forceinline__ Dual<TL, NL> operator*(double s, const Dual<TL, NL>& 
 // factors (Wp, the three strain combinations, tau_1, tau_2) wait in shared memory (slots 45..80),
 // and the element matrix is started only after the value path, so that it is not live there.  For
 // the paired-FP32 lanes, whose fully unrolled arithmetic outgrows the instruction cache.
+// l0, l1: the layers [l0, l1) of the column this call assembles (a segment; the whole column by
+// default).  A segment starts from its bottom level with nothing carried from below and scatters
+// its top level's residual and element block itself: every contribution is additive, so the
+// segments of one column give the column's sum (with atomics; the coloured scatter takes whole
+// columns only).
 template <int MODE, class TL, bool ATOMIC, bool PICARD = false, class TV = double, bool SBL = false,
           bool STAGE = false>
-__device__ __forceinline__ void assemble_column(const AsmArgs& A, const int t, TL* sbl = nullptr) {
+__device__ __forceinline__ void assemble_column(const AsmArgs& A, const int t, TL* sbl = nullptr, int l0 = 0,
+                                                int l1 = -1) {
   static_assert(std::is_same<TV, double>::value || (MODE == MODE_FACT && std::is_same<TL, float>::value) ||
                     (std::is_same<TV, f64x2>::value && MODE != MODE_DUAL),
                 "the FP32 value path exists for the factored method with FP32 lanes only, the double-single "
                 "one for the residual and the factored method");
   static_assert(!STAGE || (SBL && MODE == MODE_FACT && !PICARD), "the staged rank-one part needs SBL");
   const int L = A.L;
+  if (l1 < 0) l1 = L;
 
   // ---- column geometry (per base triangle)
   int v[3];
@@ -333,7 +364,7 @@ __device__ __forceinline__ void assemble_column(const AsmArgs& A, const int t, T
   double ub[3], vb[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    const double2 w = *reinterpret_cast<const double2*>(A.U + ubase[a]);
+    const double2 w = *reinterpret_cast<const double2*>(A.U + ubase[a] + 2 * l0);
     ub[a] = w.x;
     vb[a] = w.y;
   }
@@ -345,8 +376,8 @@ __device__ __forceinline__ void assemble_column(const AsmArgs& A, const int t, T
   // rate-factor field: hardness B = A^(-1/3) interpolated at the triangle points of the bottom level
   TV hb[3] = {cAV, cAV, cAV};
   if (A.Bn) {
-    const double b0 = A.Bn[(int64_t)v[0] * (L + 1)], b1 = A.Bn[(int64_t)v[1] * (L + 1)],
-                 b2 = A.Bn[(int64_t)v[2] * (L + 1)];
+    const double b0 = A.Bn[(int64_t)v[0] * (L + 1) + l0], b1 = A.Bn[(int64_t)v[1] * (L + 1) + l0],
+                 b2 = A.Bn[(int64_t)v[2] * (L + 1) + l0];
     const double bs = (b0 + b1 + b2) * (1.0 / 6.0);
     hb[0] = to_lane<TV>(bs + 0.5 * b0);
     hb[1] = to_lane<TV>(bs + 0.5 * b1);
@@ -369,12 +400,12 @@ __device__ __forceinline__ void assemble_column(const AsmArgs& A, const int t, T
 #define KC(k) Kc0[(k) * kcs]
   if constexpr (kAhead) {
 #pragma unroll
-    for (int a = 0; a < 3; ++a) nxt[a] = *reinterpret_cast<const double2*>(A.U + ubase[a] + 2);
+    for (int a = 0; a < 3; ++a) nxt[a] = *reinterpret_cast<const double2*>(A.U + ubase[a] + 2 * (l0 + 1));
 #pragma unroll
     for (int k = 0; k < 21; ++k) KC(k) = TL(0);
   }
 
-  for (int l = 0; l < L; ++l) {
+  for (int l = l0; l < l1; ++l) {
     double ut[3], vt[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
@@ -388,7 +419,7 @@ __device__ __forceinline__ void assemble_column(const AsmArgs& A, const int t, T
       vt[a] = w.y;
     }
     if constexpr (kAhead) {
-      if (l + 2 <= L) {
+      if (l + 2 <= l1) {
 #pragma unroll
         for (int a = 0; a < 3; ++a) nxt[a] = *reinterpret_cast<const double2*>(A.U + ubase[a] + 2 * (l + 2));
       }
@@ -915,7 +946,7 @@ __device__ __forceinline__ void assemble_column(const AsmArgs& A, const int t, T
         // the pattern, added by one vector atomic: 72 per wedge (54 with the carry) instead of 144
         // scalar ones.  The entry points require 8-byte aligned FP32 values.
         if constexpr (kAhead) {
-          if (l + 1 < L) {  // top-top block: carried to the next wedge
+          if (l + 1 < l1) {  // top-top block: carried to the next wedge
 #pragma unroll
             for (int i = 6; i < 12; ++i)
 #pragma unroll
@@ -929,7 +960,7 @@ __device__ __forceinline__ void assemble_column(const AsmArgs& A, const int t, T
           for (int nj = 0; nj < 6; ++nj) {
             const int kj = nj / 3, bj = nj % 3;
             if constexpr (kAhead) {
-              if (ni >= 3 && nj >= 3 && l + 1 < L) continue;  // carried
+              if (ni >= 3 && nj >= 3 && l + 1 < l1) continue;  // carried
             }
             const int j0 = 2 * nj, j1 = 2 * nj + 1;
             const float v0 = LaneStore<TL>::cast(K[i <= j0 ? uidx(i, j0) : uidx(j0, i)]);
@@ -946,7 +977,7 @@ __device__ __forceinline__ void assemble_column(const AsmArgs& A, const int t, T
           for (int j = i; j < 12; ++j) {
             const int nj = j >> 1, cj = j & 1, kj = nj / 3, bj = nj % 3;
             if constexpr (kAhead) {
-              if (i >= 6 && l + 1 < L) {  // top-top block: carried to the next wedge
+              if (i >= 6 && l + 1 < l1) {  // top-top block: carried to the next wedge
                 KC(uidx6(i - 6, j - 6)) = K[uidx(i, j)];
                 continue;
               }
@@ -977,8 +1008,8 @@ __device__ __forceinline__ void assemble_column(const AsmArgs& A, const int t, T
   }
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    scatter_add<ATOMIC>(A.R + ubase[a] + 2 * L, to_r(carry[a][0]));
-    scatter_add<ATOMIC>(A.R + ubase[a] + 2 * L + 1, to_r(carry[a][1]));
+    scatter_add<ATOMIC>(A.R + ubase[a] + 2 * l1, to_r(carry[a][0]));
+    scatter_add<ATOMIC>(A.R + ubase[a] + 2 * l1 + 1, to_r(carry[a][1]));
   }
 #undef KC
 }

@@ -290,3 +290,27 @@ def test_paired_fp32_lanes_closer_to_oracle_than_fp32():
     e32 = float((J32.double() - J64).abs().max()) / scale
     assert e2 <= 1e-13 and e32 >= 1e-9 and e2 <= 1e-4 * e32, (e2, e32)
 
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32", "f64x2_ds", "f32_ds"])
+def test_tail_split_columns_match_oracle(precision):
+    """A mesh a little larger than one wave of resident threads (39,200 columns against 37,888 on a
+    B300): the atomic launches take the last partial wave's columns in layer segments.  R and J
+    over the whole mesh against the oracle, and against the coloured scatter (whole columns)."""
+    c = capi()
+    mesh = synth.dome_mesh(140, 5, 91, 92, bed="sinusoidal", beta="field")
+    assert mesh.ntri == 39200
+    om = oracle.OracleMesh(mesh)
+    U = synth.random_velocity(mesh, 93)
+    dm = c.DeviceMesh(mesh)
+    prec = {"f64": c.BP_F64, "f32": c.BP_F32, "f64x2_ds": c.BP_F64X2_DS, "f32_ds": c.BP_F32_DS}[precision]
+    J, R = dm.jacobian(dev(U), precision=prec, scatter=c.BP_SCATTER_ATOMIC)
+    _, _, Jc, Rc = om.jacobian_colored(U, 8)
+    assert rel_inf(R.cpu().numpy(), Rc) <= TOL64
+    tol = TOL32 if precision in ("f32", "f32_ds") else TOL64
+    assert rel_inf(J.cpu().numpy().astype(np.float64), Jc) <= tol
+    Jk, Rk = dm.jacobian(dev(U), precision=prec, scatter=c.BP_SCATTER_COLOR)
+    assert rel_inf(R.cpu().numpy(), Rk.cpu().numpy()) <= TOL64
+    if precision == "f64":
+        Rr = dm.residual(dev(U))
+        assert rel_inf(Rr.cpu().numpy(), Rc) <= TOL64
