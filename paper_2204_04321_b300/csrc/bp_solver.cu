@@ -753,11 +753,20 @@ __global__ void __launch_bounds__(128) k_energy_change(const double2* __restrict
                                                        int64_t ndof, double cA, const double* __restrict__ Bn,
                                                        double delta, double alpha,
                                                        const double* __restrict__ U, const DT* __restrict__ D,
-                                                       double* out) {
+                                                       double* out, int nwhole, int nseg) {
   double acc = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < ndof; i += (int64_t)gridDim.x * blockDim.x)
     acc += alpha * load[i] * (double)D[i];
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  // column t, layers [l0, l1): threads below nwhole take whole columns, the rest the last columns'
+  // layer segments (the column sums are additive; only the bottom segment adds the basal term)
+  int t = blockIdx.x * blockDim.x + threadIdx.x, l0 = 0, l1 = L;
+  if (nseg > 1 && t >= nwhole) {
+    const int nrest = ntri - nwhole, j = t - nwhole;
+    const int sgm = j / nrest;
+    t = sgm < nseg ? nwhole + (j - sgm * nrest) : ntri;
+    l0 = sgm * L / nseg;
+    l1 = (sgm + 1) * L / nseg;
+  }
   if (t < ntri) {
     int v[3];
     double x[3], y[3], H[3], bb[3];
@@ -783,7 +792,7 @@ __global__ void __launch_bounds__(128) k_energy_change(const double2* __restrict
     const double Hs6 = (H[0] + H[1] + H[2]) * (1.0 / 6.0);
     int64_t ub[3];
     for (int a = 0; a < 3; ++a) ub[a] = 2LL * v[a] * (L + 1);
-    {
+    if (l0 == 0) {
       const double* Mb = basal + 6 * (int64_t)t;
       const double M[3][3] = {{Mb[0], Mb[1], Mb[2]}, {Mb[1], Mb[3], Mb[4]}, {Mb[2], Mb[4], Mb[5]}};
       for (int a = 0; a < 3; ++a)
@@ -808,10 +817,10 @@ __global__ void __launch_bounds__(128) k_energy_change(const double2* __restrict
     }
     T u0[3], v0[3], a0[3], b0[3];
     for (int a = 0; a < 3; ++a) {
-      u0[a] = to_T<T>(U[ub[a]]);
-      v0[a] = to_T<T>(U[ub[a] + 1]);
-      a0[a] = dir_T<T>(D[ub[a]]);
-      b0[a] = dir_T<T>(D[ub[a] + 1]);
+      u0[a] = to_T<T>(U[ub[a] + 2 * l0]);
+      v0[a] = to_T<T>(U[ub[a] + 2 * l0 + 1]);
+      a0[a] = dir_T<T>(D[ub[a] + 2 * l0]);
+      b0[a] = dir_T<T>(D[ub[a] + 2 * l0 + 1]);
     }
     auto grad2 = [&](const T* w, T& gx, T& gy) {
       gx = w[0] * tlx[0] + w[1] * tlx[1] + w[2] * tlx[2];
@@ -823,7 +832,7 @@ __global__ void __launch_bounds__(128) k_energy_change(const double2* __restrict
     grad2(a0, gA0[0], gA0[1]);
     grad2(b0, gB0[0], gB0[1]);
     double stress = 0.0;
-    for (int l = 0; l < L; ++l) {
+    for (int l = l0; l < l1; ++l) {
       T u1[3], v1[3], a1[3], b1[3];
       for (int a = 0; a < 3; ++a) {
         u1[a] = to_T<T>(U[ub[a] + 2 * l + 2]);
@@ -1038,10 +1047,30 @@ template <class T, class DT>
 int energy_change_host(bp_mesh* m, const double* U, const DT* D, double alpha, cudaStream_t s, double* out) {
   bp_solver_ws* w = m->ws;
   BP_CUDA_TRY(cudaMemsetAsync(w->red + 2, 0, sizeof(double), s));
-  const int grid = (int)std::max<int64_t>((m->ntri + 127) / 128, std::min<int64_t>((m->ndof + 127) / 128, 148 * 16));
+  // the columns of the last partial wave of resident threads are taken in layer segments (as the
+  // assembly's atomic launches do), so that the SMs finish together
+  static int resident = -1;
+  if (resident < 0) {
+    int dev = 0, nsm = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_energy_change<T, DT>, 128, 0) != cudaSuccess) {
+      cudaGetLastError();
+      per_sm = 0;
+    }
+    resident = nsm * per_sm * 128;
+  }
+  int nwhole = m->ntri, nseg = 0;
+  const int segs = std::min(4, m->nl / 2);
+  if (segs >= 2 && resident > 0 && m->ntri > resident && m->ntri % resident) {
+    nwhole = m->ntri - m->ntri % resident;
+    nseg = segs;
+  }
+  const int64_t threads = nwhole + (int64_t)(m->ntri - nwhole) * nseg;
+  const int grid = (int)std::max<int64_t>((threads + 127) / 128, std::min<int64_t>((m->ndof + 127) / 128, 148 * 16));
   k_energy_change<T, DT><<<grid, 128, 0, s>>>(m->xy, m->bed, m->thick, m->sigma, m->tri, m->basal, m->load, m->ntri,
                                               m->nl, m->ndof, m->cA, m->Bnode, m->p.delta, alpha, U, D,
-                                              w->red + 2);
+                                              w->red + 2, nwhole, nseg);
   BP_CUDA_TRY(cudaGetLastError());
   BP_CUDA_TRY(cudaMemcpyAsync(w->host, w->red + 2, sizeof(double), cudaMemcpyDeviceToHost, s));
   BP_CUDA_TRY(cudaStreamSynchronize(s));

@@ -365,3 +365,20 @@ def test_double_single_value_path_newton_reaches_the_fp64_solution(precision):
         with pytest.raises(c.BPError) as e:
             c.bp_newton_solve(dm.handle, U, precision=c.BP_F64X2_DS, picard_rtol=0.1)
         assert e.value.status == c.BP_EUNSUP
+
+
+def test_energy_change_with_tail_segments_matches_oracle():
+    """80,000 columns, more than one wave of resident threads of the energy-change kernel (75,776 on a
+    B300): the last partial wave's columns are taken in layer segments; the change must still equal
+    the oracle's energy difference."""
+    c = capi()
+    mesh = synth.dome_mesh(200, 4, 63, 64, bed="sinusoidal", beta="field")
+    assert mesh.ntri == 80000
+    om = oracle.OracleMesh(mesh)
+    U = om.sia()
+    D = synth.random_velocity(mesh, 9, amplitude=30.0)
+    dm = c.DeviceMesh(mesh)
+    dE = c.bp_energy_change(dm.handle, dev(U), dev(D), 1.0)
+    E0 = om.energy(U)
+    ref = om.energy(U + D) - E0
+    assert abs(dE - ref) <= 1e-9 * abs(ref) + 1e-13 * abs(E0)
