@@ -118,6 +118,59 @@ def workload_name(m: int, layers: int) -> str:
             f"layers = {ntri * layers} wedges, sinusoidal bed, correlated lognormal beta")
 
 
+def bench_config(args, ws: int) -> dict:
+    """The workload both arms name: the same dict on the GPU line and on the reference line."""
+    return {"workload": workload_name(args.mesh_m, args.layers),
+            "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU",
+            "l2": f"GPU arm: inputs larger than L2 and L2 flushed between steps ({L2_FLUSH_BYTES >> 20} MB "
+                  f"write outside the timed events)"}
+
+
+def headline(line: dict) -> dict:
+    """The nested sections' key figures in a few hundred bytes, printed as the line's last key so
+    that a reader of the line's tail sees them: FP64-accurate assembly kinds, Newton solve times,
+    the learned start over unseen fields, the ensemble and the MLP."""
+    def get(d, *path):
+        for k in path:
+            if not isinstance(d, dict) or k not in d:
+                return None
+            d = d[k]
+        return d
+
+    def r(x, nd=4):
+        return None if x is None else float(f"{x:.{nd}g}")
+
+    sec, out = line.get("secondary") or {}, {}
+    out["assembly_ms"] = {"f64": r(get(line, "roofline", "kernel_ms")),
+                          "f64x2_ds": r(get(sec, "jacobian_paired_lanes_double_single_values", "ms")),
+                          "f32_ds": r(get(sec, "jacobian_f32_lanes_double_single_values", "ms")),
+                          "f32_lanes": r(get(sec, "jacobian_f32_lanes", "ms")),
+                          "residual": r(get(sec, "residual_only", "ms"))}
+    out["roofline_frac"] = r(get(line, "roofline", "frac"), 3)
+    d = get(line, "newton", "dome-100k-tri-x10") or {}
+    ms = {k: r(1e3 * v["s"]) for k, v in d.items() if isinstance(v, dict) and "s" in v}
+    if ms:
+        out["newton_1M_ms"] = ms
+    u = get(d, "learned_start_mixed", "unseen_beta_fields")
+    if u:
+        out["learned_picard_vs_sia"] = {"seeds": u["seeds"], "speedup": r(u["speedup_learned_picard_vs_sia"]),
+                                        "ci99": [r(c) for c in u["ci99"]]}
+    d4 = get(line, "newton", "dome-400k-tri-x10") or {}
+    ms4 = {k: r(1e3 * v["s"]) for k, v in d4.items() if isinstance(v, dict) and "s" in v}
+    if ms4:
+        out["newton_4M_ms"] = ms4
+    dm = get(line, "newton", "marine-100k-tri-x10") or {}
+    msm = {k: r(1e3 * v["s"]) for k, v in dm.items() if isinstance(v, dict) and "s" in v}
+    if msm:
+        out["newton_marine_1M_ms"] = msm
+    if line.get("ensemble"):
+        out["ensemble_wedges_per_s"] = r(get(line, "ensemble", "value"))
+    if line.get("mlp"):
+        out["mlp_ms"] = {"inference": r(get(line, "mlp", "inference", "ms")),
+                         "train_step": r(get(line, "mlp", "train_step", "ms"))}
+    return out
+
+
 def max_over_ranks(x: float, ws: int, device=None) -> float:
     """The largest per-rank value over all ranks (a job takes as long as its slowest rank)."""
     if ws <= 1:
@@ -225,12 +278,11 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": workload_name(args.mesh_m, args.layers),
-                       "sample": "each step: dome-20k-tri-x10, 200,000 wedges, same generators",
-                       "oracle": f"CPU FP64, columns colour by colour on {cores} threads"},
+            "config": bench_config(args, ws),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "cpu_model": cpu_model(),
-                             "sample": f"dome-20k-tri-x10, 200,000 wedges per step, {cores} threads"},
+                             "sample": f"each step: dome-20k-tri-x10 (200,000 wedges, the same generators), "
+                                       f"CPU FP64 oracle, columns colour by colour on {cores} threads"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -414,10 +466,9 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": workload_name(args.mesh_m, args.layers),
-                       "ndof": dm.ndof, "nnz": dm.nnz, "lanes": "f64, sum-factorised",
-                       "scatter": "atomic", "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU",
-                       "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MB write outside the timed events)"},
+            "config": bench_config(args, ws),
+            "problem": {"wedges": W, "ndof": dm.ndof, "nnz": dm.nnz, "lanes": "f64, sum-factorised",
+                        "scatter": "atomic"},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
                          "frac": achieved / fp64_peak, "traffic": traffic,
                          "kernel": "k_assemble<factored, double, atomic>",
@@ -461,6 +512,7 @@ def run_ours(args):
         }
         if not args.no_cpu_baseline and ws == 1:
             line["cpu_baseline"] = cpu_oracle_sample()
+        line["headline"] = headline(line)
         print(json.dumps(line), flush=True)
     dm.close()
     if ws > 1:

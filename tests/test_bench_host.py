@@ -72,6 +72,48 @@ def test_workload_names_agree_between_arms():
     assert "1003520 wedges" in bench.workload_name(224, 10)
 
 
+def test_reference_arm_prints_the_gpu_arms_config():
+    """Both arms name the same workload dict, so the two lines compare like for like."""
+    import argparse
+    bench = load_bench()
+    p = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                        "--warmup", "0"], env=dict(os.environ, RANK="0", WORLD_SIZE="1", LOCAL_RANK="0"),
+                       capture_output=True, text=True, timeout=600)
+    assert p.returncode == 0, p.stderr
+    line = json.loads(p.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["steps"] == 1
+    assert line["config"] == bench.bench_config(argparse.Namespace(mesh_m=224, layers=10), 1)
+    assert line["e2e"]["value"] == line["value"] == line["cpu_baseline"]["value"]
+
+
+def test_headline_is_short_and_last():
+    """The line's last key carries the nested sections' key figures in a short tail."""
+    bench = load_bench()
+    solve = {"s": 0.0214, "converged": True, "newton_iters": 12, "krylov_iters": 138}
+    kinds = ["f64", "mixed_f32", "f64_accurate_double_single", "mixed_f32_double_single",
+             "mixed_f32_double_single_value32_until_1e-4"] + [f"mixed_f32_value32_until_{t}" for t in
+                                                               ("0.01", "0.001", "0.0001", "1e-05")] + \
+        ["f64_mdsc", "mixed_f32_mdsc", "mixed_f32_mdsc_amg", "mixed_f32_gmres50"]
+    dome = {k: dict(solve) for k in kinds}
+    dome["learned_start_mixed"] = {"unseen_beta_fields": {"seeds": 40, "speedup_learned_picard_vs_sia": 1.0881,
+                                                          "ci99": [1.0264, 1.1534]}}
+    line = {"roofline": {"kernel_ms": 3.5654, "frac": 0.8012},
+            "secondary": {"residual_only": {"ms": 0.774}, "jacobian_f32_lanes": {"ms": 0.893},
+                          "jacobian_paired_lanes_double_single_values": {"ms": 2.54},
+                          "jacobian_f32_lanes_double_single_values": {"ms": 0.68}},
+            "newton": {"dome-100k-tri-x10": dome,
+                       "dome-400k-tri-x10": {k: dict(solve) for k in kinds[:6]},
+                       "marine-100k-tri-x10": {k: dict(solve) for k in kinds[:4]}},
+            "ensemble": {"value": 2.75e8}, "mlp": {"inference": {"ms": 0.023}, "train_step": {"ms": 0.17}}}
+    h = bench.headline(line)
+    assert len(json.dumps(h)) < 1500
+    assert h["learned_picard_vs_sia"] == {"seeds": 40, "speedup": 1.088, "ci99": [1.026, 1.153]}
+    assert h["newton_1M_ms"]["mixed_f32_double_single_value32_until_1e-4"] == 21.4
+    assert h["assembly_ms"]["f64x2_ds"] == 2.54 and h["roofline_frac"] == 0.801
+    assert bench.headline({}) == {"assembly_ms": {k: None for k in ("f64", "f64x2_ds", "f32_ds", "f32_lanes",
+                                                                     "residual")}, "roofline_frac": None}
+
+
 def test_traffic_record_hash_follows_code_not_comments(tmp_path):
     """The DRAM-traffic record of the headline kernel is reported only while the kernel's code is
     the one it was captured from: a comment edit keeps the hash, a code edit changes it."""
