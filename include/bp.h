@@ -275,6 +275,17 @@ int bp_energy(bp_mesh* mesh, const double* U_dev, double* out_host, void* stream
 int bp_energy_change(bp_mesh* mesh, const double* U_dev, const double* D_dev, double alpha, double* out_host,
                      void* stream);
 
+/*
+ * The same energy change in the arithmetic of one of the Newton solve's line searches: BP_F64 (as
+ * bp_energy_change), BP_F64X2_DS (the per-point work in double-single pairs on the FP32 pipe,
+ * FP64-accurate: the line search of the BP_F64 and BP_F64X2_DS solves), or BP_F32 (the per-point
+ * work in FP32 with the per-column geometry and the driving and basal terms in FP64: the line
+ * search of the mixed-precision solves; ~1e-5 relative).  Inputs as for bp_energy_change.
+ * Errors: BP_EINVAL (NULL pointer, another precision), BP_ENOMEM, BP_ECUDA.
+ */
+int bp_energy_change_ex(bp_mesh* mesh, const double* U_dev, const double* D_dev, double alpha, int precision,
+                        double* out_host, void* stream);
+
 /* Initial guesses of the Newton solve (not in the paper). */
 enum { BP_GUESS_ZERO = 0, BP_GUESS_SIA = 1 };
 /*
@@ -296,8 +307,10 @@ typedef struct {
   int max_newton;     /* Newton iteration limit (<= 64) */
   int max_krylov;     /* Krylov iterations per Newton step */
   double eta_max;     /* Eisenstat-Walker forcing term cap (choice 2, gamma = 0.9) */
-  int precision;      /* BP_F64: FP64 Jacobian and Krylov; BP_F32: FP32 Jacobian lanes and Krylov
-                         (inexact Newton); the residual, viscosity, norms and update stay FP64.
+  int precision;      /* BP_F64: FP64 Jacobian and Krylov, the line search's energy change
+                         FP64-accurate in double-single pairs (bp_energy_change_ex); BP_F32: FP32
+                         Jacobian lanes and Krylov (inexact Newton), FP32 energy change; the
+                         residual, viscosity, norms and update stay FP64.
                          BP_F64X2_DS: FP64-accurate residual and Jacobian from the double-single value
                          path and paired lanes, FP64 Krylov, the line search's energy change in pairs
                          (no Picard steps); BP_F32_DS: as BP_F32 with the double-single value path

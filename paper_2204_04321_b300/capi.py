@@ -100,6 +100,7 @@ SIGNATURES = {
     "bp_mdsc_apply": (_I, [_P, _P, _P, _P, _P]),
     "bp_energy": (_I, [_P, _P, _P, _P]),
     "bp_energy_change": (_I, [_P, _P, _P, ctypes.c_double, _P, _P]),
+    "bp_energy_change_ex": (_I, [_P, _P, _P, ctypes.c_double, ctypes.c_int, _P, _P]),
     "bp_initial_guess": (_I, [_P, _I, _P, _P]),
     "bp_solve_opts_default": (None, [_P]),
     "bp_newton_solve": (_I, [_P, _P, _P, _P, _P]),
@@ -290,6 +291,13 @@ def bp_energy_change(handle, U, D, alpha, stream=None) -> float:
     out = ctypes.c_double()
     _check(lib().bp_energy_change(handle, _dptr(U), _dptr(D), alpha, ctypes.byref(out), _stream_ptr(stream)),
            "bp_energy_change")
+    return out.value
+
+
+def bp_energy_change_ex(handle, U, D, alpha, precision, stream=None) -> float:
+    out = ctypes.c_double()
+    _check(lib().bp_energy_change_ex(handle, _dptr(U), _dptr(D), alpha, precision, ctypes.byref(out),
+                                     _stream_ptr(stream)), "bp_energy_change_ex")
     return out.value
 
 

@@ -84,6 +84,11 @@ __global__ void k_find_dslot(const int32_t* __restrict__ nbr_ptr, const int32_t*
 }
 
 // ------------------------------------------------------------------ SpMV
+// a * b + c with one rounding in the type of the operands (fmaf for FP32: the overload set of fma
+// would otherwise be free to promote to FP64)
+__device__ __forceinline__ float vfma(const float a, const float b, const float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double vfma(const double a, const double b, const double c) { return fma(a, b, c); }
+
 template <class T>
 struct Pair;
 template <>
@@ -135,19 +140,22 @@ __global__ void __launch_bounds__(NT) k_spmv_pairs(const int64_t* __restrict__ r
       const int32_t* nb = nbr_idx + nbr_ptr[a];
       const M2* v0 = reinterpret_cast<const M2*>(vals + s0);
       const M2* v1 = v0 + half;
-      int sl = lane / nlev;  // k = sl nlev + dl
-      int dl = lane - sl * nlev;
+      // k = sl nlev + dl formed afresh in every step (nlev is 2 or 3: a shift or a multiply-high),
+      // so that no step depends on the one before and the unrolled steps' loads are all in flight
+      // (unrolled 4 deep for FP64 values, whose FMAs bind; 2 for FP32, where deeper unrolling
+      // costs registers and resident warps: measured on the 1M-wedge Newton solve)
+      constexpr int UNR = sizeof(M) == sizeof(double) ? 4 : 2;
+#pragma unroll UNR
       for (int k = lane; k < half; k += TPR) {
+        const int sl = nlev == 3 ? k / 3 : k >> 1;
+        const int dl = k - sl * nlev;
         const int b = __ldg(nb + sl);
         const V2 xx = *reinterpret_cast<const V2*>(x + 2 * ((int64_t)b * (L + 1) + lmin + dl));
         const M2 a0 = v0[k], a1 = v1[k];
-        y0 += (V)a0.x * xx.x + (V)a0.y * xx.y;
-        y1 += (V)a1.x * xx.x + (V)a1.y * xx.y;
-        dl += TPR;
-        while (dl >= nlev) {
-          dl -= nlev;
-          ++sl;
-        }
+        // chained FMAs: one FMA per matrix entry (a sum of two products first would cost a
+        // multiply, an FMA and an add per pair, 1.5 instructions per entry on the FP64 pipe)
+        y0 = vfma((V)a0.y, xx.y, vfma((V)a0.x, xx.x, y0));
+        y1 = vfma((V)a1.y, xx.y, vfma((V)a1.x, xx.x, y1));
       }
     }
     V keep = upper ? y1 : y0;
@@ -251,11 +259,11 @@ __device__ __forceinline__ void colprec_apply(const Prec<F>& P, int a, const V* 
 #pragma unroll 4
   for (int l = 0; l <= L; ++l) {
     F r0 = (F)r[base + 2 * l], r1 = (F)r[base + 2 * l + 1];
-    srr += r0 * r0 + r1 * r1;
+    srr = vfma(r1, r1, vfma(r0, r0, srr));  // chained FMAs: no separate multiply and add
     if (l > 0) {
       const F* Lp = P.Lm + (int64_t)(l - 1) * 4 * nv + a;
-      r0 -= Lp[0] * p0 + Lp[nv] * p1;
-      r1 -= Lp[2 * nv] * p0 + Lp[3 * nv] * p1;
+      r0 = vfma(-Lp[nv], p1, vfma(-Lp[0], p0, r0));
+      r1 = vfma(-Lp[3 * nv], p1, vfma(-Lp[2 * nv], p0, r1));
     }
     z[base + 2 * l] = (V)r0;
     z[base + 2 * l + 1] = (V)r1;
@@ -268,8 +276,8 @@ __device__ __forceinline__ void colprec_apply(const Prec<F>& P, int a, const V* 
     F t0 = (F)z[base + 2 * l], t1 = (F)z[base + 2 * l + 1];
     if (l < L) {
       const F* Fp = P.Fu + (int64_t)l * 4 * nv + a;
-      t0 -= Fp[0] * p0 + Fp[nv] * p1;
-      t1 -= Fp[2 * nv] * p0 + Fp[3 * nv] * p1;
+      t0 = vfma(-Fp[nv], p1, vfma(-Fp[0], p0, t0));
+      t1 = vfma(-Fp[3 * nv], p1, vfma(-Fp[2 * nv], p0, t1));
     }
     const F* Gp = P.Ginv + (int64_t)l * 4 * nv + a;
     const F z0 = Gp[0] * t0 + Gp[nv] * t1;
@@ -278,7 +286,7 @@ __device__ __forceinline__ void colprec_apply(const Prec<F>& P, int a, const V* 
     z[base + 2 * l + 1] = (V)z1;
     p0 = z0;
     p1 = z1;
-    srz += (F)r[base + 2 * l] * z0 + (F)r[base + 2 * l + 1] * z1;
+    srz = vfma((F)r[base + 2 * l + 1], z1, vfma((F)r[base + 2 * l], z0, srz));
   }
   *rz = (double)srz;
   *rr = (double)srr;
@@ -590,6 +598,8 @@ template <class T, class DT>
 __device__ __forceinline__ T dir_T(const DT x) {
   if constexpr (std::is_same<T, f64x2>::value) {
     return ds_of((double)x);
+  } else if constexpr (std::is_same<T, float>::value && std::is_same<DT, double>::value) {
+    return f32_of(x);  // on the integer pipe
   } else {
     return (T)x;
   }
@@ -707,7 +717,7 @@ __global__ void __launch_bounds__(128) k_energy(const double2* __restrict__ xy, 
           const double exy = 0.5 * (uy + vx);
           const double e2 = ux * ux + vy * vy + ux * vy + exy * exy + 0.25 * (uz * uz + vz * vz);
           const double xx = e2 + delta;
-          acc += (d * h / 12.0) * 1.5 * hardness_at(Bn, cA, v, L, l, p0, p1, tp) * xx * inv_cbrt(xx);
+          acc += (d * h * (1.0 / 12.0)) * 1.5 * hardness_at(Bn, cA, v, L, l, p0, p1, tp) * xx * inv_cbrt(xx);
         }
       }
     }
@@ -715,15 +725,40 @@ __global__ void __launch_bounds__(128) k_energy(const double2* __restrict__ xy, 
   block_add(acc, out);
 }
 
-// symmetric bilinear form of eps_e^2 on velocity gradients G = (u_x, u_y, u_z, v_x, v_y, v_z):
-// Q(G) = B(G, G) = eps_e^2
+// eps_e^2 as a quadratic form Q on velocity gradients G = (u_x, u_y, u_z, v_x, v_y, v_z), and its
+// polar (symmetric bilinear) form B with B(G, G) = Q(G):
+//   Q(G)    = u_x^2 + v_y^2 + u_x v_y + ((u_y + v_x)^2 + u_z^2 + v_z^2) / 4
+//   B(G, H) = u_x U_x + v_y V_y + (u_x V_y + v_y U_x) / 2 + ((u_y + v_x)(U_y + V_x) + u_z U_z + v_z V_z) / 4
+// written as chains of FMAs (8 and 11 operations)
+__device__ __forceinline__ f64x2 vfma(const f64x2 a, const f64x2 b, const f64x2 c) { return a * b + c; }
+template <class T>
+__device__ __forceinline__ T eps_quad(const T* A) {
+  const T s = A[1] + A[3];
+  const T q = vfma(A[5], A[5], vfma(A[2], A[2], s * s));
+  const T p = vfma(A[0], A[0] + A[4], A[4] * A[4]);
+  return vfma(T(0.25), q, p);
+}
 template <class T>
 __device__ __forceinline__ T eps_bilinear(const T* A, const T* B) {
-  const T exyA = T(0.5) * (A[1] + A[3]), exyB = T(0.5) * (B[1] + B[3]);
-  return A[0] * B[0] + A[4] * B[4] + T(0.5) * (A[0] * B[4] + B[0] * A[4]) + exyA * exyB +
-         T(0.25) * (A[2] * B[2] + A[5] * B[5]);
+  const T q = vfma(A[5], B[5], vfma(A[2], B[2], (A[1] + A[3]) * (B[1] + B[3])));
+  const T m = vfma(A[0], B[4], B[0] * A[4]);
+  const T p = vfma(A[4], B[4], A[0] * B[0]);
+  return vfma(T(0.25), q, vfma(T(0.5), m, p));
 }
 
+// 1 / x for x > 0: an FP32 reciprocal of x rounded to FP32 as the seed (conversions on the integer
+// pipe), then two Newton-Raphson steps r <- r + r (1 - x r) in FP64, each of which squares the
+// relative error (2^-23 -> 2^-46 -> below FP64 rounding): four FMAs on the FP64 pipe.  x outside
+// the FP32 range in which the seed is accurate takes the full division.
+__device__ __forceinline__ double recip_pos(const double x) {
+  const float xf = f32_of(x);
+  if (!(xf > 1e-30f && xf < 1e30f)) return 1.0 / x;
+  double r = f64_of(1.0f / xf);
+  r = fma(r, fma(-x, r, 1.0), r);
+  return fma(r, fma(-x, r, 1.0), r);
+}
+__device__ __forceinline__ float recip_pos(const float x) { return 1.0f / x; }
+__device__ __forceinline__ f64x2 recip_pos(const f64x2 x) { return f64x2(1.f, 0.f) / x; }
 
 __device__ __forceinline__ double cube_root(double x) {  // x^(1/3) = x (x^(-1/3))^2
   const double r = inv_cbrt(x);
@@ -846,7 +881,7 @@ __global__ void __launch_bounds__(128) k_energy_change(const double2* __restrict
       grad2(a1, gA1[0], gA1[1]);
       grad2(b1, gB1[0], gB1[1]);
       const T s_l = to_T<T>(sigma[l]), ds = to_T<T>(sigma[l + 1] - sigma[l]);
-      const T invds = T(1) / ds;
+      const T invds = recip_pos(ds);
       const T sixth = T(1.0 / 6.0);
       const T du6 = (u1[0] - u0[0] + u1[1] - u0[1] + u1[2] - u0[2]) * sixth;
       const T dv6 = (v1[0] - v0[0] + v1[1] - v0[1] + v1[2] - v0[2]) * sixth;
@@ -869,15 +904,16 @@ __global__ void __launch_bounds__(128) k_energy_change(const double2* __restrict
           const T bz = (db6 + T(0.5) * (b1[tp] - b0[tp])) * invh;
           const T G0[6] = {GUx - uz * Gzx, GUy - uz * Gzy, uz, GVx - vz * Gzx, GVy - vz * Gzy, vz};
           const T Gd[6] = {GAx - az * Gzx, GAy - az * Gzy, az, GBx - bz * Gzx, GBy - bz * Gzy, bz};
-          const T x0 = eps_bilinear(G0, G0) + tdelta;
-          const T dx = ta * (T(2) * eps_bilinear(G0, Gd) + ta * eps_bilinear(Gd, Gd));
+          const T x0 = eps_quad(G0) + tdelta;
+          const T dx = ta * vfma(ta, eps_quad(Gd), T(2) * eps_bilinear(G0, Gd));
           const T x1 = x0 + dx;
           const T ca = cube_root(x1), cb = cube_root(x0);
-          const T diff23 = dx / (ca * ca + ca * cb + cb * cb) * (ca + cb);
+          const T sab = ca + cb;  // a^2 + a b + b^2 = a (a + b) + b^2 > 0
+          const T diff23 = dx * recip_pos(vfma(ca, sab, cb * cb)) * sab;
           lstress += Hq[tp] * hardness_at_t<T>(Bn, tcA, v, L, l, p0, p1, tp) * diff23;
         }
       }
-      stress += (d * (sigma[l + 1] - sigma[l]) / 12.0) * from_T(lstress);
+      stress += (d * (sigma[l + 1] - sigma[l]) * (1.0 / 12.0)) * from_T(lstress);
       for (int a = 0; a < 3; ++a) {
         u0[a] = u1[a];
         v0[a] = v1[a];
@@ -2807,6 +2843,19 @@ extern "C" int bp_energy_change(bp_mesh* m, const double* U, const double* D, do
   return energy_change_host<double, double>(m, U, D, alpha, s, out);
 }
 
+extern "C" int bp_energy_change_ex(bp_mesh* m, const double* U, const double* D, double alpha, int precision,
+                                   double* out, void* stream) {
+  if (!m || !U || !D || !out) return BP_EINVAL;
+  if (precision != BP_F64 && precision != BP_F64X2_DS && precision != BP_F32) return BP_EINVAL;
+  bp_device_guard g(m->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc = ensure_ws(m, s);
+  if (rc) return rc;
+  if (precision == BP_F64X2_DS) return energy_change_host<f64x2, double>(m, U, D, alpha, s, out);
+  if (precision == BP_F32) return energy_change_host<float, double>(m, U, D, alpha, s, out);
+  return energy_change_host<double, double>(m, U, D, alpha, s, out);
+}
+
 extern "C" int bp_initial_guess(bp_mesh* m, int kind, double* U, void* stream) {
   if (!m || !U) return BP_EINVAL;
   if (kind != BP_GUESS_ZERO && kind != BP_GUESS_SIA) return BP_EINVAL;
@@ -3007,10 +3056,8 @@ extern "C" int bp_newton_solve(bp_mesh* m, double* U, const bp_solve_opts* opts,
         double dE;
         if (f32)
           rc = energy_change_host<float, float>(m, U, reinterpret_cast<const float*>(w->x), alpha, s, &dE);
-        else if (o.precision == BP_F64X2_DS)  // the per-point work in pairs (FP64-accurate, FP32 pipe)
+        else  // FP64-accurate: the per-point work in pairs on the FP32 pipe (2.5x faster than FP64)
           rc = energy_change_host<f64x2, double>(m, U, w->x, alpha, s, &dE);
-        else
-          rc = energy_change_host<double, double>(m, U, w->x, alpha, s, &dE);
         if (rc) return rc;
         if (dE <= c * alpha * slope || h == 10) break;
         if (o.line_search == BP_LS_QUADRATIC) {

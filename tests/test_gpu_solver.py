@@ -103,6 +103,38 @@ def test_energy_matches_oracle(kind):
 
 
 @pytest.mark.parametrize("alpha", [1.0, 1e-3])
+@pytest.mark.parametrize("precision,rtol", [("F64", 1e-9), ("F64X2_DS", 1e-9), ("F32", 1e-4)])
+def test_energy_change_kinds_match_oracle_difference(precision, rtol, alpha):
+    """The three line-search kinds (FP64, double-single pairs: the FP64 solves' line search; FP32: the
+    mixed solves') against the oracle's energy difference."""
+    c = capi()
+    mesh = synth.dome_mesh(20, 5, 61, 62, bed="sinusoidal", beta="field")
+    om = oracle.OracleMesh(mesh)
+    U = om.sia()
+    D = synth.random_velocity(mesh, 8, amplitude=30.0)
+    dm = c.DeviceMesh(mesh)
+    dE = c.bp_energy_change_ex(dm.handle, dev(U), dev(D), alpha, getattr(c, "BP_" + precision))
+    E0 = om.energy(U)
+    ref = om.energy(U + alpha * D) - E0
+    assert abs(dE - ref) <= rtol * abs(ref) + 1e-13 * abs(E0)
+    if precision == "F32":
+        return
+    a = 1e-9  # the first-order prediction alpha R . D at a tiny step, as below
+    d1 = c.bp_energy_change_ex(dm.handle, dev(U), dev(D), a, getattr(c, "BP_" + precision)) / a
+    d2 = c.bp_energy_change_ex(dm.handle, dev(U), dev(D), 2 * a, getattr(c, "BP_" + precision)) / (2 * a)
+    assert 2 * d1 - d2 == pytest.approx(float(om.residual(U) @ D), rel=1e-5)
+
+
+def test_energy_change_ex_refuses_other_kinds():
+    c = capi()
+    dm = c.DeviceMesh(synth.dome_mesh(6, 2, 61, 62))
+    U = torch.zeros(dm.ndof, dtype=torch.float64, device="cuda")
+    for bad in (c.BP_F64X2, c.BP_F32_ALL, c.BP_F32_DS, 99):
+        with pytest.raises(c.BPError):
+            c.bp_energy_change_ex(dm.handle, U, U, 1.0, bad)
+
+
+@pytest.mark.parametrize("alpha", [1.0, 1e-3])
 def test_energy_change_matches_oracle_difference(alpha):
     """Against the oracle's energy difference at steps large enough for that difference to be accurate;
     at a tiny step the GPU's change must agree with the first-order prediction alpha R . D."""
