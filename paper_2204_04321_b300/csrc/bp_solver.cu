@@ -302,20 +302,41 @@ __global__ void __launch_bounds__(128) k_colprec_apply(const Prec<F> P, const V*
 
 // ------------------------------------------------------------------ preconditioned CG (device scalars)
 // scal[3k] = p_k . A p_k, scal[3k+1] = r_k . z_k, scal[3k+2] = r_k . r_k.
+// CG start (FP64 vectors, and layer counts without a register-resident variant), staged like the
+// update below: the block's C consecutive columns are one contiguous range of the dof-ordered
+// vectors, so r = -R and x = 0 run coalesced (r.r summed by every thread), r goes to shared memory,
+// each of the first C threads solves its column there, and z and p = z go back coalesced.
+// Dynamic shared memory: 2 C 2(L+1) values of V.
 template <class V, class F>
-__global__ void __launch_bounds__(NT) k_cg_init(const Prec<F> P, const double* __restrict__ R, V* __restrict__ x,
-                                                V* __restrict__ r, V* __restrict__ z, V* __restrict__ p,
-                                                double* scal) {
-  const int a = blockIdx.x * blockDim.x + threadIdx.x;
-  double rz = 0.0, rr = 0.0;
-  if (a < P.nv) {
-    const int64_t base = 2LL * a * (P.L + 1);
-    for (int i = 0; i < 2 * (P.L + 1); ++i) {
-      r[base + i] = (V)(-R[base + i]);
-      x[base + i] = V(0);
-    }
-    colprec_apply(P, a, r, z, &rz, &rr, base);
-    for (int i = 0; i < 2 * (P.L + 1); ++i) p[base + i] = z[base + i];
+__global__ void __launch_bounds__(UPD_NT) k_cg_init_staged(const Prec<F> P, int C, const double* __restrict__ R,
+                                                           V* __restrict__ x, V* __restrict__ r, V* __restrict__ z,
+                                                           V* __restrict__ p, double* scal) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int n = 2 * (P.L + 1);
+  const int a0 = blockIdx.x * C;
+  const int ncol = min(C, P.nv - a0);
+  const int64_t base = (int64_t)a0 * n;
+  const int cnt = ncol * n;
+  V* sr = reinterpret_cast<V*>(smraw);
+  V* sz = sr + C * n;
+  V rr = V(0);
+  double rz = 0.0;
+  for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+    const V rv = (V)(-R[base + i]);
+    r[base + i] = rv;
+    x[base + i] = V(0);
+    sr[i] = rv;
+    rr += rv * rv;
+  }
+  __syncthreads();
+  if ((int)threadIdx.x < ncol) {
+    double dummy_rr;
+    colprec_apply(P, a0 + (int)threadIdx.x, sr, sz, &rz, &dummy_rr, (int64_t)threadIdx.x * n);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+    z[base + i] = sz[i];
+    p[base + i] = sz[i];
   }
   block_add(rz, scal + 1);
   block_add(rr, scal + 2);
@@ -1336,9 +1357,12 @@ int cg_solve(bp_mesh* m, const M* J, double eta, int maxit, int check_every, boo
   w->hpar[0] = eta * eta;
   w->hpar[1] = (double)maxit;
   BP_CUDA_TRY(cudaMemcpyAsync(w->cgpar, w->hpar, 2 * sizeof(double), cudaMemcpyHostToDevice, s));
-  const int gcol = (m->nv + NT - 1) / NT;
-  if (!init_cols<V>(P, w->R, x, r, z, p, w->scal, m->nl, s))
-    k_cg_init<V, V><<<gcol, NT, 0, s>>>(P, w->R, x, r, z, p, w->scal);
+  if (!init_cols<V>(P, w->R, x, r, z, p, w->scal, m->nl, s)) {
+    const int ncolv = 2 * (m->nl + 1);
+    const int C = std::max(1, std::min(32, (int)((48 << 10) / (2 * ncolv * (int)sizeof(V)))));
+    const size_t smem = 2 * (size_t)C * ncolv * sizeof(V);
+    k_cg_init_staged<V, V><<<(m->nv + C - 1) / C, UPD_NT, smem, s>>>(P, C, w->R, x, r, z, p, w->scal);
+  }
   BP_CUDA_TRY(cudaGetLastError());
   const int batches_per_check = std::max(1, (check_every + CG_BATCH - 1) / CG_BATCH);
   int k = 0, done = 0;
