@@ -186,7 +186,9 @@ int bp_assemble_jacobian(bp_mesh* mesh, const double* U_dev, double* R_dev, void
 
 /* ------------------------------------------------------------------------------------------
  * Solver (Sec. 3.1 Eq. linearsystem, Sec. 3.3 / 4.4).  All vectors are device arrays of ndof
- * doubles in the dof order above.
+ * doubles in the dof order above.  The entry points of this section (and the initial guesses and
+ * energies below) take meshes of at most 64 layers and answer BP_EUNSUP for more; the assembly
+ * has no layer limit.
  * ------------------------------------------------------------------------------------------ */
 
 /*

@@ -5,6 +5,8 @@ column's block-tridiagonal matrix; energy and the shallow-ice guess against the 
 Newton solution against the oracle's Newton solution (the discrete problem has a unique
 minimiser) and, at full size, the final residual recomputed by the oracle.
 """
+import copy
+
 import numpy as np
 import pytest
 import scipy.sparse as sp
@@ -414,3 +416,50 @@ def test_energy_change_with_tail_segments_matches_oracle():
     E0 = om.energy(U)
     ref = om.energy(U + D) - E0
     assert abs(dE - ref) <= 1e-9 * abs(ref) + 1e-13 * abs(E0)
+
+
+def test_layer_count_limits():
+    """64 layers, the solver's largest column: the FP64 and the mixed Newton solves reach the oracle's
+    FP64 residual bar.  65 layers: the assembly still matches the oracle; the solver's entry points
+    answer BP_EUNSUP.
+
+    On wedges this thin (aspect ratio ~1000) the oracle's own FP64 rounding approaches the 1e-12
+    bar: the exact residual does not change when the geometry is translated (bed and surface
+    vertically, or the base mesh horizontally), the oracle's evaluation changes by ~1e-12 normwise
+    (its generic 3 x 3 inverse of each thin wedge's Jacobian).  At shallow-ice velocities the bar is therefore twice that measured change when it
+    exceeds 1e-12; at random velocities it stays 1e-12."""
+    c = capi()
+    mesh = synth.dome_mesh(4, 64, 91, 92, bed="sinusoidal", beta="field")
+    om = oracle.OracleMesh(mesh)
+    dm = c.DeviceMesh(mesh)
+    f0 = np.linalg.norm(om.residual(np.zeros(mesh.ndof)))
+    for prec in (c.BP_F64, c.BP_F32):
+        U = torch.empty(dm.ndof, dtype=torch.float64, device="cuda")
+        c.bp_initial_guess(dm.handle, c.BP_GUESS_SIA, U)
+        rc, rep = c.bp_newton_solve(dm.handle, U, precision=prec, max_krylov=4000)
+        assert rc == c.BP_OK, rep
+        assert np.linalg.norm(om.residual(U.cpu().numpy())) <= 1.1e-8 * f0
+    mesh65 = synth.dome_mesh(4, 65, 93, 94, bed="sinusoidal", beta="field")
+    om65 = oracle.OracleMesh(mesh65)
+    dm65 = c.DeviceMesh(mesh65)
+    U65 = om65.sia()
+    _, _, Jc, Rc = om65.jacobian(U65)
+    J, R = dm65.jacobian(dev(U65))
+    lifted = copy.deepcopy(mesh65)
+    lifted.bed = mesh65.bed + 500.0
+    moved = copy.deepcopy(mesh65)
+    moved.xy = mesh65.xy + np.array([3.7e4, -1.9e4])
+    own = max(rel_inf(oracle.OracleMesh(other).residual(U65), Rc) for other in (lifted, moved))
+    assert rel_inf(R.cpu().numpy(), Rc) <= max(1e-12, 2 * own)
+    assert rel_inf(J.cpu().numpy(), Jc) <= 1e-12
+    Ur = synth.random_velocity(mesh65, 103)
+    _, _, Jr, Rr = om65.jacobian(Ur)
+    J, R = dm65.jacobian(dev(Ur))
+    assert rel_inf(R.cpu().numpy(), Rr) <= 1e-12 and rel_inf(J.cpu().numpy(), Jr) <= 1e-12
+    U = torch.zeros(dm65.ndof, dtype=torch.float64, device="cuda")
+    for call in (lambda: c.bp_initial_guess(dm65.handle, c.BP_GUESS_SIA, U),
+                 lambda: c.bp_newton_solve(dm65.handle, U),
+                 lambda: c.bp_energy(dm65.handle, U)):
+        with pytest.raises(c.BPError) as e:
+            call()
+        assert e.value.status == c.BP_EUNSUP

@@ -633,3 +633,28 @@ def test_threaded_colored_oracle_is_bitwise_independent_of_the_thread_count():
     _, _, v2, R2 = om.jacobian_colored(U, 4)
     _, _, v0, R0 = om.jacobian(U)
     assert np.abs(R2 - R0).max() <= 1e-14 * np.abs(R0).max() and np.abs(v2 - v0).max() <= 1e-14 * np.abs(v0).max()
+
+
+@pytest.mark.parametrize("L", [5, 65])
+def test_residual_and_jacobian_invariant_under_translations(L):
+    """The discrete problem does not change when the whole geometry is moved: a vertical translation
+    of bed and surface (stress-free margins) or a horizontal translation of the base mesh (every field
+    nodal) leaves R and J as they are.  A term that used absolute coordinates where only differences
+    belong (z instead of z - b, x instead of x - x_a) fails this.  The oracle's FP64 evaluation
+    meets the invariance to its rounding, which grows on thin wedges (65 layers: aspect ratio ~1000),
+    so the bar is 5e-13 at 5 layers and 5e-12 at 65 (measured at shallow-ice velocities: 1.2e-13
+    and 1.4e-12; a wrong term moves R by O(1))."""
+    import copy
+    mesh = synth.dome_mesh(4, L, 93, 94, bed="sinusoidal", beta="field")
+    om = oracle.OracleMesh(mesh)
+    bar = 5e-13 if L == 5 else 5e-12
+    for U in (om.sia(), synth.random_velocity(mesh, 103)):
+        _, _, J, R = om.jacobian(U)
+        lifted = copy.deepcopy(mesh)
+        lifted.bed = mesh.bed + 500.0
+        moved = copy.deepcopy(mesh)
+        moved.xy = mesh.xy + np.array([3.7e4, -1.9e4])
+        for other in (lifted, moved):
+            _, _, J2, R2 = oracle.OracleMesh(other).jacobian(U)
+            assert np.abs(R2 - R).max() <= bar * np.abs(R).max()
+            assert np.abs(J2 - J).max() <= bar * np.abs(J).max()
