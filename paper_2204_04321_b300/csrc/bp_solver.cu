@@ -15,7 +15,7 @@
 namespace {
 
 constexpr int MAXL = 64;       // largest layer count the column kernels handle
-constexpr int TPR = 4;         // SpMV threads per row pair (a pair holds 2 x 2 nlev deg ~ 80 entries)
+constexpr int TPR = 4;         // SpMV threads per row pair of FP32 values (grid sizing; spmv_group)
 constexpr int NT = 256;        // threads per block of the vector kernels
 constexpr int SCAL_CAP = 8192; // Krylov iterations per linear solve (scalar history capacity)
 constexpr int GRID_CAP = 148 * 8;  // grid-stride kernels: 8 blocks of NT per SM
@@ -100,7 +100,7 @@ struct Pair<float> {
   using type = float2;
 };
 
-// y = A x on the extruded pattern, one row pair per group of TPR threads.  Rows 2i and 2i + 1 (the u
+// y = A x on the extruded pattern, one row pair per group of G threads (spmv_group).  Rows 2i and 2i + 1 (the u
 // and v rows of node i = (a, l)) are adjacent in the CSR arrays and have the same columns: for each b
 // of the sorted closed neighbourhood of vertex a, levels lmin .. lmin + nlev - 1, components u, v.
 // Column indices are therefore rebuilt from the neighbour list instead of read from colidx (which
@@ -109,6 +109,14 @@ struct Pair<float> {
 // the lower half of the group carries row 2i, the upper half row 2i + 1).  With DOT, x . y is added
 // to *dot (summed in V per thread, in FP64 across threads, one atomic per block; inside the CG
 // batch graph the target is scal[3 (kbase + j)]).  Grid-stride over row pairs.
+// threads per row pair of the SpMV: 4 for FP32 values (HBM-bound: more row pairs in flight per warp
+// would cost registers), 2 for FP64 values (bound by the FP64 pipe, which a group of 4 leaves idle
+// on more lanes in the last steps of short rows: FP64 Krylov phase 25.7 -> 24.5 ms at 1M wedges)
+template <class M>
+__host__ __device__ constexpr int spmv_group() {
+  return std::is_same<M, float>::value ? 4 : 2;
+}
+
 template <class M, class V, bool DOT>
 __global__ void __launch_bounds__(NT) k_spmv_pairs(const int64_t* __restrict__ rowptr,
                                                    const int32_t* __restrict__ nbr_ptr,
@@ -122,13 +130,14 @@ __global__ void __launch_bounds__(NT) k_spmv_pairs(const int64_t* __restrict__ r
   pdl_wait();
   if (stop && *stop) return;
   if (DOT && kbase) dot += 3 * (*kbase + j);  // CG iteration k = kbase + j writes scal[3k]
-  const int lane = threadIdx.x % TPR;
-  const bool upper = lane >= TPR / 2;
+  constexpr int G = spmv_group<M>();  // threads per row pair
+  const int lane = threadIdx.x % G;
+  const bool upper = lane >= G / 2;
   V d = V(0);  // this thread's part of x . y (in V; FP64 only across threads)
   // warp-uniform loop bound: the shuffles below need all 32 lanes of the warp
-  const int stride = gridDim.x * (NT / TPR);
-  for (int base = blockIdx.x * (NT / TPR) + (threadIdx.x / 32) * (32 / TPR); base < npairs; base += stride) {
-    const int pr = base + (threadIdx.x % 32) / TPR;
+  const int stride = gridDim.x * (NT / G);
+  for (int base = blockIdx.x * (NT / G) + (threadIdx.x / 32) * (32 / G); base < npairs; base += stride) {
+    const int pr = base + (threadIdx.x % 32) / G;
     V y0 = V(0), y1 = V(0);
     if (pr < npairs) {
       const int a = pr / (L + 1);
@@ -146,7 +155,7 @@ __global__ void __launch_bounds__(NT) k_spmv_pairs(const int64_t* __restrict__ r
       // costs registers and resident warps: measured on the 1M-wedge Newton solve)
       constexpr int UNR = sizeof(M) == sizeof(double) ? 4 : 2;
 #pragma unroll UNR
-      for (int k = lane; k < half; k += TPR) {
+      for (int k = lane; k < half; k += G) {
         const int sl = nlev == 3 ? k / 3 : k >> 1;
         const int dl = k - sl * nlev;
         const int b = __ldg(nb + sl);
@@ -159,22 +168,22 @@ __global__ void __launch_bounds__(NT) k_spmv_pairs(const int64_t* __restrict__ r
       }
     }
     V keep = upper ? y1 : y0;
-    keep += __shfl_xor_sync(0xffffffffu, upper ? y0 : y1, TPR / 2, TPR);
+    keep += __shfl_xor_sync(0xffffffffu, upper ? y0 : y1, G / 2, G);
 #pragma unroll
-    for (int o = TPR / 4; o; o >>= 1) keep += __shfl_xor_sync(0xffffffffu, keep, o, TPR);
-    if (pr < npairs && (lane == 0 || lane == TPR / 2)) {
+    for (int o = G / 4; o; o >>= 1) keep += __shfl_xor_sync(0xffffffffu, keep, o, G);
+    if (pr < npairs && (lane == 0 || lane == G / 2)) {
       const int64_t row = 2 * (int64_t)pr + (upper ? 1 : 0);
       y[row] = keep;
       if (DOT) d += x[row] * keep;
     }
   }
-  if (DOT) {  // only lanes 0 and TPR / 2 of each group hold a partial: one warp adds them
-    __shared__ double sd[2 * NT / TPR];
-    if (lane == 0 || lane == TPR / 2) sd[2 * (threadIdx.x / TPR) + (upper ? 1 : 0)] = (double)d;
+  if (DOT) {  // only lanes 0 and G / 2 of each group hold a partial: one warp adds them
+    __shared__ double sd[2 * NT / G];
+    if (lane == 0 || lane == G / 2) sd[2 * (threadIdx.x / G) + (upper ? 1 : 0)] = (double)d;
     __syncthreads();
     if (threadIdx.x < 32) {
       double w = 0.0;
-      for (int i = threadIdx.x; i < 2 * NT / TPR; i += 32) w += sd[i];
+      for (int i = threadIdx.x; i < 2 * NT / G; i += 32) w += sd[i];
       w = warp_sum(w);
       if (threadIdx.x == 0) atomicAdd(dot, w);
     }
