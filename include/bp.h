@@ -372,7 +372,9 @@ void bp_solve_opts_default(bp_solve_opts* opts);
  * the Jacobian and residual are assembled (bp_assemble_jacobian; the Picard matrix instead while
  * opts->picard_rtol asks for it), the column preconditioner is factorised, J delta = -F is solved
  * by preconditioned CG to the Eisenstat-Walker tolerance, and the step length alpha is the first
- * trial of opts->line_search with bp_energy_change(U, delta, alpha) <= 1e-4 alpha F . delta
+ * trial of opts->line_search with the energy change (bp_energy_change_ex in the solve's line-search
+ * arithmetic: pairs for BP_F64 and BP_F64X2_DS, FP32 for BP_F32 and BP_F32_DS) at (U, delta, alpha)
+ * <= 1e-4 alpha F . delta
  * (Armijo on the energy; the last trial is taken if none passes).  After a full step that reduced
  * the residual tenfold (the quadratic regime) the next full step is taken without the test.
  * U_dev holds the last iterate on return.
