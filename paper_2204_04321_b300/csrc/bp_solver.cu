@@ -88,6 +88,16 @@ __global__ void k_find_dslot(const int32_t* __restrict__ nbr_ptr, const int32_t*
 // would otherwise be free to promote to FP64)
 __device__ __forceinline__ float vfma(const float a, const float b, const float c) { return fmaf(a, b, c); }
 __device__ __forceinline__ double vfma(const double a, const double b, const double c) { return fma(a, b, c); }
+// a matrix value in the vector type: FP32 values widen on the integer pipe (f64_of) when the
+// vectors are FP64, so that the FP64 pipe does only the products
+template <class V, class M>
+__device__ __forceinline__ V mat_v(const M x) {
+  if constexpr (std::is_same<V, double>::value && std::is_same<M, float>::value) {
+    return f64_of(x);
+  } else {
+    return (V)x;
+  }
+}
 
 template <class T>
 struct Pair;
@@ -163,8 +173,8 @@ __global__ void __launch_bounds__(NT) k_spmv_pairs(const int64_t* __restrict__ r
         const M2 a0 = v0[k], a1 = v1[k];
         // chained FMAs: one FMA per matrix entry (a sum of two products first would cost a
         // multiply, an FMA and an add per pair, 1.5 instructions per entry on the FP64 pipe)
-        y0 = vfma((V)a0.y, xx.y, vfma((V)a0.x, xx.x, y0));
-        y1 = vfma((V)a1.y, xx.y, vfma((V)a1.x, xx.x, y1));
+        y0 = vfma(mat_v<V>(a0.y), xx.y, vfma(mat_v<V>(a0.x), xx.x, y0));
+        y1 = vfma(mat_v<V>(a1.y), xx.y, vfma(mat_v<V>(a1.x), xx.x, y1));
       }
     }
     V keep = upper ? y1 : y0;
