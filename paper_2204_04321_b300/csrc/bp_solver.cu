@@ -187,7 +187,7 @@ __global__ void __launch_bounds__(NT) k_spmv_pairs(const int64_t* __restrict__ r
       if (DOT) d += x[row] * keep;
     }
   }
-  if (DOT) {  // only lanes 0 and G / 2 of each group hold a partial: one warp adds them
+  if (DOT && dot) {  // only lanes 0 and G / 2 of each group hold a partial: one warp adds them
     __shared__ double sd[2 * NT / G];
     if (lane == 0 || lane == G / 2) sd[2 * (threadIdx.x / G) + (upper ? 1 : 0)] = (double)d;
     __syncthreads();
@@ -2765,9 +2765,9 @@ extern "C" int bp_spmv(bp_mesh* m, const void* J, int precision, const double* x
   const int grid = grid_for(m->ndof / 2 * TPR, NT);
   const int npairs = (int)(m->ndof / 2);
   if (!bp_values_f32(precision))
-    k_spmv_pairs<double, double, false><<<grid, NT, 0, s>>>(m->rowptr, m->nbr_ptr, m->nbr_idx, m->nl,
-                                                            (const double*)J, npairs, x, y, nullptr, nullptr,
-                                                            nullptr, 0);
+    k_spmv_pairs<double, double, true><<<grid, NT, 0, s>>>(m->rowptr, m->nbr_ptr, m->nbr_idx, m->nl,
+                                                           (const double*)J, npairs, x, y, nullptr, nullptr,
+                                                           nullptr, 0);
   else
     k_spmv_pairs<float, double, false><<<grid, NT, 0, s>>>(m->rowptr, m->nbr_ptr, m->nbr_idx, m->nl,
                                                            (const float*)J, npairs, x, y, nullptr, nullptr,
