@@ -126,9 +126,17 @@ template <class M>
 __host__ __device__ constexpr int spmv_group() {
   return std::is_same<M, float>::value ? 4 : 2;
 }
+// resident blocks of NT threads asked of the register allocator: the FP32 product is bound by memory
+// latency and needs every warp slot (32 registers: 8 blocks per SM; at 40 registers, 6 blocks, the
+// mixed-precision Krylov phase took 12.3 instead of 10.3 ms); the FP64-vector products take up to
+// 64 registers (4 blocks) and spill below 48
+template <class M, class V>
+__host__ __device__ constexpr int spmv_min_blocks() {
+  return std::is_same<V, float>::value ? 8 : 4;
+}
 
 template <class M, class V, bool DOT>
-__global__ void __launch_bounds__(NT) k_spmv_pairs(const int64_t* __restrict__ rowptr,
+__global__ void __launch_bounds__(NT, spmv_min_blocks<M, V>()) k_spmv_pairs(const int64_t* __restrict__ rowptr,
                                                    const int32_t* __restrict__ nbr_ptr,
                                                    const int32_t* __restrict__ nbr_idx, int L,
                                                    const M* __restrict__ vals, int npairs, const V* __restrict__ x,
@@ -146,17 +154,34 @@ __global__ void __launch_bounds__(NT) k_spmv_pairs(const int64_t* __restrict__ r
   V d = V(0);  // this thread's part of x . y (in V; FP64 only across threads)
   // warp-uniform loop bound: the shuffles below need all 32 lanes of the warp
   const int stride = gridDim.x * (NT / G);
+  // the row pair's header (first entry, row length, neighbourhood start) is loaded one grid-stride
+  // step ahead, so that its loads are in flight while the previous row pair is summed
+  const int first = blockIdx.x * (NT / G) + (threadIdx.x / 32) * (32 / G) + (threadIdx.x % 32) / G;
+  int64_t h_s0 = 0, h_s1 = 0;
+  int h_nb = 0;
+  if (first < npairs) {
+    h_s0 = rowptr[2 * (int64_t)first];
+    h_s1 = rowptr[2 * (int64_t)first + 1];
+    h_nb = nbr_ptr[first / (L + 1)];
+  }
   for (int base = blockIdx.x * (NT / G) + (threadIdx.x / 32) * (32 / G); base < npairs; base += stride) {
     const int pr = base + (threadIdx.x % 32) / G;
+    const int64_t s0 = h_s0;
+    const int half = (int)((h_s1 - s0) >> 1);  // column pairs per row = deg nlev
+    const int nbp = h_nb;
+    const int prn = pr + stride;
+    if (prn < npairs) {
+      h_s0 = rowptr[2 * (int64_t)prn];
+      h_s1 = rowptr[2 * (int64_t)prn + 1];
+      h_nb = nbr_ptr[prn / (L + 1)];
+    }
     V y0 = V(0), y1 = V(0);
     if (pr < npairs) {
       const int a = pr / (L + 1);
       const int l = pr - a * (L + 1);
       const int nlev = bp_nlev(l, L);
       const int lmin = l > 0 ? l - 1 : 0;
-      const int64_t s0 = rowptr[2 * (int64_t)pr];
-      const int half = (int)((rowptr[2 * (int64_t)pr + 1] - s0) >> 1);  // column pairs per row = deg nlev
-      const int32_t* nb = nbr_idx + nbr_ptr[a];
+      const int32_t* nb = nbr_idx + nbp;
       const M2* v0 = reinterpret_cast<const M2*>(vals + s0);
       const M2* v1 = v0 + half;
       // k = sl nlev + dl formed afresh in every step (nlev is 2 or 3: a shift or a multiply-high),
