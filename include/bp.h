@@ -201,6 +201,15 @@ int bp_spmv(bp_mesh* mesh, const void* J_vals_dev, int precision, const double* 
             void* stream);
 
 /*
+ * y = J x with FP32 values, FP32 vectors and FP32 products and sums: the product of the mixed-
+ * precision Krylov solves and MDSC cycles (the same kernel they run).  J (float values on the
+ * bp_csr_pattern pattern), x and y (ndof floats each, dof order) are caller-owned device arrays,
+ * 16-byte aligned.  Asynchronous.  Errors: BP_EINVAL (NULL or misaligned), BP_EUNSUP (more than 64
+ * layers), BP_ECUDA.
+ */
+int bp_spmv_f32(bp_mesh* mesh, const float* J_vals_dev, const float* x_dev, float* y_dev, void* stream);
+
+/*
  * Vertical-line preconditioner: for every base vertex, the block-tridiagonal part of J that
  * couples the (L + 1) levels of its column (2 x 2 blocks) is factorised by block Thomas elimination
  * without pivoting (J is symmetric positive definite), one thread per column -- the per-vertical-line

@@ -94,6 +94,7 @@ SIGNATURES = {
     "bp_assemble_jacobian": (_I, [_P, _P, _P, _P, _I, _I, _I, _P]),
     "bp_assemble_jacobian_noalloc": (_I, [_P, _P, _P, _I, _I, _I, _P]),
     "bp_spmv": (_I, [_P, _P, _I, _P, _P, _P]),
+    "bp_spmv_f32": (_I, [_P, _P, _P, _P, _P]),
     "bp_colprec_setup": (_I, [_P, _P, _I, _P]),
     "bp_colprec_apply": (_I, [_P, _P, _P, _P]),
     "bp_mdsc_setup": (_I, [_P, _P, _I, _P]),
@@ -238,6 +239,10 @@ def bp_assemble_jacobian_noalloc(handle, U, J, precision=BP_F64, scatter=BP_SCAT
 
 def bp_spmv(handle, J, x, y, precision=BP_F64, stream=None) -> None:
     _check(lib().bp_spmv(handle, _dptr(J), precision, _dptr(x), _dptr(y), _stream_ptr(stream)), "bp_spmv")
+
+
+def bp_spmv_f32(handle, J, x, y, stream=None) -> None:
+    _check(lib().bp_spmv_f32(handle, _dptr(J), _dptr(x), _dptr(y), _stream_ptr(stream)), "bp_spmv_f32")
 
 
 def bp_colprec_setup(handle, J, precision=BP_F64, stream=None) -> None:

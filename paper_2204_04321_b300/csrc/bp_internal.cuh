@@ -38,7 +38,8 @@ struct bp_solver_ws {
   double* Ut = nullptr;       // [ndof] trial iterate of the line search
   double* scal = nullptr;     // [3 (cap + 2)] per Krylov iteration: p.q, r.z, r.r
   int scal_cap = 0;
-  int* stop = nullptr;        // Krylov stop flag (1 converged, 2 breakdown)
+  int* stop = nullptr;        // Krylov stop flag (1 converged, 2 breakdown, 3 not finite, 4 limit,
+                              // 5 a bounded wait for bulk copies gave up)
   double* red = nullptr;      // [8] reduction scalars
   double* sia = nullptr;      // [3 nv] shallow-ice scratch
   double* host = nullptr;     // pinned host mirror of scal / red

@@ -31,6 +31,40 @@ constexpr int GMRES_MAX_RESTART = 64;  // largest GMRES restart length
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
+// Bulk asynchronous copies (the non-tensor TMA form): one thread moves a contiguous global range into
+// shared memory and the copy signals an mbarrier with its byte count.  Both addresses and the size
+// must be multiples of 16 bytes.  Waits are bounded: after BULK_WAIT_SPINS polls the caller gets
+// false and flags an error instead of hanging.
+constexpr int BULK_WAIT_SPINS = 1 << 22;
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase) {
+  for (int it = 0; it < BULK_WAIT_SPINS; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(phase)
+        : "memory");
+    if (done) return true;
+    if (it > 16) __nanosleep(32);
+  }
+  return false;
+}
+
 // B300 issues FP64 at ~1/64 of the FP32 rate, so the vector kernels keep per-element reductions in
 // the vector type V and spend FP64 operations only on per-warp / per-block partial sums.
 template <class T>
@@ -503,19 +537,34 @@ struct ColFactors {
 };
 
 // CG step: alpha = r.z / p.Ap, x += alpha p, r -= alpha q, z = P^-1 r, and r.z, r.r of step k + 1.
+// The warp's slices of x, r, p and q (32 columns: one contiguous range of each vector) arrive in
+// shared memory by four bulk copies on one mbarrier, so that the element-wise step reads no global
+// memory (as plain loads its 2 (L + 1) coalesced steps were one dependent round trip each); a slice
+// whose length is not a multiple of 16 bytes (the last warp, odd column count) takes its last
+// values by plain loads.  The factors go to registers before the wait on the previous kernel.
 template <int NLEV>
 __global__ void __launch_bounds__(UPD_NT) k_cg_update_cols(const Prec<float> P, const int* kbase, int j,
                                                            float* __restrict__ x, float* __restrict__ r,
                                                            float* __restrict__ z, const float* __restrict__ p,
                                                            const float* __restrict__ q, double* scal, int* stop) {
-  constexpr int N = 2 * NLEV;     // values per column
-  constexpr int SN = N | 1;       // shared-memory stride per column
-  __shared__ float sbuf[UPD_NT / 32][32 * SN];
+  constexpr int N = 2 * NLEV;  // values per column
+  constexpr int W = 32 * N;    // values per warp slice
+  __shared__ __align__(16) float sbuf[UPD_NT / 32][4][W];  // x, r (then z), p, q
+  __shared__ uint64_t sbar[UPD_NT / 32];
   __shared__ float s_alpha;
   __shared__ int s_bad;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int a0 = (blockIdx.x * (UPD_NT / 32) + warp) * 32;
   const bool own = a0 + lane < P.nv;
+  const int ncol = min(32, P.nv - a0);  // <= 0 for a warp past the last column
+  const int cnt = max(ncol, 0) * N;
+  const int cnt16 = cnt & ~3;           // values moved by the bulk copies (whole 16-byte units)
+  const int64_t base = (int64_t)max(a0, 0) * N;
+  float* sx = sbuf[warp][0];
+  float* sr = sbuf[warp][1];
+  float* sp = sbuf[warp][2];
+  float* sq = sbuf[warp][3];
+  if (lane == 0 && cnt16 > 0) mbar_init(&sbar[warp]);
   pdl_trigger();
   ColFactors<NLEV> f;  // the factors do not depend on the previous kernels: load them before waiting
   if (own) f.load(P, a0 + lane);
@@ -531,60 +580,110 @@ __global__ void __launch_bounds__(UPD_NT) k_cg_update_cols(const Prec<float> P, 
   __syncthreads();
   if (s_bad) return;
   const float alpha = s_alpha;
-  float* sr = sbuf[warp];
-  const int ncol = min(32, P.nv - a0);  // <= 0 for a warp past the last column
-  const int64_t base = (int64_t)a0 * N;
-  float rr = 0.f;
-  for (int i = lane; i < ncol * N; i += 32) {
-    const float xv = x[base + i] + alpha * p[base + i];
-    const float rv = r[base + i] - alpha * q[base + i];
-    x[base + i] = xv;
-    r[base + i] = rv;
-    sr[(i / N) * SN + i % N] = rv;
-    rr += rv * rv;
+  bool ok = true;
+  if (cnt16 > 0) {
+    if (lane == 0) {
+      const uint32_t bytes = (uint32_t)cnt16 * 4u;
+      mbar_expect(&sbar[warp], 4u * bytes);
+      bulk_load(sx, x + base, bytes, &sbar[warp]);
+      bulk_load(sr, r + base, bytes, &sbar[warp]);
+      bulk_load(sp, p + base, bytes, &sbar[warp]);
+      bulk_load(sq, q + base, bytes, &sbar[warp]);
+    }
+    for (int i = cnt16 + lane; i < cnt; i += 32) {
+      sx[i] = x[base + i];
+      sr[i] = r[base + i];
+      sp[i] = p[base + i];
+      sq[i] = q[base + i];
+    }
+    ok = mbar_wait(&sbar[warp], 0);
+    if (!__all_sync(0xffffffffu, ok)) {  // the copies did not complete in time: flag, drain, skip
+      if (lane == 0) *stop = 5;
+      mbar_wait(&sbar[warp], 0);
+      ok = false;
+    }
   }
   __syncwarp();
+  float rr = 0.f;
   double rz = 0.0;
-  if (own) rz = (double)f.solve(sr + lane * SN);
-  __syncwarp();
-  for (int i = lane; i < ncol * N; i += 32) z[base + i] = sr[(i / N) * SN + i % N];
+  if (ok) {
+    for (int i = lane; i < cnt; i += 32) {
+      const float xv = sx[i] + alpha * sp[i];
+      const float rv = sr[i] - alpha * sq[i];
+      x[base + i] = xv;
+      r[base + i] = rv;
+      sr[i] = rv;
+      rr += rv * rv;
+    }
+    __syncwarp();
+    if (own) rz = (double)f.solve(sr + lane * N);
+    __syncwarp();
+    for (int i = lane; i < cnt; i += 32) z[base + i] = sr[i];
+  }
   block_add(rz, scal + 3 * (k + 1) + 1);
   block_add(rr, scal + 3 * (k + 1) + 2);
 }
 
-// CG start: x = 0, r = -R, z = P^-1 r, p = z, and r.z, r.r of step 0.
+// CG start: x = 0, r = -R, z = P^-1 r, p = z, and r.z, r.r of step 0.  The warp's slice of R comes
+// to shared memory by one bulk copy (its odd tail, if any, by plain loads), as in the update.
 template <int NLEV>
 __global__ void __launch_bounds__(UPD_NT) k_cg_init_cols(const Prec<float> P, const double* __restrict__ R,
                                                          float* __restrict__ x, float* __restrict__ r,
                                                          float* __restrict__ z, float* __restrict__ p,
-                                                         double* scal) {
+                                                         double* scal, int* stop) {
   constexpr int N = 2 * NLEV;
-  constexpr int SN = N | 1;
-  __shared__ float sbuf[UPD_NT / 32][32 * SN];
+  constexpr int W = 32 * N;
+  __shared__ __align__(16) double sR[UPD_NT / 32][W];
+  __shared__ __align__(16) float sbuf[UPD_NT / 32][W];
+  __shared__ uint64_t sbar[UPD_NT / 32];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int a0 = (blockIdx.x * (UPD_NT / 32) + warp) * 32;
   const bool own = a0 + lane < P.nv;
+  const int ncol = min(32, P.nv - a0);
+  const int cnt = max(ncol, 0) * N;
+  const int cnt16 = cnt & ~1;  // FP64 values moved by the bulk copy (whole 16-byte units)
+  const int64_t base = (int64_t)max(a0, 0) * N;
+  double* sd = sR[warp];
+  float* sr = sbuf[warp];
+  bool ok = true;
+  if (cnt16 > 0) {
+    if (lane == 0) {
+      mbar_init(&sbar[warp]);
+      mbar_expect(&sbar[warp], (uint32_t)cnt16 * 8u);
+      bulk_load(sd, R + base, (uint32_t)cnt16 * 8u, &sbar[warp]);
+    }
+    for (int i = cnt16 + lane; i < cnt; i += 32) sd[i] = R[base + i];
+  }
   ColFactors<NLEV> f;
   if (own) f.load(P, a0 + lane);
-  float* sr = sbuf[warp];
-  const int ncol = min(32, P.nv - a0);
-  const int64_t base = (int64_t)a0 * N;
-  float rr = 0.f;
-  for (int i = lane; i < ncol * N; i += 32) {
-    const float rv = -f32_of(R[base + i]);
-    x[base + i] = 0.f;
-    r[base + i] = rv;
-    sr[(i / N) * SN + i % N] = rv;
-    rr += rv * rv;
+  if (cnt16 > 0) {
+    __syncwarp();  // the barrier's initialisation before the other lanes poll it
+    ok = mbar_wait(&sbar[warp], 0);
+    if (!__all_sync(0xffffffffu, ok)) {
+      if (lane == 0) *stop = 5;
+      mbar_wait(&sbar[warp], 0);
+      ok = false;
+    }
   }
   __syncwarp();
+  float rr = 0.f;
   double rz = 0.0;
-  if (own) rz = (double)f.solve(sr + lane * SN);
-  __syncwarp();
-  for (int i = lane; i < ncol * N; i += 32) {
-    const float zv = sr[(i / N) * SN + i % N];
-    z[base + i] = zv;
-    p[base + i] = zv;
+  if (ok) {
+    for (int i = lane; i < cnt; i += 32) {
+      const float rv = -f32_of(sd[i]);
+      x[base + i] = 0.f;
+      r[base + i] = rv;
+      sr[i] = rv;
+      rr += rv * rv;
+    }
+    __syncwarp();
+    if (own) rz = (double)f.solve(sr + lane * N);
+    __syncwarp();
+    for (int i = lane; i < cnt; i += 32) {
+      const float zv = sr[i];
+      z[base + i] = zv;
+      p[base + i] = zv;
+    }
   }
   block_add(rz, scal + 1);
   block_add(rr, scal + 2);
@@ -1213,17 +1312,33 @@ void launch_pdl(void (*kern)(Args...), int grid, int block, size_t smem, cudaStr
   cudaLaunchKernelEx(&cfg, kern, args...);
 }
 
+// y = J x (with DOT: x . y added to dot[3 (kbase + j)], or to *dot without kbase), optionally as a
+// programmatic dependent launch.
+template <class M, class V, bool DOT>
+void spmv_launch(bp_mesh* m, const M* J, const V* x, V* y, double* dot, const int* stop, const int* kbase, int j,
+                 cudaStream_t s, bool pdl = false) {
+  const int npairs = (int)(m->ndof / 2);
+  const int grid = grid_for((int64_t)npairs * TPR, NT);
+  if (pdl)
+    launch_pdl(k_spmv_pairs<M, V, DOT>, grid, NT, 0, s, (const int64_t*)m->rowptr, (const int32_t*)m->nbr_ptr,
+               (const int32_t*)m->nbr_idx, m->nl, J, npairs, x, y, dot, stop, kbase, j);
+  else
+    k_spmv_pairs<M, V, DOT><<<grid, NT, 0, s>>>(m->rowptr, m->nbr_ptr, m->nbr_idx, m->nl, J, npairs, x, y, dot, stop,
+                                                kbase, j);
+}
+
 // FP32 CG with 5 or 10 layers: the register-resident start and update; false where they do not apply.
 template <class V>
-bool init_cols(const Prec<V>& P, const double* R, V* x, V* r, V* z, V* p, double* scal, int L, cudaStream_t s) {
+bool init_cols(const Prec<V>& P, const double* R, V* x, V* r, V* z, V* p, double* scal, int* stop, int L,
+               cudaStream_t s) {
   if constexpr (std::is_same<V, float>::value) {
     const int grid = (P.nv + UPD_NT - 1) / UPD_NT;
     if (L == 10) {
-      k_cg_init_cols<11><<<grid, UPD_NT, 0, s>>>(P, R, x, r, z, p, scal);
+      k_cg_init_cols<11><<<grid, UPD_NT, 0, s>>>(P, R, x, r, z, p, scal, stop);
       return true;
     }
     if (L == 5) {
-      k_cg_init_cols<6><<<grid, UPD_NT, 0, s>>>(P, R, x, r, z, p, scal);
+      k_cg_init_cols<6><<<grid, UPD_NT, 0, s>>>(P, R, x, r, z, p, scal, stop);
       return true;
     }
   }
@@ -1257,14 +1372,12 @@ void launch_cg_batch(bp_mesh* m, const M* J, cudaStream_t s) {
   V* z = reinterpret_cast<V*>(w->z);
   V* p = reinterpret_cast<V*>(w->p);
   V* q = reinterpret_cast<V*>(w->q);
-  const int gspmv = grid_for(n / 2 * TPR, NT);
   const int ncolv = 2 * (m->nl + 1);
   const int C = std::max(1, std::min(32, (int)((48 << 10) / (2 * ncolv * (int)sizeof(V)))));
   const size_t smem = 2 * (size_t)C * ncolv * sizeof(V);
   const int gupd = (m->nv + C - 1) / C;
   for (int j = 0; j < CG_BATCH; ++j) {
-    k_spmv_pairs<M, V, true><<<gspmv, NT, 0, s>>>(m->rowptr, m->nbr_ptr, m->nbr_idx, m->nl, J, (int)(n / 2), p, q,
-                                                  w->scal, w->stop, w->kbase, j);
+    spmv_launch<M, V, true>(m, J, p, q, w->scal, w->stop, w->kbase, j, s);
     if (!update_cols<V>(P, w, j, x, r, z, p, q, m->nl, s))
       k_cg_update_staged<V, V><<<gupd, UPD_NT, smem, s>>>(P, w->kbase, j, C, x, r, z, p, q, w->scal, w->stop);
     k_cg_direction<V><<<grid_for(n / 2, NT), NT, 0, s>>>(w->kbase, j, w->cgpar, n / 2, z, p, w->scal, w->stop,
@@ -1286,14 +1399,12 @@ void launch_cg_iteration(bp_mesh* m, const M* J, cudaStream_t s, cudaGraphCondit
   V* z = reinterpret_cast<V*>(w->z);
   V* p = reinterpret_cast<V*>(w->p);
   V* q = reinterpret_cast<V*>(w->q);
-  const int gspmv = grid_for(n / 2 * TPR, NT);
   const int ncolv = 2 * (m->nl + 1);
   const int C = std::max(1, std::min(32, (int)((48 << 10) / (2 * ncolv * (int)sizeof(V)))));
   const size_t smem = 2 * (size_t)C * ncolv * sizeof(V);
   const int gupd = (m->nv + C - 1) / C;
   for (int j = 0; j < LOOP_BODY; ++j) {
-    launch_pdl(k_spmv_pairs<M, V, true>, gspmv, NT, 0, s, m->rowptr, m->nbr_ptr, m->nbr_idx, m->nl, J, (int)(n / 2),
-               (const V*)p, q, w->scal, (const int*)w->stop, (const int*)w->kbase, j);
+    spmv_launch<M, V, true>(m, J, p, q, w->scal, w->stop, w->kbase, j, s, true);
     if (!update_cols<V>(P, w, j, x, r, z, p, q, m->nl, s, true))
       launch_pdl(k_cg_update_staged<V, V>, gupd, UPD_NT, smem, s, P, (const int*)w->kbase, j, C, x, r, z, (const V*)p,
                  (const V*)q, w->scal, w->stop);
@@ -1380,6 +1491,12 @@ int cg_batch_graph(bp_mesh* m, const M* J, cudaGraphExec_t* out) {
 // Preconditioned CG on J delta = -R to ||r|| <= eta ||R||.  delta is left in ws->x (type V).
 // The iterations run as replays of the captured batch graph; the host reads the device stop flag
 // every check_every iterations (rounded up to whole batches).
+// stop flag 5: a kernel's bounded wait for its bulk copies gave up (reported as a CUDA failure)
+int bulk_wait_failed(int line) {
+  bp_set_last_cuda_error(cudaErrorTimeout, "bulk copy wait in the CG column kernels", line);
+  return BP_ECUDA;
+}
+
 template <class M, class V>
 int cg_solve(bp_mesh* m, const M* J, double eta, int maxit, int check_every, bool device_loop, cudaStream_t s,
              int* iters, int* status) {
@@ -1401,7 +1518,7 @@ int cg_solve(bp_mesh* m, const M* J, double eta, int maxit, int check_every, boo
   w->hpar[0] = eta * eta;
   w->hpar[1] = (double)maxit;
   BP_CUDA_TRY(cudaMemcpyAsync(w->cgpar, w->hpar, 2 * sizeof(double), cudaMemcpyHostToDevice, s));
-  if (!init_cols<V>(P, w->R, x, r, z, p, w->scal, m->nl, s)) {
+  if (!init_cols<V>(P, w->R, x, r, z, p, w->scal, w->stop, m->nl, s)) {
     const int ncolv = 2 * (m->nl + 1);
     const int C = std::max(1, std::min(32, (int)((48 << 10) / (2 * ncolv * (int)sizeof(V)))));
     const size_t smem = 2 * (size_t)C * ncolv * sizeof(V);
@@ -1423,6 +1540,7 @@ int cg_solve(bp_mesh* m, const M* J, double eta, int maxit, int check_every, boo
     int stopflag;
     std::memcpy(&stopflag, w->host + w->host_cap - 1, sizeof(int));
     if (stopflag == 2) *status = 2;
+    if (stopflag == 5) return bulk_wait_failed(__LINE__);
     done = 1;
   }
   while (!done) {
@@ -1435,6 +1553,7 @@ int cg_solve(bp_mesh* m, const M* J, double eta, int maxit, int check_every, boo
     std::memcpy(&stopflag, w->host + w->host_cap - 1, sizeof(int));
     if (stopflag || k >= maxit) done = 1;
     if (stopflag == 2) *status = 2;
+    if (stopflag == 5) return bulk_wait_failed(__LINE__);
     if (done) k = kk;
   }
   // iterations actually taken: first j with r_j.r_j <= eta^2 r_0.r_0
@@ -1545,7 +1664,7 @@ int gmres_solve(bp_mesh* m, const M* J, double eta, int maxit, int restart, cuda
   V* u = reinterpret_cast<V*>(w->p);
   double* hd = w->gm_h;                 // device: h column (first half), combination coefficients (second)
   double* hh = w->host;                 // pinned host mirror
-  const int gvec = grid_for(n, NT), gcol = (m->nv + 127) / 128, gspmv = grid_for(n / 2 * TPR, NT);
+  const int gvec = grid_for(n, NT), gcol = (m->nv + 127) / 128;
   *status = 0;
   BP_CUDA_TRY(cudaMemsetAsync(x, 0, n * sizeof(V), s));
   double bnorm;
@@ -1567,8 +1686,7 @@ int gmres_solve(bp_mesh* m, const M* J, double eta, int maxit, int restart, cuda
   while (total < maxit && res > target) {
     // v_0 = r / ||r||
     if (total > 0) {
-      k_spmv_pairs<M, V, false><<<gspmv, NT, 0, s>>>(m->rowptr, m->nbr_ptr, m->nbr_idx, m->nl, J, (int)(n / 2), x,
-                                                     z, nullptr, nullptr, nullptr, 0);
+      spmv_launch<M, V, false>(m, J, x, z, nullptr, nullptr, nullptr, 0, s);
       k_gm_residual<V><<<gvec, NT, 0, s>>>(w->R, z, n, wv);
     }
     double beta;
@@ -1587,8 +1705,7 @@ int gmres_solve(bp_mesh* m, const M* J, double eta, int maxit, int restart, cuda
     for (; k < restart && total < maxit; ++k, ++total) {
       // w = J M^-1 v_k
       k_colprec_apply<V, V><<<gcol, 128, 0, s>>>(P, basis + (int64_t)k * n, z);
-      k_spmv_pairs<M, V, false><<<gspmv, NT, 0, s>>>(m->rowptr, m->nbr_ptr, m->nbr_idx, m->nl, J, (int)(n / 2), z,
-                                                     wv, nullptr, nullptr, nullptr, 0);
+      spmv_launch<M, V, false>(m, J, z, wv, nullptr, nullptr, nullptr, 0, s);
       // classical Gram-Schmidt, twice
       for (int i = 0; i <= k; ++i) Hat(i, k) = 0.0;
       for (int pass = 0; pass < 2; ++pass) {
@@ -2501,13 +2618,12 @@ void mdsc_apply_launch(bp_mesh* m, const M* J, const V* r, V* z, cudaStream_t s)
   V* sb = reinterpret_cast<V*>(w->ms);
   const int64_t n = m->ndof;
   const int gcol = (m->nv + 127) / 128, gv = (m->nv + NT - 1) / NT;
-  const int gspmv = grid_for(n / 2 * TPR, NT), gvec = grid_for(n, NT);
+  const int gvec = grid_for(n, NT);
   const F omega = (F)MDSC_OMEGA;
   // z1 = S r
   mdsc_smooth<V, F>(Pr, r, sb, nullptr, z1, omega, s);
   // rc = P^T (r - J z1)
-  k_spmv_pairs<M, V, false><<<gspmv, NT, 0, s>>>(m->rowptr, m->nbr_ptr, m->nbr_idx, m->nl, J, (int)(n / 2), z1, t,
-                                                 nullptr, nullptr, nullptr, 0);
+  spmv_launch<M, V, false>(m, J, z1, t, nullptr, nullptr, nullptr, 0, s);
   k_mdsc_sub<V><<<gvec, NT, 0, s>>>(r, t, n);
   k_mdsc_restrict<V, F><<<gcol, 128, 0, s>>>(P, t, rc, m->nv, m->nl);
   // ec = B_c rc: the Chebyshev plane iteration, or one SA-AMG V-cycle (level 0 reads rc, writes ec)
@@ -2521,8 +2637,7 @@ void mdsc_apply_launch(bp_mesh* m, const M* J, const V* r, V* z, cudaStream_t s)
   }
   // z2 = z1 + P ec (in z1);  z = z2 + S (r - J z2)
   k_mdsc_prolong_add<V, F><<<gcol, 128, 0, s>>>(P, ec, z1, m->nv, m->nl);
-  k_spmv_pairs<M, V, false><<<gspmv, NT, 0, s>>>(m->rowptr, m->nbr_ptr, m->nbr_idx, m->nl, J, (int)(n / 2), z1, t,
-                                                 nullptr, nullptr, nullptr, 0);
+  spmv_launch<M, V, false>(m, J, z1, t, nullptr, nullptr, nullptr, 0, s);
   k_mdsc_sub<V><<<gvec, NT, 0, s>>>(r, t, n);
   mdsc_smooth<V, F>(Pr, t, sb, z1, z, omega, s);
 }
@@ -2591,9 +2706,8 @@ void launch_mdsc_iteration(bp_mesh* m, const M* J, cudaStream_t s, cudaGraphCond
   V* z = reinterpret_cast<V*>(w->z);
   V* p = reinterpret_cast<V*>(w->p);
   V* q = reinterpret_cast<V*>(w->q);
-  const int gspmv = grid_for(n / 2 * TPR, NT), gvec = grid_for(n, NT);
-  k_spmv_pairs<M, V, true><<<gspmv, NT, 0, s>>>(m->rowptr, m->nbr_ptr, m->nbr_idx, m->nl, J, (int)(n / 2), p, q,
-                                                w->scal, w->stop, w->kbase, 0);
+  const int gvec = grid_for(n, NT);
+  spmv_launch<M, V, true>(m, J, p, q, w->scal, w->stop, w->kbase, 0, s);
   k_pcg_update<V><<<gvec, NT, 0, s>>>(w->kbase, 0, x, r, p, q, n, w->scal, w->stop);
   mdsc_apply_launch<M, V, V, AMG>(m, J, r, z, s);
   k_pcg_rz<V><<<gvec, NT, 0, s>>>(w->kbase, 0, 1, r, z, n, w->scal, w->stop);
@@ -2797,6 +2911,15 @@ extern "C" int bp_spmv(bp_mesh* m, const void* J, int precision, const double* x
     k_spmv_pairs<float, double, false><<<grid, NT, 0, s>>>(m->rowptr, m->nbr_ptr, m->nbr_idx, m->nl,
                                                            (const float*)J, npairs, x, y, nullptr, nullptr,
                                                            nullptr, 0);
+  BP_CUDA_TRY(cudaGetLastError());
+  return BP_OK;
+}
+
+extern "C" int bp_spmv_f32(bp_mesh* m, const float* J, const float* x, float* y, void* stream) {
+  if (!m || !J || !x || !y || !bp_aligned16(x) || !bp_aligned16(y) || !bp_aligned16(J)) return BP_EINVAL;
+  if (m->nl > MAXL) return BP_EUNSUP;
+  bp_device_guard g(m->device);
+  spmv_launch<float, float, false>(m, J, x, y, nullptr, nullptr, nullptr, 0, (cudaStream_t)stream);
   BP_CUDA_TRY(cudaGetLastError());
   return BP_OK;
 }

@@ -59,6 +59,27 @@ def test_spmv_matches_scipy(precision):
     assert rel_inf(y.cpu().numpy(), A @ x) <= 1e-13
 
 
+@pytest.mark.parametrize("size", ["small", "dome_1m"])
+def test_fp32_spmv_within_fp32_dot_product_bound(size):
+    """The mixed-precision Krylov product (FP32 values, vectors, products and sums; grid-stride
+    over row pairs, several per group on the 1M-wedge dome) against scipy's FP64 product of the
+    same FP32 data: every row within the error bound of an FP32 dot product,
+    (n + 2) u sum_j |a_ij x_j| (n the row length, u = 2^-24)."""
+    c = capi()
+    mesh = synth.dome_mesh(23, 4, 31, 32, bed="sinusoidal") if size == "small" else synth.config_medium()
+    dm = c.DeviceMesh(mesh)
+    U = dev(synth.random_velocity(mesh, 3))
+    J, _ = dm.jacobian(U, precision=1)
+    x = torch.from_numpy(np.random.default_rng(1).normal(size=dm.ndof).astype(np.float32)).cuda()
+    y = torch.full((dm.ndof,), float("nan"), dtype=torch.float32, device="cuda")
+    c.bp_spmv_f32(dm.handle, J, x, y)
+    A = _host_csr(dm, J)
+    xs = x.cpu().numpy().astype(np.float64)
+    err = np.abs(y.cpu().numpy().astype(np.float64) - A @ xs)
+    bound = (np.diff(A.indptr) + 2) * 2.0**-24 * (abs(A) @ np.abs(xs))
+    assert np.all(np.isfinite(err)) and np.all(err <= bound)
+
+
 def _column_blocks(A, mesh, a):
     L = mesh.nlayers
     idx = np.array([mesh.dof(a, l, c) for l in range(L + 1) for c in (0, 1)])
