@@ -151,6 +151,10 @@ def headline(line: dict) -> dict:
     ms = {k: r(1e3 * v["s"]) for k, v in d.items() if isinstance(v, dict) and "s" in v}
     if ms:
         out["newton_1M_ms"] = ms
+    ls = get(d, "learned_start_mixed") or {}
+    lms = {k: r(1e3 * v["s"]) for k, v in ls.items() if isinstance(v, dict) and "s" in v and "picard" in k}
+    if lms:
+        out["learned_1M_ms"] = lms
     u = get(d, "learned_start_mixed", "unseen_beta_fields")
     if u:
         out["learned_picard_vs_sia"] = {"seeds": u["seeds"], "speedup": r(u["speedup_learned_picard_vs_sia"]),
@@ -545,14 +549,17 @@ def learned_start(capi, dm, dev, reps=3, seeds=40):
                      "initial_rel_residual": rep["history"][0]}
         if name != "sia":
             out[name]["network_guess_kept"] = rep["learned_used"]
-    # the same two starts with FP32 value-path steps until 1e-3 (the fastest mixed configuration)
-    for name in ("sia", "learned_picard"):
-        times, rep = [], None
-        for _ in range(reps):
-            _, rep = learned.solve(dm, capi.BP_F32, name, mlp=net, value32_rtol=1e-3)
-            times.append(rep["wall_s"])
-        out[name + "_value32_until_1e-3"] = {"s": statistics.median(times), "newton_iters": rep["newton_iters"],
-                                             "converged": rep["converged"]}
+    # the same two starts with FP32 value-path steps until 1e-3, and with the double-single FP32
+    # lanes and FP32 value-path steps until 1e-4 (the fastest mixed configuration)
+    for tag, prec, v32 in (("_value32_until_1e-3", capi.BP_F32, 1e-3),
+                           ("_f32_ds_value32_until_1e-4", capi.BP_F32_DS, 1e-4)):
+        for name in ("sia", "learned_picard"):
+            times, rep = [], None
+            for _ in range(reps):
+                _, rep = learned.solve(dm, prec, name, mlp=net, value32_rtol=v32)
+                times.append(rep["wall_s"])
+            out[name + tag] = {"s": statistics.median(times), "newton_iters": rep["newton_iters"],
+                               "converged": rep["converged"]}
     out["judges"] = {"learned": "FP64 residual norm", "learned_energy": "FP64 discrete energy",
                      "learned_picard": f"FP64 energy, then Picard steps until ||F|| <= {learned.PICARD_RTOL} ||F(0)||"}
     mesh = dm.mesh
