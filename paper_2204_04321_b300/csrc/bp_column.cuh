@@ -40,7 +40,7 @@ struct AsmArgs {
   const double2* xy;
   const double* bed;
   const double* thick;
-  const double* sigma;
+  const double* sigma;      // [L + 1] levels, then [L] inverse layer thicknesses
   const int32_t* tri;
   const int32_t* slots;
   const double* basal;
@@ -430,7 +430,7 @@ __device__ __forceinline__ void assemble_column(const AsmArgs& A, const int t, T
     const double gvty = vt[0] * ly[0] + vt[1] * ly[1] + vt[2] * ly[2];
     const double s_l = A.sigma[l];
     const double ds = A.sigma[l + 1] - s_l;
-    const double invds = 1.0 / ds;
+    const double invds = A.sigma[L + 1 + l];  // 1 / ds, formed once at upload
     TV ht[3] = {cAV, cAV, cAV};  // hardness at the triangle points of the top level
     if (A.Bn) {
       const double b0 = A.Bn[(int64_t)v[0] * (L + 1) + l + 1], b1 = A.Bn[(int64_t)v[1] * (L + 1) + l + 1],

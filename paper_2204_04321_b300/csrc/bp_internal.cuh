@@ -88,7 +88,7 @@ struct bp_mesh {
   int32_t* nbr_ptr = nullptr; // [nv + 1] sorted closed neighbourhoods
   int32_t* nbr_idx = nullptr;
   // per level
-  double* sigma = nullptr;
+  double* sigma = nullptr;    // [L + 1] levels sigma_l, then [L] inverse layer thicknesses 1 / (sigma_{l+1} - sigma_l)
   // per triangle
   int32_t* tri = nullptr;     // [ntri][3]
   int32_t* slots = nullptr;   // [ntri][9]: slot[a][b] = rank of tri[b] in the closed neighbourhood of tri[a]
@@ -203,7 +203,9 @@ __device__ __forceinline__ double f64_of(const float f) {
 // 6 FP64 operations, the two conversions on the integer pipe.  Outside the FP32 normal range the
 // library rcbrt is used.
 __device__ __forceinline__ double inv_cbrt(double x) {
-  if (!(x > 1e-30 && x < 1e30)) return rcbrt(x);
+  // the FP32 seed needs x in [2^-99, 2^100): a test of the high word on the integer pipe (negative
+  // values, zero, infinities and NaN fail it too), which keeps comparisons off the FP64 pipe
+  if ((uint32_t)__double2hiint(x) - (924u << 20) >= (199u << 20)) return rcbrt(x);
   const double y = f64_of(rcbrtf(f32_of(x)));
   const double e = fma(-x * y, y * y, 1.0);
   return fma(y * e, fma(2.0 / 9.0, e, 1.0 / 3.0), y);

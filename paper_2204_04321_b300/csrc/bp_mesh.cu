@@ -324,7 +324,7 @@ extern "C" int bp_mesh_upload(const bp_mesh_desc* d, void* stream_, bp_mesh** ou
   BP_ALLOC(m->vdeg, nv);
   BP_ALLOC(m->nbr_ptr, nv + 1);
   BP_ALLOC(m->nbr_idx, nbr_idx.size());
-  BP_ALLOC(m->sigma, L + 1);
+  BP_ALLOC(m->sigma, 2 * L + 1);
   BP_ALLOC(m->tri, 3 * (size_t)ntri);
   BP_ALLOC(m->slots, 9 * (size_t)ntri);
   BP_ALLOC(m->basal, 6 * (size_t)ntri);
@@ -351,7 +351,12 @@ extern "C" int bp_mesh_upload(const bp_mesh_desc* d, void* stream_, bp_mesh** ou
   BP_H2D(m->vdeg, vdeg.data(), nv);
   BP_H2D(m->nbr_ptr, nbr_ptr.data(), nv + 1);
   BP_H2D(m->nbr_idx, nbr_idx.data(), nbr_idx.size());
-  BP_H2D(m->sigma, d->sigma, L + 1);
+  // the levels, then the inverse layer thicknesses 1 / (sigma_{l+1} - sigma_l) (IEEE division here,
+  // bitwise what the kernels would form)
+  std::vector<double> sig(2 * (size_t)L + 1);
+  for (int l = 0; l <= L; ++l) sig[l] = d->sigma[l];
+  for (int l = 0; l < L; ++l) sig[L + 1 + l] = 1.0 / (d->sigma[l + 1] - d->sigma[l]);
+  BP_H2D(m->sigma, sig.data(), 2 * (size_t)L + 1);
   BP_H2D(m->tri, d->tri, 3 * (size_t)ntri);
   BP_H2D(m->slots, slots.data(), 9 * (size_t)ntri);
   BP_H2D(m->color_tris, color_tris.data(), ntri);
