@@ -495,8 +495,10 @@ int bp_mesh_set_beta(bp_mesh* mesh, const double* beta_host, void* stream);
 int bp_mesh_set_rate_factor(bp_mesh* mesh, const double* A_host, void* stream);
 /* How bp_initial_guess_learned decides between the network's guess and the shallow-ice guess:
  *   BP_JUDGE_RESIDUAL  keep the guess with the smaller FP64 residual norm;
- *   BP_JUDGE_ENERGY    keep the guess with the smaller FP64 discrete energy Pi_h (the functional
- *                      Newton minimises: Pi_h(U) - Pi_h(U*) ~ 1/2 |U - U*|^2 in the Jacobian's norm);
+ *   BP_JUDGE_ENERGY    keep the guess with the smaller discrete energy Pi_h (the functional
+ *                      Newton minimises: Pi_h(U) - Pi_h(U*) ~ 1/2 |U - U*|^2 in the Jacobian's norm),
+ *                      decided by the sign of the FP64-accurate energy change from the shallow-ice
+ *                      guess to the network's (bp_energy_change_ex with BP_F64X2_DS);
  *   BP_JUDGE_NONE      always keep the network's guess (evaluation). */
 enum { BP_JUDGE_RESIDUAL = 0, BP_JUDGE_ENERGY = 1, BP_JUDGE_NONE = 2 };
 /*

@@ -535,6 +535,12 @@ __global__ void k_scatter_prediction(const float* __restrict__ Y, const double* 
 //   |s_b b + s_d d - u|^2 + reg^2 (|b|^2 (s_b - 1)^2 + |d|^2 (s_d - 1)^2)
 // (2 x 2 normal equations, solved in FP64 by Cramer's rule; a numerically singular system keeps
 // s = 1), written as y = s - 1 clipped to [-5, 5] in T[a][0..3]; T[a][4..31] = 0.
+// d = a - b (the step from the shallow-ice guess to the network's, for the energy judge)
+__global__ void k_diff(const double* __restrict__ a, const double* __restrict__ b, int64_t n, double* __restrict__ d) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    d[i] = a[i] - b[i];
+}
+
 __global__ void k_profile_scales(const double* __restrict__ U, const double* __restrict__ Usia, int nv, int L,
                                  double reg2, float* __restrict__ T) {
   const int a = blockIdx.x * blockDim.x + threadIdx.x;
@@ -920,15 +926,20 @@ extern "C" int bp_initial_guess_learned(bp_mesh* m, bp_mlp* net, double* U, int 
   if ((rc = check_err(net, s))) return rc;
   // the FP64 residual norm (or the FP64 energy) judges the prediction against the shallow-ice guess
   bool keep = true;
-  if (judge != BP_JUDGE_NONE) {
+  if (judge == BP_JUDGE_RESIDUAL) {
     double f_mlp, f_sia;
-    if (judge == BP_JUDGE_RESIDUAL) {
-      if ((rc = bp_assemble_residual(m, U, R, s)) || (rc = bp_norm2_host(m, R, s, &f_mlp))) return rc;
-      if ((rc = bp_assemble_residual(m, Usia, R, s)) || (rc = bp_norm2_host(m, R, s, &f_sia))) return rc;
-    } else {
-      if ((rc = bp_energy(m, U, &f_mlp, s)) || (rc = bp_energy(m, Usia, &f_sia, s))) return rc;
-    }
+    if ((rc = bp_assemble_residual(m, U, R, s)) || (rc = bp_norm2_host(m, R, s, &f_mlp))) return rc;
+    if ((rc = bp_assemble_residual(m, Usia, R, s)) || (rc = bp_norm2_host(m, R, s, &f_sia))) return rc;
     keep = std::isfinite(f_mlp) && f_mlp <= f_sia;
+  } else if (judge == BP_JUDGE_ENERGY) {
+    // Pi_h(U_net) <= Pi_h(U_sia) decided by the sign of the energy change from the shallow-ice guess
+    // to the network's, formed term by term in FP64-accurate pairs (one pass instead of two full
+    // energies, and exact where the two energies agree to many digits)
+    k_diff<<<(int)std::min<int64_t>((m->ndof + 255) / 256, 148 * 16), 256, 0, s>>>(U, Usia, m->ndof, R);
+    BP_CUDA_TRY(cudaGetLastError());
+    double dE;
+    if ((rc = bp_energy_change_ex(m, Usia, R, 1.0, BP_F64X2_DS, &dE, s))) return rc;
+    keep = std::isfinite(dE) && dE <= 0.0;
   }
   if (!keep) BP_CUDA_TRY(cudaMemcpyAsync(U, Usia, m->ndof * sizeof(double), cudaMemcpyDeviceToDevice, s));
   BP_CUDA_TRY(cudaStreamSynchronize(s));
