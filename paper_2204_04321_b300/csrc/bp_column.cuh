@@ -256,6 +256,33 @@ __device__ __forceinline__ Dual<TL, NL> operator*(double s, const Dual<TL, NL>& 
   return r;
 }
 
+// p_{(a,k),c} = psi_k alpha_{a,c} -/+ t_{a,c}, the factors of the rank-one part eta' p p^T at
+// triangle point tp (node (a, k) -> entries 2 (3k + a) + c): alpha_{a,c} = g_c,xy . Lambda_a with
+// alpha_2 = -(alpha_0 + alpha_1) (the barycentric gradients sum to zero), and t_{a,c} = lambda_a(tp)
+// tau_c / 2, i.e. tq_c for a != tp and 4 tq_c for a == tp, given tq = tau / 12.
+template <class TL>
+__device__ __forceinline__ void rank_one_factors(TL (&p)[12], const TL g1x, const TL exy, const TL g2y,
+                                                 const TL tq1, const TL tq2, const TL ps0, const TL ps1,
+                                                 const int tp, const TL (&clx)[3], const TL (&cly)[3]) {
+  TL al1[3], al2[3];
+#pragma unroll
+  for (int a = 0; a < 2; ++a) {
+    al1[a] = g1x * clx[a] + exy * cly[a];
+    al2[a] = exy * clx[a] + g2y * cly[a];
+  }
+  al1[2] = -(al1[0] + al1[1]);
+  al2[2] = -(al2[0] + al2[1]);
+  const TL f1 = TL(4) * tq1, f2 = TL(4) * tq2;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const TL t1a = a == tp ? f1 : tq1, t2a = a == tp ? f2 : tq2;
+    p[2 * a] = ps0 * al1[a] - t1a;
+    p[2 * a + 1] = ps0 * al2[a] - t2a;
+    p[2 * (3 + a)] = ps1 * al1[a] + t1a;
+    p[2 * (3 + a) + 1] = ps1 * al2[a] + t2a;
+  }
+}
+
 // ------------------------------------------------------------------ the column kernel
 // Assembles every wedge of the column above base triangle t (one thread).
 // PICARD (factored method only): leave out the eta' rank-one part, i.e. assemble the fixed-viscosity
@@ -461,11 +488,12 @@ __device__ __forceinline__ void assemble_column(const AsmArgs& A, const int t, T
     // per triangle point: vertical shear, weights
     const double dus6 = (ut[0] - ub[0] + ut[1] - ub[1] + ut[2] - ub[2]) * (1.0 / 6.0);
     const double dvs6 = (vt[0] - vb[0] + vt[1] - vb[1] + vt[2] - vb[2]) * (1.0 / 6.0);
-    double cq[3], invh[3];
+    double cq[3], invh[3], invh6[3];
     TV uz[3], vz[3], ez[3], cqV[3];
 #pragma unroll
     for (int tp = 0; tp < 3; ++tp) {
       invh[tp] = invds * invHq[tp];
+      invh6[tp] = invh[tp] * (1.0 / 6.0);
       const TV invhV = to_lane<TV>(invh[tp]);
       uz[tp] = to_lane<TV>(dus6 + 0.5 * (ut[tp] - ub[tp])) * invhV;
       vz[tp] = to_lane<TV>(dvs6 + 0.5 * (vt[tp] - vb[tp])) * invhV;
@@ -590,6 +618,22 @@ __device__ __forceinline__ void assemble_column(const AsmArgs& A, const int t, T
       // indices are compile-time constants (the unrolled loop below), warp-uniform selects when they
       // are not (the double-single value path runs the 6 points in a loop that is not unrolled: its
       // pair arithmetic, ~10 instructions per FP64 one, would not fit the instruction cache 6 times).
+      // hardness at the 6 points, psi_0 hb + psi_1 ht (the constant A^(-1/3) without a field), formed
+      // once per wedge for the FP64 and FP32 value paths; the double-single path, short of registers,
+      // forms it per point
+      constexpr bool kHq = !std::is_same<TV, f64x2>::value;
+      TV hq[2][3];
+      if (!kHq) {
+      } else if (A.Bn) {
+#pragma unroll
+        for (int tp = 0; tp < 3; ++tp) {
+          hq[0][tp] = TV(BP_QP_P) * hb[tp] + TV(BP_QP_Q) * ht[tp];
+          hq[1][tp] = TV(BP_QP_Q) * hb[tp] + TV(BP_QP_P) * ht[tp];
+        }
+      } else {
+#pragma unroll
+        for (int tp = 0; tp < 3; ++tp) hq[0][tp] = hq[1][tp] = cAV;
+      }
       auto point = [&](const int z, const int tp) {
         const TV gzx = sel2(GzxV, z), gzy = sel2(GzyV, z);
         const TV uzp = sel3(uz, tp), vzp = sel3(vz, tp);
@@ -601,8 +645,13 @@ __device__ __forceinline__ void assemble_column(const AsmArgs& A, const int t, T
         const TV e2 = fma_t(ux, ux, fma_t(vy, vy + ux, fma_t(exy, exy, sel3(ez, tp))));
         const TV xx = e2 + deltaV;
         const TV r = inv_cbrt_t(xx);
-        const TV ps0 = z ? TV(BP_QP_Q) : TV(BP_QP_P), ps1 = z ? TV(BP_QP_P) : TV(BP_QP_Q);  // psi_0, psi_1 at z
-        const TV eta = (ps0 * sel3(hb, tp) + ps1 * sel3(ht, tp)) * r;
+        TV eta;
+        if constexpr (kHq) {
+          eta = (z ? sel3(hq[1], tp) : sel3(hq[0], tp)) * r;
+        } else {
+          const TV ps0 = z ? TV(BP_QP_Q) : TV(BP_QP_P), ps1 = z ? TV(BP_QP_P) : TV(BP_QP_Q);  // psi_k at z
+          eta = (ps0 * sel3(hb, tp) + ps1 * sel3(ht, tp)) * r;
+        }
         const TV W = sel3(cqV, tp) * eta;
         const TV g1x = TV(2.0) * ux + vy, g2y = ux + TV(2.0) * vy;
         put2(P1x, z, fma_t(W, g1x, sel2(P1x, z)));
@@ -616,27 +665,27 @@ __device__ __forceinline__ void assemble_column(const AsmArgs& A, const int t, T
         put3(TW2, tp, fma_t(W6, t2, sel3(TW2, tp)));
         if constexpr (MODE == MODE_FACT) {
           // rank-one part eta' p_i p_j with p_{(a,k),c} = psi_k g_c,xy . Lambda_a + lambda_a psi_k' g_c . Z
-          TL Wp, tau1, tau2, eq;
+          TL Wp, tau1, tau2, eq;  // tau1, tau2 hold tau_c / 12 (see rank_one_factors)
           if constexpr (kF32) {  // from r, t1, t2 converted once: FP32 arithmetic only
             const float rf = lane_from<float>(r);
             const float ef = lane_from<float>(eta);
             eq = ef;
             Wp = (-1.0f / 3.0f) * sel3(cqL, tp) * ef * (rf * rf * rf);
-            const float ih = sel3(invhL, tp);
-            tau1 = 2.0f * ih * lane_from<float>(t1);
-            tau2 = 2.0f * ih * lane_from<float>(t2);
+            const float ih6 = sel3(invhL, tp) * (1.0f / 6.0f);
+            tau1 = ih6 * lane_from<float>(t1);  // tau / 12 (rank_one_factors)
+            tau2 = ih6 * lane_from<float>(t2);
           } else if constexpr (std::is_same<TV, f64x2>::value) {  // double-single value path, paired lanes
             eq = eta;
             Wp = TV(-1.0 / 3.0) * W * (r * r * r);
-            const TV ih2 = to_lane<TV>(2.0 * sel3(invh, tp));
-            tau1 = ih2 * t1;
-            tau2 = ih2 * t2;
+            const TV ih6 = to_lane<TV>(sel3(invh6, tp));
+            tau1 = ih6 * t1;  // tau / 12
+            tau2 = ih6 * t2;
           } else {
             eq = to_lane<TL>(eta);
             Wp = to_lane<TL>(-(1.0 / 3.0) * W * (r * r * r));
-            const double ih = sel3(invh, tp);
-            tau1 = to_lane<TL>(2.0 * ih * t1);
-            tau2 = to_lane<TL>(2.0 * ih * t2);
+            const double ih6 = sel3(invh6, tp);
+            tau1 = to_lane<TL>(ih6 * t1);  // tau / 12
+            tau2 = to_lane<TL>(ih6 * t2);
           }
           if (z)
             put3(eta_q[1], tp, eq);
@@ -654,19 +703,8 @@ __device__ __forceinline__ void assemble_column(const AsmArgs& A, const int t, T
           } else if constexpr (!PICARD) {
             const TL fg1x = lane_from<TL>(g1x), fexy = lane_from<TL>(exy), fg2y = lane_from<TL>(g2y);
             const TL pl0 = z ? TL(BP_QP_Q) : TL(BP_QP_P), pl1 = z ? TL(BP_QP_P) : TL(BP_QP_Q);
-            // p_{(a,k),c} = psi_k alpha_{a,c} -/+ t_{a,c},  alpha = g_c,xy . Lambda_a,  t = lambda_a tau_c / 2
             TL p[12];
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-              const TL al1 = fg1x * clx[a] + fexy * cly[a];
-              const TL al2 = fexy * clx[a] + fg2y * cly[a];
-              const TL h = a == tp ? TL(1.0 / 3.0) : TL(1.0 / 12.0);  // lambda_a(tp) / 2
-              const TL t1a = h * tau1, t2a = h * tau2;
-              p[2 * a] = pl0 * al1 - t1a;
-              p[2 * a + 1] = pl0 * al2 - t2a;
-              p[2 * (3 + a)] = pl1 * al1 + t1a;
-              p[2 * (3 + a) + 1] = pl1 * al2 + t2a;
-            }
+            rank_one_factors(p, fg1x, fexy, fg2y, tau1, tau2, pl0, pl1, tp, clx, cly);
 #pragma unroll
             for (int i = 0; i < 12; ++i) {
               const TL pw = Wp * p[i];
@@ -711,17 +749,7 @@ __device__ __forceinline__ void assemble_column(const AsmArgs& A, const int t, T
                    tau2 = sq[5 * bs];
           const TL ps0 = z ? TL(BP_QP_Q) : TL(BP_QP_P), ps1 = z ? TL(BP_QP_P) : TL(BP_QP_Q);
           TL p[12];
-#pragma unroll
-          for (int a = 0; a < 3; ++a) {
-            const TL al1 = fg1x * clx[a] + fexy * cly[a];
-            const TL al2 = fexy * clx[a] + fg2y * cly[a];
-            const TL h = a == tp ? TL(1.0 / 3.0) : TL(1.0 / 12.0);  // lambda_a(tp) / 2
-            const TL t1a = h * tau1, t2a = h * tau2;
-            p[2 * a] = ps0 * al1 - t1a;
-            p[2 * a + 1] = ps0 * al2 - t2a;
-            p[2 * (3 + a)] = ps1 * al1 + t1a;
-            p[2 * (3 + a) + 1] = ps1 * al2 + t2a;
-          }
+          rank_one_factors(p, fg1x, fexy, fg2y, tau1, tau2, ps0, ps1, tp, clx, cly);
 #pragma unroll
           for (int i = 0; i < 12; ++i) {
             const TL pw = Wp * p[i];
