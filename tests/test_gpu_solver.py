@@ -80,6 +80,23 @@ def test_fp32_spmv_within_fp32_dot_product_bound(size):
     assert np.all(np.isfinite(err)) and np.all(err <= bound)
 
 
+def test_fp32_spmv_refuses_misaligned_buffers():
+    """bp_spmv_f32 reads (u, v) pairs: x, y and J must start on 16-byte boundaries (BP_EINVAL,
+    nothing read or written otherwise)."""
+    c = capi()
+    mesh = synth.dome_mesh(8, 3, 31, 32)
+    dm = c.DeviceMesh(mesh)
+    J, _ = dm.jacobian(dev(synth.random_velocity(mesh, 3)), precision=1)
+    x = torch.zeros(dm.ndof + 4, dtype=torch.float32, device="cuda")
+    y = torch.full((dm.ndof + 4,), 7.0, dtype=torch.float32, device="cuda")
+    for args in ((J, x[1:], y[:dm.ndof]), (J, x[:dm.ndof], y[1:]), (J[1:], x[:dm.ndof], y[:dm.ndof])):
+        with pytest.raises(c.BPError) as e:
+            c.bp_spmv_f32(dm.handle, *args)
+        assert e.value.status == c.BP_EINVAL
+    torch.cuda.synchronize()
+    assert bool((y == 7.0).all())
+
+
 def _column_blocks(A, mesh, a):
     L = mesh.nlayers
     idx = np.array([mesh.dof(a, l, c) for l in range(L + 1) for c in (0, 1)])
